@@ -1,0 +1,335 @@
+"""Loader for the HWFV1 CPU oracle (oracle/hwfv1_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the oracle is the plain, slow statement of the
+method that the CUDA library is checked against.  Only tests/,
+``__graft_entry__.smoke()`` and bench.py's cpu_baseline / ``--impl reference``
+legs may import this package; the library in paper_2206_05761_gb300/ never
+does.  It is compiled with gcc on first use (or by ``build()``) with
+``-ffp-contract=off`` so that its operation order is exactly the one written
+in the C source.
+
+All arrays here are numpy, row-major over a level (index j*2^n + i).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hwfv1_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liborc_hwfv1.so")
+_lock = threading.Lock()
+_lib = None
+
+BC = {"closed": 0, "transmissive": 1, "inflow": 2}
+
+
+def build(force=False):
+    """Compile the oracle shared library with gcc (no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Problem(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("lx", C.c_double), ("ly", C.c_double),
+                ("L", C.c_int), ("reg_predict", C.c_int), ("reg_close", C.c_int),
+                ("inflow_a0", C.c_int), ("inflow_a1", C.c_int), ("inflow_n", C.c_int),
+                ("bc", C.c_int * 4),
+                ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
+                ("manning_n", C.c_double), ("tol_h", C.c_double), ("dt_max", C.c_double),
+                ("inflow_t", C.POINTER(C.c_double)), ("inflow_Q", C.POINTER(C.c_double))]
+
+
+class StepOut(C.Structure):
+    _fields_ = [("T", C.POINTER(C.c_uint8)), ("S", C.POINTER(C.c_uint8)),
+                ("leaves", C.POINTER(C.c_uint32)), ("leaves_cap", C.c_int64),
+                ("hier_out", C.POINTER(C.c_double)),
+                ("num_leaves", C.c_int64), ("dt_next", C.c_double)]
+
+
+_dp = C.POINTER(C.c_double)
+_u8p = C.POINTER(C.c_uint8)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            L = _lib
+            L.orc_version.restype = C.c_int
+            L.orc_morton.restype = C.c_uint64
+            L.orc_morton.argtypes = [C.c_uint32, C.c_uint32]
+            L.orc_demorton.argtypes = [C.c_uint64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            L.orc_zindex.restype = C.c_int64
+            L.orc_zindex.argtypes = [C.c_int, C.c_uint64]
+            L.orc_encode_parent.argtypes = [_dp, _dp]
+            L.orc_decode_parent.argtypes = [_dp, _dp]
+            L.orc_encode.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.orc_decode_all.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.orc_smax.restype = C.c_double
+            L.orc_smax.argtypes = [C.c_int, _dp]
+            L.orc_threshold_flags.argtypes = [C.c_int, C.c_double, C.POINTER(_dp), _dp, _u8p]
+            L.orc_regularise.argtypes = [C.c_int, C.c_int, C.c_int, _u8p, _u8p]
+            L.orc_leaves_dft.restype = C.c_int64
+            L.orc_leaves_dft.argtypes = [C.c_int, _u8p, C.POINTER(C.c_uint32), C.c_int64]
+            L.orc_leaves_ptt.argtypes = [C.c_int, _u8p, C.POINTER(C.c_int64)]
+            L.orc_hll_x.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp]
+            L.orc_cfl_rmin.restype = C.c_double
+            L.orc_cfl_rmin.argtypes = [C.POINTER(Problem), _dp, _dp, _dp]
+            L.orc_next_dt.restype = C.c_double
+            L.orc_next_dt.argtypes = [C.POINTER(Problem), _dp, _dp, _dp]
+            L.orc_hwfv1_step.restype = C.c_int
+            L.orc_hwfv1_step.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, C.c_double,
+                                         C.c_double, C.POINTER(StepOut)]
+            L.orc_fv1_step.restype = C.c_int
+            L.orc_fv1_step.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, C.c_double,
+                                       C.c_double]
+            L.orc_run.restype = C.c_int
+            L.orc_run.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double,
+                                  C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    return _lib
+
+
+def _d(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def level_start(n):
+    return ((1 << (2 * n)) - 1) // 3
+
+
+def make_problem(p):
+    """ctypes Problem from a synth.problem() dict (keeps the hydrograph
+    arrays alive on the returned object)."""
+    s = Problem()
+    s.x0, s.y0, s.lx, s.ly = p["x0"], p["y0"], p["lx"], p["ly"]
+    s.L = p["L"]
+    s.reg_predict = int(p["reg_predict"])
+    s.reg_close = int(p["reg_close"])
+    for k in range(4):
+        s.bc[k] = BC[p["bc"][k]]
+    s.eps, s.cfl, s.g = p["eps"], p["cfl"], p["g"]
+    s.manning_n, s.tol_h, s.dt_max = p["manning_n"], p["tol_h"], p["dt_max"]
+    inf = p.get("inflow")
+    if inf:
+        t = np.ascontiguousarray(inf["t"], dtype=np.float64)
+        q = np.ascontiguousarray(inf["Q"], dtype=np.float64)
+        s._keep = (t, q)
+        s.inflow_t, s.inflow_Q = _d(t), _d(q)
+        s.inflow_n = len(t)
+        s.inflow_a0, s.inflow_a1 = inf["a0"], inf["a1"]
+    else:
+        s.inflow_n = 0
+    return s
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers
+# ---------------------------------------------------------------------------
+
+def morton(i, j):
+    return int(lib().orc_morton(int(i), int(j)))
+
+
+def demorton(code):
+    a, b = C.c_uint32(), C.c_uint32()
+    lib().orc_demorton(int(code), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def zindex(n, code):
+    return int(lib().orc_zindex(int(n), int(code)))
+
+
+def morton_map(n):
+    """Array m[j, i] = Morton code of cell (i, j) of a 2^n x 2^n level."""
+    s = 1 << n
+    out = np.empty((s, s), dtype=np.int64)
+    f = lib().orc_morton
+    for j in range(s):
+        for i in range(s):
+            out[j, i] = f(i, j)
+    return out
+
+
+def encode_parent(c):
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    o = np.empty(4)
+    lib().orc_encode_parent(_d(c), _d(o))
+    return o
+
+
+def decode_parent(p):
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    o = np.empty(4)
+    lib().orc_decode_parent(_d(p), _d(o))
+    return o
+
+
+def encode(L, fine):
+    """Return (hier, det): hier has all levels 0..L (length (4^(L+1)-1)/3),
+    det the three details of every parent (shape (P, 3))."""
+    fine = np.ascontiguousarray(fine, dtype=np.float64).reshape(-1)
+    hier = np.empty(level_start(L + 1))
+    det = np.empty(3 * max(level_start(L), 1))
+    lib().orc_encode(L, _d(fine), _d(hier), _d(det))
+    return hier, det[: 3 * level_start(L)].reshape(-1, 3)
+
+
+def decode_all(L, hier, det):
+    det = np.ascontiguousarray(det, dtype=np.float64).reshape(-1)
+    out = np.empty(1 << (2 * L))
+    c0 = np.ascontiguousarray(hier[:1], dtype=np.float64)
+    lib().orc_decode_all(L, _d(c0), _d(det), _d(out))
+    return out.reshape(1 << L, 1 << L)
+
+
+def level(hier, n):
+    s = 1 << n
+    return hier[level_start(n): level_start(n) + s * s].reshape(s, s)
+
+
+def smax(L, fine):
+    return float(lib().orc_smax(L, _d(np.ascontiguousarray(fine, dtype=np.float64).reshape(-1))))
+
+
+def threshold_flags(L, eps, dets, smaxes):
+    """dets: four detail arrays (P, 3) for h, qx, qy, z; smaxes: four s_max."""
+    dets = [np.ascontiguousarray(d, dtype=np.float64).reshape(-1) for d in dets]
+    arr = (_dp * 4)(*[_d(d) for d in dets])
+    sm = np.ascontiguousarray(smaxes, dtype=np.float64)
+    T = np.zeros(max(level_start(L), 1), dtype=np.uint8)
+    lib().orc_threshold_flags(L, float(eps), arr, _d(sm), T.ctypes.data_as(_u8p))
+    return T[: level_start(L)]
+
+
+def regularise(L, T, predict=True, close=True):
+    T = np.ascontiguousarray(T, dtype=np.uint8)
+    S = np.zeros(max(level_start(L), 1), dtype=np.uint8)
+    Tb = T if T.size else np.zeros(1, np.uint8)
+    lib().orc_regularise(L, int(predict), int(close), Tb.ctypes.data_as(_u8p), S.ctypes.data_as(_u8p))
+    return S[: level_start(L)]
+
+
+def leaves_dft(L, S):
+    S = np.ascontiguousarray(S, dtype=np.uint8)
+    Sb = S if S.size else np.zeros(1, np.uint8)
+    n = lib().orc_leaves_dft(L, Sb.ctypes.data_as(_u8p), None, 0)
+    out = np.empty(n, dtype=np.uint32)
+    lib().orc_leaves_dft(L, Sb.ctypes.data_as(_u8p), out.ctypes.data_as(C.POINTER(C.c_uint32)), n)
+    return out
+
+
+def leaves_ptt(L, S):
+    S = np.ascontiguousarray(S, dtype=np.uint8)
+    Sb = S if S.size else np.zeros(1, np.uint8)
+    out = np.empty(1 << (2 * L), dtype=np.int64)
+    lib().orc_leaves_ptt(L, Sb.ctypes.data_as(_u8p), out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return out
+
+
+def hll_x(g, tol_h, left, right):
+    a = np.ascontiguousarray(left, dtype=np.float64)
+    b = np.ascontiguousarray(right, dtype=np.float64)
+    F = np.empty(3)
+    lib().orc_hll_x(float(g), float(tol_h), _d(a), _d(b), _d(F))
+    return F
+
+
+class State:
+    """Finest-grid state (h, qx, qy, z row-major) plus time and next dt."""
+
+    def __init__(self, p, fields, t=0.0, dt=None):
+        self.p = p
+        self.cp = make_problem(p)
+        self.h = np.ascontiguousarray(fields["h"], dtype=np.float64).copy()
+        self.qx = np.ascontiguousarray(fields["qx"], dtype=np.float64).copy()
+        self.qy = np.ascontiguousarray(fields["qy"], dtype=np.float64).copy()
+        self.z = np.ascontiguousarray(fields["z"], dtype=np.float64).copy()
+        self.t = float(t)
+        self.dt = self.next_dt() if dt is None else float(dt)
+        self.steps = 0
+        self.leaf_updates = 0
+
+    def next_dt(self):
+        return float(lib().orc_next_dt(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy)))
+
+    def cfl_rmin(self):
+        return float(lib().orc_cfl_rmin(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy)))
+
+    def step(self, dt=None, want=()):
+        """One HWFV1 step of size dt (default: the current dt).  `want` may
+        hold "T", "S", "leaves", "hier" to return those intermediates."""
+        L = self.p["L"]
+        P, N = level_start(L), 1 << (2 * L)
+        dt = self.dt if dt is None else float(dt)
+        o = StepOut()
+        res = {}
+        if "T" in want:
+            res["T"] = np.zeros(max(P, 1), np.uint8)
+            o.T = res["T"].ctypes.data_as(_u8p)
+        if "S" in want:
+            res["S"] = np.zeros(max(P, 1), np.uint8)
+            o.S = res["S"].ctypes.data_as(_u8p)
+        if "leaves" in want:
+            res["leaves"] = np.zeros(N, np.uint32)
+            o.leaves = res["leaves"].ctypes.data_as(C.POINTER(C.c_uint32))
+            o.leaves_cap = N
+        if "hier" in want:
+            res["hier"] = np.zeros(3 * (N + P))
+            o.hier_out = _d(res["hier"])
+        rc = lib().orc_hwfv1_step(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy),
+                                  _d(self.z), self.t, dt, C.byref(o))
+        if rc:
+            raise MemoryError("oracle step failed")
+        if "T" in res:
+            res["T"] = res["T"][:P]
+        if "S" in res:
+            res["S"] = res["S"][:P]
+        if "leaves" in res:
+            res["leaves"] = res["leaves"][: o.num_leaves]
+        if "hier" in res:
+            res["hier"] = res["hier"].reshape(3, N + P)
+        self.t += dt
+        self.dt = o.dt_next
+        self.steps += 1
+        self.leaf_updates += o.num_leaves
+        res["num_leaves"] = int(o.num_leaves)
+        return res
+
+    def fv1_step(self, dt=None):
+        dt = self.dt if dt is None else float(dt)
+        lib().orc_fv1_step(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy), _d(self.z),
+                           self.t, dt)
+        self.t += dt
+        self.dt = self.next_dt()
+        self.steps += 1
+        self.leaf_updates += 1 << (2 * self.p["L"])
+
+    def run(self, t_end=np.inf, max_steps=1 << 62, uniform=False):
+        t, dt = C.c_double(self.t), C.c_double(self.dt)
+        steps, lu = C.c_int64(0), C.c_int64(0)
+        rc = lib().orc_run(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy), _d(self.z),
+                           C.byref(t), C.byref(dt), float(t_end), int(max_steps), int(uniform),
+                           C.byref(steps), C.byref(lu))
+        if rc:
+            raise MemoryError("oracle run failed")
+        self.t, self.dt = t.value, dt.value
+        self.steps += steps.value
+        self.leaf_updates += lu.value
+        return steps.value
