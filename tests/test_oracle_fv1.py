@@ -226,10 +226,11 @@ def test_dt_from_cfl_and_dry_default():
 def test_dry_bumpy_domain_stays_dry():
     # a dry coarse leaf hands its depth (0) down unchanged: no water appears
     # in the hollows of the bed
-    p, f = synth.terrain_flood(L=6)
-    p["bc"] = ("closed",) * 4
+    p, f = synth.bumpy_dam_break(L=6)
+    f["h"][:] = 0.0
     st = oracle.State(p, f)
     for _ in range(10):
-        res = st.step()
-        assert res["num_leaves"] < 1 << 12
+        res = st.step(want=("leaves",))
+        levels = res["leaves"] >> 28
+        assert levels.min() < p["L"]          # coarse dry leaves exist
     assert np.all(st.h == 0.0) and np.all(st.qx == 0.0) and np.all(st.qy == 0.0)
