@@ -1,0 +1,327 @@
+"""Benchmark of the HWFV1 hot path on one GB300 (or N independent replicas).
+
+Workload: the synthetic terrain flood at L = 12 (4096 x 4096 finest cells
+over a 10 km square, seeded 1/f^2 DEM with a carved channel, triangular
+inflow hydrograph peaking at 500 m^3/s, Manning n = 0.03, eps = 1e-3,
+float64 unless --precision 32).  A step is one pass of the whole hot path:
+encode + flag + regularise + traverse/compact + FV1 update + decode-back +
+time advance.  The state (about 1 GB) is larger than L2, so no flush is
+needed between steps.
+
+Prints one JSON line (see the design doc for every key).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "adaptive steps/s at L=12 (terrain flood, 4096x4096)"
+UNIT = "steps/s"
+
+
+def parse():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=200)
+    a.add_argument("--warmup", type=int, default=20)
+    a.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    a.add_argument("--precision", type=int, default=64, choices=[64, 32])
+    a.add_argument("--L", type=int, default=12)
+    a.add_argument("--spinup", type=int, default=200, help="untimed steps before warm-up")
+    a.add_argument("--no-cpu-baseline", action="store_true")
+    a.add_argument("--cpu-steps", type=int, default=2)
+    return a.parse_args()
+
+
+def workload(L):
+    import synth
+    return synth.terrain_flood(L=L)
+
+
+def config_dict(args, extra=None):
+    d = {"workload": "terrain_flood", "L": args.L, "finest_cells": 1 << (2 * args.L),
+         "domain_m": 10000.0, "eps": 1e-3, "manning_n": 0.03, "inflow_peak_m3s": 500.0,
+         "precision": args.precision, "spinup_steps": args.spinup,
+         "l2_policy": "state (>1 GB) larger than L2; no flush",
+         "parallelism": "replicas" if args.gpus > 1 else "single"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled with nvidia-smi during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def kernels_per_step(L):
+    passes = (L + 4) // 5
+    # clear + encode passes + flag + (count, scan, write) + fv1 + decode + finish
+    return 1 + passes + 1 + 3 + 1 + 1 + 1
+
+
+def roofline_terms(L, M, precision):
+    """Algorithmic bytes of one launch of each kernel."""
+    N = 1 << (2 * L)
+    P = (N - 1) // 3
+    b = 8 if precision == 64 else 4
+    return {
+        # read finest h, qx, qy; write every coarser level of them; flag bits
+        "encode": 3 * b * N + 3 * b * P + 2 * P / 8,
+        # leaf id + own 4 values + 3 new values (neighbours served from L2)
+        "fv1": M * (4 + 4 * b + 3 * b),
+        # every finest cell under a coarser leaf: written 3 values + its bed
+        "decode": None,
+        "traverse": 3 * P / 8 * 2 + 4 * M,
+    }
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as H
+
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    p, f = workload(args.L)
+    N = 1 << (2 * args.L)
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda")
+
+    # ---- end-to-end through the C ABI with host buffers -----------------
+    host = {k: torch.from_numpy(np.ascontiguousarray(f[k]).reshape(-1)).pin_memory()
+            for k in ("z", "h", "qx", "qy")}
+    outs = {k: torch.empty(N, dtype=torch.float64).pin_memory() for k in ("h", "qx", "qy")}
+    dbufs = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("z", "h", "qx", "qy")}
+    spec = H.make_problem(p, args.precision)
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in dbufs:
+            dbufs[k].copy_(host[k], non_blocking=True)
+    hd = H.hwfv1_init(spec, dbufs["z"], dbufs["h"], dbufs["qx"], dbufs["qy"], stream)
+    H.hwfv1_advance(hd, float("inf"), args.spinup + e2e_steps)
+    H.hwfv1_get_fields(hd, dbufs["h"], dbufs["qx"], dbufs["qy"])
+    with torch.cuda.stream(stream):
+        for k in outs:
+            outs[k].copy_(dbufs[k], non_blocking=True)
+    stream.synchronize()
+    t_e2e = time.perf_counter() - t0
+    H.hwfv1_destroy(hd)
+    e2e_total_steps = args.spinup + e2e_steps
+
+    # ---- device-timed steps (fresh start from the initial fields) --------
+    with torch.cuda.stream(stream):
+        for k in dbufs:
+            dbufs[k].copy_(host[k], non_blocking=True)
+    stream.synchronize()
+    hd = H.hwfv1_init(spec, dbufs["z"], dbufs["h"], dbufs["qx"], dbufs["qy"], stream)
+    if args.spinup:
+        H.hwfv1_advance(hd, float("inf"), args.spinup)
+    H.hwfv1_advance(hd, float("inf"), max(args.warmup, 3))
+    stream.synchronize()
+    # per-phase timing on the library's stream (CUDA events)
+    phases = {"encode": [], "flag": [], "traverse": [], "fv1": [], "decode": []}
+    Ms = []
+    for _ in range(5):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            H.hwfv1_encode(hd); ev[1].record(stream)
+            H.hwfv1_flag(hd); ev[2].record(stream)
+            H.hwfv1_traverse(hd); ev[3].record(stream)
+            H.hwfv1_step(hd); ev[4].record(stream)
+            H.hwfv1_decode(hd); ev[5].record(stream)
+        stream.synchronize()
+        for i, k in enumerate(phases):
+            phases[k].append(ev[i].elapsed_time(ev[i + 1]))
+        Ms.append(H.hwfv1_get_stats(hd)[0])
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        H.hwfv1_advance(hd, float("inf"), args.steps)
+        e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    t_now, dt_now, nsteps = H.hwfv1_get_time(hd)
+    M_last, smax = H.hwfv1_get_stats(hd)
+    H.hwfv1_destroy(hd)
+    ph = {k: statistics.median(v) for k, v in phases.items()}
+    return dict(ms=ms, e2e_s=t_e2e, e2e_steps=e2e_total_steps, phases_ms=ph,
+                M_mean=float(sum(Ms) / len(Ms)), M_last=M_last, t=t_now, dt=dt_now,
+                clocks=clocks, N=N)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(args, sample_steps):
+    import oracle
+    p, f = workload(args.L)
+    st = oracle.State(p, f)
+    t0 = time.perf_counter()
+    st.run(max_steps=sample_steps)
+    el = time.perf_counter() - t0
+    return {"value": sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d oracle steps of the same L=%d workload from t=0 (single-threaded C, %.1f s)"
+                      % (sample_steps, args.L, el)}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the oracle (single-threaded C) on the same workload; a step takes
+        # seconds at L = 12, so the timed sample is bounded to ~2 minutes
+        import oracle
+        p, f = workload(args.L)
+        st = oracle.State(p, f)
+        t0 = time.perf_counter()
+        st.run(max_steps=1)                      # one warm-up step
+        per = time.perf_counter() - t0
+        k = max(1, min(args.steps, int(120.0 / max(per, 1e-3))))
+        t1 = time.perf_counter()
+        st.run(max_steps=k)
+        el = time.perf_counter() - t1
+        v = k / el
+        sample = ("%d oracle steps of the L=%d workload after 1 warm-up step "
+                  "(single-threaded C, %.1f s)" % (k, args.L, el))
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+               "steps": k, "warmup": 1, "ms_per_step": 1e3 * el / k,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": config_dict(args, {"spinup_steps": 1}),
+               "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample},
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    ms = r["ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms, r["e2e_s"]], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    else:
+        e2e_s = r["e2e_s"]
+    if rank != 0:
+        return
+    value = world * args.steps / (ms / 1e3)
+    N = r["N"]
+    b = 8 if args.precision == 64 else 4
+    pk, src = peaks()
+    # dominant kernel by live CUDA-event timing
+    ph = r["phases_ms"]
+    dom = max(ph, key=ph.get)
+    terms = roofline_terms(args.L, r["M_mean"], args.precision)
+    alg = terms.get(dom)
+    roof = None
+    if alg:
+        ach = alg / (ph[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": src}
+    e2e_val = world * r["e2e_steps"] / e2e_s
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32",
+        "data": "synthetic", "config": config_dict(args),
+        "leaf_updates_per_s": value * r["M_mean"], "mean_leaves": r["M_mean"],
+        "phases_ms": ph, "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * N * 8 / r["e2e_steps"],
+                "d2h_bytes_per_step": 3 * N * 8 / r["e2e_steps"],
+                "note": "host fields -> init -> %d steps -> fields back to host" % r["e2e_steps"]},
+        "gpu_launches": kernels_per_step(args.L) * args.steps,
+        "clocks": r["clocks"], "sim_time_s": r["t"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, args.cpu_steps)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * hwfv1.h -- C ABI of the GB300 library for the adaptive Haar-wavelet
+ * first-order finite-volume shallow-water model (HWFV1) of Chowdhury,
+ * Kesserwani, Rouge & Richmond, arXiv 2206.05761.
+ *
+ * One timestep of HWFV1 (Algorithm 3) is, in this order:
+ *   hwfv1_encode    Haar encoding of the finest h, hu, hv up the hierarchy
+ *                   and threshold flags (Eq. 3a-3d, Algorithm 1)
+ *   hwfv1_flag      regularised significance tree
+ *   hwfv1_traverse  leaf cells of the tree, compacted in Z-order
+ *                   (Algorithm 5, Sec. 2.2.3)
+ *   hwfv1_step      FV1 update of every leaf from its same-level neighbours
+ *                   (Eq. 1-2, Sec. 2.1.3, Sec. 2.2.3)
+ *   hwfv1_decode    leaf values back onto the finest grid (Eq. 4 with zero
+ *                   details below the leaves) and time advance with the new
+ *                   CFL timestep (Algorithm 3 lines 8-9)
+ * hwfv1_advance runs that sequence for many steps.
+ *
+ * Conventions
+ *  - Every call is asynchronous on the CUDA stream given to hwfv1_init
+ *    unless it says it synchronises.  Pointers documented as "device" must
+ *    be device memory of the current CUDA device; "host" pointers are read
+ *    or written before the call returns.
+ *  - Fields exchanged with the caller are float64, row-major over the
+ *    finest 2^L x 2^L grid: element (i, j) at j*2^L + i, i along x, j along
+ *    y.  The caller owns every pointer it passes; the handle owns all its
+ *    internal buffers and frees them in hwfv1_destroy.
+ *  - Errors are returned as hwfv1_status.  A bad problem description fails
+ *    in hwfv1_init before any device memory is touched.  Conditions found
+ *    on the device (non-finite values) are latched and returned by the next
+ *    call that synchronises (hwfv1_get_time, hwfv1_advance with
+ *    synchronisation, hwfv1_save); hwfv1_last_error gives a message.
+ *  - Nothing here allocates memory outside hwfv1_init, and no call falls
+ *    back to a CPU computation.
+ */
+#ifndef HWFV1_H
+#define HWFV1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HWFV1_OK = 0,
+    HWFV1_ERR_INVALID_SPEC = 1, /* problem description or argument rejected */
+    HWFV1_ERR_OOM = 2,          /* device allocation failed                 */
+    HWFV1_ERR_CUDA = 3,         /* a CUDA call failed                       */
+    HWFV1_ERR_NONFINITE = 4,    /* a non-finite value appeared on the device */
+    HWFV1_ERR_NEG_DEPTH = 5,    /* reserved: negative depth in an input     */
+    HWFV1_ERR_TIMEOUT = 6,      /* reserved: a bounded device wait ran out  */
+    HWFV1_ERR_STATE = 7         /* call not valid in the handle's state      */
+} hwfv1_status;
+
+/* Boundary kinds (Sec. 3 test cases use closed walls, open boundaries and
+ * an inflow boundary). */
+typedef enum {
+    HWFV1_BC_CLOSED = 0,        /* reflective wall: ghost = cell, normal q negated */
+    HWFV1_BC_TRANSMISSIVE = 1,  /* open boundary: ghost = copy of the cell         */
+    HWFV1_BC_INFLOW = 2         /* wall plus a volume source Q(t) on the inlet     */
+} hwfv1_bc_kind;
+
+/* Regularisation switches (hwfv1_problem.flags). */
+#define HWFV1_REG_PREDICT 1u    /* children of a significant detail become significant */
+#define HWFV1_REG_CLOSE 2u      /* ancestors of a significant detail become significant */
+
+/* Problem description.  The user inputs of Algorithm 3 are L and eps (t_end
+ * is given to hwfv1_advance); CFL = 0.5 is the paper's choice (Sec. 2.1.3).
+ * All lengths in metres, times in seconds. */
+typedef struct hwfv1_problem {
+    double x0, y0;       /* domain origin                                         */
+    double lx, ly;       /* domain extent (> 0); finest cell dx = lx/2^L           */
+    double eps;          /* error threshold: 0, or in [1e-200, 1e300]             */
+    double cfl;          /* Courant number in (0, 1]                              */
+    double g;            /* gravitational acceleration (> 0)                      */
+    double manning_n;    /* Manning coefficient (>= 0; 0 = frictionless), Eq. 1   */
+    double tol_h;        /* wet/dry depth tolerance (> 0)                         */
+    double dt_max;       /* largest timestep, also the step when all is dry (> 0) */
+    int32_t L;           /* maximum refinement level, 1..14                       */
+    int32_t precision;   /* 64 (parity path) or 32                                */
+    int32_t bc[4];       /* hwfv1_bc_kind of the W, E, S, N sides                 */
+    int32_t inflow_a0;   /* inflow side: finest cells [a0, a1) along the side     */
+    int32_t inflow_a1;   /*   (j for W/E, i for S/N)                              */
+    int32_t inflow_n;    /* number of hydrograph points (>= 1 with an inflow side) */
+    uint32_t flags;      /* HWFV1_REG_* bits                                       */
+    const double* inflow_t; /* host, inflow_n strictly increasing times           */
+    const double* inflow_Q; /* host, inflow_n discharges (m^3/s); Q(t) is
+                               piecewise linear, constant outside the range      */
+} hwfv1_problem;
+
+typedef struct hwfv1_handle hwfv1_handle;
+
+/* Create a simulation from the initial finest fields (device, row-major,
+ * float64, 4^L elements each; qx = hu, qy = hv) and bed z.  Copies them into
+ * the handle's Morton-ordered hierarchy, encodes the static bed once, and
+ * sets t = 0 and dt from the CFL condition on the initial state.  `stream`
+ * is a cudaStream_t (NULL = legacy default stream).  Synchronises.
+ * Initial discretisation: Algorithm 3 line 2. */
+hwfv1_status hwfv1_init(const hwfv1_problem* spec, const double* z, const double* h,
+                        const double* qx, const double* qy, void* stream,
+                        hwfv1_handle** out);
+
+/* Encoding (Eq. 3a-3d, Algorithm 1): scaling coefficients of h, hu, hv for
+ * every level below L from the finest grid, threshold flags of every
+ * parent against the normalised threshold 2^(n-L)*eps*s_max (Sec. 2.1.2),
+ * and the upward closure of those flags. */
+hwfv1_status hwfv1_encode(hwfv1_handle* hd);
+
+/* Regularised significance: the encoded flags joined with the bed's
+ * (static) flags, the children of every significant detail, and (with
+ * HWFV1_REG_CLOSE) every ancestor of a significant detail. */
+hwfv1_status hwfv1_flag(hwfv1_handle* hd);
+
+/* Leaf cells of the significance tree (Algorithm 5: a finest cell's walk
+ * from the root stops at the first insignificant detail or at level L),
+ * duplicates removed by stream compaction (Sec. 2.2.3), in Z-order.  If
+ * num_leaves is not NULL the count is written there (host) and the call
+ * synchronises; otherwise it stays on the device. */
+hwfv1_status hwfv1_traverse(hwfv1_handle* hd, int64_t* num_leaves);
+
+/* FV1 forward-Euler update (Eq. 2) of every leaf with L_c built from the
+ * leaf's coefficients and its same-level neighbours' (Sec. 2.1.3): HLL
+ * fluxes with hydrostatic reconstruction, bed slope, Manning friction,
+ * inflow source; reduces the CFL bound of the updated leaves. */
+hwfv1_status hwfv1_step(hwfv1_handle* hd);
+
+/* Decode-back: every finest cell under a coarser leaf takes the leaf's
+ * discharges and free surface (Eq. 4 with zero details below leaves);
+ * then t += dt and the next dt = CFL * (min CFL bound) (Algorithm 3 lines
+ * 8-9), clamped so that no step passes the t_end of hwfv1_advance. */
+hwfv1_status hwfv1_decode(hwfv1_handle* hd);
+
+/* Run up to max_steps full steps (encode, flag, traverse, step, decode),
+ * stopping at t_end: a step never passes t_end and steps after it are
+ * no-ops.  Captures one step in a CUDA graph on first use and replays it.
+ * Does not synchronise. */
+hwfv1_status hwfv1_advance(hwfv1_handle* hd, double t_end, int64_t max_steps);
+
+/* Current finest fields h, hu, hv (device, row-major float64, 4^L each;
+ * any pointer may be NULL). */
+hwfv1_status hwfv1_get_fields(hwfv1_handle* hd, double* h, double* qx, double* qy);
+
+/* Replace the finest h, hu, hv (device, row-major float64) keeping t and dt;
+ * s_max is recomputed from the new fields. */
+hwfv1_status hwfv1_set_fields(hwfv1_handle* hd, const double* h, const double* qx,
+                              const double* qy);
+
+/* Leaves of the last traversal (device output, `cap` uint32 entries), each
+ * packed as (level << 28) | Morton code within the level, in Z-order of
+ * their first finest cell.  *n (host) receives the count.  Synchronises.
+ * Returns HWFV1_ERR_INVALID_SPEC if cap is too small (nothing written). */
+hwfv1_status hwfv1_get_leaves(hwfv1_handle* hd, uint32_t* packed, int64_t cap, int64_t* n);
+
+/* Significance bits (device output).  which = 0: threshold flags of
+ * h, hu, hv and z (Algorithm 1 line 8); 1: regularised flags used by the
+ * traversal.  Level n (0..L-1) occupies words [w(n), w(n+1)) with w(n) = n
+ * for n <= 3 and 3 + (4^n - 64)/96 above; bit b of word k of level n is
+ * the parent with Morton code 32k + b.  `cap_words` must be >= w(L). */
+hwfv1_status hwfv1_get_flags(hwfv1_handle* hd, int32_t which, uint32_t* bits, int64_t cap_words);
+
+/* Encoded coefficients of one level (device output, float64, 4^level
+ * values in Morton order).  field: 0 h, 1 hu, 2 hv, 3 z. */
+hwfv1_status hwfv1_get_level(hwfv1_handle* hd, int32_t field, int32_t level, double* out);
+
+/* Time, next timestep and number of steps taken (host outputs, any may be
+ * NULL).  Synchronises and reports latched device errors. */
+hwfv1_status hwfv1_get_time(hwfv1_handle* hd, double* t, double* dt, int64_t* step);
+
+/* Set the time and the timestep of the next step (dt > 0). */
+hwfv1_status hwfv1_set_time(hwfv1_handle* hd, double t, double dt);
+
+/* Diagnostics of the last completed step (host outputs, synchronises):
+ * number of leaves and the maxima of |h|, |hu|, |hv| used for s_max. */
+hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax3);
+
+/* Checkpoint: the finest h, hu, hv (Morton order, the handle's precision),
+ * t, dt and the step count, written to a host buffer.  With host_buf NULL
+ * only *used is set to the size needed.  Synchronises. */
+hwfv1_status hwfv1_save(hwfv1_handle* hd, void* host_buf, size_t cap, size_t* used);
+
+/* Restore a checkpoint written by hwfv1_save for the same problem. */
+hwfv1_status hwfv1_load(hwfv1_handle* hd, const void* host_buf, size_t n);
+
+/* Message of the last error on this handle ("" if none). */
+const char* hwfv1_last_error(hwfv1_handle* hd);
+
+/* Free all device memory of the handle. */
+void hwfv1_destroy(hwfv1_handle* hd);
+
+/* Library version, for the loader's sanity check. */
+int32_t hwfv1_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HWFV1_H */

@@ -50,9 +50,10 @@
  *  R-cfl    dt = CFL * min over wet leaves (h >= tol_h) of
  *           min(dx_L/(|u|+sqrt(gh)), dy_L/(|v|+sqrt(gh))) with the finest
  *           spacing dx_L, dy_L and the leaf's updated state (the grid may
- *           refine by one level before the next update); dt_max when every
- *           leaf is dry.  Before the first step the same formula runs over
- *           the finest cells of the initial state.
+ *           refine by one level before the next update), capped at dt_max
+ *           (which is also the step when every leaf is dry).  Before the
+ *           first step the same formula runs over the finest cells of the
+ *           initial state.
  *  R-decode after the update the finest cells under a leaf take the leaf's
  *           discharges (Eq. 4 with the details below leaves set to zero).
  *           Their depth restores the leaf's free surface: with
@@ -574,8 +575,8 @@ double orc_cfl_rmin(const orc_problem* p, const double* h, const double* qx, con
 }
 
 static double dt_from_rmin(const orc_problem* p, double r) {
-    if (r == INFINITY) return p->dt_max;
-    return p->cfl * r;
+    double dt = p->cfl * r;                 /* +inf when every cell is dry */
+    return dt < p->dt_max ? dt : p->dt_max;
 }
 
 /* dt from the finest cells of a state (used before the first step). */

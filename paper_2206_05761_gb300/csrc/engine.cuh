@@ -1,0 +1,465 @@
+// engine.cuh -- host side of one HWFV1 simulation: device buffers, the
+// launch sequence of a timestep, CUDA-graph replay, checkpoints.
+#pragma once
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine_iface.h"
+#include "kernels.cuh"
+
+namespace hwfv1 {
+
+template <typename T>
+class EngineT final : public Engine {
+   public:
+    EngineT(const hwfv1_problem& s, cudaStream_t stream) : spec_(s), stream_(stream) {
+        L_ = s.L;
+        N_ = 1ull << (2 * L_);
+        H_ = hier_size(L_);
+        kt_ = L_ < 5 ? L_ : 5;
+        ntiles_ = 1u << (2 * (L_ - kt_));
+        words_ = bits_words(L_);
+        if (s.inflow_n > 0 && s.inflow_t) {
+            it_.assign(s.inflow_t, s.inflow_t + s.inflow_n);
+            iq_.assign(s.inflow_Q, s.inflow_Q + s.inflow_n);
+        }
+    }
+    ~EngineT() override {
+        if (exec_) cudaGraphExecDestroy(exec_);
+        for (void* p : allocs_) cudaFree(p);
+        if (own_stream_) cudaStreamDestroy(stream_);
+    }
+
+    hwfv1_status init(const double* z, const double* h, const double* qx,
+                      const double* qy) override {
+        if (!stream_) {
+            if (cudaStreamCreate(&stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "stream");
+            own_stream_ = true;
+        }
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q)
+                if (!alloc(&f_[b][q], H_ * sizeof(T))) return oom();
+        if (!alloc(&z_, H_ * sizeof(T))) return oom();
+        if (!alloc(&bits_, (size_t)words_ * 6 * sizeof(uint32_t))) return oom();
+        Tb_ = bits_;
+        Cb_ = bits_ + words_;
+        Tz_ = bits_ + 2 * words_;
+        Cz_ = bits_ + 3 * words_;
+        Sz_ = bits_ + 4 * words_;
+        Sb_ = bits_ + 5 * words_;
+        if (!alloc(&leaves_, N_ * sizeof(uint32_t))) return oom();
+        if (!alloc(&counts_, (size_t)ntiles_ * 2 * sizeof(uint32_t))) return oom();
+        offs_ = counts_ + ntiles_;
+        if (!alloc(&st_, sizeof(DevState))) return oom();
+        if (!alloc(&zaux_, 256)) return oom();
+        if (!it_.empty()) {
+            if (!alloc(&it_d_, it_.size() * sizeof(double))) return oom();
+            if (!alloc(&iq_d_, iq_.size() * sizeof(double))) return oom();
+            cudaMemcpyAsync(it_d_, it_.data(), it_.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
+            cudaMemcpyAsync(iq_d_, iq_.data(), iq_.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
+        }
+        cudaMemsetAsync(bits_, 0, (size_t)words_ * 6 * sizeof(uint32_t), stream_);
+        cudaMemsetAsync(st_, 0, sizeof(DevState), stream_);
+        // finest fields into the Morton hierarchy
+        const int g = grid_for(N_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(z, z_ + lvl_off(L_), L_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(h, f_[0][0] + lvl_off(L_), L_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(qx, f_[0][1] + lvl_off(L_), L_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(qy, f_[0][2] + lvl_off(L_), L_);
+        // bed: s_max, thresholds, one-off encode and its static flags
+        unsigned long long* zmax = reinterpret_cast<unsigned long long*>(zaux_);
+        double* smax_z = reinterpret_cast<double*>(zaux_ + 8);
+        double* thr_zd = reinterpret_cast<double*>(zaux_ + 16);     // up to 14 doubles
+        float* thr_zf = reinterpret_cast<float*>(zaux_ + 16 + 8 * kMaxL);
+        k_maxabs<T><<<g, 256, 0, stream_>>>(z_ + lvl_off(L_), N_, zmax);
+        k_z_thresholds<<<1, 32, 0, stream_>>>(zmax, thr_zd, thr_zf, smax_z, L_, spec_.eps);
+        {
+            EncodeArgs<T, 1> a;
+            a.f[0][0] = a.f[1][0] = z_;
+            a.thr = thr_z();
+            a.Tb = Tz_;
+            a.Cb = Cz_;
+            a.st = nullptr;
+            a.L = L_;
+            encode_passes(a);
+        }
+        k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tz_, Cz_, nullptr, Sz_, L_, predict(), close(),
+                                                       nullptr);
+        // initial state scalars
+        reduce_state(/*set_dt=*/1);
+        return check("init", true);
+    }
+
+    hwfv1_status encode() override {
+        launch_encode();
+        return check("encode");
+    }
+    hwfv1_status flag() override {
+        launch_flag();
+        return check("flag");
+    }
+    hwfv1_status traverse(int64_t* num_leaves) override {
+        launch_traverse();
+        if (num_leaves) {
+            DevState s;
+            if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            *num_leaves = s.M;
+        }
+        return check("traverse");
+    }
+    hwfv1_status step() override {
+        launch_fv1();
+        return check("step");
+    }
+    hwfv1_status decode() override {
+        launch_decode();
+        return check("decode");
+    }
+
+    hwfv1_status advance(double t_end, int64_t max_steps) override {
+        if (max_steps < 0) return fail(HWFV1_ERR_INVALID_SPEC, "max_steps < 0");
+        k_set_tend<<<1, 32, 0, stream_>>>(st_, fin_args(), t_end);
+        if (max_steps == 0) return check("advance");
+        const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
+        if (use_graph && !exec_) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return fail(HWFV1_ERR_CUDA, "graph capture begin");
+            launch_step_all();
+            if (cudaStreamEndCapture(stream_, &g) != cudaSuccess)
+                return fail(HWFV1_ERR_CUDA, "graph capture end");
+            cudaError_t e = cudaGraphInstantiate(&exec_, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                exec_ = nullptr;
+                return fail(HWFV1_ERR_CUDA, "graph instantiate");
+            }
+        }
+        for (int64_t s = 0; s < max_steps; ++s) {
+            if (use_graph) {
+                if (cudaGraphLaunch(exec_, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
+            } else {
+                launch_step_all();
+            }
+        }
+        return check("advance");
+    }
+
+    hwfv1_status get_fields(double* h, double* qx, double* qy) override {
+        double* out[3] = {h, qx, qy};
+        for (int q = 0; q < 3; ++q)
+            if (out[q])
+                k_morton_to_rm<T><<<grid_for(N_), 256, 0, stream_>>>(
+                    f_[0][q] + lvl_off(L_), f_[1][q] + lvl_off(L_), st_, out[q], L_);
+        return check("get_fields");
+    }
+
+    hwfv1_status set_fields(const double* h, const double* qx, const double* qy) override {
+        const double* in[3] = {h, qx, qy};
+        for (int q = 0; q < 3; ++q) {
+            if (!in[q]) return fail(HWFV1_ERR_INVALID_SPEC, "set_fields: NULL field");
+            k_rm_to_morton_cur<T><<<grid_for(N_), 256, 0, stream_>>>(
+                in[q], f_[0][q] + lvl_off(L_), f_[1][q] + lvl_off(L_), st_, L_);
+        }
+        reduce_state(/*set_dt=*/0);
+        return check("set_fields");
+    }
+
+    hwfv1_status get_leaves(uint32_t* out, int64_t cap, int64_t* n) override {
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        if (n) *n = s.M;
+        if (!out) return HWFV1_OK;
+        if (cap < (int64_t)s.M) return fail(HWFV1_ERR_INVALID_SPEC, "get_leaves: cap too small");
+        cudaMemcpyAsync(out, leaves_, sizeof(uint32_t) * s.M, cudaMemcpyDeviceToDevice, stream_);
+        return check("get_leaves", true);
+    }
+
+    hwfv1_status get_flags(int which, uint32_t* out, int64_t cap_words) override {
+        if (cap_words < (int64_t)words_) return fail(HWFV1_ERR_INVALID_SPEC, "get_flags: cap too small");
+        if (which == 0)
+            k_or_words<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Tz_, out, words_);
+        else if (which == 1)
+            cudaMemcpyAsync(out, Sb_, sizeof(uint32_t) * words_, cudaMemcpyDeviceToDevice, stream_);
+        else
+            return fail(HWFV1_ERR_INVALID_SPEC, "get_flags: which must be 0 or 1");
+        return check("get_flags");
+    }
+
+    hwfv1_status get_level(int field, int level, double* out) override {
+        if (field < 0 || field > 3 || level < 0 || level > L_)
+            return fail(HWFV1_ERR_INVALID_SPEC, "get_level: bad field or level");
+        const uint64_t n = 1ull << (2 * level);
+        if (field == 3)
+            k_copy_level<T><<<grid_for(n), 256, 0, stream_>>>(z_ + lvl_off(level), nullptr, st_, out, n);
+        else
+            k_copy_level<T><<<grid_for(n), 256, 0, stream_>>>(
+                f_[0][field] + lvl_off(level), f_[1][field] + lvl_off(level), st_, out, n);
+        return check("get_level");
+    }
+
+    hwfv1_status get_time(double* t, double* dt, int64_t* step) override {
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        if (t) *t = s.t;
+        if (dt) *dt = s.dt;
+        if (step) *step = s.step;
+        if (s.err & kErrNonFinite) return fail(HWFV1_ERR_NONFINITE, "non-finite value in the state");
+        return HWFV1_OK;
+    }
+
+    hwfv1_status set_time(double t, double dt) override {
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        s.t = t;
+        s.dt = dt;
+        cudaMemcpyAsync(st_, &s, sizeof s, cudaMemcpyHostToDevice, stream_);
+        k_set_tend<<<1, 32, 0, stream_>>>(st_, fin_args(), s.t_end);
+        return check("set_time", true);
+    }
+
+    hwfv1_status get_stats(int64_t* M, double* smax3) override {
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        if (M) *M = s.M;
+        if (smax3)
+            for (int q = 0; q < 3; ++q) smax3[q] = s.smax[q];
+        return HWFV1_OK;
+    }
+
+    hwfv1_status save(void* buf, size_t cap, size_t* used) override {
+        const size_t need = sizeof(SaveHeader) + 3 * N_ * sizeof(T);
+        if (used) *used = need;
+        if (!buf) return HWFV1_OK;
+        if (cap < need) return fail(HWFV1_ERR_INVALID_SPEC, "save: buffer too small");
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        SaveHeader hd{kSaveMagic, L_, (int32_t)(sizeof(T) * 8), s.t, s.dt, s.step};
+        std::memcpy(buf, &hd, sizeof hd);
+        char* p = static_cast<char*>(buf) + sizeof hd;
+        for (int q = 0; q < 3; ++q)
+            cudaMemcpyAsync(p + q * N_ * sizeof(T), f_[s.cur][q] + lvl_off(L_), N_ * sizeof(T),
+                            cudaMemcpyDeviceToHost, stream_);
+        return check("save", true);
+    }
+
+    hwfv1_status load(const void* buf, size_t n) override {
+        const size_t need = sizeof(SaveHeader) + 3 * N_ * sizeof(T);
+        if (!buf || n < need) return fail(HWFV1_ERR_INVALID_SPEC, "load: buffer too small");
+        SaveHeader hd;
+        std::memcpy(&hd, buf, sizeof hd);
+        if (hd.magic != kSaveMagic || hd.L != L_ || hd.precision != (int32_t)(sizeof(T) * 8))
+            return fail(HWFV1_ERR_INVALID_SPEC, "load: checkpoint of another problem");
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        const char* p = static_cast<const char*>(buf) + sizeof hd;
+        for (int q = 0; q < 3; ++q)
+            cudaMemcpyAsync(f_[s.cur][q] + lvl_off(L_), p + q * N_ * sizeof(T), N_ * sizeof(T),
+                            cudaMemcpyHostToDevice, stream_);
+        s.t = hd.t;
+        s.dt = hd.dt;
+        s.step = hd.step;
+        s.err = 0;
+        cudaMemcpyAsync(st_, &s, sizeof s, cudaMemcpyHostToDevice, stream_);
+        reduce_state(/*set_dt=*/0);
+        return check("load", true);
+    }
+
+   private:
+    // ---- launch helpers -------------------------------------------------
+    int grid_for(uint64_t n) const {
+        uint64_t g = (n + 255) / 256;
+        const uint64_t cap = (uint64_t)nsm_ * 8;
+        if (g > cap) g = cap;
+        return g < 1 ? 1 : (int)g;
+    }
+    int predict() const { return (spec_.flags & HWFV1_REG_PREDICT) ? 1 : 0; }
+    int close() const { return (spec_.flags & HWFV1_REG_CLOSE) ? 1 : 0; }
+    const T* thr_z() const;
+    const T* thr_dyn() const;
+
+    template <int NF>
+    void encode_passes(EncodeArgs<T, NF> a) {
+        int ls = L_;
+        while (ls > 0) {
+            const int k = ls < 5 ? ls : 5;
+            a.ls = ls;
+            a.k = k;
+            k_encode<T, NF><<<1u << (2 * (ls - k)), 256, 0, stream_>>>(a);
+            ls -= k;
+        }
+    }
+
+    void launch_encode() {
+        k_clear_words<<<grid_for(2 * (uint64_t)words_), 256, 0, stream_>>>(Tb_, 2 * words_, st_);
+        EncodeArgs<T, 3> a;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
+        a.thr = thr_dyn();
+        a.Tb = Tb_;
+        a.Cb = Cb_;
+        a.st = st_;
+        a.L = L_;
+        encode_passes(a);
+    }
+    void launch_flag() {
+        k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
+    }
+    void launch_traverse() {
+        k_trav_count<<<ntiles_, 256, 0, stream_>>>(Sb_, counts_, L_, kt_, st_);
+        k_scan_tiles<<<1, 1024, 0, stream_>>>(counts_, offs_, ntiles_, st_);
+        k_trav_write<<<ntiles_, 256, 0, stream_>>>(Sb_, offs_, leaves_, L_, kt_, st_);
+    }
+    StepArgs<T> step_args() const {
+        StepArgs<T> a;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
+        a.z = z_;
+        a.leaves = leaves_;
+        a.st = st_;
+        a.P = phys();
+        a.lx = (T)spec_.lx;
+        a.ly = (T)spec_.ly;
+        a.L = L_;
+        a.inflow_side = -1;
+        for (int s = 0; s < 4; ++s) {
+            a.bc_ref[s] = spec_.bc[s] != HWFV1_BC_TRANSMISSIVE;
+            if (spec_.bc[s] == HWFV1_BC_INFLOW && spec_.inflow_n > 0 && spec_.inflow_a1 > spec_.inflow_a0)
+                a.inflow_side = s;
+        }
+        a.a0 = spec_.inflow_a0;
+        a.a1 = spec_.inflow_a1;
+        return a;
+    }
+    Phys<T> phys() const {
+        Phys<T> P;
+        P.g = (T)spec_.g;
+        P.tol = (T)spec_.tol_h;
+        P.nM = (T)spec_.manning_n;
+        P.cfl = (T)spec_.cfl;
+        P.dxL = (T)std::ldexp(spec_.lx, -L_);
+        P.dyL = (T)std::ldexp(spec_.ly, -L_);
+        return P;
+    }
+    void launch_fv1() {
+        k_fv1<T><<<grid_for(N_), 256, 0, stream_>>>(step_args());
+    }
+    void launch_decode() {
+        DecodeArgs<T> a;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
+        a.z = z_;
+        a.Sb = Sb_;
+        a.st = st_;
+        a.tol = (T)spec_.tol_h;
+        a.L = L_;
+        a.kt = kt_;
+        k_decode<T><<<ntiles_, 256, 0, stream_>>>(a);
+        k_finish<<<1, 32, 0, stream_>>>(st_, fin_args());
+    }
+    void launch_step_all() {
+        launch_encode();
+        launch_flag();
+        launch_traverse();
+        launch_fv1();
+        launch_decode();
+    }
+    FinishArgs fin_args() const {
+        FinishArgs a;
+        a.inflow_t = it_d_;
+        a.inflow_Q = iq_d_;
+        a.inflow_n = it_.empty() ? 0 : (int)it_.size();
+        a.L = L_;
+        a.eps = spec_.eps;
+        a.cfl = spec_.cfl;
+        a.dt_max = spec_.dt_max;
+        return a;
+    }
+    // s_max (and dt when set_dt) from the finest fields of the current buffer
+    void reduce_state(int set_dt) {
+        k_reset_red<<<1, 32, 0, stream_>>>(st_);
+        const int g = grid_for(N_);
+        k_maxabs_cur<T><<<g, 256, 0, stream_>>>(f_[0][0] + lvl_off(L_), f_[1][0] + lvl_off(L_), st_, N_, 0);
+        k_maxabs_cur<T><<<g, 256, 0, stream_>>>(f_[0][1] + lvl_off(L_), f_[1][1] + lvl_off(L_), st_, N_, 1);
+        k_maxabs_cur<T><<<g, 256, 0, stream_>>>(f_[0][2] + lvl_off(L_), f_[1][2] + lvl_off(L_), st_, N_, 2);
+        if (set_dt) {
+            k_cfl_cur<T><<<g, 256, 0, stream_>>>(f_[0][0] + lvl_off(L_), f_[1][0] + lvl_off(L_),
+                                                  f_[0][1] + lvl_off(L_), f_[1][1] + lvl_off(L_),
+                                                  f_[0][2] + lvl_off(L_), f_[1][2] + lvl_off(L_), st_,
+                                                  N_, phys());
+        }
+        k_init_state<<<1, 32, 0, stream_>>>(st_, fin_args(), set_dt);
+    }
+
+    hwfv1_status read_state(DevState* s) {
+        if (cudaMemcpyAsync(s, st_, sizeof *s, cudaMemcpyDeviceToHost, stream_) != cudaSuccess ||
+            cudaStreamSynchronize(stream_) != cudaSuccess)
+            return fail(HWFV1_ERR_CUDA, std::string("read_state: ") + cudaGetErrorString(cudaGetLastError()));
+        return HWFV1_OK;
+    }
+    template <typename P>
+    bool alloc(P** p, size_t bytes) {
+        void* v = nullptr;
+        if (cudaMalloc(&v, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        allocs_.push_back(v);
+        *p = static_cast<P*>(v);
+        return true;
+    }
+    hwfv1_status oom() { return fail(HWFV1_ERR_OOM, "device allocation failed"); }
+    hwfv1_status fail(hwfv1_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    hwfv1_status check(const char* what, bool sync = false) {
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream_);
+        if (e != cudaSuccess) return fail(HWFV1_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        return HWFV1_OK;
+    }
+
+    hwfv1_problem spec_;
+    cudaStream_t stream_ = nullptr;
+    bool own_stream_ = false;
+    int nsm_ = 152;
+    int L_, kt_;
+    uint64_t N_, H_;
+    uint32_t ntiles_, words_;
+    std::vector<double> it_, iq_;
+    std::vector<void*> allocs_;
+    T* f_[2][3] = {};
+    T* z_ = nullptr;
+    uint32_t *bits_ = nullptr, *Tb_ = nullptr, *Cb_ = nullptr, *Tz_ = nullptr, *Cz_ = nullptr,
+             *Sz_ = nullptr, *Sb_ = nullptr;
+    uint32_t *leaves_ = nullptr, *counts_ = nullptr, *offs_ = nullptr;
+    DevState* st_ = nullptr;
+    char* zaux_ = nullptr;
+    double *it_d_ = nullptr, *iq_d_ = nullptr;
+    cudaGraphExec_t exec_ = nullptr;
+};
+
+template <>
+inline const double* EngineT<double>::thr_z() const {
+    return reinterpret_cast<const double*>(zaux_ + 16);
+}
+template <>
+inline const float* EngineT<float>::thr_z() const {
+    return reinterpret_cast<const float*>(zaux_ + 16 + 8 * kMaxL);
+}
+template <>
+inline const double* EngineT<double>::thr_dyn() const {
+    return st_->thr;
+}
+template <>
+inline const float* EngineT<float>::thr_dyn() const {
+    return st_->thrf;
+}
+
+}  // namespace hwfv1

@@ -1,0 +1,49 @@
+// engine_iface.h -- the interface between the C ABI (api.cu) and the
+// per-precision engines (engine_f64.cu, engine_f32.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hwfv1.h"
+
+namespace hwfv1 {
+
+class Engine {
+   public:
+    virtual ~Engine() {}
+    virtual hwfv1_status init(const double* z, const double* h, const double* qx,
+                              const double* qy) = 0;
+    virtual hwfv1_status encode() = 0;
+    virtual hwfv1_status flag() = 0;
+    virtual hwfv1_status traverse(int64_t* num_leaves) = 0;
+    virtual hwfv1_status step() = 0;
+    virtual hwfv1_status decode() = 0;
+    virtual hwfv1_status advance(double t_end, int64_t max_steps) = 0;
+    virtual hwfv1_status get_fields(double* h, double* qx, double* qy) = 0;
+    virtual hwfv1_status set_fields(const double* h, const double* qx, const double* qy) = 0;
+    virtual hwfv1_status get_leaves(uint32_t* out, int64_t cap, int64_t* n) = 0;
+    virtual hwfv1_status get_flags(int which, uint32_t* out, int64_t cap_words) = 0;
+    virtual hwfv1_status get_level(int field, int level, double* out) = 0;
+    virtual hwfv1_status get_time(double* t, double* dt, int64_t* step) = 0;
+    virtual hwfv1_status set_time(double t, double dt) = 0;
+    virtual hwfv1_status get_stats(int64_t* M, double* smax3) = 0;
+    virtual hwfv1_status save(void* buf, size_t cap, size_t* used) = 0;
+    virtual hwfv1_status load(const void* buf, size_t n) = 0;
+    std::string err;
+};
+
+Engine* make_engine_f64(const hwfv1_problem& spec, cudaStream_t stream);
+Engine* make_engine_f32(const hwfv1_problem& spec, cudaStream_t stream);
+
+struct SaveHeader {
+    uint64_t magic;
+    int32_t L, precision;
+    double t, dt;
+    int64_t step;
+};
+constexpr uint64_t kSaveMagic = 0x31564657484D5248ull;   // "HRMHWFV1"
+
+}  // namespace hwfv1

@@ -1,0 +1,835 @@
+// kernels.cuh -- HWFV1 device kernels, templated on the arithmetic type T
+// (double: the parity path; float: the 32-bit path).
+//
+// Every kernel that belongs to a timestep reads its scalars (timestep,
+// thresholds, leaf count, which state buffer is current) from DevState in
+// device memory, so one step can be captured in a CUDA graph and replayed.
+// The double instantiation evaluates the method in the operation order of
+// the readings documented in the design notes (no FMA contraction: the
+// library is compiled with --fmad=false); where a cheaper form is used it
+// is equal for every finite input (noted at the spot).
+#pragma once
+#include "common.cuh"
+
+namespace hwfv1 {
+
+template <typename T> struct Vec4;
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double* p, double& a, double& b, double& c,
+                                                double& d) {
+        const double2 u = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        a = u.x; b = u.y; c = v.x; d = v.y;
+    }
+    static __device__ __forceinline__ void store(double* p, double a, double b, double c, double d) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+    }
+};
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float& a, float& b, float& c,
+                                                float& d) {
+        const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+        a = u.x; b = u.y; c = u.z; d = u.w;
+    }
+    static __device__ __forceinline__ void store(float* p, float a, float b, float c, float d) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    }
+};
+
+template <typename T> __device__ __forceinline__ bool same4(T a, T b, T c, T d);
+template <> __device__ __forceinline__ bool same4<double>(double a, double b, double c, double d) {
+    const long long x = __double_as_longlong(a);
+    // equal bit patterns and |a| < 2^1022 (so 4a does not overflow)
+    return x == __double_as_longlong(b) && x == __double_as_longlong(c) &&
+           x == __double_as_longlong(d) && ((x >> 52) & 0x7FF) < 0x7FD;
+}
+template <> __device__ __forceinline__ bool same4<float>(float a, float b, float c, float d) {
+    const int x = __float_as_int(a);
+    return x == __float_as_int(b) && x == __float_as_int(c) && x == __float_as_int(d) &&
+           ((x >> 23) & 0xFF) < 0xFD;
+}
+
+// Haar parent (Eq. 3a) and the largest detail magnitude (Eq. 3b-3d) of four
+// children [0]=(2i,2j) [1]=(2i+1,2j) [2]=(2i,2j+1) [3]=(2i+1,2j+1).
+// dmax = 0.25*max(|d+e|, |a-b|, |d-e|) equals max(|0.25(d+e)|, ...) because
+// scaling by 0.25 and rounding commute with max.  Four equal children give
+// s = c0 and dmax = 0 in every arithmetic, so that case skips the sums.
+template <typename T>
+__device__ __forceinline__ void haar4(T c0, T c1, T c2, T c3, T& s, T& dmax) {
+    if (same4<T>(c0, c1, c2, c3)) {
+        s = c0;
+        dmax = T(0);
+        return;
+    }
+    const T a = c0 + c2, b = c1 + c3, d = c0 - c2, e = c1 - c3;
+    s = T(0.25) * (a + b);
+    const T da = fabs(d + e), db = fabs(a - b), dg = fabs(d - e);
+    T m = da > db ? da : db;
+    m = m > dg ? m : dg;
+    dmax = T(0.25) * m;
+}
+
+// Write the per-thread flag of `cnt` consecutive parents (codes base..) of
+// level n.  Full words are stored; a partial word (cnt < 32) is OR-ed into
+// a word cleared before the pass.  Called by every thread of the block.
+__device__ __forceinline__ uint32_t put_bits(uint32_t* bits, int n, uint32_t base, uint32_t cnt,
+                                             bool flag) {
+    const uint32_t ballot = __ballot_sync(0xffffffffu, flag);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (cnt >= 32u) {
+        if (lane == 0 && warp * 32u < cnt) bits[word_off(n) + (base >> 5) + warp] = ballot;
+    } else if (threadIdx.x == 0 && ballot) {
+        atomicOr(bits + word_off(n) + (base >> 5), ballot << (base & 31u));
+    }
+    return ballot;
+}
+
+// ---------------------------------------------------------------------------
+// Encoding + threshold flags + closure (Eq. 3, Algorithm 1)
+// ---------------------------------------------------------------------------
+template <typename T, int NF>
+struct EncodeArgs {
+    T* f[2][NF];          // hierarchy of each quantity, per state buffer
+    const T* thr;         // threshold of level n, quantity q at thr[n*NF + q]
+    uint32_t* Tb;         // threshold flags
+    uint32_t* Cb;         // upward closure of the threshold flags
+    const DevState* st;   // NULL: buffer 0, always active
+    int L, ls, k;         // source level ls; produces levels ls-1 .. ls-k
+};
+
+// One CTA encodes one tile: the 4^k cells of level ls under one level-(ls-k)
+// cell, k <= 5 levels in one pass.  The first level reads four children
+// per thread with 128-bit loads; the next levels work from shared memory.
+template <typename T, int NF>
+static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
+    if (a.st && !a.st->active) return;
+    const int par = a.st ? (int)a.st->cur : 0;
+    __shared__ T sv[2][NF][256];
+    __shared__ uint32_t sc[2][8];
+    const uint32_t tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    uint32_t cnt = 1u << (2 * (a.k - 1));
+    int n = a.ls - 1;
+    {   // level ls-1
+        const bool act = tid < cnt;
+        const uint32_t p = tile * cnt + tid;
+        bool tf = false;
+        uint32_t cchild = 0;
+        T s[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) s[q] = T(0);
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                T c0, c1, c2, c3, dm;
+                T* fq = par ? a.f[1][q] : a.f[0][q];
+                Vec4<T>::load(fq + lvl_off(a.ls) + 4ull * p, c0, c1, c2, c3);
+                haar4<T>(c0, c1, c2, c3, s[q], dm);
+                tf = tf || (dm >= a.thr[n * NF + q]);
+                fq[lvl_off(n) + p] = s[q];
+            }
+            if (a.ls < a.L) {
+                const uint32_t cb = 4u * p;
+                cchild = (__ldg(a.Cb + word_off(a.ls) + (cb >> 5)) >> (cb & 31u)) & 0xFu;
+            }
+        }
+        const bool cf = act && (tf || cchild);
+        put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
+        const uint32_t cball = put_bits(a.Cb, n, tile * cnt, cnt, cf);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) sv[0][q][tid] = s[q];
+        if (lane == 0) sc[0][warp] = cball;
+    }
+    for (int j = 2; j <= a.k; ++j) {
+        __syncthreads();
+        n = a.ls - j;
+        cnt >>= 2;
+        const int rbuf = (j - 2) & 1, wbuf = (j - 1) & 1;   // level j-1 wrote buffer (j-2)&1
+        const bool act = tid < cnt;
+        const uint32_t p = tile * cnt + tid;
+        bool tf = false;
+        uint32_t cchild = 0;
+        T s[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) s[q] = T(0);
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                T dm;
+                T* fq = par ? a.f[1][q] : a.f[0][q];
+                haar4<T>(sv[rbuf][q][4 * tid], sv[rbuf][q][4 * tid + 1], sv[rbuf][q][4 * tid + 2],
+                         sv[rbuf][q][4 * tid + 3], s[q], dm);
+                tf = tf || (dm >= a.thr[n * NF + q]);
+                fq[lvl_off(n) + p] = s[q];
+            }
+            cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
+        }
+        const bool cf = act && (tf || cchild);
+        put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
+        const uint32_t cball = put_bits(a.Cb, n, tile * cnt, cnt, cf);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) sv[wbuf][q][tid] = s[q];
+        if (lane == 0) sc[wbuf][warp] = cball;
+    }
+}
+
+// Clear bit arrays before an encode (the partial words are OR-ed into).
+static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, const DevState* st) {
+    if (st && !st->active) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x)
+        w[i] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Regularised significance, word-parallel:
+//   S(n,c) = Sbase(n,c) | (close ? C(n,c) : T(n,c)) | (predict ? T(n-1,c/4) : 0)
+// ---------------------------------------------------------------------------
+static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
+                       const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb, int L,
+                       int predict, int close, const DevState* st) {
+    if (st && !st->active) return;
+    const uint32_t total = bits_words(L);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+        int n = 0;
+        while (n + 1 < L && word_off(n + 1) <= w) ++n;
+        const uint32_t lw = w - word_off(n);
+        uint32_t s = (close ? Cb[w] : Tb[w]);
+        if (Sbase) s |= Sbase[w];
+        if (predict && n >= 1) {
+            uint32_t pb;
+            if (n >= 3) {
+                pb = expand4x8(Tb[word_off(n - 1) + (lw >> 2)] >> (8u * (lw & 3u)));
+            } else if (n == 2) {   // 16 cells, parents are the 4 cells of level 1
+                pb = expand4x8(Tb[word_off(1)] & 0xFu);
+            } else {               // level 1: the root's four children
+                pb = (Tb[word_off(0)] & 1u) ? 0xFu : 0u;
+            }
+            s |= pb;
+        }
+        if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
+        Sb[w] = s;
+    }
+}
+
+// OR of two bit arrays (threshold flags of h, qx, qy with those of z).
+static __global__ void k_or_words(const uint32_t* a, const uint32_t* b, uint32_t* out, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = a[i] | b[i];
+}
+
+// ---------------------------------------------------------------------------
+// Leaf identification (Algorithm 5) and compaction (Sec. 2.2.3).
+// A tile is the 4^kt finest cells under one level-(L-kt) cell; thread t owns
+// the four finest cells 4t..4t+3 of the tile (one level-(L-1) parent).
+// ---------------------------------------------------------------------------
+struct TileWalk {
+    int l;          // leaf level of the thread's four cells (common ancestor path)
+    uint32_t m0;    // first finest Morton code of the thread
+    bool act;
+};
+
+// Level at which the walk from the root towards the tile stops (<= L-kt), or
+// L-kt+1 if every cell on the path is significant.  Run by one thread.
+__device__ __forceinline__ int walk_root(const uint32_t* Sb, int Lr, uint32_t tile) {
+    for (int n = 0; n <= Lr; ++n)
+        if (!sig_bit(Sb, n, tile >> (2 * (Lr - n)))) return n;
+    return Lr + 1;
+}
+
+__device__ __forceinline__ TileWalk walk_tile(const uint32_t* Sb, int L, int kt, uint32_t tile,
+                                              int l0) {
+    TileWalk w;
+    const int Lr = L - kt;
+    w.act = threadIdx.x < (1u << (2 * (kt - 1)));
+    w.m0 = (tile << (2 * kt)) + 4u * threadIdx.x;
+    if (!w.act) {            // threads past the tile touch no memory
+        w.l = L;
+        return w;
+    }
+    if (l0 <= Lr) {
+        w.l = l0;
+    } else {
+        w.l = L;
+        for (int n = Lr + 1; n <= L - 1; ++n)
+            if (!sig_bit(Sb, n, w.m0 >> (2 * (L - n)))) { w.l = n; break; }
+    }
+    return w;
+}
+
+// number of leaves whose first finest cell is among the thread's 4 cells
+__device__ __forceinline__ uint32_t heads_of(const TileWalk& w, int L) {
+    if (!w.act) return 0u;
+    if (w.l == L) return 4u;
+    const uint32_t mask = (1u << (2 * (L - w.l))) - 1u;
+    return (w.m0 & mask) == 0u ? 1u : 0u;
+}
+
+static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __restrict__ Sb,
+                                                    uint32_t* __restrict__ counts, int L, int kt,
+                                                    const DevState* st) {
+    if (st && !st->active) return;
+    __shared__ int s_l0;
+    const uint32_t tile = blockIdx.x;
+    if (threadIdx.x == 0) s_l0 = walk_root(Sb, L - kt, tile);
+    __syncthreads();
+    const TileWalk w = walk_tile(Sb, L, kt, tile, s_l0);
+    uint32_t total;
+    block_excl_scan(heads_of(w, L), &total);
+    if (threadIdx.x == 0) counts[tile] = total;
+}
+
+// exclusive scan of the tile counts; M = total (one CTA of 1024 threads)
+static __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ counts,
+                                                     uint32_t* __restrict__ offs, uint32_t ntiles,
+                                                     DevState* st) {
+    if (st && !st->active) return;
+    const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = threadIdx.x * per, e = min(ntiles, b + per);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += counts[i];
+    uint32_t total;
+    uint32_t run = block_excl_scan(sum, &total);
+    for (uint32_t i = b; i < e; ++i) {
+        offs[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == 0) st->M = total;
+}
+
+static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __restrict__ Sb,
+                                                    const uint32_t* __restrict__ offs,
+                                                    uint32_t* __restrict__ leaves, int L, int kt,
+                                                    const DevState* st) {
+    if (st && !st->active) return;
+    __shared__ int s_l0;
+    const uint32_t tile = blockIdx.x;
+    if (threadIdx.x == 0) s_l0 = walk_root(Sb, L - kt, tile);
+    __syncthreads();
+    const TileWalk w = walk_tile(Sb, L, kt, tile, s_l0);
+    const uint32_t hc = heads_of(w, L);
+    uint32_t pos = offs[tile] + block_excl_scan(hc, nullptr);
+    if (hc == 4u) {
+#pragma unroll
+        for (uint32_t e = 0; e < 4u; ++e) leaves[pos + e] = ((uint32_t)L << kLeafShift) | (w.m0 + e);
+    } else if (hc == 1u) {
+        leaves[pos] = ((uint32_t)w.l << kLeafShift) | (w.m0 >> (2 * (L - w.l)));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FV1 update of one cell (Eq. 1-2; the L_c reading: hydrostatic
+// reconstruction, HLL, Audusse bed source, Manning friction)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cell { T h, qx, qy, z; };
+
+template <typename T>
+struct Phys {
+    T g, tol, nM, cfl, dxL, dyL;
+};
+
+template <typename T>
+__device__ __forceinline__ void velocity(const Cell<T>& c, T tol, T& u, T& v) {
+    if (c.h >= tol) {
+        const T rh = T(1) / c.h;
+        u = c.qx * rh;
+        v = c.qy * rh;
+    } else {
+        u = T(0);
+        v = T(0);
+    }
+}
+
+// HLL flux across a face with normal from L to R; F = (mass, normal
+// momentum, tangential momentum), hLs/hRs the reconstructed depths.
+template <typename T>
+__device__ __forceinline__ void hll_face(T g, T tol, T hL, T zL, T unL, T utL, T hR, T zR, T unR,
+                                         T utR, T F[3], T& hLs_o, T& hRs_o) {
+    const T zf = zL > zR ? zL : zR;
+    const T dL = (hL + zL) - zf;
+    const T dR = (hR + zR) - zf;
+    const T hLs = dL >= tol ? dL : T(0);
+    const T hRs = dR >= tol ? dR : T(0);
+    hLs_o = hLs;
+    hRs_o = hRs;
+    if (hLs == T(0) && hRs == T(0)) {
+        F[0] = F[1] = F[2] = T(0);
+        return;
+    }
+    const T aL = sqrt(g * hLs), aR = sqrt(g * hRs);
+    T SL, SR;
+    if (hLs > T(0) && hRs > T(0)) {
+        const T us = T(0.5) * (unL + unR) + aL - aR;
+        const T as = T(0.5) * (aL + aR) + T(0.25) * (unL - unR);
+        const T a1 = unL - aL, a2 = us - as;
+        const T b1 = unR + aR, b2 = us + as;
+        SL = a1 < a2 ? a1 : a2;
+        SR = b1 > b2 ? b1 : b2;
+    } else if (hLs == T(0)) {
+        SL = unR - T(2) * aR;
+        SR = unR + aR;
+    } else {
+        SL = unL - aL;
+        SR = unL + T(2) * aL;
+    }
+    const T qnL = hLs * unL, qtL = hLs * utL;
+    const T qnR = hRs * unR, qtR = hRs * utR;
+    const T FL0 = qnL, FL1 = qnL * unL + T(0.5) * g * hLs * hLs, FL2 = qnL * utL;
+    const T FR0 = qnR, FR1 = qnR * unR + T(0.5) * g * hRs * hRs, FR2 = qnR * utR;
+    if (SL >= T(0)) {
+        F[0] = FL0; F[1] = FL1; F[2] = FL2;
+    } else if (SR <= T(0)) {
+        F[0] = FR0; F[1] = FR1; F[2] = FR2;
+    } else {
+        const T inv = T(1) / (SR - SL);
+        F[0] = (SR * FL0 - SL * FR0 + SL * SR * (hRs - hLs)) * inv;
+        F[1] = (SR * FL1 - SL * FR1 + SL * SR * (qnR - qnL)) * inv;
+        F[2] = (SR * FL2 - SL * FR2 + SL * SR * (qtR - qtL)) * inv;
+    }
+}
+
+// New (h, qx, qy) of a cell of size dx x dy: rx = dt/dx, ry = dt/dy.
+template <typename T>
+__device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+                                            const Cell<T>& W, const Cell<T>& E, const Cell<T>& S,
+                                            const Cell<T>& N, bool inlet, T dh, T out[3]) {
+    const T g = P.g, tol = P.tol;
+    T FW[3], FE[3], GS[3], GN[3];
+    T hW_R, hE_L, hS_R, hN_L, dummy;
+    if (C.h == T(0) && W.h == T(0) && E.h == T(0) && S.h == T(0) && N.h == T(0)) {
+        // all five cells dry with zero depth: every reconstructed depth is 0
+        // and every face flux is 0 (what the general path computes)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) FW[k] = FE[k] = GS[k] = GN[k] = T(0);
+        hW_R = hE_L = hS_R = hN_L = T(0);
+    } else {
+        T uC, vC, uW, vW, uE, vE, uS, vS, uN, vN;
+        velocity(C, tol, uC, vC);
+        velocity(W, tol, uW, vW);
+        velocity(E, tol, uE, vE);
+        velocity(S, tol, uS, vS);
+        velocity(N, tol, uN, vN);
+        hll_face(g, tol, W.h, W.z, uW, vW, C.h, C.z, uC, vC, FW, dummy, hW_R);
+        hll_face(g, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hE_L, dummy);
+        hll_face(g, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
+        hll_face(g, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hN_L, dummy);
+    }
+    const T bx = T(0.5) * g * (hW_R * hW_R - hE_L * hE_L);
+    const T by = T(0.5) * g * (hS_R * hS_R - hN_L * hN_L);
+    T h = C.h - rx * (FE[0] - FW[0]) - ry * (GN[0] - GS[0]);
+    T qx = C.qx - rx * ((FE[1] - FW[1]) + bx) - ry * (GN[2] - GS[2]);
+    T qy = C.qy - rx * (FE[2] - FW[2]) - ry * ((GN[1] - GS[1]) + by);
+    if (inlet) h = h + dh;
+    h = h > T(0) ? h : T(0);
+    if (h < tol) {
+        qx = T(0);
+        qy = T(0);
+    } else if (P.nM > T(0)) {
+        const T rh = T(1) / h;
+        const T u = qx * rh, v = qy * rh;
+        const T speed = sqrt(u * u + v * v);
+        const T nM = P.nM;
+        const T D = T(1) + dt * g * nM * nM * speed / (h * cbrt(h));
+        const T rD = T(1) / D;
+        qx = qx * rD;
+        qy = qy * rD;
+    }
+    out[0] = h;
+    out[1] = qx;
+    out[2] = qy;
+}
+
+// CFL bound of an updated cell: min(dx/(|u|+a), dy/(|v|+a)), +inf if dry
+template <typename T>
+__device__ __forceinline__ T cfl_bound(const Phys<T>& P, T h, T qx, T qy) {
+    if (h < P.tol) return T(INFINITY);
+    const T rh = T(1) / h;
+    const T u = fabs(qx * rh), v = fabs(qy * rh);
+    const T a = sqrt(P.g * h);
+    const T rx = P.dxL / (u + a), ry = P.dyL / (v + a);
+    return rx < ry ? rx : ry;
+}
+
+template <typename T>
+struct StepArgs {
+    T* f[2][3];              // h, qx, qy hierarchies of the two state buffers
+    const T* z;              // bed hierarchy
+    const uint32_t* leaves;
+    DevState* st;
+    Phys<T> P;
+    T lx, ly;
+    int L;
+    int bc_ref[4];           // 1: the side reflects (closed or inflow)
+    int inflow_side;         // -1: none
+    int a0, a1;
+};
+
+template <typename T>
+struct CellSrc { const T *h, *qx, *qy, *z; };
+
+template <typename T>
+__device__ __forceinline__ Cell<T> fetch(const CellSrc<T>& a, uint64_t idx) {
+    Cell<T> c;
+    c.h = __ldg(a.h + idx);
+    c.qx = __ldg(a.qx + idx);
+    c.qy = __ldg(a.qy + idx);
+    c.z = __ldg(a.z + idx);
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ Cell<T> ghost(const Cell<T>& c, bool reflect, bool xside) {
+    Cell<T> g = c;
+    if (reflect) {
+        if (xside) g.qx = -g.qx;
+        else g.qy = -g.qy;
+    }
+    return g;
+}
+
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1(StepArgs<T> a) {
+    DevState* st = a.st;
+    if (!st->active) return;
+    const int par = (int)st->cur, nxt = par ^ 1;
+    const uint32_t M = st->M;
+    const T dt = (T)st->dt_use;
+    const T rx0 = dt / a.lx, ry0 = dt / a.ly;   // dt/dx_n = (dt/lx)*2^n exactly
+    const T Qdt = (T)st->Qdt;
+    CellSrc<T> src;
+    src.h = par ? a.f[1][0] : a.f[0][0];
+    src.qx = par ? a.f[1][1] : a.f[0][1];
+    src.qy = par ? a.f[1][2] : a.f[0][2];
+    src.z = a.z;
+    T* const oh = nxt ? a.f[1][0] : a.f[0][0];
+    T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
+    T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
+    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const uint32_t pk = __ldg(a.leaves + k);
+        const int n = (int)(pk >> kLeafShift);
+        const uint32_t code = pk & kCodeMask;
+        const uint32_t i = compact16(code), j = compact16(code >> 1);
+        const uint32_t last = (1u << n) - 1u;
+        const uint64_t base = lvl_off(n);
+        const Cell<T> C = fetch(src, base + code);
+        const Cell<T> W = i > 0 ? fetch(src, base + morton2(i - 1, j)) : ghost(C, a.bc_ref[0], true);
+        const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
+        const Cell<T> S = j > 0 ? fetch(src, base + morton2(i, j - 1)) : ghost(C, a.bc_ref[2], false);
+        const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
+        const T scale = (T)(1u << n);
+        const T rx = rx0 * scale, ry = ry0 * scale;
+        bool inlet = false;
+        T dh = T(0);
+        if (a.inflow_side >= 0) {
+            const int s = a.inflow_side;
+            const bool touch = (s == 0 && i == 0) || (s == 1 && i == last) || (s == 2 && j == 0) ||
+                               (s == 3 && j == last);
+            if (touch) {
+                const int64_t w = 1ll << (a.L - n);
+                const int64_t pos = (s <= 1) ? (int64_t)j : (int64_t)i;
+                int64_t lo = pos * w, hi = lo + w;
+                if (lo < a.a0) lo = a.a0;
+                if (hi > a.a1) hi = a.a1;
+                if (hi > lo) {
+                    inlet = true;
+                    const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
+                    const T inv2n = T(1) / scale;
+                    const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
+                    dh = (Qdt * frac) / (dxn * dyn);
+                }
+            }
+        }
+        T out[3];
+        cell_update(a.P, rx, ry, dt, C, W, E, S, N, inlet, dh, out);
+        oh[base + code] = out[0];
+        oqx[base + code] = out[1];
+        oqy[base + code] = out[2];
+        const T r = cfl_bound(a.P, out[0], out[1], out[2]);
+        const unsigned long long rb = obits((double)r);
+        rmin = rb < rmin ? rb : rmin;
+        if (n == a.L) {
+            const unsigned long long b0 = obits((double)fabs(out[0]));
+            const unsigned long long b1 = obits((double)fabs(out[1]));
+            const unsigned long long b2 = obits((double)fabs(out[2]));
+            mh = b0 > mh ? b0 : mh;
+            mqx = b1 > mqx ? b1 : mqx;
+            mqy = b2 > mqy ? b2 : mqy;
+        }
+        if (!(isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]))) atomicOr(&st->err, kErrNonFinite);
+    }
+    block_atomic_u64<false>(rmin, &st->rmin_bits);
+    block_atomic_u64<true>(mh, &st->max_bits[0]);
+    block_atomic_u64<true>(mqx, &st->max_bits[1]);
+    block_atomic_u64<true>(mqy, &st->max_bits[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Decode-back (Eq. 4 with zero details below leaves, free surface restored
+// on wet coarse leaves), tile-parallel like the traversal.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DecodeArgs {
+    T* f[2][3];
+    const T* z;
+    const uint32_t* Sb;
+    DevState* st;
+    T tol;
+    int L, kt;
+};
+
+template <typename T>
+static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
+    DevState* st = a.st;
+    if (!st->active) return;
+    const int nxt = (int)st->cur ^ 1;
+    __shared__ int s_l0;
+    const uint32_t tile = blockIdx.x;
+    if (threadIdx.x == 0) s_l0 = walk_root(a.Sb, a.L - a.kt, tile);
+    __syncthreads();
+    const TileWalk w = walk_tile(a.Sb, a.L, a.kt, tile, s_l0);
+    unsigned long long mh = 0, mqx = 0, mqy = 0;
+    T* const fh = nxt ? a.f[1][0] : a.f[0][0];
+    T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
+    T* const fqy = nxt ? a.f[1][2] : a.f[0][2];
+    if (w.act && w.l < a.L) {
+        const uint64_t slot = lvl_off(w.l) + (w.m0 >> (2 * (a.L - w.l)));
+        const T hl = fh[slot], qxl = fqx[slot], qyl = fqy[slot];
+        const bool restore = hl >= a.tol;
+        const T eta = restore ? hl + __ldg(a.z + slot) : T(0);
+        const uint64_t fo = lvl_off(a.L) + w.m0;
+        T hf[4];
+        if (restore) {
+            T z0, z1, z2, z3;
+            Vec4<T>::load(a.z + fo, z0, z1, z2, z3);
+            const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
+            hf[0] = d0 > T(0) ? d0 : T(0);
+            hf[1] = d1 > T(0) ? d1 : T(0);
+            hf[2] = d2 > T(0) ? d2 : T(0);
+            hf[3] = d3 > T(0) ? d3 : T(0);
+        } else {
+            hf[0] = hf[1] = hf[2] = hf[3] = hl;
+        }
+        Vec4<T>::store(fh + fo, hf[0], hf[1], hf[2], hf[3]);
+        Vec4<T>::store(fqx + fo, qxl, qxl, qxl, qxl);
+        Vec4<T>::store(fqy + fo, qyl, qyl, qyl, qyl);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned long long b = obits((double)fabs(hf[e]));
+            mh = b > mh ? b : mh;
+        }
+        mqx = obits((double)fabs(qxl));
+        mqy = obits((double)fabs(qyl));
+    }
+    block_atomic_u64<true>(mh, &st->max_bits[0]);
+    block_atomic_u64<true>(mqx, &st->max_bits[1]);
+    block_atomic_u64<true>(mqy, &st->max_bits[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Time advance and next-step scalars (Algorithm 3 lines 8-9)
+// ---------------------------------------------------------------------------
+struct FinishArgs {
+    const double* inflow_t;
+    const double* inflow_Q;
+    int inflow_n;
+    int L;
+    double eps, cfl, dt_max;
+};
+
+__device__ inline double inflow_Q(const FinishArgs& a, double t) {
+    const int n = a.inflow_n;
+    if (n <= 0) return 0.0;
+    if (t <= a.inflow_t[0]) return a.inflow_Q[0];
+    if (t >= a.inflow_t[n - 1]) return a.inflow_Q[n - 1];
+    int k = 0;
+    while (!(t >= a.inflow_t[k] && t < a.inflow_t[k + 1])) k++;
+    const double w = (t - a.inflow_t[k]) / (a.inflow_t[k + 1] - a.inflow_t[k]);
+    return a.inflow_Q[k] + (a.inflow_Q[k + 1] - a.inflow_Q[k]) * w;
+}
+
+// Thresholds, timestep clamp and inflow volume of the step about to run.
+__device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
+    for (int q = 0; q < 3; ++q) {
+        for (int n = 0; n < a.L; ++n) {
+            st->thr[n * 3 + q] = ldexp(a.eps, n - a.L) * st->smax[q];
+            st->thrf[n * 3 + q] = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
+        }
+    }
+    st->active = st->t < st->t_end ? 1u : 0u;
+    double dt_use = st->dt;
+    if (st->t + dt_use > st->t_end) dt_use = st->t_end - st->t;
+    st->dt_use = dt_use;
+    st->Qdt = inflow_Q(a, st->t) * dt_use;
+    st->rmin_bits = kInfBits;
+    st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
+}
+
+// next timestep: CFL * (min CFL bound), capped at dt_max (+inf when dry)
+__device__ inline double dt_from(const FinishArgs& a, double r) {
+    const double dt = a.cfl * r;
+    return dt < a.dt_max ? dt : a.dt_max;
+}
+
+__device__ inline double smax_of(unsigned long long bits) {
+    const double m = from_obits(bits);
+    return 1.0 > m ? 1.0 : m;
+}
+
+static __global__ void k_finish(DevState* st, FinishArgs a) {
+    if (threadIdx.x != 0 || !st->active) return;
+    st->t = st->t + st->dt_use;
+    st->dt = dt_from(a, from_obits(st->rmin_bits));
+    for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
+    if (!isfinite(st->dt) || !isfinite(st->smax[0]) || !isfinite(st->smax[1]) ||
+        !isfinite(st->smax[2]))
+        st->err |= kErrNonFinite;
+    st->step += 1;
+    st->cur ^= 1u;
+    prepare_step(st, a);
+}
+
+// Set t_end (hwfv1_advance) and recompute the step scalars.
+static __global__ void k_set_tend(DevState* st, FinishArgs a, double t_end) {
+    if (threadIdx.x != 0) return;
+    st->t_end = t_end;
+    prepare_step(st, a);
+}
+
+// State from the reductions of the initial (or reloaded) fields:
+// s_max from max_bits[0..2], and, if set_dt, dt from rmin_bits.
+static __global__ void k_init_state(DevState* st, FinishArgs a, int set_dt) {
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
+    if (set_dt) st->dt = dt_from(a, from_obits(st->rmin_bits));
+    prepare_step(st, a);
+}
+
+// z thresholds for the one-off bed encode
+static __global__ void k_z_thresholds(const unsigned long long* zmax_bits, double* thr_d, float* thr_f,
+                               double* smax_z, int L, double eps) {
+    if (threadIdx.x != 0) return;
+    const double s = smax_of(*zmax_bits);
+    *smax_z = s;
+    for (int n = 0; n < L; ++n) {
+        thr_d[n] = ldexp(eps, n - L) * s;
+        thr_f[n] = ldexpf((float)eps, n - L) * (float)s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions over the finest grid (initial state)
+// ---------------------------------------------------------------------------
+template <typename T>
+static __global__ void __launch_bounds__(256) k_maxabs(const T* __restrict__ x, uint64_t n,
+                                                unsigned long long* dst) {
+    unsigned long long m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = obits((double)fabs(x[i]));
+        m = b > m ? b : m;
+    }
+    block_atomic_u64<true>(m, dst);
+}
+
+template <typename T>
+static __global__ void __launch_bounds__(256) k_cfl_finest(const T* __restrict__ h, const T* __restrict__ qx,
+                                                    const T* __restrict__ qy, uint64_t n, Phys<T> P,
+                                                    unsigned long long* dst) {
+    unsigned long long m = kInfBits;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = obits((double)cfl_bound(P, h[i], qx[i], qy[i]));
+        m = b < m ? b : m;
+    }
+    block_atomic_u64<false>(m, dst);
+}
+
+// Reductions into DevState over the finest level of the current buffer
+// (set_fields / load / init).
+static __global__ void k_reset_red(DevState* st) {
+    if (threadIdx.x != 0) return;
+    st->rmin_bits = kInfBits;
+    st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
+}
+
+template <typename T>
+static __global__ void __launch_bounds__(256) k_maxabs_cur(const T* __restrict__ x0, const T* __restrict__ x1,
+                                                    DevState* st, uint64_t n, int q) {
+    const T* x = st->cur ? x1 : x0;
+    unsigned long long m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = obits((double)fabs(x[i]));
+        m = b > m ? b : m;
+    }
+    block_atomic_u64<true>(m, &st->max_bits[q]);
+}
+
+template <typename T>
+static __global__ void __launch_bounds__(256) k_cfl_cur(const T* h0, const T* h1, const T* qx0, const T* qx1,
+                                                 const T* qy0, const T* qy1, DevState* st, uint64_t n,
+                                                 Phys<T> P) {
+    const bool c = st->cur != 0;
+    const T* h = c ? h1 : h0;
+    const T* qx = c ? qx1 : qx0;
+    const T* qy = c ? qy1 : qy0;
+    unsigned long long m = kInfBits;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = obits((double)cfl_bound(P, h[i], qx[i], qy[i]));
+        m = b < m ? b : m;
+    }
+    block_atomic_u64<false>(m, &st->rmin_bits);
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversion: row-major (j*2^L + i, float64) <-> Morton (type T)
+// ---------------------------------------------------------------------------
+template <typename T>
+static __global__ void k_rm_to_morton(const double* __restrict__ src, T* __restrict__ dst, int L) {
+    const uint64_t N = 1ull << (2 * L);
+    for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < N;
+         m += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = compact16((uint32_t)m), j = compact16((uint32_t)(m >> 1));
+        dst[m] = (T)src[((uint64_t)j << L) + i];
+    }
+}
+
+// dst_rm[j*2^L+i] = src[Morton(i,j)]; src chosen by the current buffer when
+// `src2` is given (src = buffer 0, src2 = buffer 1)
+template <typename T>
+static __global__ void k_morton_to_rm(const T* __restrict__ src, const T* __restrict__ src2,
+                               const DevState* st, double* __restrict__ dst, int L) {
+    const T* s = (src2 && st && st->cur) ? src2 : src;
+    const uint64_t N = 1ull << (2 * L);
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(r & ((1ull << L) - 1)), j = (uint32_t)(r >> L);
+        dst[r] = (double)s[morton2(i, j)];
+    }
+}
+
+template <typename T>
+static __global__ void k_copy_level(const T* __restrict__ src, const T* __restrict__ src2,
+                             const DevState* st, double* __restrict__ dst, uint64_t n) {
+    const T* s = (src2 && st && st->cur) ? src2 : src;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)s[i];
+}
+
+// into the current buffer (set_fields / load)
+template <typename T>
+static __global__ void k_rm_to_morton_cur(const double* __restrict__ src, T* dst0, T* dst1,
+                                   const DevState* st, int L) {
+    T* dst = st->cur ? dst1 : dst0;
+    const uint64_t N = 1ull << (2 * L);
+    for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < N;
+         m += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = compact16((uint32_t)m), j = compact16((uint32_t)(m >> 1));
+        dst[m] = (T)src[((uint64_t)j << L) + i];
+    }
+}
+
+}  // namespace hwfv1

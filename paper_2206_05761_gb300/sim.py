@@ -1,0 +1,120 @@
+"""Convenience wrapper over the C ABI for tests and benchmarks: owns the
+torch CUDA tensors handed to the library and converts results to numpy.
+Every computation happens in libhwfv1.so."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import hwfv1 as H
+
+
+class Simulation:
+    def __init__(self, p, fields, precision=64, stream=None, device="cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("HWFV1 needs a CUDA device; there is no CPU fallback")
+        self.p = p
+        self.L = p["L"]
+        self.N = 1 << (2 * self.L)
+        self.dev = torch.device(device)
+        self.stream = stream
+        self.spec = H.make_problem(p, precision)
+        dt = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1),
+                                       device=self.dev)
+        z, h, qx, qy = (dt(fields[k]) for k in ("z", "h", "qx", "qy"))
+        self.hd = H.hwfv1_init(self.spec, z, h, qx, qy, stream)
+        self._bufs = [torch.empty(self.N, dtype=torch.float64, device=self.dev) for _ in range(3)]
+
+    # -- the five phases of a step and the loop ---------------------------
+    def encode(self):
+        H.hwfv1_encode(self.hd)
+
+    def flag(self):
+        H.hwfv1_flag(self.hd)
+
+    def traverse(self, want_count=False):
+        return H.hwfv1_traverse(self.hd, want_count)
+
+    def fv1(self):
+        H.hwfv1_step(self.hd)
+
+    def decode(self):
+        H.hwfv1_decode(self.hd)
+
+    def step(self):
+        self.encode()
+        self.flag()
+        self.traverse()
+        self.fv1()
+        self.decode()
+
+    def advance(self, t_end=float("inf"), max_steps=1):
+        H.hwfv1_advance(self.hd, t_end, max_steps)
+
+    # -- results ------------------------------------------------------------
+    def fields(self):
+        h, qx, qy = self._bufs
+        H.hwfv1_get_fields(self.hd, h, qx, qy)
+        s = 1 << self.L
+        return {k: v.cpu().numpy().reshape(s, s).copy() for k, v in zip(("h", "qx", "qy"), (h, qx, qy))}
+
+    def set_fields(self, f):
+        t = [torch.as_tensor(np.ascontiguousarray(f[k], dtype=np.float64).reshape(-1), device=self.dev)
+             for k in ("h", "qx", "qy")]
+        H.hwfv1_set_fields(self.hd, *t)
+
+    def leaves(self):
+        n = H.hwfv1_get_leaves(self.hd)
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=self.dev)
+        H.hwfv1_get_leaves(self.hd, out)
+        return out[:n].cpu().numpy().view(np.uint32).copy()
+
+    def flags(self, which):
+        w = H.bits_words(self.L)
+        out = torch.zeros(max(w, 1), dtype=torch.int32, device=self.dev)
+        H.hwfv1_get_flags(self.hd, which, out)
+        return out[:w].cpu().numpy().view(np.uint32).copy()
+
+    def level(self, field, n):
+        out = torch.empty(1 << (2 * n), dtype=torch.float64, device=self.dev)
+        H.hwfv1_get_level(self.hd, field, n, out)
+        return out.cpu().numpy()
+
+    def time(self):
+        return H.hwfv1_get_time(self.hd)
+
+    def set_time(self, t, dt):
+        H.hwfv1_set_time(self.hd, t, dt)
+
+    def stats(self):
+        return H.hwfv1_get_stats(self.hd)
+
+    def save(self):
+        return H.hwfv1_save(self.hd)
+
+    def load(self, blob):
+        H.hwfv1_load(self.hd, blob)
+
+    def close(self):
+        if self.hd is not None:
+            H.hwfv1_destroy(self.hd)
+            self.hd = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_bits(words, L):
+    """Significance bits (get_flags layout) -> per-level uint8 arrays in
+    Morton order."""
+    out = []
+    for n in range(L):
+        w0 = H.word_off(n)
+        cnt = 1 << (2 * n)
+        nw = max(1, cnt // 32)
+        bits = np.unpackbits(words[w0:w0 + nw].astype("<u4").view(np.uint8), bitorder="little")
+        out.append(bits[:cnt].astype(np.uint8))
+    return out

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs.  In float64 the significance flags, leaf lists,
+encoded coefficients, fields and timesteps must be bit-identical when there
+is no friction; with Manning friction (cbrt is not correctly rounded on
+either side) fields are held to 1e-12 relative."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+from _util import level_slice, rm_to_morton
+
+pytestmark = pytest.mark.gpu
+
+RTOL_FRICTION = 1e-12
+
+
+def _sim(p, f, precision=64):
+    from paper_2206_05761_gb300.sim import Simulation
+    return Simulation(p, f, precision)
+
+
+def _unpack(words, L):
+    from paper_2206_05761_gb300.sim import unpack_bits
+    return unpack_bits(words, L)
+
+
+def _compare_fields(sim, ref, exact=True):
+    g = sim.fields()
+    for k in ("h", "qx", "qy"):
+        o = getattr(ref, k)
+        if exact:
+            assert np.array_equal(g[k], o), "field %s: max diff %g" % (k, np.abs(g[k] - o).max())
+        else:
+            scale = max(np.abs(o).max(), 1e-300)
+            assert np.abs(g[k] - o).max() <= RTOL_FRICTION * scale, k
+
+
+def one_step_parity(p, f, exact=True, pre_steps=0):
+    """Run pre_steps on both sides (state compared after them), then one
+    step phase by phase, comparing every intermediate."""
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    L = p["L"]
+    t, dt, _ = sim.time()
+    assert dt == ref.dt and t == ref.t
+    for _ in range(pre_steps):
+        sim.step()
+        ref.step()
+    if pre_steps:
+        _compare_fields(sim, ref, exact)
+        if not exact:      # continue from an identical state
+            sim.set_fields({"h": ref.h, "qx": ref.qx, "qy": ref.qy})
+        t, dt, _ = sim.time()
+        if not exact:
+            sim.set_time(ref.t, ref.dt)
+        else:
+            assert t == ref.t and dt == ref.dt
+    res = ref.step(want=("T", "S", "leaves", "hier"))
+    sim.encode()
+    N = 1 << (2 * L)
+    P = (N - 1) // 3
+    for q in range(3):
+        hier = res["hier"][q]
+        for n in range(L):
+            got = sim.level(q, n)
+            exp = rm_to_morton(hier[level_slice(n)], n)
+            assert np.array_equal(got, exp), "field %d level %d" % (q, n)
+    sim.flag()
+    T = _unpack(sim.flags(0), L)
+    S = _unpack(sim.flags(1), L)
+    for n in range(L):
+        assert np.array_equal(T[n], rm_to_morton(res["T"][level_slice(n)], n)), "T level %d" % n
+        assert np.array_equal(S[n], rm_to_morton(res["S"][level_slice(n)], n)), "S level %d" % n
+    assert P == len(res["T"])
+    M = sim.traverse(want_count=True)
+    assert M == res["num_leaves"]
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    sim.fv1()
+    sim.decode()
+    _compare_fields(sim, ref, exact)
+    t, dt, steps = sim.time()
+    assert t == ref.t
+    if exact:
+        assert dt == ref.dt
+    else:
+        assert abs(dt - ref.dt) <= RTOL_FRICTION * ref.dt
+    sim.close()
+    return res
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 6])
+def test_circular_dam_break_small_levels(L):
+    p, f = synth.circular_dam_break(L=L, eps=1e-3)
+    one_step_parity(p, f)
+
+
+def test_circular_dam_break_L6_after_steps():
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    one_step_parity(p, f, pre_steps=20)
+
+
+@pytest.mark.parametrize("seed", [2, 11])
+def test_bumpy_dam_break_wet_dry(seed):
+    p, f = synth.bumpy_dam_break(L=7, eps=1e-3, seed=seed)
+    one_step_parity(p, f, pre_steps=5)
+
+
+def test_lake_at_rest_dry_humps():
+    p, f = synth.lake_at_rest(L=7, eps=1e-3, wet=False)
+    one_step_parity(p, f, pre_steps=3)
+
+
+def test_inflow_basin():
+    p, f = synth.inflow_basin(L=6, eps=1e-3, q=0.01)
+    one_step_parity(p, f, pre_steps=4)
+
+
+def test_non_square_domain_open_boundaries():
+    p, f = synth.pseudo_2d_dam_break(L=7, eps=1e-3)
+    one_step_parity(p, f, pre_steps=3)
+
+
+def test_eps_zero_every_leaf_finest():
+    p, f = synth.circular_dam_break(L=5, eps=0.0)
+    res = one_step_parity(p, f)
+    assert res["num_leaves"] == 1 << 10
+
+
+def test_huge_eps_single_root_leaf():
+    p, f = synth.lake_at_rest(L=5, eps=1e300)
+    f["z"][:] = 0.0
+    f["h"][:] = 1.0
+    res = one_step_parity(p, f)
+    assert res["num_leaves"] == 1
+
+
+@pytest.mark.parametrize("predict,close", [(True, False), (False, True), (False, False)])
+def test_regularisation_variants(predict, close):
+    p, f = synth.bumpy_dam_break(L=6, eps=1e-3)
+    p["reg_predict"], p["reg_close"] = predict, close
+    one_step_parity(p, f, pre_steps=2)
+
+
+def test_all_dry_terrain():
+    p, f = synth.terrain_flood(L=7)
+    p["bc"] = ("closed",) * 4
+    p["inflow"] = None
+    one_step_parity(p, f, pre_steps=2)
+
+
+def test_terrain_flood_with_friction_and_inflow():
+    p, f = synth.terrain_flood(L=7)
+    one_step_parity(p, f, exact=False, pre_steps=30)
+
+
+def test_uniform_friction_flow():
+    p, f = synth.uniform_flow(L=4, manning_n=0.03)
+    one_step_parity(p, f, exact=False, pre_steps=5)
+
+
+def test_trajectory_circular_dam_break_100_steps():
+    # configs: circular dam-break, 64 x 64, eps 1e-3, 100 steps; the graph
+    # replay path (hwfv1_advance) against the oracle's time loop
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    for chunk in range(10):
+        sim.advance(max_steps=10)
+        for _ in range(9):
+            ref.step()
+        res = ref.step(want=("leaves",))
+        assert np.array_equal(sim.leaves(), res["leaves"]), "chunk %d" % chunk
+        _compare_fields(sim, ref)
+        t, dt, steps = sim.time()
+        assert t == ref.t and dt == ref.dt and steps == ref.steps
+    sim.close()
+
+
+def test_advance_stops_at_t_end():
+    p, f = synth.circular_dam_break(L=5, eps=1e-3)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    t_end = 0.02
+    sim.advance(t_end=t_end, max_steps=1000)
+    n = ref.run(t_end=t_end)
+    t, dt, steps = sim.time()
+    assert steps == n and t == ref.t == t_end
+    _compare_fields(sim, ref)
+    sim.close()
+
+
+def test_bumpy_dam_break_L10_one_step():
+    # configs: bumpy dam-break 1024 x 1024 (L = 10), eps 1e-3 and 1e-4
+    for eps in (1e-3, 1e-4):
+        p, f = synth.bumpy_dam_break(L=10, eps=eps)
+        one_step_parity(p, f, pre_steps=2)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    p, f = synth.bumpy_dam_break(L=6, eps=1e-3)
+    a = _sim(p, f)
+    a.advance(max_steps=5)
+    blob = a.save()
+    a.advance(max_steps=7)
+    ga = a.fields()
+    ta = a.time()
+    b = _sim(p, f)
+    b.load(blob)
+    assert b.time()[2] == 5
+    b.advance(max_steps=7)
+    gb = b.fields()
+    assert b.time() == ta
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k])
+    a.close()
+    b.close()
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2206_05761_gb300.hwfv1 import Hwfv1Error
+    p, f = synth.circular_dam_break(L=4, eps=1e-3)
+    f["h"][3, 3] = np.nan
+    sim = _sim(p, f)
+    sim.step()
+    with pytest.raises(Hwfv1Error) as e:
+        sim.time()
+    assert e.value.status == 4
+    sim.close()
+
+
+def test_float32_path_errors_stated():
+    # 32-bit arithmetic against the float64 oracle: errors per field after
+    # 20 steps of the circular dam-break are reported and stay small
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    sim = _sim(p, f, precision=32)
+    ref = oracle.State(p, f)
+    t_end = 0.02
+    sim.advance(t_end=t_end, max_steps=10000)
+    ref.run(t_end=t_end)
+    g = sim.fields()
+    errs = {k: float(np.abs(g[k] - getattr(ref, k)).max()) for k in ("h", "qx", "qy")}
+    print("float32 vs float64 oracle at t=%g: max abs error %s" % (t_end, errs))
+    assert errs["h"] < 1e-4 and errs["qx"] < 1e-4 and errs["qy"] < 1e-4
+    sim.close()
