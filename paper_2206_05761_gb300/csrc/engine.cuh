@@ -1,6 +1,7 @@
 // engine.cuh -- host side of one HWFV1 simulation: device buffers, the
 // launch sequence of a timestep, CUDA-graph replay, checkpoints.
 #pragma once
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -64,7 +65,14 @@ class EngineT final : public Engine {
             cudaMemcpyAsync(iq_d_, iq_.data(), iq_.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
         }
         cudaMemsetAsync(bits_, 0, (size_t)words_ * 6 * sizeof(uint32_t), stream_);
-        cudaMemsetAsync(st_, 0, sizeof(DevState), stream_);
+        {   // t = 0, no end time until hwfv1_advance sets one, buffer 0 current
+            DevState s0;
+            std::memset(&s0, 0, sizeof s0);
+            s0.t_end = HUGE_VAL;
+            s0.active = 1u;
+            cudaMemcpyAsync(st_, &s0, sizeof s0, cudaMemcpyHostToDevice, stream_);
+            cudaStreamSynchronize(stream_);
+        }
         // finest fields into the Morton hierarchy
         const int g = grid_for(N_);
         k_rm_to_morton<T><<<g, 256, 0, stream_>>>(z, z_ + lvl_off(L_), L_);
@@ -77,7 +85,7 @@ class EngineT final : public Engine {
         double* thr_zd = reinterpret_cast<double*>(zaux_ + 16);     // up to 14 doubles
         float* thr_zf = reinterpret_cast<float*>(zaux_ + 16 + 8 * kMaxL);
         k_maxabs<T><<<g, 256, 0, stream_>>>(z_ + lvl_off(L_), N_, zmax);
-        k_z_thresholds<<<1, 32, 0, stream_>>>(zmax, thr_zd, thr_zf, smax_z, L_, spec_.eps);
+        k_z_thresholds<<<1, 32, 0, stream_>>>(zmax, thr_zd, thr_zf, smax_z, L_, spec_.eps, st_);
         {
             EncodeArgs<T, 1> a;
             a.f[0][0] = a.f[1][0] = z_;

@@ -701,16 +701,20 @@ static __global__ void k_set_tend(DevState* st, FinishArgs a, double t_end) {
 static __global__ void k_init_state(DevState* st, FinishArgs a, int set_dt) {
     if (threadIdx.x != 0) return;
     for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
+    // a NaN or inf anywhere in the fields shows up in its maximum
+    for (int q = 0; q < 3; ++q)
+        if (!isfinite(st->smax[q])) st->err |= kErrNonFinite;
     if (set_dt) st->dt = dt_from(a, from_obits(st->rmin_bits));
     prepare_step(st, a);
 }
 
 // z thresholds for the one-off bed encode
 static __global__ void k_z_thresholds(const unsigned long long* zmax_bits, double* thr_d, float* thr_f,
-                               double* smax_z, int L, double eps) {
+                               double* smax_z, int L, double eps, DevState* st) {
     if (threadIdx.x != 0) return;
     const double s = smax_of(*zmax_bits);
     *smax_z = s;
+    if (!isfinite(s)) st->err |= kErrNonFinite;
     for (int n = 0; n < L; ++n) {
         thr_d[n] = ldexp(eps, n - L) * s;
         thr_f[n] = ldexpf((float)eps, n - L) * (float)s;

@@ -117,13 +117,15 @@ def spectral_dem(n, seed, relief):
 
 def terrain_flood(L=12, eps=1e-3, seed=3, side_m=10_000.0, relief=50.0, width=60.0,
                   depth=4.0, tilt=1e-3, q_peak=500.0, t_peak=1800.0, t_end=3600.0,
-                  manning_n=0.03, amplitude=None, wavelength=None):
+                  manning_n=0.03, amplitude=None, wavelength=None, fill=0.0, fill_q=0.0):
     """Synthetic terrain flood: a seeded 1/f^2 DEM of the given relief over a
     square of side `side_m`, tilted down W->E by `tilt`, with a channel of the
     given width and depth carved along a sinusoidal W->E centreline.  The
     domain starts dry; a triangular hydrograph (0 -> q_peak at t_peak -> 0 at
     t_end, m^3/s) enters through the channel inlet on the west side, the
-    other sides are closed walls; Manning friction n."""
+    other sides are closed walls; Manning friction n.  With fill > 0 the
+    channel instead starts `fill` metres deep with discharge fill_q (m^2/s,
+    towards +x) along its whole length: a wet state for one-step checks."""
     n = 1 << L
     amplitude = 0.1 * side_m if amplitude is None else amplitude
     wavelength = 0.5 * side_m if wavelength is None else wavelength
@@ -140,6 +142,11 @@ def terrain_flood(L=12, eps=1e-3, seed=3, side_m=10_000.0, relief=50.0, width=60
     inflow = dict(a0=a0, a1=a1, t=[0.0, t_peak, t_end], Q=[0.0, q_peak, 0.0])
     p = problem(L, lx=side_m, ly=side_m, eps=eps, manning_n=manning_n,
                 bc=("inflow", "closed", "closed", "closed"), inflow=inflow)
+    if fill > 0.0:
+        inside = np.abs(y - yc) < 0.5 * width
+        h = np.where(inside, fill, 0.0)
+        return p, dict(h=np.ascontiguousarray(h), qx=np.ascontiguousarray(np.where(inside, fill_q, 0.0)),
+                       qy=np.zeros_like(h), z=np.ascontiguousarray(z))
     eta = np.full_like(z, -1e9)          # dry start
     return p, _fields(p, eta, z)
 

@@ -183,7 +183,7 @@ def test_advance_stops_at_t_end():
     sim = _sim(p, f)
     ref = oracle.State(p, f)
     t_end = 0.02
-    sim.advance(t_end=t_end, max_steps=1000)
+    sim.advance(t_end=t_end, max_steps=200)
     n = ref.run(t_end=t_end)
     t, dt, steps = sim.time()
     assert steps == n and t == ref.t == t_end
@@ -218,11 +218,29 @@ def test_checkpoint_resume_is_bit_identical():
     b.close()
 
 
-def test_nonfinite_input_is_reported():
+@pytest.mark.parametrize("field", ["h", "qx", "z"])
+def test_nonfinite_input_is_reported(field):
+    # a NaN planted in the initial fields (on the host) is latched on the
+    # device and reported by the next synchronising call
     from paper_2206_05761_gb300.hwfv1 import Hwfv1Error
     p, f = synth.circular_dam_break(L=4, eps=1e-3)
-    f["h"][3, 3] = np.nan
+    f[field][3, 3] = np.nan
     sim = _sim(p, f)
+    with pytest.raises(Hwfv1Error) as e:
+        sim.time()
+    assert e.value.status == 4
+    sim.close()
+
+
+def test_nonfinite_discharge_during_run_is_reported():
+    # a state that turns non-finite during a step (huge discharge overflows
+    # the momentum flux) is caught by the step's own check
+    from paper_2206_05761_gb300.hwfv1 import Hwfv1Error
+    p, f = synth.circular_dam_break(L=4, eps=1e-3)
+    sim = _sim(p, f)
+    g = {k: f[k].copy() for k in ("h", "qx", "qy")}
+    g["qx"][3, 3] = 1e300
+    sim.set_fields(g)
     sim.step()
     with pytest.raises(Hwfv1Error) as e:
         sim.time()
@@ -237,10 +255,30 @@ def test_float32_path_errors_stated():
     sim = _sim(p, f, precision=32)
     ref = oracle.State(p, f)
     t_end = 0.02
-    sim.advance(t_end=t_end, max_steps=10000)
+    sim.advance(t_end=t_end, max_steps=200)
     ref.run(t_end=t_end)
     g = sim.fields()
     errs = {k: float(np.abs(g[k] - getattr(ref, k)).max()) for k in ("h", "qx", "qy")}
     print("float32 vs float64 oracle at t=%g: max abs error %s" % (t_end, errs))
     assert errs["h"] < 1e-4 and errs["qx"] < 1e-4 and errs["qy"] < 1e-4
+    sim.close()
+
+
+def test_full_size_terrain_flood_L12_bench_launch_path():
+    # the bench workload at full size (4096 x 4096, 10 km, eps 1e-3, Manning
+    # 0.03, inflow) with its channel flowing, advanced one step through the
+    # same graph-replay path bench.py times, against one oracle step
+    p, f = synth.terrain_flood(L=12, fill=2.0, fill_q=1.0)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    t, dt, _ = sim.time()
+    assert dt == ref.dt
+    sim.advance(max_steps=1)
+    res = ref.step(want=("leaves",))
+    lv = sim.leaves()
+    assert len(lv) == res["num_leaves"] and np.array_equal(lv, res["leaves"])
+    _compare_fields(sim, ref, exact=False)
+    t, dt, steps = sim.time()
+    assert steps == 1 and t == ref.t
+    assert abs(dt - ref.dt) <= RTOL_FRICTION * ref.dt
     sim.close()
