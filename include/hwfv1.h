@@ -189,6 +189,32 @@ const char* hwfv1_last_error(hwfv1_handle* hd);
 /* Free all device memory of the handle. */
 void hwfv1_destroy(hwfv1_handle* hd);
 
+/* Leaf list from a regularised significance bit array, for callers that
+ * cannot allocate device memory (a host framework whose pool allocator owns
+ * the device memory budget, a fixed-footprint deployment, a latency-bound
+ * loop that cannot take cudaMalloc's implicit synchronisation).  The paper
+ * has no counterpart: it is the traversal and compaction of hwfv1_traverse
+ * with its per-tile scratch held in a fixed 128 KiB __device__ array inside
+ * the library instead of handle-owned buffers.
+ *   sig_bits    device, levels 0..L-1 in the layout of hwfv1_get_flags
+ *               (which = 1), at least w(L) words; read only
+ *   L           1..12 (the scratch is sized for L <= 12; larger L returns
+ *               HWFV1_ERR_INVALID_SPEC)
+ *   leaves      device output, `cap` entries, packed as in hwfv1_get_leaves;
+ *               leaves past cap are not written
+ *   num_leaves  device output, one uint32: the number of leaves (may exceed
+ *               cap, so the caller can tell the list was cut)
+ *   stream      cudaStream_t the three kernels run on (asynchronous)
+ * No call allocates memory.  The first call on each device looks up the
+ * scratch array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the scratch, so calls
+ * that overlap on the GPU (different streams or devices' contexts running
+ * concurrently on one device) race; serialise them.  Every scratch word a
+ * call reads is written by that call first, so no clearing is needed
+ * between calls. */
+hwfv1_status hwfv1_traverse_noalloc(const uint32_t* sig_bits, int32_t L, uint32_t* leaves,
+                                    int64_t cap, uint32_t* num_leaves, void* stream);
+
 /* Library version, for the loader's sanity check. */
 int32_t hwfv1_version(void);
 

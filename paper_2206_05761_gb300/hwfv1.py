@@ -79,6 +79,7 @@ def lib():
             L.hwfv1_load.argtypes = [_H, C.c_void_p, C.c_size_t]
             L.hwfv1_last_error.argtypes = [_H]
             L.hwfv1_last_error.restype = C.c_char_p
+            L.hwfv1_traverse_noalloc.argtypes = [_dp, C.c_int32, _dp, C.c_int64, _dp, C.c_void_p]
             L.hwfv1_destroy.argtypes = [_H]
             L.hwfv1_destroy.restype = None
             _lib = L
@@ -90,7 +91,7 @@ def exported_symbols():
             "hwfv1_decode", "hwfv1_advance", "hwfv1_get_fields", "hwfv1_set_fields",
             "hwfv1_get_leaves", "hwfv1_get_flags", "hwfv1_get_level", "hwfv1_get_time",
             "hwfv1_set_time", "hwfv1_get_stats", "hwfv1_save", "hwfv1_load",
-            "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version"]
+            "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version", "hwfv1_traverse_noalloc"]
 
 
 def _check(st, what, hd=None):
@@ -228,6 +229,16 @@ def hwfv1_save(hd):
 def hwfv1_load(hd, data):
     buf = C.create_string_buffer(data, len(data))
     _check(lib().hwfv1_load(hd, buf, len(data)), "hwfv1_load", hd)
+
+
+def hwfv1_traverse_noalloc(sig_bits, L, leaves, num_leaves, stream=None):
+    """Leaf list of a significance bit array with no device allocation:
+    sig_bits (CUDA int32/uint32, get_flags layout), leaves (CUDA
+    int32/uint32 output), num_leaves (CUDA int32/uint32, one element)."""
+    sp = stream.cuda_stream if stream is not None else None
+    st = lib().hwfv1_traverse_noalloc(_ptr(sig_bits), int(L), _ptr(leaves), leaves.numel(),
+                                      _ptr(num_leaves), sp)
+    _check(st, "hwfv1_traverse_noalloc")
 
 
 def hwfv1_last_error(hd):
