@@ -71,6 +71,15 @@ __host__ __device__ inline uint32_t expand4x8(uint32_t x) {
     return x * 0xFu;
 }
 
+// ordered bits of |x| (sign cleared with an integer op)
+__device__ __forceinline__ unsigned long long abs_obits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long abs_obits(float x) {
+    // |x| widened to double is exact; its bits order like the value
+    return (unsigned long long)__double_as_longlong((double)__int_as_float(__float_as_int(x) & 0x7FFFFFFF));
+}
+
 // ordered bits of a non-negative double (min/max by integer atomics)
 __device__ __forceinline__ unsigned long long obits(double x) {
     return (unsigned long long)__double_as_longlong(x);
@@ -118,6 +127,37 @@ __device__ __forceinline__ void block_atomic_u64(unsigned long long v, unsigned 
     }
 }
 
+// Block-wide max of three uint64 values, then one atomicMax each into
+// dst[0..2].  Every thread of the block must call it.
+__device__ __forceinline__ void block_max3_u64(unsigned long long a, unsigned long long b,
+                                               unsigned long long c, unsigned long long* dst) {
+    __shared__ unsigned long long red3[3][32];
+    a = warp_max_u64(a);
+    b = warp_max_u64(b);
+    c = warp_max_u64(c);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red3[0][warp] = a;
+        red3[1][warp] = b;
+        red3[2][warp] = c;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = lane < nw ? red3[0][lane] : 0ull;
+        b = lane < nw ? red3[1][lane] : 0ull;
+        c = lane < nw ? red3[2][lane] : 0ull;
+        a = warp_max_u64(a);
+        b = warp_max_u64(b);
+        c = warp_max_u64(c);
+        if (lane == 0) {
+            if (a) atomicMax(dst, a);
+            if (b) atomicMax(dst + 1, b);
+            if (c) atomicMax(dst + 2, c);
+        }
+    }
+}
+
 // Exclusive block scan of one uint32 per thread (blockDim <= 1024).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
     __shared__ uint32_t ws[32];
@@ -160,10 +200,33 @@ struct DevState {
     uint32_t active;                  // t < t_end
     uint32_t cur;                     // which state buffer holds the state
     uint32_t err;                     // latched device error bits
+    unsigned long long ticket;        // running tile ticket of the traversal
+    uint32_t nwet;                    // leaves queued for the full FV1 update
+    uint32_t pad0;
+    double rx0, ry0;                  // dt_use/lx, dt_use/ly (dt/dx_n = rx0 * 2^n)
+    float rx0f, ry0f;                 // same, float arithmetic
     double thr[kMaxL * 3];            // eps*2^(n-L)*s_max,q for h, qx, qy
     float thrf[kMaxL * 3];            // same, float arithmetic (32-bit path)
 };
 
-enum : uint32_t { kErrNonFinite = 1u };
+enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };
+
+// a double that is +0 or -0 (integer test, no FP64 instruction)
+__device__ __forceinline__ bool is_zero(double x) {
+    return (__double_as_longlong(x) << 1) == 0;
+}
+__device__ __forceinline__ bool is_zero(float x) { return (__float_as_int(x) << 1) == 0; }
+
+// x >= y decided on the bit patterns.  Equal to the IEEE comparison for
+// every x (negative, NaN and inf included) when y > 0, and when y == +0 for
+// every x except -0 (callers use it with y > 0, or with x never -0).
+__device__ __forceinline__ bool ge_nonneg(double x, double y) {
+    const long long bx = __double_as_longlong(x);
+    return bx >= __double_as_longlong(y) && bx <= 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool ge_nonneg(float x, float y) {
+    const int bx = __float_as_int(x);
+    return bx >= __float_as_int(y) && bx <= 0x7F800000;
+}
 
 }  // namespace hwfv1

@@ -54,8 +54,9 @@ class EngineT final : public Engine {
         Sz_ = bits_ + 4 * words_;
         Sb_ = bits_ + 5 * words_;
         if (!alloc(&leaves_, N_ * sizeof(uint32_t))) return oom();
-        if (!alloc(&counts_, (size_t)ntiles_ * 2 * sizeof(uint32_t))) return oom();
-        offs_ = counts_ + ntiles_;
+        if (!alloc(&wet_, N_ * sizeof(uint32_t))) return oom();
+        if (!alloc(&status_, (size_t)ntiles_ * sizeof(unsigned long long))) return oom();
+        cudaMemsetAsync(status_, 0, (size_t)ntiles_ * sizeof(unsigned long long), stream_);
         if (!alloc(&st_, sizeof(DevState))) return oom();
         if (!alloc(&zaux_, 256)) return oom();
         if (!it_.empty()) {
@@ -131,7 +132,7 @@ class EngineT final : public Engine {
 
     hwfv1_status advance(double t_end, int64_t max_steps) override {
         if (max_steps < 0) return fail(HWFV1_ERR_INVALID_SPEC, "max_steps < 0");
-        k_set_tend<<<1, 32, 0, stream_>>>(st_, fin_args(), t_end);
+        k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), t_end);
         if (max_steps == 0) return check("advance");
         const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
         if (use_graph && !exec_) {
@@ -218,6 +219,7 @@ class EngineT final : public Engine {
         if (dt) *dt = s.dt;
         if (step) *step = s.step;
         if (s.err & kErrNonFinite) return fail(HWFV1_ERR_NONFINITE, "non-finite value in the state");
+        if (s.err & kErrTimeout) return fail(HWFV1_ERR_TIMEOUT, "a bounded device wait ran out");
         return HWFV1_OK;
     }
 
@@ -227,7 +229,7 @@ class EngineT final : public Engine {
         s.t = t;
         s.dt = dt;
         cudaMemcpyAsync(st_, &s, sizeof s, cudaMemcpyHostToDevice, stream_);
-        k_set_tend<<<1, 32, 0, stream_>>>(st_, fin_args(), s.t_end);
+        k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), s.t_end);
         return check("set_time", true);
     }
 
@@ -319,9 +321,7 @@ class EngineT final : public Engine {
         k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
     }
     void launch_traverse() {
-        k_trav_count<<<ntiles_, 256, 0, stream_>>>(Sb_, counts_, L_, kt_, st_);
-        k_scan_tiles<<<1, 1024, 0, stream_>>>(counts_, offs_, ntiles_, st_);
-        k_trav_write<<<ntiles_, 256, 0, stream_>>>(Sb_, offs_, leaves_, L_, kt_, st_);
+        k_traverse<<<ntiles_, 256, 0, stream_>>>(Sb_, status_, leaves_, L_, kt_, st_);
     }
     StepArgs<T> step_args() const {
         StepArgs<T> a;
@@ -329,6 +329,7 @@ class EngineT final : public Engine {
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.z = z_;
         a.leaves = leaves_;
+        a.wet = wet_;
         a.st = st_;
         a.P = phys();
         a.lx = (T)spec_.lx;
@@ -355,7 +356,9 @@ class EngineT final : public Engine {
         return P;
     }
     void launch_fv1() {
-        k_fv1<T><<<grid_for(N_), 256, 0, stream_>>>(step_args());
+        const StepArgs<T> a = step_args();
+        k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+        k_fv1_wet<T><<<grid_for(N_), 256, 0, stream_>>>(a);
     }
     void launch_decode() {
         DecodeArgs<T> a;
@@ -368,7 +371,7 @@ class EngineT final : public Engine {
         a.L = L_;
         a.kt = kt_;
         k_decode<T><<<ntiles_, 256, 0, stream_>>>(a);
-        k_finish<<<1, 32, 0, stream_>>>(st_, fin_args());
+        k_finish<<<1, 64, 0, stream_>>>(st_, fin_args());
     }
     void launch_step_all() {
         launch_encode();
@@ -386,6 +389,8 @@ class EngineT final : public Engine {
         a.eps = spec_.eps;
         a.cfl = spec_.cfl;
         a.dt_max = spec_.dt_max;
+        a.lx = spec_.lx;
+        a.ly = spec_.ly;
         return a;
     }
     // s_max (and dt when set_dt) from the finest fields of the current buffer
@@ -401,7 +406,7 @@ class EngineT final : public Engine {
                                                   f_[0][2] + lvl_off(L_), f_[1][2] + lvl_off(L_), st_,
                                                   N_, phys());
         }
-        k_init_state<<<1, 32, 0, stream_>>>(st_, fin_args(), set_dt);
+        k_init_state<<<1, 64, 0, stream_>>>(st_, fin_args(), set_dt);
     }
 
     hwfv1_status read_state(DevState* s) {
@@ -446,7 +451,9 @@ class EngineT final : public Engine {
     T* z_ = nullptr;
     uint32_t *bits_ = nullptr, *Tb_ = nullptr, *Cb_ = nullptr, *Tz_ = nullptr, *Cz_ = nullptr,
              *Sz_ = nullptr, *Sb_ = nullptr;
-    uint32_t *leaves_ = nullptr, *counts_ = nullptr, *offs_ = nullptr;
+    uint32_t* leaves_ = nullptr;
+    uint32_t* wet_ = nullptr;
+    unsigned long long* status_ = nullptr;
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;

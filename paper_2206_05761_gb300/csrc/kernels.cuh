@@ -37,6 +37,14 @@ template <> struct Vec4<float> {
     }
 };
 
+struct Vec4u {
+    // leaves pos..pos+3 = (L << 28) | (m0 + e); pos need not be aligned
+    static __device__ __forceinline__ void store(uint32_t* p, uint32_t tag_m0, uint32_t) {
+#pragma unroll
+        for (uint32_t e = 0; e < 4u; ++e) p[e] = tag_m0 + e;
+    }
+};
+
 template <typename T> __device__ __forceinline__ bool same4(T a, T b, T c, T d);
 template <> __device__ __forceinline__ bool same4<double>(double a, double b, double c, double d) {
     const long long x = __double_as_longlong(a);
@@ -49,6 +57,12 @@ template <> __device__ __forceinline__ bool same4<float>(float a, float b, float
     return x == __float_as_int(b) && x == __float_as_int(c) && x == __float_as_int(d) &&
            ((x >> 23) & 0xFF) < 0xFD;
 }
+
+// |x| by clearing the sign bit (no FP64 instruction)
+__device__ __forceinline__ double absval(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ float absval(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
 
 // Haar parent (Eq. 3a) and the largest detail magnitude (Eq. 3b-3d) of four
 // children [0]=(2i,2j) [1]=(2i+1,2j) [2]=(2i,2j+1) [3]=(2i+1,2j+1).
@@ -64,7 +78,7 @@ __device__ __forceinline__ void haar4(T c0, T c1, T c2, T c3, T& s, T& dmax) {
     }
     const T a = c0 + c2, b = c1 + c3, d = c0 - c2, e = c1 - c3;
     s = T(0.25) * (a + b);
-    const T da = fabs(d + e), db = fabs(a - b), dg = fabs(d - e);
+    const T da = absval(d + e), db = absval(a - b), dg = absval(d - e);
     T m = da > db ? da : db;
     m = m > dg ? m : dg;
     dmax = T(0.25) * m;
@@ -125,7 +139,7 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
                 T* fq = par ? a.f[1][q] : a.f[0][q];
                 Vec4<T>::load(fq + lvl_off(a.ls) + 4ull * p, c0, c1, c2, c3);
                 haar4<T>(c0, c1, c2, c3, s[q], dm);
-                tf = tf || (dm >= a.thr[n * NF + q]);
+                tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
                 fq[lvl_off(n) + p] = s[q];
             }
             if (a.ls < a.L) {
@@ -159,7 +173,7 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
                 T* fq = par ? a.f[1][q] : a.f[0][q];
                 haar4<T>(sv[rbuf][q][4 * tid], sv[rbuf][q][4 * tid + 1], sv[rbuf][q][4 * tid + 2],
                          sv[rbuf][q][4 * tid + 3], s[q], dm);
-                tf = tf || (dm >= a.thr[n * NF + q]);
+                tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
                 fq[lvl_off(n) + p] = s[q];
             }
             cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
@@ -278,41 +292,154 @@ static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __res
     if (threadIdx.x == 0) counts[tile] = total;
 }
 
-// exclusive scan of the tile counts; M = total (one CTA of 1024 threads)
-static __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ counts,
-                                                     uint32_t* __restrict__ offs, uint32_t ntiles,
-                                                     DevState* st) {
-    if (st && !st->active) return;
-    const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-    const uint32_t b = threadIdx.x * per, e = min(ntiles, b + per);
-    uint32_t sum = 0;
-    for (uint32_t i = b; i < e; ++i) sum += counts[i];
-    uint32_t total;
-    uint32_t run = block_excl_scan(sum, &total);
-    for (uint32_t i = b; i < e; ++i) {
-        offs[i] = run;
-        run += counts[i];
+// ---------------------------------------------------------------------------
+// Single-pass traversal + compaction.  Each CTA takes a tile by ticket (so
+// every earlier tile is already running), stages the tile's significance
+// bits in shared memory, finds the leaves of its 1024 finest cells, and gets
+// the number of leaves before it by decoupled look-back over the per-tile
+// status words.  A status word is (launch epoch << 32 | flag << 30 | count);
+// the epoch comes from the running ticket, so nothing is cleared between
+// launches.
+// ---------------------------------------------------------------------------
+struct TileBits {
+    uint32_t w[12];   // levels Lr+1..Lr+4 under the tile: j=1 w[0], j=2 w[1], j=3 w[2..3], j=4 w[4..11]
+    int l0;           // leaf level if a cell on the root path (levels 0..Lr) is insignificant, else Lr+1
+};
+
+__device__ __forceinline__ int tb_slot(int j) { return j == 1 ? 0 : (j == 2 ? 1 : (j == 3 ? 2 : 4)); }
+
+// Called by the whole block; ends with __syncthreads.
+__device__ __forceinline__ void load_tile_bits(const uint32_t* __restrict__ Sb, int L, int kt,
+                                               uint32_t tile, TileBits& tb) {
+    const int Lr = L - kt;
+    const int t = threadIdx.x;
+    if (t < 32) {
+        bool zero = false;
+        if (t <= Lr) zero = sig_bit(Sb, t, tile >> (2 * (Lr - t))) == 0u;
+        const uint32_t z = __ballot_sync(0xffffffffu, zero);
+        if (t == 0) tb.l0 = z ? (__ffs(z) - 1) : Lr + 1;
+    } else if (t < 44) {
+        const int k = t - 32;                       // word slot 0..11
+        int j, idx;
+        if (k == 0) { j = 1; idx = 0; }
+        else if (k == 1) { j = 2; idx = 0; }
+        else if (k < 4) { j = 3; idx = k - 2; }
+        else { j = 4; idx = k - 4; }
+        uint32_t v = 0u;
+        if (j <= kt - 1) {
+            const int n = Lr + j;
+            const uint32_t cnt = 1u << (2 * j);
+            const uint32_t first = tile * cnt;        // first code of the tile at level n
+            if (cnt < 32u) {
+                v = (__ldg(Sb + word_off(n) + (first >> 5)) >> (first & 31u)) & ((1u << cnt) - 1u);
+            } else if ((uint32_t)idx * 32u < cnt) {
+                v = __ldg(Sb + word_off(n) + (first >> 5) + idx);
+            }
+        }
+        tb.w[k] = v;
     }
-    if (threadIdx.x == 0) st->M = total;
+    __syncthreads();
 }
 
-static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __restrict__ Sb,
-                                                    const uint32_t* __restrict__ offs,
-                                                    uint32_t* __restrict__ leaves, int L, int kt,
-                                                    const DevState* st) {
-    if (st && !st->active) return;
-    __shared__ int s_l0;
-    const uint32_t tile = blockIdx.x;
-    if (threadIdx.x == 0) s_l0 = walk_root(Sb, L - kt, tile);
+// leaf level of the thread's group of four finest cells (local group g)
+__device__ __forceinline__ int group_level(const TileBits& tb, int L, int kt, uint32_t g) {
+    const int Lr = L - kt;
+    if (tb.l0 <= Lr) return tb.l0;
+    for (int j = 1; j <= kt - 1; ++j) {
+        const uint32_t c = (4u * g) >> (2 * (kt - j));    // local code at level Lr+j
+        if (!((tb.w[tb_slot(j) + (c >> 5)] >> (c & 31u)) & 1u)) return Lr + j;
+    }
+    return L;
+}
+
+constexpr uint32_t kFlagAgg = 1u, kFlagPre = 2u;
+
+__device__ __forceinline__ unsigned long long tile_status(uint32_t epoch, uint32_t flag, uint32_t v) {
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | v;
+}
+
+static __global__ void __launch_bounds__(256) k_traverse(const uint32_t* __restrict__ Sb,
+                                                         unsigned long long* status,
+                                                         uint32_t* __restrict__ leaves, int L, int kt,
+                                                         DevState* st) {
+    if (!st->active) return;
+    __shared__ TileBits tb;
+    __shared__ uint32_t s_tile, s_epoch, s_prefix, s_total;
+    const uint32_t lgt = 2u * (uint32_t)(L - kt);      // ntiles = 2^lgt
+    if (threadIdx.x == 0) {
+        const unsigned long long g = atomicAdd(&st->ticket, 1ull);
+        s_tile = (uint32_t)(g & ((1ull << lgt) - 1ull));
+        s_epoch = (uint32_t)(g >> lgt) + 1u;
+    }
     __syncthreads();
-    const TileWalk w = walk_tile(Sb, L, kt, tile, s_l0);
-    const uint32_t hc = heads_of(w, L);
-    uint32_t pos = offs[tile] + block_excl_scan(hc, nullptr);
-    if (hc == 4u) {
+    const uint32_t tile = s_tile, epoch = s_epoch;
+    load_tile_bits(Sb, L, kt, tile, tb);
+    const uint32_t g = threadIdx.x;
+    const bool act = g < (1u << (2 * (kt - 1)));
+    const uint32_t m0 = (tile << (2 * kt)) + 4u * g;
+    int l = L;
+    uint32_t hc = 0u;
+    if (act) {
+        l = group_level(tb, L, kt, g);
+        hc = l == L ? 4u : ((m0 & ((1u << (2 * (L - l))) - 1u)) == 0u ? 1u : 0u);
+    }
+    uint32_t total;
+    const uint32_t local = block_excl_scan(hc, &total);
+    if (threadIdx.x < 32) {
+        // publish the aggregate (tile 0: its inclusive prefix), then look back
+        const uint32_t lane = threadIdx.x;
+        if (lane == 0) {
+            __threadfence();
+            atomicExch(status + tile, tile_status(epoch, tile == 0 ? kFlagPre : kFlagAgg, total));
+        }
+        uint32_t prefix = 0u;
+        if (tile > 0) {
+            int64_t base = (int64_t)tile - 1;     // window [base-31, base]
+            bool done = false;
+            while (!done) {
+                const int64_t q = base - (int64_t)lane;
+                unsigned long long v = tile_status(epoch, kFlagPre, 0u);   // past tile 0: neutral
+                if (q >= 0) {
+                    volatile unsigned long long* sp = status + q;
+                    uint32_t it = 0;
+                    for (;;) {
+                        v = *sp;
+                        if ((uint32_t)(v >> 32) == epoch && ((v >> 30) & 3u) != 0u) break;
+                        if (++it > (1u << 24)) {          // bounded wait: report and move on
+                            atomicOr(&st->err, kErrTimeout);
+                            v = tile_status(epoch, kFlagPre, 0u);
+                            break;
+                        }
+                        if (it > 64u) __nanosleep(64);
+                    }
+                }
+                const bool isP = ((v >> 30) & 3u) == kFlagPre;
+                const uint32_t pm = __ballot_sync(0xffffffffu, isP);
+                const uint32_t stop = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;    // nearest P
+                uint32_t c = lane <= stop ? (uint32_t)(v & 0x3FFFFFFFull) : 0u;
 #pragma unroll
-        for (uint32_t e = 0; e < 4u; ++e) leaves[pos + e] = ((uint32_t)L << kLeafShift) | (w.m0 + e);
+                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                prefix += c;
+                done = pm != 0u;
+                base -= 32;
+            }
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(status + tile, tile_status(epoch, kFlagPre, prefix + total));
+            }
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            s_total = total;
+            if (tile == (1u << lgt) - 1u) st->M = prefix + total;
+        }
+    }
+    __syncthreads();
+    const uint32_t pos = s_prefix + local;
+    if (hc == 4u) {
+        Vec4u::store(leaves + pos, ((uint32_t)L << kLeafShift) | m0, m0);
     } else if (hc == 1u) {
-        leaves[pos] = ((uint32_t)w.l << kLeafShift) | (w.m0 >> (2 * (L - w.l)));
+        leaves[pos] = ((uint32_t)l << kLeafShift) | (m0 >> (2 * (L - l)));
     }
 }
 
@@ -330,7 +457,7 @@ struct Phys {
 
 template <typename T>
 __device__ __forceinline__ void velocity(const Cell<T>& c, T tol, T& u, T& v) {
-    if (c.h >= tol) {
+    if (ge_nonneg(c.h, tol)) {                         // h >= tol (tol > 0)
         const T rh = T(1) / c.h;
         u = c.qx * rh;
         v = c.qy * rh;
@@ -442,9 +569,9 @@ __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, 
 // CFL bound of an updated cell: min(dx/(|u|+a), dy/(|v|+a)), +inf if dry
 template <typename T>
 __device__ __forceinline__ T cfl_bound(const Phys<T>& P, T h, T qx, T qy) {
-    if (h < P.tol) return T(INFINITY);
+    if (!ge_nonneg(h, P.tol)) return T(INFINITY);      // h < tol (tol > 0)
     const T rh = T(1) / h;
-    const T u = fabs(qx * rh), v = fabs(qy * rh);
+    const T u = absval(qx * rh), v = absval(qy * rh);
     const T a = sqrt(P.g * h);
     const T rx = P.dxL / (u + a), ry = P.dyL / (v + a);
     return rx < ry ? rx : ry;
@@ -455,6 +582,7 @@ struct StepArgs {
     T* f[2][3];              // h, qx, qy hierarchies of the two state buffers
     const T* z;              // bed hierarchy
     const uint32_t* leaves;
+    uint32_t* wet;           // leaves that need the full update
     DevState* st;
     Phys<T> P;
     T lx, ly;
@@ -487,14 +615,94 @@ __device__ __forceinline__ Cell<T> ghost(const Cell<T>& c, bool reflect, bool xs
     return g;
 }
 
+// Inlet test of leaf (n, i, j): whether it touches the inflow range, and
+// the covered range of finest cells.
 template <typename T>
-static __global__ void __launch_bounds__(256) k_fv1(StepArgs<T> a) {
+__device__ __forceinline__ bool inlet_range(const StepArgs<T>& a, int n, uint32_t i, uint32_t j,
+                                            uint32_t last, int64_t& lo, int64_t& hi) {
+    const int s = a.inflow_side;
+    if (s < 0) return false;
+    const bool touch = (s == 0 && i == 0) || (s == 1 && i == last) || (s == 2 && j == 0) ||
+                       (s == 3 && j == last);
+    if (!touch) return false;
+    const int64_t w = 1ll << (a.L - n);
+    const int64_t pos = (s <= 1) ? (int64_t)j : (int64_t)i;
+    lo = pos * w;
+    hi = lo + w;
+    if (lo < a.a0) lo = a.a0;
+    if (hi > a.a1) hi = a.a1;
+    return hi > lo;
+}
+
+template <typename T> __device__ __forceinline__ T rx0_of(const DevState* st);
+template <> __device__ __forceinline__ double rx0_of<double>(const DevState* st) { return st->rx0; }
+template <> __device__ __forceinline__ float rx0_of<float>(const DevState* st) { return st->rx0f; }
+template <typename T> __device__ __forceinline__ T ry0_of(const DevState* st);
+template <> __device__ __forceinline__ double ry0_of<double>(const DevState* st) { return st->ry0; }
+template <> __device__ __forceinline__ float ry0_of<float>(const DevState* st) { return st->ry0f; }
+
+// FV1, first kernel: every leaf whose own and four same-level neighbour
+// depths are exactly zero and that has no inflow gets (+0, +0, +0) -- what
+// the full update computes for it (all reconstructed depths and fluxes are
+// 0, its CFL bound is infinite) -- decided on the depth bits alone.  Every
+// other leaf is queued for k_fv1_wet.  Needs few registers, so many warps
+// hide the gather latency.
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
     DevState* st = a.st;
     if (!st->active) return;
     const int par = (int)st->cur, nxt = par ^ 1;
     const uint32_t M = st->M;
+    const T* __restrict__ hsrc = par ? a.f[1][0] : a.f[0][0];
+    T* const oh = nxt ? a.f[1][0] : a.f[0][0];
+    T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
+    T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const uint32_t pk = __ldg(a.leaves + k);
+        const int n = (int)(pk >> kLeafShift);
+        const uint32_t code = pk & kCodeMask;
+        const uint32_t i = compact16(code), j = compact16(code >> 1);
+        const uint32_t last = (1u << n) - 1u;
+        const uint64_t base = lvl_off(n);
+        const uint64_t iC = base + code;
+        int64_t lo, hi;
+        bool dry = !inlet_range(a, n, i, j, last, lo, hi) && is_zero(__ldg(hsrc + iC));
+        if (dry) {
+            const uint64_t iW = i > 0 ? base + morton2(i - 1, j) : iC;
+            const uint64_t iE = i < last ? base + morton2(i + 1, j) : iC;
+            const uint64_t iS = j > 0 ? base + morton2(i, j - 1) : iC;
+            const uint64_t iN = j < last ? base + morton2(i, j + 1) : iC;
+            dry = is_zero(__ldg(hsrc + iW)) && is_zero(__ldg(hsrc + iE)) && is_zero(__ldg(hsrc + iS)) &&
+                  is_zero(__ldg(hsrc + iN));
+        }
+        if (dry) {
+            oh[iC] = T(0);
+            oqx[iC] = T(0);
+            oqy[iC] = T(0);
+        } else {
+            // warp-aggregated append to the queue of full updates
+            const uint32_t m = __activemask();
+            const uint32_t lane = threadIdx.x & 31u;
+            const uint32_t leader = __ffs(m) - 1u;
+            uint32_t base_pos = 0;
+            if (lane == leader) base_pos = atomicAdd(&st->nwet, (uint32_t)__popc(m));
+            base_pos = __shfl_sync(m, base_pos, leader);
+            a.wet[base_pos + __popc(m & ((1u << lane) - 1u))] = k;
+        }
+    }
+}
+
+// FV1, second kernel: the full update (Eq. 2 with the L_c reading) of every
+// queued leaf, with the CFL and s_max reductions.
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
+    DevState* st = a.st;
+    if (!st->active) return;
+    const uint32_t nq = st->nwet;
+    if (blockIdx.x * blockDim.x >= nq) return;          // whole block idle
+    const int par = (int)st->cur, nxt = par ^ 1;
     const T dt = (T)st->dt_use;
-    const T rx0 = dt / a.lx, ry0 = dt / a.ly;   // dt/dx_n = (dt/lx)*2^n exactly
+    const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
     const T Qdt = (T)st->Qdt;
     CellSrc<T> src;
     src.h = par ? a.f[1][0] : a.f[0][0];
@@ -505,53 +713,43 @@ static __global__ void __launch_bounds__(256) k_fv1(StepArgs<T> a) {
     T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
     unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nq; w += gridDim.x * blockDim.x) {
+        const uint32_t k = a.wet[w];
         const uint32_t pk = __ldg(a.leaves + k);
         const int n = (int)(pk >> kLeafShift);
         const uint32_t code = pk & kCodeMask;
         const uint32_t i = compact16(code), j = compact16(code >> 1);
         const uint32_t last = (1u << n) - 1u;
         const uint64_t base = lvl_off(n);
-        const Cell<T> C = fetch(src, base + code);
+        const uint64_t iC = base + code;
+        const Cell<T> C = fetch(src, iC);
         const Cell<T> W = i > 0 ? fetch(src, base + morton2(i - 1, j)) : ghost(C, a.bc_ref[0], true);
         const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
         const Cell<T> S = j > 0 ? fetch(src, base + morton2(i, j - 1)) : ghost(C, a.bc_ref[2], false);
         const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
         const T scale = (T)(1u << n);
         const T rx = rx0 * scale, ry = ry0 * scale;
-        bool inlet = false;
+        int64_t lo = 0, hi = 0;
+        const bool inlet = inlet_range(a, n, i, j, last, lo, hi);
         T dh = T(0);
-        if (a.inflow_side >= 0) {
-            const int s = a.inflow_side;
-            const bool touch = (s == 0 && i == 0) || (s == 1 && i == last) || (s == 2 && j == 0) ||
-                               (s == 3 && j == last);
-            if (touch) {
-                const int64_t w = 1ll << (a.L - n);
-                const int64_t pos = (s <= 1) ? (int64_t)j : (int64_t)i;
-                int64_t lo = pos * w, hi = lo + w;
-                if (lo < a.a0) lo = a.a0;
-                if (hi > a.a1) hi = a.a1;
-                if (hi > lo) {
-                    inlet = true;
-                    const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
-                    const T inv2n = T(1) / scale;
-                    const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
-                    dh = (Qdt * frac) / (dxn * dyn);
-                }
-            }
+        if (inlet) {
+            const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
+            const T inv2n = T(1) / scale;
+            const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
+            dh = (Qdt * frac) / (dxn * dyn);
         }
         T out[3];
         cell_update(a.P, rx, ry, dt, C, W, E, S, N, inlet, dh, out);
-        oh[base + code] = out[0];
-        oqx[base + code] = out[1];
-        oqy[base + code] = out[2];
+        oh[iC] = out[0];
+        oqx[iC] = out[1];
+        oqy[iC] = out[2];
         const T r = cfl_bound(a.P, out[0], out[1], out[2]);
         const unsigned long long rb = obits((double)r);
         rmin = rb < rmin ? rb : rmin;
         if (n == a.L) {
-            const unsigned long long b0 = obits((double)fabs(out[0]));
-            const unsigned long long b1 = obits((double)fabs(out[1]));
-            const unsigned long long b2 = obits((double)fabs(out[2]));
+            const unsigned long long b0 = abs_obits(out[0]);
+            const unsigned long long b1 = abs_obits(out[1]);
+            const unsigned long long b2 = abs_obits(out[2]);
             mh = b0 > mh ? b0 : mh;
             mqx = b1 > mqx ? b1 : mqx;
             mqy = b2 > mqy ? b2 : mqy;
@@ -559,9 +757,7 @@ static __global__ void __launch_bounds__(256) k_fv1(StepArgs<T> a) {
         if (!(isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]))) atomicOr(&st->err, kErrNonFinite);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
-    block_atomic_u64<true>(mh, &st->max_bits[0]);
-    block_atomic_u64<true>(mqx, &st->max_bits[1]);
-    block_atomic_u64<true>(mqy, &st->max_bits[2]);
+    block_max3_u64(mh, mqx, mqy, st->max_bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,23 +779,25 @@ static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
     DevState* st = a.st;
     if (!st->active) return;
     const int nxt = (int)st->cur ^ 1;
-    __shared__ int s_l0;
+    __shared__ TileBits tb;
     const uint32_t tile = blockIdx.x;
-    if (threadIdx.x == 0) s_l0 = walk_root(a.Sb, a.L - a.kt, tile);
-    __syncthreads();
-    const TileWalk w = walk_tile(a.Sb, a.L, a.kt, tile, s_l0);
-    unsigned long long mh = 0, mqx = 0, mqy = 0;
+    load_tile_bits(a.Sb, a.L, a.kt, tile, tb);
+    const uint32_t g = threadIdx.x;
+    const bool act = g < (1u << (2 * (a.kt - 1)));
+    const int l = act ? group_level(tb, a.L, a.kt, g) : a.L;
     T* const fh = nxt ? a.f[1][0] : a.f[0][0];
     T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const fqy = nxt ? a.f[1][2] : a.f[0][2];
-    if (w.act && w.l < a.L) {
-        const uint64_t slot = lvl_off(w.l) + (w.m0 >> (2 * (a.L - w.l)));
+    unsigned long long mh = 0, mqx = 0, mqy = 0;
+    if (l < a.L) {
+        const uint32_t m0 = (tile << (2 * a.kt)) + 4u * g;
+        const uint64_t slot = lvl_off(l) + (m0 >> (2 * (a.L - l)));
         const T hl = fh[slot], qxl = fqx[slot], qyl = fqy[slot];
-        const bool restore = hl >= a.tol;
-        const T eta = restore ? hl + __ldg(a.z + slot) : T(0);
-        const uint64_t fo = lvl_off(a.L) + w.m0;
+        const bool restore = ge_nonneg(hl, a.tol);      // hl >= tol (tol > 0)
+        const uint64_t fo = lvl_off(a.L) + m0;
         T hf[4];
         if (restore) {
+            const T eta = hl + __ldg(a.z + slot);
             T z0, z1, z2, z3;
             Vec4<T>::load(a.z + fo, z0, z1, z2, z3);
             const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
@@ -615,15 +813,15 @@ static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
         Vec4<T>::store(fqy + fo, qyl, qyl, qyl, qyl);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const unsigned long long b = obits((double)fabs(hf[e]));
+            const unsigned long long b = abs_obits(hf[e]);
             mh = b > mh ? b : mh;
         }
-        mqx = obits((double)fabs(qxl));
-        mqy = obits((double)fabs(qyl));
+        mqx = abs_obits(qxl);
+        mqy = abs_obits(qyl);
     }
-    block_atomic_u64<true>(mh, &st->max_bits[0]);
-    block_atomic_u64<true>(mqx, &st->max_bits[1]);
-    block_atomic_u64<true>(mqy, &st->max_bits[2]);
+    // skip the reductions when no thread of the block wrote anything
+    if (!__syncthreads_or(l < a.L)) return;
+    block_max3_u64(mh, mqx, mqy, st->max_bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,7 +832,7 @@ struct FinishArgs {
     const double* inflow_Q;
     int inflow_n;
     int L;
-    double eps, cfl, dt_max;
+    double eps, cfl, dt_max, lx, ly;
 };
 
 __device__ inline double inflow_Q(const FinishArgs& a, double t) {
@@ -649,17 +847,24 @@ __device__ inline double inflow_Q(const FinishArgs& a, double t) {
 }
 
 // Thresholds, timestep clamp and inflow volume of the step about to run.
+// Called by every thread of a one-block launch after s_max is final; the
+// (level, quantity) thresholds are spread over the threads.
 __device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
-    for (int q = 0; q < 3; ++q) {
-        for (int n = 0; n < a.L; ++n) {
-            st->thr[n * 3 + q] = ldexp(a.eps, n - a.L) * st->smax[q];
-            st->thrf[n * 3 + q] = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
-        }
+    for (int k = threadIdx.x; k < 3 * a.L; k += blockDim.x) {
+        const int n = k / 3, q = k - 3 * n;
+        st->thr[n * 3 + q] = ldexp(a.eps, n - a.L) * st->smax[q];
+        st->thrf[n * 3 + q] = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
     }
+    if (threadIdx.x != 0) return;
     st->active = st->t < st->t_end ? 1u : 0u;
     double dt_use = st->dt;
     if (st->t + dt_use > st->t_end) dt_use = st->t_end - st->t;
     st->dt_use = dt_use;
+    st->rx0 = dt_use / a.lx;            // dt/dx_n = (dt/lx) * 2^n exactly
+    st->ry0 = dt_use / a.ly;
+    st->rx0f = (float)dt_use / (float)a.lx;
+    st->ry0f = (float)dt_use / (float)a.ly;
+    st->nwet = 0u;
     st->Qdt = inflow_Q(a, st->t) * dt_use;
     st->rmin_bits = kInfBits;
     st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
@@ -676,35 +881,43 @@ __device__ inline double smax_of(unsigned long long bits) {
     return 1.0 > m ? 1.0 : m;
 }
 
+// One block: thread 0 advances the scalars, then all threads prepare the
+// next step.
 static __global__ void k_finish(DevState* st, FinishArgs a) {
-    if (threadIdx.x != 0 || !st->active) return;
-    st->t = st->t + st->dt_use;
-    st->dt = dt_from(a, from_obits(st->rmin_bits));
-    for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
-    if (!isfinite(st->dt) || !isfinite(st->smax[0]) || !isfinite(st->smax[1]) ||
-        !isfinite(st->smax[2]))
-        st->err |= kErrNonFinite;
-    st->step += 1;
-    st->cur ^= 1u;
+    if (!st->active) return;
+    __syncthreads();                 // every thread has read `active`
+    if (threadIdx.x == 0) {
+        st->t = st->t + st->dt_use;
+        st->dt = dt_from(a, from_obits(st->rmin_bits));
+        for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
+        if (!isfinite(st->dt) || !isfinite(st->smax[0]) || !isfinite(st->smax[1]) ||
+            !isfinite(st->smax[2]))
+            st->err |= kErrNonFinite;
+        st->step += 1;
+        st->cur ^= 1u;
+    }
+    __syncthreads();
     prepare_step(st, a);
 }
 
 // Set t_end (hwfv1_advance) and recompute the step scalars.
 static __global__ void k_set_tend(DevState* st, FinishArgs a, double t_end) {
-    if (threadIdx.x != 0) return;
-    st->t_end = t_end;
+    if (threadIdx.x == 0) st->t_end = t_end;
+    __syncthreads();
     prepare_step(st, a);
 }
 
 // State from the reductions of the initial (or reloaded) fields:
 // s_max from max_bits[0..2], and, if set_dt, dt from rmin_bits.
 static __global__ void k_init_state(DevState* st, FinishArgs a, int set_dt) {
-    if (threadIdx.x != 0) return;
-    for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
-    // a NaN or inf anywhere in the fields shows up in its maximum
-    for (int q = 0; q < 3; ++q)
-        if (!isfinite(st->smax[q])) st->err |= kErrNonFinite;
-    if (set_dt) st->dt = dt_from(a, from_obits(st->rmin_bits));
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
+        // a NaN or inf anywhere in the fields shows up in its maximum
+        for (int q = 0; q < 3; ++q)
+            if (!isfinite(st->smax[q])) st->err |= kErrNonFinite;
+        if (set_dt) st->dt = dt_from(a, from_obits(st->rmin_bits));
+    }
+    __syncthreads();
     prepare_step(st, a);
 }
 
@@ -730,7 +943,7 @@ static __global__ void __launch_bounds__(256) k_maxabs(const T* __restrict__ x, 
     unsigned long long m = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long b = obits((double)fabs(x[i]));
+        const unsigned long long b = abs_obits(x[i]);
         m = b > m ? b : m;
     }
     block_atomic_u64<true>(m, dst);
@@ -764,7 +977,7 @@ static __global__ void __launch_bounds__(256) k_maxabs_cur(const T* __restrict__
     unsigned long long m = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long b = obits((double)fabs(x[i]));
+        const unsigned long long b = abs_obits(x[i]);
         m = b > m ? b : m;
     }
     block_atomic_u64<true>(m, &st->max_bits[q]);
