@@ -57,6 +57,15 @@ __host__ __device__ inline uint32_t morton2(uint32_t i, uint32_t j) {
     return spread16(i) | (spread16(j) << 1);
 }
 
+// Same-level neighbours in the interleaved (Morton) domain: x occupies the
+// even bits, y the odd bits.  Adding 1 to the x bits alone = set the y bits
+// so that the carry runs through them, add, keep the x bits.
+constexpr uint32_t kXBits = 0x55555555u, kYBits = 0xAAAAAAAAu;
+__host__ __device__ inline uint32_t mort_xp(uint32_t c) { return (((c | kYBits) + 1u) & kXBits) | (c & kYBits); }
+__host__ __device__ inline uint32_t mort_xm(uint32_t c) { return (((c & kXBits) - 1u) & kXBits) | (c & kYBits); }
+__host__ __device__ inline uint32_t mort_yp(uint32_t c) { return (((c | kXBits) + 2u) & kYBits) | (c & kXBits); }
+__host__ __device__ inline uint32_t mort_ym(uint32_t c) { return (((c & kYBits) - 2u) & kYBits) | (c & kXBits); }
+
 // significance bit (n, code)
 __device__ __forceinline__ uint32_t sig_bit(const uint32_t* __restrict__ b, int n, uint32_t code) {
     return (__ldg(b + word_off(n) + (code >> 5)) >> (code & 31u)) & 1u;
@@ -202,7 +211,7 @@ struct DevState {
     uint32_t err;                     // latched device error bits
     unsigned long long ticket;        // running tile ticket of the traversal
     uint32_t nwet;                    // leaves queued for the full FV1 update
-    uint32_t pad0;
+    uint32_t ndec;                    // tiles listed for the decode kernel
     double rx0, ry0;                  // dt_use/lx, dt_use/ly (dt/dx_n = rx0 * 2^n)
     float rx0f, ry0f;                 // same, float arithmetic
     double thr[kMaxL * 3];            // eps*2^(n-L)*s_max,q for h, qx, qy

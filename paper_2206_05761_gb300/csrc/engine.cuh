@@ -55,8 +55,9 @@ class EngineT final : public Engine {
         Sb_ = bits_ + 5 * words_;
         if (!alloc(&leaves_, N_ * sizeof(uint32_t))) return oom();
         if (!alloc(&wet_, N_ * sizeof(uint32_t))) return oom();
-        if (!alloc(&status_, (size_t)ntiles_ * sizeof(unsigned long long))) return oom();
-        cudaMemsetAsync(status_, 0, (size_t)ntiles_ * sizeof(unsigned long long), stream_);
+        if (!alloc(&counts_, (size_t)ntiles_ * 3 * sizeof(uint32_t))) return oom();
+        offs_ = counts_ + ntiles_;
+        dlist_ = counts_ + 2 * ntiles_;
         if (!alloc(&st_, sizeof(DevState))) return oom();
         if (!alloc(&zaux_, 256)) return oom();
         if (!it_.empty()) {
@@ -321,7 +322,11 @@ class EngineT final : public Engine {
         k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
     }
     void launch_traverse() {
-        k_traverse<<<ntiles_, 256, 0, stream_>>>(Sb_, status_, leaves_, L_, kt_, st_);
+        cudaMemsetAsync(&st_->ndec, 0, sizeof(uint32_t), stream_);
+        const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
+        k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, counts_, dlist_, L_, kt_, ntiles_, st_);
+        k_trav_scan<<<1, 1024, 0, stream_>>>(counts_, offs_, nct, st_);
+        k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, offs_, leaves_, L_, kt_, ntiles_, st_);
     }
     StepArgs<T> step_args() const {
         StepArgs<T> a;
@@ -366,11 +371,12 @@ class EngineT final : public Engine {
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.z = z_;
         a.Sb = Sb_;
+        a.dlist = dlist_;
         a.st = st_;
         a.tol = (T)spec_.tol_h;
         a.L = L_;
         a.kt = kt_;
-        k_decode<T><<<ntiles_, 256, 0, stream_>>>(a);
+        k_decode<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(a);
         k_finish<<<1, 64, 0, stream_>>>(st_, fin_args());
     }
     void launch_step_all() {
@@ -453,7 +459,7 @@ class EngineT final : public Engine {
              *Sz_ = nullptr, *Sb_ = nullptr;
     uint32_t* leaves_ = nullptr;
     uint32_t* wet_ = nullptr;
-    unsigned long long* status_ = nullptr;
+    uint32_t *counts_ = nullptr, *offs_ = nullptr, *dlist_ = nullptr;
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;

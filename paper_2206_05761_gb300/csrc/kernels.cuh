@@ -45,6 +45,18 @@ struct Vec4u {
     }
 };
 
+template <> struct Vec4<uint32_t> {
+    // p[0..3] = v + 0..3; one 128-bit store when p is 16-byte aligned
+    static __device__ __forceinline__ void store_u(uint32_t* p, uint32_t v) {
+        if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0u) {
+            *reinterpret_cast<uint4*>(p) = make_uint4(v, v + 1u, v + 2u, v + 3u);
+        } else {
+#pragma unroll
+            for (uint32_t e = 0; e < 4u; ++e) p[e] = v + e;
+        }
+    }
+};
+
 template <typename T> __device__ __forceinline__ bool same4(T a, T b, T c, T d);
 template <> __device__ __forceinline__ bool same4<double>(double a, double b, double c, double d) {
     const long long x = __double_as_longlong(a);
@@ -119,7 +131,8 @@ template <typename T, int NF>
 static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
     if (a.st && !a.st->active) return;
     const int par = a.st ? (int)a.st->cur : 0;
-    __shared__ T sv[2][NF][256];
+    __shared__ T sv0[NF][256];        // level ls-1 (and ls-3, ls-5)
+    __shared__ T sv1[NF][64];         // level ls-2 (and ls-4)
     __shared__ uint32_t sc[2][8];
     const uint32_t tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     uint32_t cnt = 1u << (2 * (a.k - 1));
@@ -151,7 +164,7 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
         put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
         const uint32_t cball = put_bits(a.Cb, n, tile * cnt, cnt, cf);
 #pragma unroll
-        for (int q = 0; q < NF; ++q) sv[0][q][tid] = s[q];
+        for (int q = 0; q < NF; ++q) sv0[q][tid] = s[q];
         if (lane == 0) sc[0][warp] = cball;
     }
     for (int j = 2; j <= a.k; ++j) {
@@ -171,8 +184,8 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
             for (int q = 0; q < NF; ++q) {
                 T dm;
                 T* fq = par ? a.f[1][q] : a.f[0][q];
-                haar4<T>(sv[rbuf][q][4 * tid], sv[rbuf][q][4 * tid + 1], sv[rbuf][q][4 * tid + 2],
-                         sv[rbuf][q][4 * tid + 3], s[q], dm);
+                const T* r = rbuf ? sv1[q] : sv0[q];
+                haar4<T>(r[4 * tid], r[4 * tid + 1], r[4 * tid + 2], r[4 * tid + 3], s[q], dm);
                 tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
                 fq[lvl_off(n) + p] = s[q];
             }
@@ -181,8 +194,10 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
         const bool cf = act && (tf || cchild);
         put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
         const uint32_t cball = put_bits(a.Cb, n, tile * cnt, cnt, cf);
+        if (tid < cnt) {
 #pragma unroll
-        for (int q = 0; q < NF; ++q) sv[wbuf][q][tid] = s[q];
+            for (int q = 0; q < NF; ++q) (wbuf ? sv1[q] : sv0[q])[tid] = s[q];
+        }
         if (lane == 0) sc[wbuf][warp] = cball;
     }
 }
@@ -278,7 +293,7 @@ __device__ __forceinline__ uint32_t heads_of(const TileWalk& w, int L) {
     return (w.m0 & mask) == 0u ? 1u : 0u;
 }
 
-static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __restrict__ Sb,
+static __global__ void __launch_bounds__(256) k_trav_count_walk(const uint32_t* __restrict__ Sb,
                                                     uint32_t* __restrict__ counts, int L, int kt,
                                                     const DevState* st) {
     if (st && !st->active) return;
@@ -293,13 +308,10 @@ static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __res
 }
 
 // ---------------------------------------------------------------------------
-// Single-pass traversal + compaction.  Each CTA takes a tile by ticket (so
-// every earlier tile is already running), stages the tile's significance
-// bits in shared memory, finds the leaves of its 1024 finest cells, and gets
-// the number of leaves before it by decoupled look-back over the per-tile
-// status words.  A status word is (launch epoch << 32 | flag << 30 | count);
-// the epoch comes from the running ticket, so nothing is cleared between
-// launches.
+// Traversal + compaction in three deterministic passes (count, scan, write).
+// Each CTA stages its tile's significance bits in shared memory (the root
+// path is read by 32 threads at once), then finds the leaf of every group of
+// four finest cells from shared memory.
 // ---------------------------------------------------------------------------
 struct TileBits {
     uint32_t w[12];   // levels Lr+1..Lr+4 under the tile: j=1 w[0], j=2 w[1], j=3 w[2..3], j=4 w[4..11]
@@ -352,94 +364,178 @@ __device__ __forceinline__ int group_level(const TileBits& tb, int L, int kt, ui
     return L;
 }
 
-constexpr uint32_t kFlagAgg = 1u, kFlagPre = 2u;
+// Leaves of up to 16 finest cells (levels L-1, L-2) are decoded by the FV1
+// kernels themselves; larger ones by k_decode over the tiles listed here.
+__device__ __forceinline__ bool needs_decode_kernel(int l, int L) { return l < L - 2; }
 
-__device__ __forceinline__ unsigned long long tile_status(uint32_t epoch, uint32_t flag, uint32_t v) {
-    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | v;
+// One warp per tile.  Lane t reads bit t of the root path (levels 0..Lr) and
+// word slot t of the tile's own levels; group_level then works from the
+// warp's copy in shared memory.  Lane t owns the groups 8t..8t+7 (32
+// consecutive finest cells), so its leaves are consecutive in Z-order.
+constexpr int kTilesPerCta = 8;
+constexpr int kGroupsPerLane = 8;
+
+__device__ __forceinline__ void warp_tile_bits(const uint32_t* __restrict__ Sb, int L, int kt,
+                                               uint32_t tile, TileBits& tb) {
+    const int Lr = L - kt;
+    const int t = threadIdx.x & 31;
+    bool zero = false;
+    if (t <= Lr) zero = sig_bit(Sb, t, tile >> (2 * (Lr - t))) == 0u;
+    const uint32_t z = __ballot_sync(0xffffffffu, zero);
+    if (t < 12) {
+        int j, idx;
+        if (t == 0) { j = 1; idx = 0; }
+        else if (t == 1) { j = 2; idx = 0; }
+        else if (t < 4) { j = 3; idx = t - 2; }
+        else { j = 4; idx = t - 4; }
+        uint32_t v = 0u;
+        if (j <= kt - 1) {
+            const int n = Lr + j;
+            const uint32_t cnt = 1u << (2 * j);
+            const uint32_t first = tile * cnt;
+            if (cnt < 32u) {
+                v = (__ldg(Sb + word_off(n) + (first >> 5)) >> (first & 31u)) & ((1u << cnt) - 1u);
+            } else if ((uint32_t)idx * 32u < cnt) {
+                v = __ldg(Sb + word_off(n) + (first >> 5) + idx);
+            }
+        }
+        tb.w[t] = v;
+    }
+    if (t == 0) tb.l0 = z ? (__ffs(z) - 1) : Lr + 1;
+    __syncwarp();
 }
 
-static __global__ void __launch_bounds__(256) k_traverse(const uint32_t* __restrict__ Sb,
-                                                         unsigned long long* status,
-                                                         uint32_t* __restrict__ leaves, int L, int kt,
-                                                         DevState* st) {
-    if (!st->active) return;
-    __shared__ TileBits tb;
-    __shared__ uint32_t s_tile, s_epoch, s_prefix, s_total;
-    const uint32_t lgt = 2u * (uint32_t)(L - kt);      // ntiles = 2^lgt
-    if (threadIdx.x == 0) {
-        const unsigned long long g = atomicAdd(&st->ticket, 1ull);
-        s_tile = (uint32_t)(g & ((1ull << lgt) - 1ull));
-        s_epoch = (uint32_t)(g >> lgt) + 1u;
-    }
-    __syncthreads();
-    const uint32_t tile = s_tile, epoch = s_epoch;
-    load_tile_bits(Sb, L, kt, tile, tb);
-    const uint32_t g = threadIdx.x;
-    const bool act = g < (1u << (2 * (kt - 1)));
-    const uint32_t m0 = (tile << (2 * kt)) + 4u * g;
-    int l = L;
-    uint32_t hc = 0u;
-    if (act) {
-        l = group_level(tb, L, kt, g);
-        hc = l == L ? 4u : ((m0 & ((1u << (2 * (L - l))) - 1u)) == 0u ? 1u : 0u);
-    }
-    uint32_t total;
-    const uint32_t local = block_excl_scan(hc, &total);
-    if (threadIdx.x < 32) {
-        // publish the aggregate (tile 0: its inclusive prefix), then look back
-        const uint32_t lane = threadIdx.x;
-        if (lane == 0) {
-            __threadfence();
-            atomicExch(status + tile, tile_status(epoch, tile == 0 ? kFlagPre : kFlagAgg, total));
-        }
-        uint32_t prefix = 0u;
-        if (tile > 0) {
-            int64_t base = (int64_t)tile - 1;     // window [base-31, base]
-            bool done = false;
-            while (!done) {
-                const int64_t q = base - (int64_t)lane;
-                unsigned long long v = tile_status(epoch, kFlagPre, 0u);   // past tile 0: neutral
-                if (q >= 0) {
-                    volatile unsigned long long* sp = status + q;
-                    uint32_t it = 0;
-                    for (;;) {
-                        v = *sp;
-                        if ((uint32_t)(v >> 32) == epoch && ((v >> 30) & 3u) != 0u) break;
-                        if (++it > (1u << 24)) {          // bounded wait: report and move on
-                            atomicOr(&st->err, kErrTimeout);
-                            v = tile_status(epoch, kFlagPre, 0u);
-                            break;
-                        }
-                        if (it > 64u) __nanosleep(64);
-                    }
-                }
-                const bool isP = ((v >> 30) & 3u) == kFlagPre;
-                const uint32_t pm = __ballot_sync(0xffffffffu, isP);
-                const uint32_t stop = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;    // nearest P
-                uint32_t c = lane <= stop ? (uint32_t)(v & 0x3FFFFFFFull) : 0u;
+// Leaf heads of the lane's groups: returns the count; level of group e in lv[e].
+__device__ __forceinline__ uint32_t lane_heads(const TileBits& tb, int L, int kt, uint32_t tile,
+                                               int lv[kGroupsPerLane]) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t ngroups = 1u << (2 * (kt - 1));
+    uint32_t cnt = 0u;
 #pragma unroll
-                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                prefix += c;
-                done = pm != 0u;
-                base -= 32;
-            }
-            if (lane == 0) {
-                __threadfence();
-                atomicExch(status + tile, tile_status(epoch, kFlagPre, prefix + total));
-            }
-        }
-        if (lane == 0) {
-            s_prefix = prefix;
-            s_total = total;
-            if (tile == (1u << lgt) - 1u) st->M = prefix + total;
+    for (int e = 0; e < kGroupsPerLane; ++e) {
+        const uint32_t g = lane * kGroupsPerLane + e;
+        lv[e] = -1;
+        if (g < ngroups) {
+            const int l = group_level(tb, L, kt, g);
+            lv[e] = l;
+            const uint32_t m0 = (tile << (2 * kt)) + 4u * g;
+            cnt += l == L ? 4u : ((m0 & ((1u << (2 * (L - l))) - 1u)) == 0u ? 1u : 0u);
         }
     }
+    return cnt;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ uint32_t warp_excl(uint32_t v) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x - v;
+}
+
+// Traversal, pass 1: leaves per CTA (8 tiles); tiles holding a leaf of more
+// than 16 finest cells are listed for the decode kernel.
+static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __restrict__ Sb,
+                                                           uint32_t* __restrict__ csum,
+                                                           uint32_t* __restrict__ dlist, int L, int kt,
+                                                           uint32_t ntiles, DevState* st) {
+    if (!st->active) return;
+    __shared__ TileBits tbs[kTilesPerCta];
+    __shared__ uint32_t wsum[kTilesPerCta];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t tile = blockIdx.x * kTilesPerCta + warp;
+    uint32_t total = 0u;
+    if (tile < ntiles) {
+        TileBits& tb = tbs[warp];
+        warp_tile_bits(Sb, L, kt, tile, tb);
+        int lv[kGroupsPerLane];
+        const uint32_t c = lane_heads(tb, L, kt, tile, lv);
+        bool big = false;
+#pragma unroll
+        for (int e = 0; e < kGroupsPerLane; ++e) big = big || (lv[e] >= 0 && needs_decode_kernel(lv[e], L));
+        total = warp_sum(c);
+        if (__any_sync(0xffffffffu, big) && lane == 0) {
+            const uint32_t pos = atomicAdd(&st->ndec, 1u);
+            dlist[pos] = tile;           // one entry per tile at most
+        }
+    }
+    if (lane == 0) wsum[warp] = total;
     __syncthreads();
-    const uint32_t pos = s_prefix + local;
-    if (hc == 4u) {
-        Vec4u::store(leaves + pos, ((uint32_t)L << kLeafShift) | m0, m0);
-    } else if (hc == 1u) {
-        leaves[pos] = ((uint32_t)l << kLeafShift) | (m0 >> (2 * (L - l)));
+    if (threadIdx.x == 0) {
+        uint32_t s = 0u;
+        for (int w = 0; w < kTilesPerCta; ++w) s += wsum[w];
+        csum[blockIdx.x] = s;
+    }
+}
+
+// Traversal, pass 2: exclusive scan of the per-CTA counts (one CTA); M = total.
+static __global__ void __launch_bounds__(1024) k_trav_scan(const uint32_t* __restrict__ counts,
+                                                           uint32_t* __restrict__ offs, uint32_t n,
+                                                           DevState* st) {
+    if (!st->active) return;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = threadIdx.x * per, e = min(n, b + per);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += counts[i];
+    uint32_t total;
+    uint32_t run = block_excl_scan(sum, &total);
+    for (uint32_t i = b; i < e; ++i) {
+        offs[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == 0) st->M = total;
+}
+
+// Traversal, pass 3: each warp writes its tile's leaves in Z-order, 32
+// consecutive groups per round (lane t takes group 32r + t), so the stores
+// of a round are contiguous.
+static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __restrict__ Sb,
+                                                           const uint32_t* __restrict__ coffs,
+                                                           uint32_t* __restrict__ leaves, int L, int kt,
+                                                           uint32_t ntiles, const DevState* st) {
+    if (!st->active) return;
+    __shared__ TileBits tbs[kTilesPerCta];
+    __shared__ uint32_t wsum[kTilesPerCta];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t tile = blockIdx.x * kTilesPerCta + warp;
+    uint32_t total = 0u;
+    if (tile < ntiles) {
+        TileBits& tb = tbs[warp];
+        warp_tile_bits(Sb, L, kt, tile, tb);
+        int lv[kGroupsPerLane];
+        total = warp_sum(lane_heads(tb, L, kt, tile, lv));
+    }
+    if (lane == 0) wsum[warp] = total;
+    __syncthreads();
+    if (tile >= ntiles) return;
+    const TileBits& tb = tbs[warp];
+    uint32_t base = __ldg(coffs + blockIdx.x);
+    for (uint32_t w = 0; w < warp; ++w) base += wsum[w];
+    const uint32_t ngroups = 1u << (2 * (kt - 1));
+    for (uint32_t r = 0; r * 32u < ngroups; ++r) {
+        const uint32_t g = r * 32u + lane;
+        int l = L;
+        uint32_t c = 0u;
+        const uint32_t m0 = (tile << (2 * kt)) + 4u * g;
+        if (g < ngroups) {
+            l = group_level(tb, L, kt, g);
+            c = l == L ? 4u : ((m0 & ((1u << (2 * (L - l))) - 1u)) == 0u ? 1u : 0u);
+        }
+        const uint32_t pos = base + warp_excl(c);
+        if (c == 4u) {
+            Vec4<uint32_t>::store_u(leaves + pos, ((uint32_t)L << kLeafShift) | m0);
+        } else if (c == 1u) {
+            leaves[pos] = ((uint32_t)l << kLeafShift) | (m0 >> (2 * (L - l)));
+        }
+        base += warp_sum(c);
     }
 }
 
@@ -647,6 +743,74 @@ template <> __device__ __forceinline__ float ry0_of<float>(const DevState* st) {
 // 0, its CFL bound is infinite) -- decided on the depth bits alone.  Every
 // other leaf is queued for k_fv1_wet.  Needs few registers, so many warps
 // hide the gather latency.
+// Neighbour depth addresses of a leaf from its packed id (Morton-domain
+// arithmetic; ghosts read the leaf itself).
+struct DryProbe {
+    uint64_t iC, iW, iE, iS, iN;
+    uint32_t code;
+    int n;
+};
+__device__ __forceinline__ DryProbe dry_probe(uint32_t pk) {
+    DryProbe d;
+    d.n = (int)(pk >> kLeafShift);
+    d.code = pk & kCodeMask;
+    const uint64_t base = lvl_off(d.n);
+    const uint32_t lm = (1u << (2 * d.n)) - 1u;
+    const uint32_t xs = d.code & kXBits & lm, ys = d.code & kYBits;
+    d.iC = base + d.code;
+    d.iW = xs != 0u ? base + mort_xm(d.code) : d.iC;
+    d.iE = xs != (kXBits & lm) ? base + mort_xp(d.code) : d.iC;
+    d.iS = ys != 0u ? base + mort_ym(d.code) : d.iC;
+    d.iN = ys != (kYBits & lm) ? base + mort_yp(d.code) : d.iC;
+    return d;
+}
+
+template <typename T>
+__device__ __forceinline__ bool dry5(const T* __restrict__ h, const DryProbe& d) {
+    const T a = __ldg(h + d.iC), b = __ldg(h + d.iW), c = __ldg(h + d.iE), e = __ldg(h + d.iS),
+            f = __ldg(h + d.iN);
+    return is_zero(a) && is_zero(b) && is_zero(c) && is_zero(e) && is_zero(f);
+}
+
+// FV1, first kernel: every leaf whose own and four same-level neighbour
+// depths are exactly zero and that has no inflow gets (+0, +0, +0) -- what
+// the full update computes for it (all reconstructed depths and fluxes are
+// 0, its CFL bound is infinite) -- decided on the depth bits alone.  Every
+// other leaf is queued for k_fv1_wet.  Few registers and two leaves per
+// iteration, so many independent loads are in flight.
+template <typename T>
+__device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T* oh, T* oqx, T* oqy,
+                                           const DryProbe& d, bool dry, uint32_t k) {
+    if (dry && a.inflow_side >= 0) {
+        int64_t lo, hi;
+        dry = !inlet_range(a, d.n, compact16(d.code), compact16(d.code >> 1), (1u << d.n) - 1u, lo, hi);
+    }
+    if (dry) {
+        if (d.n == a.L || needs_decode_kernel(d.n, a.L)) {
+            oh[d.iC] = T(0);
+            oqx[d.iC] = T(0);
+            oqy[d.iC] = T(0);
+        } else {                              // 4 or 16 finest cells: decode here
+            const uint64_t fo = lvl_off(a.L) + ((uint64_t)d.code << (2 * (a.L - d.n)));
+            const uint32_t cnt = 1u << (2 * (a.L - d.n));
+            for (uint32_t e = 0; e < cnt; e += 4) {
+                Vec4<T>::store(oh + fo + e, T(0), T(0), T(0), T(0));
+                Vec4<T>::store(oqx + fo + e, T(0), T(0), T(0), T(0));
+                Vec4<T>::store(oqy + fo + e, T(0), T(0), T(0), T(0));
+            }
+        }
+    } else {
+        // warp-aggregated append to the queue of full updates
+        const uint32_t m = __activemask();
+        const uint32_t lane = threadIdx.x & 31u;
+        const uint32_t leader = __ffs(m) - 1u;
+        uint32_t base_pos = 0;
+        if (lane == leader) base_pos = atomicAdd(&st->nwet, (uint32_t)__popc(m));
+        base_pos = __shfl_sync(m, base_pos, leader);
+        a.wet[base_pos + __popc(m & ((1u << lane) - 1u))] = k;
+    }
+}
+
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
     DevState* st = a.st;
@@ -657,38 +821,16 @@ static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
     T* const oh = nxt ? a.f[1][0] : a.f[0][0];
     T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-        const uint32_t pk = __ldg(a.leaves + k);
-        const int n = (int)(pk >> kLeafShift);
-        const uint32_t code = pk & kCodeMask;
-        const uint32_t i = compact16(code), j = compact16(code >> 1);
-        const uint32_t last = (1u << n) - 1u;
-        const uint64_t base = lvl_off(n);
-        const uint64_t iC = base + code;
-        int64_t lo, hi;
-        bool dry = !inlet_range(a, n, i, j, last, lo, hi) && is_zero(__ldg(hsrc + iC));
-        if (dry) {
-            const uint64_t iW = i > 0 ? base + morton2(i - 1, j) : iC;
-            const uint64_t iE = i < last ? base + morton2(i + 1, j) : iC;
-            const uint64_t iS = j > 0 ? base + morton2(i, j - 1) : iC;
-            const uint64_t iN = j < last ? base + morton2(i, j + 1) : iC;
-            dry = is_zero(__ldg(hsrc + iW)) && is_zero(__ldg(hsrc + iE)) && is_zero(__ldg(hsrc + iS)) &&
-                  is_zero(__ldg(hsrc + iN));
-        }
-        if (dry) {
-            oh[iC] = T(0);
-            oqx[iC] = T(0);
-            oqy[iC] = T(0);
-        } else {
-            // warp-aggregated append to the queue of full updates
-            const uint32_t m = __activemask();
-            const uint32_t lane = threadIdx.x & 31u;
-            const uint32_t leader = __ffs(m) - 1u;
-            uint32_t base_pos = 0;
-            if (lane == leader) base_pos = atomicAdd(&st->nwet, (uint32_t)__popc(m));
-            base_pos = __shfl_sync(m, base_pos, leader);
-            a.wet[base_pos + __popc(m & ((1u << lane) - 1u))] = k;
-        }
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += 2u * stride) {
+        const uint32_t k2 = k + stride;
+        const bool two = k2 < M;
+        const DryProbe d1 = dry_probe(__ldg(a.leaves + k));
+        const DryProbe d2 = dry_probe(two ? __ldg(a.leaves + k2) : 0u);
+        const bool y1 = dry5(hsrc, d1);
+        const bool y2 = two && dry5(hsrc, d2);
+        dry_finish(a, st, oh, oqx, oqy, d1, y1, k);
+        if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, k2);
     }
 }
 
@@ -740,18 +882,53 @@ static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
         }
         T out[3];
         cell_update(a.P, rx, ry, dt, C, W, E, S, N, inlet, dh, out);
-        oh[iC] = out[0];
-        oqx[iC] = out[1];
-        oqy[iC] = out[2];
         const T r = cfl_bound(a.P, out[0], out[1], out[2]);
         const unsigned long long rb = obits((double)r);
         rmin = rb < rmin ? rb : rmin;
-        if (n == a.L) {
-            const unsigned long long b0 = abs_obits(out[0]);
+        if (n == a.L || needs_decode_kernel(n, a.L)) {
+            oh[iC] = out[0];
+            oqx[iC] = out[1];
+            oqy[iC] = out[2];
+            if (n == a.L) {
+                const unsigned long long b0 = abs_obits(out[0]);
+                mh = b0 > mh ? b0 : mh;
+                const unsigned long long b1 = abs_obits(out[1]);
+                mqx = b1 > mqx ? b1 : mqx;
+                const unsigned long long b2 = abs_obits(out[2]);
+                mqy = b2 > mqy ? b2 : mqy;
+            }
+        } else {
+            // decode-back of a leaf of 4 or 16 finest cells (as k_decode does)
+            const uint64_t fo = lvl_off(a.L) + ((uint64_t)code << (2 * (a.L - n)));
+            const uint32_t cnt = 1u << (2 * (a.L - n));
+            const T hl = out[0];
+            const bool restore = ge_nonneg(hl, a.P.tol);
+            const T eta = restore ? hl + C.z : T(0);
+            for (uint32_t e = 0; e < cnt; e += 4) {
+                T hf[4];
+                if (restore) {
+                    T z0, z1, z2, z3;
+                    Vec4<T>::load(src.z + fo + e, z0, z1, z2, z3);
+                    const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
+                    hf[0] = d0 > T(0) ? d0 : T(0);
+                    hf[1] = d1 > T(0) ? d1 : T(0);
+                    hf[2] = d2 > T(0) ? d2 : T(0);
+                    hf[3] = d3 > T(0) ? d3 : T(0);
+                } else {
+                    hf[0] = hf[1] = hf[2] = hf[3] = hl;
+                }
+                Vec4<T>::store(oh + fo + e, hf[0], hf[1], hf[2], hf[3]);
+                Vec4<T>::store(oqx + fo + e, out[1], out[1], out[1], out[1]);
+                Vec4<T>::store(oqy + fo + e, out[2], out[2], out[2], out[2]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned long long b = abs_obits(hf[q]);
+                    mh = b > mh ? b : mh;
+                }
+            }
             const unsigned long long b1 = abs_obits(out[1]);
-            const unsigned long long b2 = abs_obits(out[2]);
-            mh = b0 > mh ? b0 : mh;
             mqx = b1 > mqx ? b1 : mqx;
+            const unsigned long long b2 = abs_obits(out[2]);
             mqy = b2 > mqy ? b2 : mqy;
         }
         if (!(isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]))) atomicOr(&st->err, kErrNonFinite);
@@ -769,27 +946,35 @@ struct DecodeArgs {
     T* f[2][3];
     const T* z;
     const uint32_t* Sb;
+    const uint32_t* dlist;    // tiles holding a leaf of more than 16 finest cells
     DevState* st;
     T tol;
     int L, kt;
 };
 
+// Decode-back of the leaves of more than 16 finest cells, over the tiles the
+// traversal listed (smaller leaves were decoded by the FV1 kernels): every
+// finest cell takes the leaf's discharges and free surface (R-decode).
 template <typename T>
 static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
     DevState* st = a.st;
     if (!st->active) return;
+    const uint32_t nd = st->ndec;
+    if (blockIdx.x >= nd) return;                   // whole block idle
     const int nxt = (int)st->cur ^ 1;
     __shared__ TileBits tb;
-    const uint32_t tile = blockIdx.x;
-    load_tile_bits(a.Sb, a.L, a.kt, tile, tb);
-    const uint32_t g = threadIdx.x;
-    const bool act = g < (1u << (2 * (a.kt - 1)));
-    const int l = act ? group_level(tb, a.L, a.kt, g) : a.L;
     T* const fh = nxt ? a.f[1][0] : a.f[0][0];
     T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const fqy = nxt ? a.f[1][2] : a.f[0][2];
     unsigned long long mh = 0, mqx = 0, mqy = 0;
-    if (l < a.L) {
+    const uint32_t g = threadIdx.x;
+    const bool act = g < (1u << (2 * (a.kt - 1)));
+    for (uint32_t d = blockIdx.x; d < nd; d += gridDim.x) {
+        const uint32_t tile = a.dlist[d];
+        __syncthreads();                            // tb reused across tiles
+        load_tile_bits(a.Sb, a.L, a.kt, tile, tb);
+        const int l = act ? group_level(tb, a.L, a.kt, g) : a.L;
+        if (!needs_decode_kernel(l, a.L)) continue;
         const uint32_t m0 = (tile << (2 * a.kt)) + 4u * g;
         const uint64_t slot = lvl_off(l) + (m0 >> (2 * (a.L - l)));
         const T hl = fh[slot], qxl = fqx[slot], qyl = fqy[slot];
@@ -816,11 +1001,10 @@ static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
             const unsigned long long b = abs_obits(hf[e]);
             mh = b > mh ? b : mh;
         }
-        mqx = abs_obits(qxl);
-        mqy = abs_obits(qyl);
+        const unsigned long long bx = abs_obits(qxl), by = abs_obits(qyl);
+        mqx = bx > mqx ? bx : mqx;
+        mqy = by > mqy ? by : mqy;
     }
-    // skip the reductions when no thread of the block wrote anything
-    if (!__syncthreads_or(l < a.L)) return;
     block_max3_u64(mh, mqx, mqy, st->max_bits);
 }
 

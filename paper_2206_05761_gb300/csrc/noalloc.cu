@@ -104,7 +104,7 @@ extern "C" hwfv1_status hwfv1_traverse_noalloc(const uint32_t* sig_bits, int32_t
     uint32_t* counts = scratch;
     uint32_t* offs = scratch + kMaxTiles;
     // every count and offset the call reads is written by the call itself
-    k_trav_count<<<ntiles, 256, 0, st>>>(sig_bits, counts, L, kt, nullptr);
+    k_trav_count_walk<<<ntiles, 256, 0, st>>>(sig_bits, counts, L, kt, nullptr);
     k_scan_noalloc<<<1, 1024, 0, st>>>(counts, offs, ntiles, num_leaves);
     k_write_noalloc<<<ntiles, 256, 0, st>>>(sig_bits, offs, leaves, (uint64_t)cap, L, kt);
     return cudaGetLastError() == cudaSuccess ? HWFV1_OK : HWFV1_ERR_CUDA;
