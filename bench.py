@@ -38,6 +38,7 @@ def parse():
     a.add_argument("--L", type=int, default=12)
     a.add_argument("--spinup", type=int, default=200, help="untimed steps before warm-up")
     a.add_argument("--no-cpu-baseline", action="store_true")
+    a.add_argument("--no-ensemble", action="store_true")
     a.add_argument("--cpu-steps", type=int, default=2)
     return a.parse_args()
 
@@ -222,6 +223,56 @@ def run_ours(args, rank, world):
                 clocks=clocks, N=N)
 
 
+def run_ensemble(args, steps=50):
+    """Batched ensemble (64 bumpy dam-breaks, L drawn from {7,8,9,10}, eps
+    1e-3): the batched form (one launch per phase for all domains, one graph
+    per ensemble step, autotuned) against the same 64 domains advanced one
+    after another through the single-domain path."""
+    import torch
+    import synth
+    from paper_2206_05761_gb300 import hwfv1 as H
+    from paper_2206_05761_gb300.sim import Ensemble, Simulation
+
+    cases = synth.ensemble(count=64, seed=4)
+    levels = [p["L"] for p, _ in cases]
+    stream = torch.cuda.Stream()
+    # plain: one handle (one captured step graph) per domain
+    sims = [Simulation(p, f, args.precision, stream=stream) for p, f in cases]
+    for s_ in sims:
+        s_.advance(max_steps=3)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in sims:
+        s_.advance(max_steps=steps)
+    e1.record(stream)
+    stream.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    for s_ in sims:
+        s_.close()
+    del sims
+    torch.cuda.synchronize()
+    # batched
+    ens = Ensemble(cases, args.precision, stream=stream)
+    choice = ens.autotune(trial_steps=2)
+    ens.advance(max_steps=3)
+    stream.synchronize()
+    e0.record(stream)
+    ens.advance(max_steps=steps)
+    e1.record(stream)
+    stream.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    leaves = sum(ens.member_stats(d)[0] for d in range(len(cases)))
+    lps = ens.launches_per_step()
+    ens.close()
+    return {"domains": len(cases), "levels": {str(L): levels.count(L) for L in sorted(set(levels))},
+            "steps": steps, "batched_steps_per_s": steps / (batch_ms / 1e3),
+            "plain_steps_per_s": steps / (plain_ms / 1e3), "speedup_vs_plain": plain_ms / batch_ms,
+            "leaf_updates_per_s": leaves * steps / (batch_ms / 1e3),
+            "autotune": {"encode_levels_per_pass": choice[0], "fv1_cells_per_thread": choice[1]},
+            "launches_per_step": lps}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -318,6 +369,8 @@ def main():
         "gpu_launches": kernels_per_step(args.L) * args.steps,
         "clocks": r["clocks"], "sim_time_s": r["t"],
     }
+    if world == 1 and not args.no_ensemble:
+        out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, args.cpu_steps)
     print(json.dumps(out))

@@ -189,6 +189,43 @@ const char* hwfv1_last_error(hwfv1_handle* hd);
 /* Free all device memory of the handle. */
 void hwfv1_destroy(hwfv1_handle* hd);
 
+/* ------------------------------------------------------------------------
+ * Batched ensembles: many independent domains (each its own problem, its
+ * own L, its own t and dt) advanced together.  Every phase of a step is one
+ * launch over all domains (a flat grid mapped onto (domain, block) through a
+ * per-domain block table) and one ensemble step is one CUDA graph.  The
+ * paper runs one domain; this is the batched form of the same path.
+ * ------------------------------------------------------------------------ */
+typedef struct hwfv1_batch hwfv1_batch;
+
+/* n problems (all with the same precision) and their initial fields (arrays
+ * of n device pointers, each field as in hwfv1_init).  Synchronises. */
+hwfv1_status hwfv1_batch_init(const hwfv1_problem* specs, int32_t n, const double* const* z,
+                              const double* const* h, const double* const* qx,
+                              const double* const* qy, void* stream, hwfv1_batch** out);
+
+/* Up to max_steps ensemble steps; each domain stops at t_end (its later
+ * steps are no-ops).  Does not synchronise. */
+hwfv1_status hwfv1_batch_advance(hwfv1_batch* b, double t_end, int64_t max_steps);
+
+/* Time trial_steps ensemble steps under each candidate launch configuration
+ * (encode levels per pass in {5,4,3}, finest cells per FV1 thread in
+ * {8,32,128,512}) and keep the fastest; choice (host, 2 int32, may be NULL)
+ * receives it.  All candidates give bit-identical results; the trials
+ * advance the ensemble by 12 x (trial_steps + 1) steps.  Synchronises. */
+hwfv1_status hwfv1_batch_autotune(hwfv1_batch* b, int64_t trial_steps, int32_t* choice);
+
+/* Handle of member d for the single-domain getters (hwfv1_get_fields,
+ * hwfv1_get_time, hwfv1_get_leaves, ...).  The batch owns it: hwfv1_destroy
+ * on it does nothing; it is freed by hwfv1_batch_destroy. */
+hwfv1_status hwfv1_batch_member(hwfv1_batch* b, int32_t d, hwfv1_handle** view);
+
+/* Kernel launches in one ensemble step (the captured graph's nodes). */
+int64_t hwfv1_batch_launches_per_step(hwfv1_batch* b);
+
+const char* hwfv1_batch_last_error(hwfv1_batch* b);
+void hwfv1_batch_destroy(hwfv1_batch* b);
+
 /* Leaf list from a regularised significance bit array, for callers that
  * cannot allocate device memory (a host framework whose pool allocator owns
  * the device memory budget, a fixed-footprint deployment, a latency-bound

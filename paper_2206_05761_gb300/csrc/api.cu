@@ -4,11 +4,19 @@
 #include <cmath>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "engine_iface.h"
 
 struct hwfv1_handle {
     hwfv1::Engine* eng = nullptr;
+    std::string msg;
+    bool borrowed = false;       // a member view of a batch: the batch owns the engine
+};
+
+struct hwfv1_batch {
+    hwfv1::Batch* b = nullptr;
+    std::vector<hwfv1_handle*> views;
     std::string msg;
 };
 
@@ -169,9 +177,83 @@ const char* hwfv1_last_error(hwfv1_handle* hd) {
     return hd->msg.c_str();
 }
 void hwfv1_destroy(hwfv1_handle* hd) {
-    if (!hd) return;
+    if (!hd || hd->borrowed) return;      // member views are freed with their batch
     delete hd->eng;
     delete hd;
+}
+
+// ---------------------------------------------------------------------------
+// Batched ensembles
+// ---------------------------------------------------------------------------
+hwfv1_status hwfv1_batch_init(const hwfv1_problem* specs, int32_t n, const double* const* z,
+                              const double* const* h, const double* const* qx, const double* const* qy,
+                              void* stream, hwfv1_batch** out) {
+    if (!out) return HWFV1_ERR_INVALID_SPEC;
+    *out = nullptr;
+    if (!specs || n < 1 || n > 4096 || !z || !h || !qx || !qy) return HWFV1_ERR_INVALID_SPEC;
+    for (int d = 0; d < n; ++d) {
+        std::string msg;
+        const hwfv1_status s = validate(specs + d, &msg);
+        if (s != HWFV1_OK) return s;
+        if (specs[d].precision != specs[0].precision) return HWFV1_ERR_INVALID_SPEC;
+        if (!z[d] || !h[d] || !qx[d] || !qy[d]) return HWFV1_ERR_INVALID_SPEC;
+    }
+    hwfv1_batch* bt = new (std::nothrow) hwfv1_batch;
+    if (!bt) return HWFV1_ERR_OOM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bt->b = specs[0].precision == 64 ? hwfv1::make_batch_f64(specs, n, st) : hwfv1::make_batch_f32(specs, n, st);
+    const hwfv1_status s = bt->b->init(z, h, qx, qy);
+    if (s != HWFV1_OK) {
+        delete bt->b;
+        delete bt;
+        return s;
+    }
+    for (int d = 0; d < n; ++d) {
+        hwfv1_handle* v = new hwfv1_handle;
+        v->eng = bt->b->member(d);
+        v->borrowed = true;
+        bt->views.push_back(v);
+    }
+    *out = bt;
+    return HWFV1_OK;
+}
+
+hwfv1_status hwfv1_batch_advance(hwfv1_batch* bt, double t_end, int64_t max_steps) {
+    if (!bt || !bt->b) return HWFV1_ERR_STATE;
+    if (std::isnan(t_end)) return HWFV1_ERR_INVALID_SPEC;
+    const hwfv1_status s = bt->b->advance(t_end, max_steps);
+    if (s != HWFV1_OK) bt->msg = bt->b->err;
+    return s;
+}
+
+hwfv1_status hwfv1_batch_autotune(hwfv1_batch* bt, int64_t trial_steps, int32_t* choice) {
+    if (!bt || !bt->b) return HWFV1_ERR_STATE;
+    const hwfv1_status s = bt->b->autotune(trial_steps, choice);
+    if (s != HWFV1_OK) bt->msg = bt->b->err;
+    return s;
+}
+
+hwfv1_status hwfv1_batch_member(hwfv1_batch* bt, int32_t d, hwfv1_handle** view) {
+    if (!bt || !bt->b || !view) return HWFV1_ERR_STATE;
+    if (d < 0 || d >= (int32_t)bt->views.size()) return HWFV1_ERR_INVALID_SPEC;
+    *view = bt->views[d];
+    return HWFV1_OK;
+}
+
+int64_t hwfv1_batch_launches_per_step(hwfv1_batch* bt) {
+    return (bt && bt->b) ? bt->b->launches_per_step() : 0;
+}
+
+const char* hwfv1_batch_last_error(hwfv1_batch* bt) {
+    if (!bt) return "NULL batch";
+    return bt->msg.c_str();
+}
+
+void hwfv1_batch_destroy(hwfv1_batch* bt) {
+    if (!bt) return;
+    for (hwfv1_handle* v : bt->views) delete v;
+    delete bt->b;
+    delete bt;
 }
 
 }  // extern "C"

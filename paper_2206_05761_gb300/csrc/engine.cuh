@@ -281,6 +281,53 @@ class EngineT final : public Engine {
         return check("load", true);
     }
 
+    // Everything a batched step needs for this domain (see batch.cuh):
+    // encode passes of at most enc_k levels, FV1 work of about fv1_cells
+    // finest cells per thread (the block count is set by the batch).
+    template <class Plan>
+    void fill_plan(Plan& p, int enc_k, int /*fv1_cells*/) const {
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) p.enc.f[b][q] = f_[b][q];
+        p.enc.thr = thr_dyn();
+        p.enc.Tb = Tb_;
+        p.enc.Cb = Cb_;
+        p.enc.st = st_;
+        p.enc.L = L_;
+        p.enc.ls = L_;
+        p.enc.k = enc_k;
+        p.npass = 0;
+        for (int ls = L_; ls > 0 && p.npass < (int)(sizeof(p.ls) / sizeof(p.ls[0]));) {
+            const int k = ls < enc_k ? ls : enc_k;
+            p.ls[p.npass] = ls;
+            p.kk[p.npass] = k;
+            p.npass++;
+            ls -= k;
+        }
+        p.clear_w = Tb_;
+        p.clear_n = 2 * words_;
+        p.flag.Tb = Tb_;
+        p.flag.Cb = Cb_;
+        p.flag.Sbase = Sz_;
+        p.flag.Sb = Sb_;
+        p.flag.L = L_;
+        p.flag.predict = predict();
+        p.flag.close = close();
+        p.flag.st = st_;
+        p.Sb = Sb_;
+        p.csum = counts_;
+        p.coffs = offs_;
+        p.dlist = dlist_;
+        p.leaves = leaves_;
+        p.L = L_;
+        p.kt = kt_;
+        p.ntiles = ntiles_;
+        p.nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
+        p.step = step_args();
+        p.dec = decode_args();
+        p.fin = fin_args();
+        p.st = st_;
+    }
+
    private:
     // ---- launch helpers -------------------------------------------------
     int grid_for(uint64_t n) const {
@@ -365,7 +412,7 @@ class EngineT final : public Engine {
         k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
         k_fv1_wet<T><<<grid_for(N_), 256, 0, stream_>>>(a);
     }
-    void launch_decode() {
+    DecodeArgs<T> decode_args() const {
         DecodeArgs<T> a;
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
@@ -376,7 +423,10 @@ class EngineT final : public Engine {
         a.tol = (T)spec_.tol_h;
         a.L = L_;
         a.kt = kt_;
-        k_decode<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(a);
+        return a;
+    }
+    void launch_decode() {
+        k_decode<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(decode_args());
         k_finish<<<1, 64, 0, stream_>>>(st_, fin_args());
     }
     void launch_step_all() {

@@ -38,6 +38,23 @@ class Engine {
 Engine* make_engine_f64(const hwfv1_problem& spec, cudaStream_t stream);
 Engine* make_engine_f32(const hwfv1_problem& spec, cudaStream_t stream);
 
+// Many domains advanced together (batch.cuh).
+class Batch {
+   public:
+    virtual ~Batch() {}
+    virtual hwfv1_status init(const double* const* z, const double* const* h, const double* const* qx,
+                              const double* const* qy) = 0;
+    virtual hwfv1_status advance(double t_end, int64_t max_steps) = 0;
+    virtual hwfv1_status autotune(int64_t trial_steps, int32_t* choice) = 0;
+    virtual Engine* member(int d) = 0;
+    virtual int size() const = 0;
+    virtual int64_t launches_per_step() const = 0;
+    std::string err;
+};
+
+Batch* make_batch_f64(const hwfv1_problem* specs, int n, cudaStream_t stream);
+Batch* make_batch_f32(const hwfv1_problem* specs, int n, cudaStream_t stream);
+
 struct SaveHeader {
     uint64_t magic;
     int32_t L, precision;

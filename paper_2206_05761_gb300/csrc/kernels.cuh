@@ -76,6 +76,14 @@ __device__ __forceinline__ double absval(double x) {
 }
 __device__ __forceinline__ float absval(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
 
+// A block of a (possibly batched) launch: its index among the blocks given
+// to one domain and their number.  Single-domain launches use blockIdx.x and
+// gridDim.x; batched launches (batch.cuh) map a flat grid onto domains.
+struct Blk {
+    uint32_t id, n;
+};
+__device__ __forceinline__ Blk this_blk() { return Blk{blockIdx.x, gridDim.x}; }
+
 // Haar parent (Eq. 3a) and the largest detail magnitude (Eq. 3b-3d) of four
 // children [0]=(2i,2j) [1]=(2i+1,2j) [2]=(2i,2j+1) [3]=(2i+1,2j+1).
 // dmax = 0.25*max(|d+e|, |a-b|, |d-e|) equals max(|0.25(d+e)|, ...) because
@@ -128,15 +136,15 @@ struct EncodeArgs {
 // cell, k <= 5 levels in one pass.  The first level reads four children
 // per thread with 128-bit loads; the next levels work from shared memory.
 template <typename T, int NF>
-static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
+__device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, int kk, uint32_t bid) {
     if (a.st && !a.st->active) return;
     const int par = a.st ? (int)a.st->cur : 0;
     __shared__ T sv0[NF][256];        // level ls-1 (and ls-3, ls-5)
     __shared__ T sv1[NF][64];         // level ls-2 (and ls-4)
     __shared__ uint32_t sc[2][8];
-    const uint32_t tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    uint32_t cnt = 1u << (2 * (a.k - 1));
-    int n = a.ls - 1;
+    const uint32_t tile = bid, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    uint32_t cnt = 1u << (2 * (kk - 1));
+    int n = ls - 1;
     {   // level ls-1
         const bool act = tid < cnt;
         const uint32_t p = tile * cnt + tid;
@@ -150,14 +158,14 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
             for (int q = 0; q < NF; ++q) {
                 T c0, c1, c2, c3, dm;
                 T* fq = par ? a.f[1][q] : a.f[0][q];
-                Vec4<T>::load(fq + lvl_off(a.ls) + 4ull * p, c0, c1, c2, c3);
+                Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
                 haar4<T>(c0, c1, c2, c3, s[q], dm);
                 tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
                 fq[lvl_off(n) + p] = s[q];
             }
-            if (a.ls < a.L) {
+            if (ls < a.L) {
                 const uint32_t cb = 4u * p;
-                cchild = (__ldg(a.Cb + word_off(a.ls) + (cb >> 5)) >> (cb & 31u)) & 0xFu;
+                cchild = (__ldg(a.Cb + word_off(ls) + (cb >> 5)) >> (cb & 31u)) & 0xFu;
             }
         }
         const bool cf = act && (tf || cchild);
@@ -167,9 +175,9 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
         for (int q = 0; q < NF; ++q) sv0[q][tid] = s[q];
         if (lane == 0) sc[0][warp] = cball;
     }
-    for (int j = 2; j <= a.k; ++j) {
+    for (int j = 2; j <= kk; ++j) {
         __syncthreads();
-        n = a.ls - j;
+        n = ls - j;
         cnt >>= 2;
         const int rbuf = (j - 2) & 1, wbuf = (j - 1) & 1;   // level j-1 wrote buffer (j-2)&1
         const bool act = tid < cnt;
@@ -202,23 +210,37 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
     }
 }
 
+template <typename T, int NF>
+static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
+    encode_body<T, NF>(a, a.ls, a.k, blockIdx.x);
+}
+
 // Clear bit arrays before an encode (the partial words are OR-ed into).
-static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, const DevState* st) {
+__device__ __forceinline__ void clear_body(uint32_t* w, uint32_t nwords, const DevState* st, Blk B) {
     if (st && !st->active) return;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x)
-        w[i] = 0u;
+    for (uint32_t i = B.id * blockDim.x + threadIdx.x; i < nwords; i += B.n * blockDim.x) w[i] = 0u;
+}
+static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, const DevState* st) {
+    clear_body(w, nwords, st, this_blk());
 }
 
 // ---------------------------------------------------------------------------
 // Regularised significance, word-parallel:
 //   S(n,c) = Sbase(n,c) | (close ? C(n,c) : T(n,c)) | (predict ? T(n-1,c/4) : 0)
 // ---------------------------------------------------------------------------
-static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
-                       const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb, int L,
-                       int predict, int close, const DevState* st) {
+struct FlagArgs {
+    const uint32_t *Tb, *Cb, *Sbase;
+    uint32_t* Sb;
+    int L, predict, close;
+    DevState* st;
+};
+
+__device__ __forceinline__ void flag_body(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
+                                          const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb,
+                                          int L, int predict, int close, const DevState* st, Blk B) {
     if (st && !st->active) return;
     const uint32_t total = bits_words(L);
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+    for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < total; w += B.n * blockDim.x) {
         int n = 0;
         while (n + 1 < L && word_off(n + 1) <= w) ++n;
         const uint32_t lw = w - word_off(n);
@@ -238,6 +260,11 @@ static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* _
         if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
         Sb[w] = s;
     }
+}
+static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
+                              const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb, int L,
+                              int predict, int close, const DevState* st) {
+    flag_body(Tb, Cb, Sbase, Sb, L, predict, close, st, this_blk());
 }
 
 // OR of two bit arrays (threshold flags of h, qx, qy with those of z).
@@ -443,15 +470,14 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t v) {
 
 // Traversal, pass 1: leaves per CTA (8 tiles); tiles holding a leaf of more
 // than 16 finest cells are listed for the decode kernel.
-static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __restrict__ Sb,
-                                                           uint32_t* __restrict__ csum,
-                                                           uint32_t* __restrict__ dlist, int L, int kt,
-                                                           uint32_t ntiles, DevState* st) {
+__device__ __forceinline__ void trav_count_body(const uint32_t* __restrict__ Sb, uint32_t* __restrict__ csum,
+                                                uint32_t* __restrict__ dlist, int L, int kt, uint32_t ntiles,
+                                                DevState* st, Blk B) {
     if (!st->active) return;
     __shared__ TileBits tbs[kTilesPerCta];
     __shared__ uint32_t wsum[kTilesPerCta];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t tile = blockIdx.x * kTilesPerCta + warp;
+    const uint32_t tile = B.id * kTilesPerCta + warp;
     uint32_t total = 0u;
     if (tile < ntiles) {
         TileBits& tb = tbs[warp];
@@ -472,14 +498,19 @@ static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __res
     if (threadIdx.x == 0) {
         uint32_t s = 0u;
         for (int w = 0; w < kTilesPerCta; ++w) s += wsum[w];
-        csum[blockIdx.x] = s;
+        csum[B.id] = s;
     }
+}
+static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __restrict__ Sb,
+                                                           uint32_t* __restrict__ csum,
+                                                           uint32_t* __restrict__ dlist, int L, int kt,
+                                                           uint32_t ntiles, DevState* st) {
+    trav_count_body(Sb, csum, dlist, L, kt, ntiles, st, this_blk());
 }
 
 // Traversal, pass 2: exclusive scan of the per-CTA counts (one CTA); M = total.
-static __global__ void __launch_bounds__(1024) k_trav_scan(const uint32_t* __restrict__ counts,
-                                                           uint32_t* __restrict__ offs, uint32_t n,
-                                                           DevState* st) {
+__device__ __forceinline__ void trav_scan_body(const uint32_t* __restrict__ counts, uint32_t* __restrict__ offs,
+                                               uint32_t n, DevState* st) {
     if (!st->active) return;
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     const uint32_t b = threadIdx.x * per, e = min(n, b + per);
@@ -493,19 +524,23 @@ static __global__ void __launch_bounds__(1024) k_trav_scan(const uint32_t* __res
     }
     if (threadIdx.x == 0) st->M = total;
 }
+static __global__ void __launch_bounds__(1024) k_trav_scan(const uint32_t* __restrict__ counts,
+                                                           uint32_t* __restrict__ offs, uint32_t n,
+                                                           DevState* st) {
+    trav_scan_body(counts, offs, n, st);
+}
 
 // Traversal, pass 3: each warp writes its tile's leaves in Z-order, 32
 // consecutive groups per round (lane t takes group 32r + t), so the stores
 // of a round are contiguous.
-static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __restrict__ Sb,
-                                                           const uint32_t* __restrict__ coffs,
-                                                           uint32_t* __restrict__ leaves, int L, int kt,
-                                                           uint32_t ntiles, const DevState* st) {
+__device__ __forceinline__ void trav_write_body(const uint32_t* __restrict__ Sb, const uint32_t* __restrict__ coffs,
+                                                uint32_t* __restrict__ leaves, int L, int kt, uint32_t ntiles,
+                                                const DevState* st, Blk B) {
     if (!st->active) return;
     __shared__ TileBits tbs[kTilesPerCta];
     __shared__ uint32_t wsum[kTilesPerCta];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t tile = blockIdx.x * kTilesPerCta + warp;
+    const uint32_t tile = B.id * kTilesPerCta + warp;
     uint32_t total = 0u;
     if (tile < ntiles) {
         TileBits& tb = tbs[warp];
@@ -517,7 +552,7 @@ static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __res
     __syncthreads();
     if (tile >= ntiles) return;
     const TileBits& tb = tbs[warp];
-    uint32_t base = __ldg(coffs + blockIdx.x);
+    uint32_t base = __ldg(coffs + B.id);
     for (uint32_t w = 0; w < warp; ++w) base += wsum[w];
     const uint32_t ngroups = 1u << (2 * (kt - 1));
     for (uint32_t r = 0; r * 32u < ngroups; ++r) {
@@ -537,6 +572,12 @@ static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __res
         }
         base += warp_sum(c);
     }
+}
+static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __restrict__ Sb,
+                                                           const uint32_t* __restrict__ coffs,
+                                                           uint32_t* __restrict__ leaves, int L, int kt,
+                                                           uint32_t ntiles, const DevState* st) {
+    trav_write_body(Sb, coffs, leaves, L, kt, ntiles, st, this_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -812,7 +853,7 @@ __device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T
 }
 
 template <typename T>
-static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
+__device__ __forceinline__ void fv1_dry_body(const StepArgs<T>& a, Blk B) {
     DevState* st = a.st;
     if (!st->active) return;
     const int par = (int)st->cur, nxt = par ^ 1;
@@ -821,8 +862,8 @@ static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
     T* const oh = nxt ? a.f[1][0] : a.f[0][0];
     T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += 2u * stride) {
+    const uint32_t stride = B.n * blockDim.x;
+    for (uint32_t k = B.id * blockDim.x + threadIdx.x; k < M; k += 2u * stride) {
         const uint32_t k2 = k + stride;
         const bool two = k2 < M;
         const DryProbe d1 = dry_probe(__ldg(a.leaves + k));
@@ -833,15 +874,19 @@ static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
         if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, k2);
     }
 }
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
+    fv1_dry_body<T>(a, this_blk());
+}
 
 // FV1, second kernel: the full update (Eq. 2 with the L_c reading) of every
 // queued leaf, with the CFL and s_max reductions.
 template <typename T>
-static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
+__device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
     DevState* st = a.st;
     if (!st->active) return;
     const uint32_t nq = st->nwet;
-    if (blockIdx.x * blockDim.x >= nq) return;          // whole block idle
+    if (B.id * blockDim.x >= nq) return;          // whole block idle
     const int par = (int)st->cur, nxt = par ^ 1;
     const T dt = (T)st->dt_use;
     const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
@@ -855,7 +900,7 @@ static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
     T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
     unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nq; w += gridDim.x * blockDim.x) {
+    for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
         const uint32_t k = a.wet[w];
         const uint32_t pk = __ldg(a.leaves + k);
         const int n = (int)(pk >> kLeafShift);
@@ -936,6 +981,10 @@ static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
     block_atomic_u64<false>(rmin, &st->rmin_bits);
     block_max3_u64(mh, mqx, mqy, st->max_bits);
 }
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
+    fv1_wet_body<T>(a, this_blk());
+}
 
 // ---------------------------------------------------------------------------
 // Decode-back (Eq. 4 with zero details below leaves, free surface restored
@@ -956,11 +1005,11 @@ struct DecodeArgs {
 // traversal listed (smaller leaves were decoded by the FV1 kernels): every
 // finest cell takes the leaf's discharges and free surface (R-decode).
 template <typename T>
-static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
+__device__ __forceinline__ void decode_body(const DecodeArgs<T>& a, Blk B) {
     DevState* st = a.st;
     if (!st->active) return;
     const uint32_t nd = st->ndec;
-    if (blockIdx.x >= nd) return;                   // whole block idle
+    if (B.id >= nd) return;                   // whole block idle
     const int nxt = (int)st->cur ^ 1;
     __shared__ TileBits tb;
     T* const fh = nxt ? a.f[1][0] : a.f[0][0];
@@ -969,7 +1018,7 @@ static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
     unsigned long long mh = 0, mqx = 0, mqy = 0;
     const uint32_t g = threadIdx.x;
     const bool act = g < (1u << (2 * (a.kt - 1)));
-    for (uint32_t d = blockIdx.x; d < nd; d += gridDim.x) {
+    for (uint32_t d = B.id; d < nd; d += B.n) {
         const uint32_t tile = a.dlist[d];
         __syncthreads();                            // tb reused across tiles
         load_tile_bits(a.Sb, a.L, a.kt, tile, tb);
@@ -1006,6 +1055,10 @@ static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
         mqy = by > mqy ? by : mqy;
     }
     block_max3_u64(mh, mqx, mqy, st->max_bits);
+}
+template <typename T>
+static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
+    decode_body<T>(a, this_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -1067,7 +1120,7 @@ __device__ inline double smax_of(unsigned long long bits) {
 
 // One block: thread 0 advances the scalars, then all threads prepare the
 // next step.
-static __global__ void k_finish(DevState* st, FinishArgs a) {
+__device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
     if (!st->active) return;
     __syncthreads();                 // every thread has read `active`
     if (threadIdx.x == 0) {
@@ -1083,12 +1136,18 @@ static __global__ void k_finish(DevState* st, FinishArgs a) {
     __syncthreads();
     prepare_step(st, a);
 }
+static __global__ void k_finish(DevState* st, FinishArgs a) {
+    finish_body(st, a);
+}
 
 // Set t_end (hwfv1_advance) and recompute the step scalars.
-static __global__ void k_set_tend(DevState* st, FinishArgs a, double t_end) {
+__device__ __forceinline__ void set_tend_body(DevState* st, const FinishArgs& a, double t_end) {
     if (threadIdx.x == 0) st->t_end = t_end;
     __syncthreads();
     prepare_step(st, a);
+}
+static __global__ void k_set_tend(DevState* st, FinishArgs a, double t_end) {
+    set_tend_body(st, a, t_end);
 }
 
 // State from the reductions of the initial (or reloaded) fields:

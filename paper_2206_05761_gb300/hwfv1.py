@@ -80,6 +80,18 @@ def lib():
             L.hwfv1_last_error.argtypes = [_H]
             L.hwfv1_last_error.restype = C.c_char_p
             L.hwfv1_traverse_noalloc.argtypes = [_dp, C.c_int32, _dp, C.c_int64, _dp, C.c_void_p]
+            _pp = C.POINTER(C.c_void_p)
+            L.hwfv1_batch_init.argtypes = [C.POINTER(Problem), C.c_int32, _pp, _pp, _pp, _pp, C.c_void_p,
+                                           C.POINTER(C.c_void_p)]
+            L.hwfv1_batch_advance.argtypes = [C.c_void_p, C.c_double, C.c_int64]
+            L.hwfv1_batch_autotune.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_int32)]
+            L.hwfv1_batch_member.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_H)]
+            L.hwfv1_batch_launches_per_step.argtypes = [C.c_void_p]
+            L.hwfv1_batch_launches_per_step.restype = C.c_int64
+            L.hwfv1_batch_last_error.argtypes = [C.c_void_p]
+            L.hwfv1_batch_last_error.restype = C.c_char_p
+            L.hwfv1_batch_destroy.argtypes = [C.c_void_p]
+            L.hwfv1_batch_destroy.restype = None
             L.hwfv1_destroy.argtypes = [_H]
             L.hwfv1_destroy.restype = None
             _lib = L
@@ -91,7 +103,9 @@ def exported_symbols():
             "hwfv1_decode", "hwfv1_advance", "hwfv1_get_fields", "hwfv1_set_fields",
             "hwfv1_get_leaves", "hwfv1_get_flags", "hwfv1_get_level", "hwfv1_get_time",
             "hwfv1_set_time", "hwfv1_get_stats", "hwfv1_save", "hwfv1_load",
-            "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version", "hwfv1_traverse_noalloc"]
+            "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version", "hwfv1_traverse_noalloc",
+            "hwfv1_batch_init", "hwfv1_batch_advance", "hwfv1_batch_autotune", "hwfv1_batch_member",
+            "hwfv1_batch_launches_per_step", "hwfv1_batch_last_error", "hwfv1_batch_destroy"]
 
 
 def _check(st, what, hd=None):
@@ -259,3 +273,59 @@ def bits_words(L):
 
 def word_off(n):
     return bits_words(n)
+
+
+# ---------------------------------------------------------------------------
+# Batched ensembles
+# ---------------------------------------------------------------------------
+
+def _check_batch(st, what, bt=None):
+    if st != OK:
+        msg = ""
+        if bt is not None:
+            m = lib().hwfv1_batch_last_error(bt)
+            msg = m.decode() if m else ""
+        raise Hwfv1Error(st, what, msg)
+
+
+def hwfv1_batch_init(specs, z, h, qx, qy, stream=None):
+    """specs: list of Problem (same precision); z, h, qx, qy: lists of CUDA
+    float64 tensors.  Returns a batch handle."""
+    n = len(specs)
+    arr = (Problem * n)(*specs)
+    ptrs = [(C.c_void_p * n)(*[_ptr(t) for t in xs]) for xs in (z, h, qx, qy)]
+    bt = C.c_void_p()
+    sp = stream.cuda_stream if stream is not None else None
+    st = lib().hwfv1_batch_init(arr, n, *[C.cast(p, C.POINTER(C.c_void_p)) for p in ptrs], sp, C.byref(bt))
+    _check_batch(st, "hwfv1_batch_init")
+    return bt
+
+
+def hwfv1_batch_advance(bt, t_end, max_steps):
+    _check_batch(lib().hwfv1_batch_advance(bt, float(t_end), int(max_steps)), "hwfv1_batch_advance", bt)
+
+
+def hwfv1_batch_autotune(bt, trial_steps):
+    ch = (C.c_int32 * 2)()
+    _check_batch(lib().hwfv1_batch_autotune(bt, int(trial_steps), ch), "hwfv1_batch_autotune", bt)
+    return ch[0], ch[1]
+
+
+def hwfv1_batch_member(bt, d):
+    hd = _H()
+    _check_batch(lib().hwfv1_batch_member(bt, int(d), C.byref(hd)), "hwfv1_batch_member", bt)
+    return hd
+
+
+def hwfv1_batch_launches_per_step(bt):
+    return int(lib().hwfv1_batch_launches_per_step(bt))
+
+
+def hwfv1_batch_last_error(bt):
+    m = lib().hwfv1_batch_last_error(bt)
+    return m.decode() if m else ""
+
+
+def hwfv1_batch_destroy(bt):
+    lib().hwfv1_batch_destroy(bt)
+

@@ -118,3 +118,60 @@ def unpack_bits(words, L):
         bits = np.unpackbits(words[w0:w0 + nw].astype("<u4").view(np.uint8), bitorder="little")
         out.append(bits[:cnt].astype(np.uint8))
     return out
+
+
+class Ensemble:
+    """Many independent domains advanced together (hwfv1_batch_*)."""
+
+    def __init__(self, cases, precision=64, stream=None, device="cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("HWFV1 needs a CUDA device; there is no CPU fallback")
+        self.dev = torch.device(device)
+        self.specs = [H.make_problem(p, precision) for p, _ in cases]
+        self.L = [p["L"] for p, _ in cases]
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device=self.dev)
+        self._inputs = {k: [t(f[k]) for _, f in cases] for k in ("z", "h", "qx", "qy")}
+        self.bt = H.hwfv1_batch_init(self.specs, self._inputs["z"], self._inputs["h"], self._inputs["qx"],
+                                     self._inputs["qy"], stream)
+        self._inputs = None
+
+    def advance(self, t_end=float("inf"), max_steps=1):
+        H.hwfv1_batch_advance(self.bt, t_end, max_steps)
+
+    def autotune(self, trial_steps=3):
+        return H.hwfv1_batch_autotune(self.bt, trial_steps)
+
+    def member_fields(self, d):
+        hd = H.hwfv1_batch_member(self.bt, d)
+        n = 1 << (2 * self.L[d])
+        bufs = [torch.empty(n, dtype=torch.float64, device=self.dev) for _ in range(3)]
+        H.hwfv1_get_fields(hd, *bufs)
+        s = 1 << self.L[d]
+        return {k: v.cpu().numpy().reshape(s, s) for k, v in zip(("h", "qx", "qy"), bufs)}
+
+    def member_leaves(self, d):
+        hd = H.hwfv1_batch_member(self.bt, d)
+        n = H.hwfv1_get_leaves(hd)
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=self.dev)
+        H.hwfv1_get_leaves(hd, out)
+        return out[:n].cpu().numpy().view(np.uint32).copy()
+
+    def member_time(self, d):
+        return H.hwfv1_get_time(H.hwfv1_batch_member(self.bt, d))
+
+    def member_stats(self, d):
+        return H.hwfv1_get_stats(H.hwfv1_batch_member(self.bt, d))
+
+    def launches_per_step(self):
+        return H.hwfv1_batch_launches_per_step(self.bt)
+
+    def close(self):
+        if self.bt is not None:
+            H.hwfv1_batch_destroy(self.bt)
+            self.bt = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
