@@ -39,6 +39,7 @@ def parse():
     a.add_argument("--spinup", type=int, default=200, help="untimed steps before warm-up")
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--no-ensemble", action="store_true")
+    a.add_argument("--no-learned", action="store_true")
     a.add_argument("--cpu-steps", type=int, default=2)
     return a.parse_args()
 
@@ -117,12 +118,6 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
-def kernels_per_step(L):
-    passes = (L + 4) // 5
-    # clear + encode passes + flag + (count, scan, write) + fv1 + decode + finish
-    return 1 + passes + 1 + 3 + 1 + 1 + 1
-
-
 def roofline_terms(L, M, precision):
     """Algorithmic bytes of one launch of each kernel."""
     N = 1 << (2 * L)
@@ -202,6 +197,7 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+    c0 = H.hwfv1_get_counters(hd)          # also captures the step graph (untimed)
     torch.cuda.synchronize()
     clk = ClockSampler(torch.cuda.current_device())
     clk.start()
@@ -216,11 +212,13 @@ def run_ours(args, rank, world):
     ms = e0.elapsed_time(e1)
     t_now, dt_now, nsteps = H.hwfv1_get_time(hd)
     M_last, smax = H.hwfv1_get_stats(hd)
+    c1 = H.hwfv1_get_counters(hd)
     H.hwfv1_destroy(hd)
     ph = {k: statistics.median(v) for k, v in phases.items()}
     return dict(ms=ms, e2e_s=t_e2e, e2e_steps=e2e_total_steps, phases_ms=ph,
                 M_mean=float(sum(Ms) / len(Ms)), M_last=M_last, t=t_now, dt=dt_now,
-                clocks=clocks, N=N)
+                clocks=clocks, N=N, timed_steps=c1[0] - c0[0], timed_leaf_updates=c1[1] - c0[1],
+                timed_wet_updates=c1[2] - c0[2], kernels_per_step=c1[3])
 
 
 def run_ensemble(args, steps=50):
@@ -271,6 +269,116 @@ def run_ensemble(args, steps=50):
             "leaf_updates_per_s": leaves * steps / (batch_ms / 1e3),
             "autotune": {"encode_levels_per_pass": choice[0], "fv1_cells_per_thread": choice[1]},
             "launches_per_step": lps}
+
+
+def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100, steps=400):
+    """Learned look-ahead at L = 11: the subtree CNN trained (BF16 tensor
+    cores) on trajectories of seeded cases run on the GPU path, then a
+    held-out case advanced `steps` steps plain, and learned to the same
+    simulated time.  Reports steps/s, simulated seconds per second, mean
+    leaves, the L1 depth difference learned - plain, and the network's
+    under-prediction rate on held-out samples."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2206_05761_gb300 import hwfv1 as H
+    from paper_2206_05761_gb300 import learn
+    from paper_2206_05761_gb300.sim import Simulation
+
+    make = {"bumpy": lambda s: synth.bumpy_dam_break(L=L, eps=1e-3, seed=s),
+            "columns": lambda s: synth.columns_dam_break(L=L, eps=1e-3, seed=s)}[kind]
+    t0 = time.perf_counter()
+    x, y = learn.collect([make(s) for s in train_seeds], steps=400, every=20)
+    x, y = learn.augment(x, y)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, loss = learn.train(x, y, epochs=6, batch=8, lr=3e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    xh, yh = learn.collect([make(test_seed)], steps=steps, every=40)
+    under = learn.under_prediction_rate(net, xh, yh, 0.02)
+    del x, y, xh, yh
+    p, f = make(test_seed)
+    stream = torch.cuda.Stream()
+
+    def timed(net_, t_end, max_steps):
+        sim = Simulation(p, f, args.precision, stream=stream)
+        if net_ is not None:
+            sim.set_skipnet(net_, audit_K=10, margin=0.02)
+        sim.counters()                        # captures the step graph (untimed)
+        sim.advance(max_steps=0)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.advance(t_end=t_end, max_steps=max_steps)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        n, lu, wu, kps = sim.counters()
+        t = sim.time()[0]
+        fl = sim.fields()
+        sim.close()
+        return dict(ms=ms, steps=n, lu=lu, kps=kps, t=t, h=fl["h"])
+
+    plain = timed(None, float("inf"), steps)
+    # the learned run's step count to the same simulated time, then a timed
+    # run of exactly that many steps (no idle launches after t_end)
+    n_l = timed(net, plain["t"], 4 * steps)["steps"]
+    lrn = timed(net, plain["t"], n_l)
+    H.hwfv1_skipnet_destroy(net)
+    cell = 1.0 / (1 << (2 * L))
+    d = float(np.abs(lrn["h"] - plain["h"]).sum() * cell)
+
+    def rep(r):
+        return {"steps": r["steps"], "ms": r["ms"], "steps_per_s": r["steps"] / (r["ms"] / 1e3),
+                "sim_s_per_s": r["t"] / (r["ms"] / 1e3), "mean_leaves": r["lu"] / max(r["steps"], 1),
+                "leaf_updates_per_s": r["lu"] / (r["ms"] / 1e3), "kernels_per_step": r["kps"]}
+
+    return {"workload": "%s dam-break L=%d eps=1e-3 (train seeds %d..%d, held-out seed %d)"
+                        % (kind, L, min(train_seeds), max(train_seeds), test_seed),
+            "finest_cells": 1 << (2 * L), "sim_time_s": plain["t"],
+            "plain": rep(plain), "learned": rep(lrn),
+            "speedup_sim_time": (plain["ms"] / lrn["ms"]) if lrn["t"] >= plain["t"] * (1 - 1e-12) else None,
+            "leaves_ratio": (lrn["lu"] / lrn["steps"]) / (plain["lu"] / plain["steps"]),
+            "l1_depth_learned_vs_plain_m": d, "held_out_under_prediction": under,
+            "training": {"images": int(8 * 20 * len(train_seeds)), "image_px": 1 << (L - 4),
+                         "last_batch_loss": loss, "collect_s": t_collect, "train_s": t_train,
+                         "epochs": 6, "batch": 8, "augment": "8 symmetries of the square"},
+            "audit_K": 10, "margin": 0.02}
+
+
+def combine_ranks(ms, e2e_s, world, device="cuda"):
+    """Replicas only: each rank times its own independent simulation; the
+    job's time is the slowest rank's (max over ranks)."""
+    if world <= 1:
+        return ms, e2e_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, e2e_s], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(t[1])
+
+
+def time_precision(args, precision, steps=100):
+    """Device-timed steps/s of the same workload in another precision."""
+    import numpy as np
+    import torch
+    from paper_2206_05761_gb300.sim import Simulation
+    p, f = workload(args.L)
+    stream = torch.cuda.Stream()
+    sim = Simulation(p, f, precision, stream=stream)
+    sim.advance(max_steps=args.spinup + max(args.warmup, 3))
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.advance(max_steps=steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    M = sim.stats()[0]
+    sim.close()
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "leaves": M,
+            "dtype": "f32" if precision == 32 else "f64"}
 
 
 def peaks():
@@ -329,15 +437,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     r = run_ours(args, rank, world)
-    ms = r["ms"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([ms, r["e2e_s"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
-    else:
-        e2e_s = r["e2e_s"]
+    ms, e2e_s = combine_ranks(r["ms"], r["e2e_s"], world, device="cuda")
     if rank != 0:
         return
     value = world * args.steps / (ms / 1e3)
@@ -360,17 +460,23 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32",
         "data": "synthetic", "config": config_dict(args),
-        "leaf_updates_per_s": value * r["M_mean"], "mean_leaves": r["M_mean"],
+        "leaf_updates_per_s": world * r["timed_leaf_updates"] / (ms / 1e3),
+        "mean_leaves": r["timed_leaf_updates"] / max(r["timed_steps"], 1),
+        "wet_fraction": r["timed_wet_updates"] / max(r["timed_leaf_updates"], 1),
         "phases_ms": ph, "roofline": roof,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * 8 / r["e2e_steps"],
                 "d2h_bytes_per_step": 3 * N * 8 / r["e2e_steps"],
                 "note": "host fields -> init -> %d steps -> fields back to host" % r["e2e_steps"]},
-        "gpu_launches": kernels_per_step(args.L) * args.steps,
+        "gpu_launches": r["kernels_per_step"] * r["timed_steps"],
         "clocks": r["clocks"], "sim_time_s": r["t"],
     }
+    if world == 1:
+        out["other_precision"] = time_precision(args, 32 if args.precision == 64 else 64)
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
+    if world == 1 and not args.no_learned:
+        out["learned"] = {k: run_learned(args, k) for k in ("columns", "bumpy")}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, args.cpu_steps)
     print(json.dumps(out))

@@ -175,6 +175,15 @@ hwfv1_status hwfv1_set_time(hwfv1_handle* hd, double t, double dt);
  * number of leaves and the maxima of |h|, |hu|, |hv| used for s_max. */
 hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax3);
 
+/* Running counters (host outputs, any may be NULL; synchronises): steps
+ * taken, leaves updated summed over those steps (sum of M, the work of
+ * Sec. 2.3's leaf loop), the part of them that took the full FV1 update
+ * (not entirely dry), and the number of kernels one captured step launches
+ * (the learned step's when a network is attached; capturing the graph here
+ * if no step has run yet).  No counterpart in the paper: diagnostics. */
+hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates,
+                                int64_t* wet_updates, int64_t* kernels_per_step);
+
 /* Checkpoint: the finest h, hu, hv (Morton order, the handle's precision),
  * t, dt and the step count, written to a host buffer.  With host_buf NULL
  * only *used is set to the size needed.  Synchronises. */
@@ -188,6 +197,59 @@ const char* hwfv1_last_error(hwfv1_handle* hd);
 
 /* Free all device memory of the handle. */
 void hwfv1_destroy(hwfv1_handle* hd);
+
+/* ------------------------------------------------------------------------
+ * Learned look-ahead.  The paper's grid adaptation only coarsens from the
+ * finest grid; the regularisation that lets the grid refine ahead of the
+ * flow (children of significant details become significant) is this
+ * library's reading, and it refines one level everywhere.  A small CNN
+ * (3 layers of 3x3 convolutions, 4 -> 16 -> 16 -> 5 channels, ReLU, BF16
+ * weights and activations, FP32 accumulation on the tensor cores) reads the
+ * level-(L-4) coefficients of h, hu, hv, z (each over its s_max) and
+ * predicts, per 16 x 16-cell subtree, the deepest level the next step's
+ * threshold tree will need; children are then added only above that level.
+ * Every audit_K-th step is an exact step with the plain look-ahead.
+ * Parameters are FP32 in the layout w1[16][4][3][3], b1[16], w2[16][16][3][3],
+ * b2[16], w3[5][16][3][3], b3[5] (hwfv1_skipnet_num_params() floats).
+ * ------------------------------------------------------------------------ */
+typedef struct hwfv1_skipnet hwfv1_skipnet;
+
+int32_t hwfv1_skipnet_num_params(void);
+/* New network with seeded He-initialised weights (device memory). */
+hwfv1_status hwfv1_skipnet_create(uint32_t seed, hwfv1_skipnet** out);
+hwfv1_status hwfv1_skipnet_set_params(hwfv1_skipnet* net, const float* host, int64_t n);
+hwfv1_status hwfv1_skipnet_get_params(hwfv1_skipnet* net, float* host, int64_t n);
+/* Logits of nimg images x (device, bf16 bits, [nimg][H][W][4] channels
+ * last) into logits (device, float, [nimg*H*W][16], classes 0..4 valid).
+ * Synchronises; HWFV1_ERR_TIMEOUT if a tensor-core wait ran out. */
+hwfv1_status hwfv1_skipnet_forward(hwfv1_skipnet* net, const uint16_t* x, int32_t nimg, int32_t H, int32_t W,
+                                   float* logits);
+/* Mean softmax cross-entropy (host *loss) and its gradient (host grads,
+ * hwfv1_skipnet_num_params() floats) for labels (device, uint8 per pixel,
+ * classes 0..4).  Synchronises. */
+hwfv1_status hwfv1_skipnet_gradients(hwfv1_skipnet* net, const uint16_t* x, const uint8_t* labels, int32_t nimg,
+                                     int32_t H, int32_t W, double* loss, float* grads);
+/* Adam training over nimg images in minibatches of `batch` images (shuffled
+ * by batch with `seed`) for `epochs`; *last_loss (host) gets the loss of the
+ * last minibatch.  Synchronises. */
+hwfv1_status hwfv1_skipnet_train(hwfv1_skipnet* net, const uint16_t* x, const uint8_t* labels, int32_t nimg,
+                                 int32_t H, int32_t W, int32_t batch, int32_t epochs, float lr, uint32_t seed,
+                                 double* last_loss);
+void hwfv1_skipnet_destroy(hwfv1_skipnet* net);
+
+/* Use `net` (NULL: stop) for the look-ahead of hwfv1_advance: a subtree may
+ * refine only above the smallest level whose predicted cumulative
+ * probability reaches 1 - margin (margin < 0 keeps every level, which equals
+ * the plain method); every audit_K-th step is exact.  Needs L >= 6.  The
+ * network must outlive its use. */
+hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin);
+/* CNN input of the current state (device output, bf16 bits, 4 x 4^(L-4)
+ * values, channels last, row j of subtrees major); call after hwfv1_encode. */
+hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap);
+/* Training label of every subtree for the current state (device output,
+ * uint8 per subtree, row-major): 1 + the deepest level >= L-4 holding a
+ * closed threshold flag, minus (L-4); 0 if none.  Call after hwfv1_encode. */
+hwfv1_status hwfv1_get_labels(hwfv1_handle* hd, uint8_t* out, int64_t cap);
 
 /* ------------------------------------------------------------------------
  * Batched ensembles: many independent domains (each its own problem, its

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "engine_iface.h"
+#include "skipnet.h"
 
 struct hwfv1_handle {
     hwfv1::Engine* eng = nullptr;
@@ -164,6 +165,11 @@ hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax
     HWFV1_CHECK_HANDLE(hd);
     return from_engine(hd, hd->eng->get_stats(num_leaves, smax3));
 }
+hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates, int64_t* wet_updates,
+                                int64_t* kernels_per_step) {
+    HWFV1_CHECK_HANDLE(hd);
+    return from_engine(hd, hd->eng->get_counters(steps, leaf_updates, wet_updates, kernels_per_step));
+}
 hwfv1_status hwfv1_save(hwfv1_handle* hd, void* host_buf, size_t cap, size_t* used) {
     HWFV1_CHECK_HANDLE(hd);
     return from_engine(hd, hd->eng->save(host_buf, cap, used));
@@ -180,6 +186,21 @@ void hwfv1_destroy(hwfv1_handle* hd) {
     if (!hd || hd->borrowed) return;      // member views are freed with their batch
     delete hd->eng;
     delete hd;
+}
+
+hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin) {
+    HWFV1_CHECK_HANDLE(hd);
+    return from_engine(hd, hd->eng->set_skipnet(net ? net->net : nullptr, audit_K, margin));
+}
+hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (!out) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->get_features(out, cap));
+}
+hwfv1_status hwfv1_get_labels(hwfv1_handle* hd, uint8_t* out, int64_t cap) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (!out) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->get_labels(out, cap));
 }
 
 // ---------------------------------------------------------------------------

@@ -216,6 +216,8 @@ struct DevState {
     float rx0f, ry0f;                 // same, float arithmetic
     double thr[kMaxL * 3];            // eps*2^(n-L)*s_max,q for h, qx, qy
     float thrf[kMaxL * 3];            // same, float arithmetic (32-bit path)
+    unsigned long long leaf_updates;  // leaves updated, summed over the steps taken
+    unsigned long long wet_updates;   // of them, leaves that took the full FV1 update
 };
 
 enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };

@@ -9,8 +9,23 @@
 
 #include "engine_iface.h"
 #include "kernels.cuh"
+#include "skipnet.h"
 
 namespace hwfv1 {
+
+// Kernel nodes of a captured graph (memset and copy nodes are not counted).
+inline int64_t count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
 
 template <typename T>
 class EngineT final : public Engine {
@@ -29,6 +44,8 @@ class EngineT final : public Engine {
     }
     ~EngineT() override {
         if (exec_) cudaGraphExecDestroy(exec_);
+        if (exec_learned_) cudaGraphExecDestroy(exec_learned_);
+        skipwork_free(&skw_);
         for (void* p : allocs_) cudaFree(p);
         if (own_stream_) cudaStreamDestroy(stream_);
     }
@@ -136,28 +153,62 @@ class EngineT final : public Engine {
         k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), t_end);
         if (max_steps == 0) return check("advance");
         const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
-        if (use_graph && !exec_) {
-            cudaGraph_t g = nullptr;
-            if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-                return fail(HWFV1_ERR_CUDA, "graph capture begin");
-            launch_step_all();
-            if (cudaStreamEndCapture(stream_, &g) != cudaSuccess)
-                return fail(HWFV1_ERR_CUDA, "graph capture end");
-            cudaError_t e = cudaGraphInstantiate(&exec_, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                exec_ = nullptr;
-                return fail(HWFV1_ERR_CUDA, "graph instantiate");
-            }
-        }
+        if (use_graph && !exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        if (use_graph && skip_ && !exec_learned_ && capture(&exec_learned_, true) != HWFV1_OK)
+            return HWFV1_ERR_CUDA;
         for (int64_t s = 0; s < max_steps; ++s) {
+            // with the learned look-ahead every audit_K-th step is an exact
+            // (plain) step
+            const bool learned = skip_ && (lstep_++ % audit_K_) != 0;
             if (use_graph) {
-                if (cudaGraphLaunch(exec_, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
+                if (cudaGraphLaunch(learned ? exec_learned_ : exec_, stream_) != cudaSuccess)
+                    return fail(HWFV1_ERR_CUDA, "graph launch");
+            } else if (learned) {
+                launch_step_learned();
             } else {
                 launch_step_all();
             }
         }
         return check("advance");
+    }
+
+    hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin) override {
+        if (net && (L_ < 6 || audit_K < 1)) return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead needs L >= 6, K >= 1");
+        skip_ = net;
+        audit_K_ = audit_K < 1 ? 1 : audit_K;
+        margin_ = margin;
+        lstep_ = 0;
+        if (exec_learned_) {
+            cudaGraphExecDestroy(exec_learned_);
+            exec_learned_ = nullptr;
+        }
+        if (!net) return HWFV1_OK;
+        const uint64_t npx = 1ull << (2 * (L_ - 4));
+        if (!feat_ && !alloc(&feat_, npx * 4 * sizeof(__nv_bfloat16))) return oom();
+        if (!phat_ && !alloc(&phat_, npx)) return oom();
+        if (!skipwork_reserve(&skw_, (int64_t)npx)) return oom();
+        // capture both step graphs now (capturing runs nothing), so that the
+        // first advance does not pay for it
+        if (std::getenv("HWFV1_NO_GRAPH") == nullptr) {
+            if (!exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (capture(&exec_learned_, true) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        }
+        return HWFV1_OK;
+    }
+
+    hwfv1_status get_features(uint16_t* out, int64_t cap) override {
+        if (L_ < 6) return fail(HWFV1_ERR_INVALID_SPEC, "features need L >= 6");
+        if (cap < (int64_t)(4ull << (2 * (L_ - 4)))) return fail(HWFV1_ERR_INVALID_SPEC, "features: cap too small");
+        launch_features(reinterpret_cast<__nv_bfloat16*>(out));
+        return check("get_features");
+    }
+
+    hwfv1_status get_labels(uint8_t* out, int64_t cap) override {
+        if (L_ < 6) return fail(HWFV1_ERR_INVALID_SPEC, "labels need L >= 6");
+        if (cap < (int64_t)(1ull << (2 * (L_ - 4)))) return fail(HWFV1_ERR_INVALID_SPEC, "labels: cap too small");
+        const uint32_t n = 1u << (2 * (L_ - 4));
+        k_labels<<<grid_for(n), 256, 0, stream_>>>(Cb_, Cz_, L_, L_ - 4, out);
+        return check("get_labels");
     }
 
     hwfv1_status get_fields(double* h, double* qx, double* qy) override {
@@ -232,6 +283,19 @@ class EngineT final : public Engine {
         cudaMemcpyAsync(st_, &s, sizeof s, cudaMemcpyHostToDevice, stream_);
         k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), s.t_end);
         return check("set_time", true);
+    }
+
+    hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* wu, int64_t* kps) override {
+        if (kps) {
+            if (!exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            *kps = skip_ ? kernels_learned_ : kernels_plain_;
+        }
+        DevState s;
+        if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        if (steps) *steps = s.step;
+        if (lu) *lu = (int64_t)s.leaf_updates;
+        if (wu) *wu = (int64_t)s.wet_updates;
+        return HWFV1_OK;
     }
 
     hwfv1_status get_stats(int64_t* M, double* smax3) override {
@@ -436,6 +500,41 @@ class EngineT final : public Engine {
         launch_fv1();
         launch_decode();
     }
+    void launch_features(__nv_bfloat16* out) {
+        const uint32_t n = 1u << (2 * (L_ - 4));
+        const double* smax_z = reinterpret_cast<const double*>(zaux_ + 8);
+        k_features<T><<<grid_for(n), 256, 0, stream_>>>(
+            f_[0][0], f_[1][0], f_[0][1], f_[1][1], f_[0][2], f_[1][2], z_, st_, smax_z, L_ - 4, out);
+    }
+    // one step with the learned look-ahead in place of R1
+    void launch_step_learned() {
+        launch_encode();
+        launch_features(feat_);
+        const int S = 1 << (L_ - 4);
+        skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
+        k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+        k_flag_learned<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
+                                                              close(), st_);
+        launch_traverse();
+        launch_fv1();
+        launch_decode();
+    }
+    hwfv1_status capture(cudaGraphExec_t* out, bool learned) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(HWFV1_ERR_CUDA, "graph capture begin");
+        if (learned) launch_step_learned();
+        else launch_step_all();
+        if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph capture end");
+        (learned ? kernels_learned_ : kernels_plain_) = count_kernel_nodes(g);
+        const cudaError_t e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            *out = nullptr;
+            return fail(HWFV1_ERR_CUDA, "graph instantiate");
+        }
+        return HWFV1_OK;
+    }
     FinishArgs fin_args() const {
         FinishArgs a;
         a.inflow_t = it_d_;
@@ -514,6 +613,16 @@ class EngineT final : public Engine {
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
+    // learned look-ahead
+    SkipNet* skip_ = nullptr;
+    int audit_K_ = 10;
+    float margin_ = 0.02f;
+    int64_t lstep_ = 0;
+    SkipWork skw_;
+    __nv_bfloat16* feat_ = nullptr;
+    uint8_t* phat_ = nullptr;
+    cudaGraphExec_t exec_learned_ = nullptr;
+    int64_t kernels_plain_ = 0, kernels_learned_ = 0;   // kernel nodes of the captured step graphs
 };
 
 template <>

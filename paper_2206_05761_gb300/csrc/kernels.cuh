@@ -9,6 +9,8 @@
 // library is compiled with --fmad=false); where a cheaper form is used it
 // is equal for every finite input (noted at the spot).
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace hwfv1 {
@@ -1131,6 +1133,8 @@ __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
             !isfinite(st->smax[2]))
             st->err |= kErrNonFinite;
         st->step += 1;
+        st->leaf_updates += st->M;
+        st->wet_updates += st->nwet;
         st->cur ^= 1u;
     }
     __syncthreads();
@@ -1289,6 +1293,133 @@ static __global__ void k_rm_to_morton_cur(const double* __restrict__ src, T* dst
          m += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t i = compact16((uint32_t)m), j = compact16((uint32_t)(m >> 1));
         dst[m] = (T)src[((uint64_t)j << L) + i];
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Learned look-ahead (subtree CNN).  A subtree is one cell of level
+// Ls = L - 4 (16 x 16 finest cells).
+// ---------------------------------------------------------------------------
+
+// CNN input: the level-Ls coefficients of h, qx, qy (current buffer) and z,
+// each over its s_max, as bf16 channels-last pixels (row j, column i).
+template <typename T>
+static __global__ void k_features(const T* h0, const T* h1, const T* qx0, const T* qx1, const T* qy0,
+                                  const T* qy1, const T* z, const DevState* st, const double* smax_z, int Ls,
+                                  __nv_bfloat16* out) {
+    const bool c1 = st->cur != 0;
+    const T* h = c1 ? h1 : h0;
+    const T* qx = c1 ? qx1 : qx0;
+    const T* qy = c1 ? qy1 : qy0;
+    const uint32_t n = 1u << (2 * Ls), S = 1u << Ls;
+    const uint64_t o = lvl_off(Ls);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const uint32_t pix = compact16(c >> 1) * S + compact16(c);
+        out[4 * pix + 0] = __float2bfloat16((float)((double)h[o + c] / st->smax[0]));
+        out[4 * pix + 1] = __float2bfloat16((float)((double)qx[o + c] / st->smax[1]));
+        out[4 * pix + 2] = __float2bfloat16((float)((double)qy[o + c] / st->smax[2]));
+        out[4 * pix + 3] = __float2bfloat16((float)((double)z[o + c] / *smax_z));
+    }
+}
+
+// Training label of every subtree: 1 + the deepest level (>= Ls) holding a
+// closed threshold flag (C | Cz) in the subtree, minus Ls; 0 if none.  One
+// byte per pixel, row-major.
+static __global__ void k_labels(const uint32_t* __restrict__ Cb, const uint32_t* __restrict__ Cz, int L, int Ls,
+                                uint8_t* __restrict__ out) {
+    const uint32_t n = 1u << (2 * Ls), S = 1u << Ls;
+    for (uint32_t sub = blockIdx.x * blockDim.x + threadIdx.x; sub < n; sub += gridDim.x * blockDim.x) {
+        int deepest = -1;
+        for (int lv = Ls; lv < L; ++lv) {
+            const uint32_t cnt = 1u << (2 * (lv - Ls)), first = sub * cnt;
+            bool any = false;
+            if (cnt < 32u) {
+                const uint32_t w = word_off(lv) + (first >> 5);
+                const uint32_t m = ((Cb[w] | Cz[w]) >> (first & 31u)) & ((1u << cnt) - 1u);
+                any = m != 0u;
+            } else {
+                for (uint32_t k = 0; k < cnt / 32u && !any; ++k) {
+                    const uint32_t w = word_off(lv) + (first >> 5) + k;
+                    any = (Cb[w] | Cz[w]) != 0u;
+                }
+            }
+            if (any) deepest = lv;
+        }
+        const int lab = deepest < 0 ? 0 : deepest + 1 - Ls;
+        out[compact16(sub >> 1) * S + compact16(sub)] = (uint8_t)lab;
+    }
+}
+
+// Predicted deepest level per subtree (Morton order): the smallest class
+// whose cumulative probability reaches 1 - margin (so levels are only cut
+// where the network is confident); margin < 0 keeps every level (L).
+static __global__ void k_predict(const float* __restrict__ logits, int Ls, float margin, uint8_t* __restrict__ phat) {
+    const uint32_t n = 1u << (2 * Ls), S = 1u << Ls;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int cls = 4;
+        if (margin >= 0.f) {
+            const uint32_t pix = compact16(c >> 1) * S + compact16(c);
+            float z[5], m = -INFINITY;
+            for (int o = 0; o < 5; ++o) {
+                z[o] = logits[(size_t)pix * 16 + o];
+                m = fmaxf(m, z[o]);
+            }
+            float se = 0.f;
+            for (int o = 0; o < 5; ++o) se += expf(z[o] - m);
+            float cum = 0.f;
+            for (int o = 0; o < 4; ++o) {
+                cum += expf(z[o] - m) / se;
+                if (cum >= 1.f - margin) {
+                    cls = o;
+                    break;
+                }
+            }
+        }
+        phat[c] = (uint8_t)(Ls + cls);
+    }
+}
+
+// Regularised significance with the learned look-ahead: the closed
+// threshold tree is kept, and a child of a significant detail is added only
+// while its level stays shallower than its subtree's predicted level:
+//   S(n,c) = base(n,c) | [T|Tz](n-1, c/4) & (n <= Ls or n < phat(subtree))
+// base = C | Cz with closure, T | Tz without.  With phat = L everywhere this
+// is exactly k_flag.
+static __global__ void k_flag_learned(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
+                                      const uint32_t* __restrict__ Tz, const uint32_t* __restrict__ Cz,
+                                      uint32_t* __restrict__ Sb, const uint8_t* __restrict__ phat, int L, int Ls,
+                                      int predict, int close, const DevState* st) {
+    if (st && !st->active) return;
+    const uint32_t total = bits_words(L);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+        int n = 0;
+        while (n + 1 < L && word_off(n + 1) <= w) ++n;
+        const uint32_t lw = w - word_off(n);
+        uint32_t s = close ? (Cb[w] | Cz[w]) : (Tb[w] | Tz[w]);
+        if (predict && n >= 1) {
+            uint32_t pb;
+            if (n >= 3) {
+                const uint32_t pw = word_off(n - 1) + (lw >> 2);
+                pb = expand4x8((Tb[pw] | Tz[pw]) >> (8u * (lw & 3u)));
+            } else if (n == 2) {
+                pb = expand4x8((Tb[word_off(1)] | Tz[word_off(1)]) & 0xFu);
+            } else {
+                pb = ((Tb[word_off(0)] | Tz[word_off(0)]) & 1u) ? 0xFu : 0u;
+            }
+            if (n > Ls) {
+                const int sh = 2 * (n - Ls);
+                uint32_t allow = 0u;
+                for (uint32_t b = 0; b < 32u; ++b) {
+                    const uint32_t c = 32u * lw + b;
+                    if (n < (int)phat[c >> sh]) allow |= 1u << b;
+                }
+                pb &= allow;
+            }
+            s |= pb;
+        }
+        if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
+        Sb[w] = s;
     }
 }
 

@@ -75,6 +75,7 @@ def lib():
                                          C.POINTER(C.c_int64)]
             L.hwfv1_set_time.argtypes = [_H, C.c_double, C.c_double]
             L.hwfv1_get_stats.argtypes = [_H, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+            L.hwfv1_get_counters.argtypes = [_H] + [C.POINTER(C.c_int64)] * 4
             L.hwfv1_save.argtypes = [_H, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
             L.hwfv1_load.argtypes = [_H, C.c_void_p, C.c_size_t]
             L.hwfv1_last_error.argtypes = [_H]
@@ -92,6 +93,20 @@ def lib():
             L.hwfv1_batch_last_error.restype = C.c_char_p
             L.hwfv1_batch_destroy.argtypes = [C.c_void_p]
             L.hwfv1_batch_destroy.restype = None
+            L.hwfv1_skipnet_num_params.restype = C.c_int32
+            L.hwfv1_skipnet_create.argtypes = [C.c_uint32, C.POINTER(C.c_void_p)]
+            L.hwfv1_skipnet_set_params.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int64]
+            L.hwfv1_skipnet_get_params.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int64]
+            L.hwfv1_skipnet_forward.argtypes = [C.c_void_p, _dp, C.c_int32, C.c_int32, C.c_int32, _dp]
+            L.hwfv1_skipnet_gradients.argtypes = [C.c_void_p, _dp, _dp, C.c_int32, C.c_int32, C.c_int32,
+                                                  C.POINTER(C.c_double), C.POINTER(C.c_float)]
+            L.hwfv1_skipnet_train.argtypes = [C.c_void_p, _dp, _dp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                              C.c_int32, C.c_float, C.c_uint32, C.POINTER(C.c_double)]
+            L.hwfv1_skipnet_destroy.argtypes = [C.c_void_p]
+            L.hwfv1_skipnet_destroy.restype = None
+            L.hwfv1_set_skipnet.argtypes = [_H, C.c_void_p, C.c_int32, C.c_float]
+            L.hwfv1_get_features.argtypes = [_H, _dp, C.c_int64]
+            L.hwfv1_get_labels.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_destroy.argtypes = [_H]
             L.hwfv1_destroy.restype = None
             _lib = L
@@ -102,10 +117,14 @@ def exported_symbols():
     return ["hwfv1_init", "hwfv1_encode", "hwfv1_flag", "hwfv1_traverse", "hwfv1_step",
             "hwfv1_decode", "hwfv1_advance", "hwfv1_get_fields", "hwfv1_set_fields",
             "hwfv1_get_leaves", "hwfv1_get_flags", "hwfv1_get_level", "hwfv1_get_time",
-            "hwfv1_set_time", "hwfv1_get_stats", "hwfv1_save", "hwfv1_load",
+            "hwfv1_set_time", "hwfv1_get_stats", "hwfv1_get_counters", "hwfv1_save", "hwfv1_load",
             "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version", "hwfv1_traverse_noalloc",
             "hwfv1_batch_init", "hwfv1_batch_advance", "hwfv1_batch_autotune", "hwfv1_batch_member",
-            "hwfv1_batch_launches_per_step", "hwfv1_batch_last_error", "hwfv1_batch_destroy"]
+            "hwfv1_batch_launches_per_step", "hwfv1_batch_last_error", "hwfv1_batch_destroy",
+            "hwfv1_skipnet_num_params", "hwfv1_skipnet_create", "hwfv1_skipnet_set_params",
+            "hwfv1_skipnet_get_params", "hwfv1_skipnet_forward", "hwfv1_skipnet_gradients",
+            "hwfv1_skipnet_train", "hwfv1_skipnet_destroy", "hwfv1_set_skipnet", "hwfv1_get_features",
+            "hwfv1_get_labels"]
 
 
 def _check(st, what, hd=None):
@@ -232,6 +251,13 @@ def hwfv1_get_stats(hd):
     return m.value, list(sm)
 
 
+def hwfv1_get_counters(hd):
+    """(steps, leaf_updates, wet_updates, kernels_per_step)."""
+    v = [C.c_int64() for _ in range(4)]
+    _check(lib().hwfv1_get_counters(hd, *[C.byref(x) for x in v]), "hwfv1_get_counters", hd)
+    return tuple(x.value for x in v)
+
+
 def hwfv1_save(hd):
     used = C.c_size_t()
     _check(lib().hwfv1_save(hd, None, 0, C.byref(used)), "hwfv1_save", hd)
@@ -328,4 +354,71 @@ def hwfv1_batch_last_error(bt):
 
 def hwfv1_batch_destroy(bt):
     lib().hwfv1_batch_destroy(bt)
+
+
+# ---------------------------------------------------------------------------
+# Learned look-ahead (subtree CNN)
+# ---------------------------------------------------------------------------
+
+def hwfv1_skipnet_num_params():
+    return int(lib().hwfv1_skipnet_num_params())
+
+
+def hwfv1_skipnet_create(seed=0):
+    net = C.c_void_p()
+    _check(lib().hwfv1_skipnet_create(int(seed), C.byref(net)), "hwfv1_skipnet_create")
+    return net
+
+
+def hwfv1_skipnet_set_params(net, params):
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().hwfv1_skipnet_set_params(net, a.ctypes.data_as(C.POINTER(C.c_float)), a.size),
+           "hwfv1_skipnet_set_params")
+
+
+def hwfv1_skipnet_get_params(net):
+    import numpy as np
+    a = np.empty(hwfv1_skipnet_num_params(), dtype=np.float32)
+    _check(lib().hwfv1_skipnet_get_params(net, a.ctypes.data_as(C.POINTER(C.c_float)), a.size),
+           "hwfv1_skipnet_get_params")
+    return a
+
+
+def hwfv1_skipnet_forward(net, x, nimg, H, W, logits):
+    """x: CUDA int16/bfloat16 tensor [nimg*H*W*4]; logits: CUDA float32 [nimg*H*W*16]."""
+    _check(lib().hwfv1_skipnet_forward(net, _ptr(x), int(nimg), int(H), int(W), _ptr(logits)),
+           "hwfv1_skipnet_forward")
+
+
+def hwfv1_skipnet_gradients(net, x, labels, nimg, H, W):
+    import numpy as np
+    g = np.empty(hwfv1_skipnet_num_params(), dtype=np.float32)
+    loss = C.c_double()
+    _check(lib().hwfv1_skipnet_gradients(net, _ptr(x), _ptr(labels), int(nimg), int(H), int(W), C.byref(loss),
+                                         g.ctypes.data_as(C.POINTER(C.c_float))), "hwfv1_skipnet_gradients")
+    return loss.value, g
+
+
+def hwfv1_skipnet_train(net, x, labels, nimg, H, W, batch, epochs, lr, seed=0):
+    loss = C.c_double()
+    _check(lib().hwfv1_skipnet_train(net, _ptr(x), _ptr(labels), int(nimg), int(H), int(W), int(batch),
+                                     int(epochs), float(lr), int(seed), C.byref(loss)), "hwfv1_skipnet_train")
+    return loss.value
+
+
+def hwfv1_skipnet_destroy(net):
+    lib().hwfv1_skipnet_destroy(net)
+
+
+def hwfv1_set_skipnet(hd, net, audit_K=10, margin=0.02):
+    _check(lib().hwfv1_set_skipnet(hd, net, int(audit_K), float(margin)), "hwfv1_set_skipnet", hd)
+
+
+def hwfv1_get_features(hd, out):
+    _check(lib().hwfv1_get_features(hd, _ptr(out), out.numel()), "hwfv1_get_features", hd)
+
+
+def hwfv1_get_labels(hd, out):
+    _check(lib().hwfv1_get_labels(hd, _ptr(out), out.numel()), "hwfv1_get_labels", hd)
 

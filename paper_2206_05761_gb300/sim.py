@@ -89,11 +89,38 @@ class Simulation:
     def stats(self):
         return H.hwfv1_get_stats(self.hd)
 
+    def counters(self):
+        """(steps, leaf_updates, wet_updates, kernels_per_step)."""
+        return H.hwfv1_get_counters(self.hd)
+
     def save(self):
         return H.hwfv1_save(self.hd)
 
     def load(self, blob):
         H.hwfv1_load(self.hd, blob)
+
+    def features(self):
+        """CNN input of the current state (call after encode): float32
+        array [S, S, 4] of the bf16 values."""
+        S = 1 << (self.L - 4)
+        out = torch.empty(S * S * 4, dtype=torch.bfloat16, device=self.dev)
+        H.hwfv1_get_features(self.hd, out)
+        return out.float().cpu().numpy().reshape(S, S, 4)
+
+    def features_dev(self, out):
+        H.hwfv1_get_features(self.hd, out)
+
+    def labels(self):
+        S = 1 << (self.L - 4)
+        out = torch.empty(S * S, dtype=torch.uint8, device=self.dev)
+        H.hwfv1_get_labels(self.hd, out)
+        return out.cpu().numpy().reshape(S, S)
+
+    def labels_dev(self, out):
+        H.hwfv1_get_labels(self.hd, out)
+
+    def set_skipnet(self, net, audit_K=10, margin=0.02):
+        H.hwfv1_set_skipnet(self.hd, net, audit_K, margin)
 
     def close(self):
         if self.hd is not None:

@@ -89,6 +89,23 @@ def circular_dam_break(L=6, eps=1e-3, radius=0.25, h_in=2.0, h_out=1.0):
     return p, _fields(p, eta, z)
 
 
+def columns_dam_break(L=8, eps=1e-3, seed=0, k=3, h_out=1.0):
+    """k seeded circular water columns collapsing on a flat bed: centres
+    U[0.2, 0.8]^2, radii U[0.05, 0.15], depths U[1.3, 2.0] over h_out, at rest,
+    closed walls, no friction.  Only the moving flow sets the refinement
+    (the bed has no details)."""
+    p = problem(L, eps=eps, bc=("closed",) * 4)
+    rng = np.random.default_rng(seed)
+    x, y = centres(p)
+    eta = np.full_like(x, h_out)
+    for _ in range(k):
+        cx, cy = rng.uniform(0.2, 0.8, size=2)
+        r = rng.uniform(0.05, 0.15)
+        hin = rng.uniform(1.3, 2.0)
+        eta = np.where((x - cx) ** 2 + (y - cy) ** 2 < r * r, np.maximum(eta, hin), eta)
+    return p, _fields(p, eta, np.zeros_like(x))
+
+
 def bumpy_dam_break(L=10, eps=1e-3, seed=2, eta_up=1.0, eta_down=0.5, dam_x=0.3):
     """Dam-break over 8 seeded Gaussian humps on the unit square: free
     surface eta_up behind x = dam_x, eta_down elsewhere, closed walls; humps

@@ -1,0 +1,68 @@
+"""Learned look-ahead end to end: training data from the GPU path, training
+on the tensor cores, then a held-out run with the network in
+the time loop against plain HWFV1 (regularisation by one-level prediction)
+and against uniform FV1 (eps = 0).  Water columns collapsing on a flat bed:
+the refinement follows the moving flow alone, which is where a look-ahead
+tighter than one blanket level can cut leaves."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+L = 8
+
+
+def _run(p, f, t_end, net=None, audit_K=10, margin=0.02, max_steps=20000):
+    from paper_2206_05761_gb300.sim import Simulation
+    sim = Simulation(p, f)
+    if net is not None:
+        sim.set_skipnet(net, audit_K=audit_K, margin=margin)
+    ms = []
+    while sim.time()[0] < t_end and len(ms) < max_steps:
+        sim.advance(t_end=t_end, max_steps=1)
+        ms.append(sim.stats()[0])
+    out = sim.fields(), float(np.mean(ms)), len(ms)
+    sim.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    from paper_2206_05761_gb300 import learn
+    cases = [synth.columns_dam_break(L=L, eps=1e-3, seed=s) for s in range(100, 108)]
+    x, y = learn.collect(cases, steps=600, every=10)
+    x, y = learn.augment(x, y)
+    net, loss = learn.train(x, y, epochs=15, batch=32, lr=3e-3, seed=1)
+    print("training: %d images of %dx%d, last batch loss %.4f" % (x.shape[0], x.shape[1], x.shape[2], loss))
+    yield net, learn
+    Hh.hwfv1_skipnet_destroy(net)
+
+
+def test_network_predicts_held_out_levels(trained):
+    net, learn = trained
+    x, y = learn.collect([synth.columns_dam_break(L=L, eps=1e-3, seed=200)], steps=600, every=20)
+    under = learn.under_prediction_rate(net, x, y, 0.02)
+    exact = float((learn.predict_levels(net, x, 0.0) == y).float().mean())
+    print("held out: %.4f of subtrees under-predicted at margin 0.02; %.3f exact at margin 0" % (under, exact))
+    assert under < 0.05
+
+
+def test_learned_run_uses_fewer_leaves_at_bounded_cost(trained):
+    net, _ = trained
+    t_end = 0.25
+    p, f = synth.columns_dam_break(L=L, eps=1e-3, seed=200)
+    fp, mp, tp = _run(p, f, t_end)
+    fl, ml, tl = _run(p, f, t_end, net=net)
+    pu, fu = synth.columns_dam_break(L=L, eps=0.0, seed=200)
+    fu_, mu, tu = _run(pu, fu, t_end)
+    cell = 1.0 / (1 << (2 * L))
+    d_lp = np.abs(fl["h"] - fp["h"]).sum() * cell
+    d_pu = np.abs(fp["h"] - fu_["h"]).sum() * cell
+    print("mean leaves: uniform %.0f, plain %.0f, learned %.0f (%.3f of plain); steps: %d %d %d"
+          % (mu, mp, ml, ml / mp, tu, tp, tl))
+    print("L1 depth: |learned - plain| = %.3e, |plain - uniform| = %.3e" % (d_lp, d_pu))
+    assert ml < mp
+    assert d_lp <= 2.0 * d_pu + 1e-12

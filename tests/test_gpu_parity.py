@@ -178,6 +178,22 @@ def test_trajectory_circular_dam_break_100_steps():
     sim.close()
 
 
+def test_counters_sum_the_leaf_updates():
+    # the running leaf-update count equals the oracle's sum of M over the
+    # same steps; the captured step graph launches a positive, fixed number
+    # of kernels
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    sim.advance(max_steps=25)
+    for _ in range(25):
+        ref.step()
+    steps, lu, wu, kps = sim.counters()
+    assert steps == 25 and lu == ref.leaf_updates
+    assert 0 < wu <= lu and 0 < kps < 64
+    sim.close()
+
+
 def test_advance_stops_at_t_end():
     p, f = synth.circular_dam_break(L=5, eps=1e-3)
     sim = _sim(p, f)

@@ -1,0 +1,165 @@
+"""The subtree CNN on the tensor cores against its CPU oracle (forward values
+and gradients), its training, the features and labels the simulation hands
+it, and the learned look-ahead in the time loop."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    import torch
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def _flat(params):
+    return np.concatenate([p.reshape(-1) for p in params]).astype(np.float32)
+
+
+def _unflat(flat, like):
+    out, k = [], 0
+    for p in like:
+        out.append(flat[k:k + p.size].reshape(p.shape).astype(np.float64))
+        k += p.size
+    return out
+
+
+def _setup(seed, nimg=3, H=9, W=13):
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    rng = np.random.default_rng(seed)
+    params = cnn.init_params(rng)
+    params[1] = 0.1 * rng.standard_normal(16)
+    params[3] = 0.1 * rng.standard_normal(16)
+    params[5] = 0.1 * rng.standard_normal(5)
+    params = [_bf16(p) if p.ndim == 4 else p for p in params]   # the GPU uses bf16 weights
+    x = _bf16(rng.standard_normal((nimg, H, W, 4)))
+    labels = rng.integers(0, 5, size=(nimg, H, W)).astype(np.uint8)
+    net = Hh.hwfv1_skipnet_create(seed)
+    Hh.hwfv1_skipnet_set_params(net, _flat(params))
+    xd = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).reshape(-1).cuda()
+    ld = torch.as_tensor(labels).reshape(-1).cuda()
+    return net, params, x, labels, xd, ld
+
+
+def test_forward_matches_oracle():
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    net, params, x, labels, xd, _ = _setup(1)
+    nimg, H, W, _ = x.shape
+    logits = torch.empty(nimg * H * W * 16, dtype=torch.float32, device="cuda")
+    Hh.hwfv1_skipnet_forward(net, xd, nimg, H, W, logits)
+    got = logits.cpu().numpy().reshape(nimg, H, W, 16)[..., :5].transpose(0, 3, 1, 2)
+    ref, _ = cnn.forward(params, x.transpose(0, 3, 1, 2))
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print("forward: max error / max |logit| = %.3g" % err)
+    assert err < 2e-2
+    Hh.hwfv1_skipnet_destroy(net)
+
+
+def test_gradients_match_oracle():
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    net, params, x, labels, xd, ld = _setup(2)
+    nimg, H, W, _ = x.shape
+    loss, g = Hh.hwfv1_skipnet_gradients(net, xd, ld, nimg, H, W)
+    logits, cache = cnn.forward(params, x.transpose(0, 3, 1, 2))
+    ref_loss, dl = cnn.loss_and_dlogits(logits, labels)
+    ref = cnn.backward(params, cache, dl)
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss
+    for name, a, b in zip(("w1", "b1", "w2", "b2", "w3", "b3"), _unflat(g, ref), ref):
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print("gradient %s: relative error %.3g" % (name, rel))
+        assert rel < 5e-2, name
+    Hh.hwfv1_skipnet_destroy(net)
+
+
+def test_training_reduces_loss():
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    rng = np.random.default_rng(3)
+    nimg, H, W = 64, 16, 16
+    x = rng.standard_normal((nimg, H, W, 4)).astype(np.float32)
+    # a label the network can learn: the level of a local average of channel 0
+    sm = x[..., 0].copy()
+    for _ in range(2):
+        sm = (sm + np.roll(sm, 1, 1) + np.roll(sm, -1, 1) + np.roll(sm, 1, 2) + np.roll(sm, -1, 2)) / 5.0
+    labels = np.clip(np.floor((sm / sm.std() + 2.5)), 0, 4).astype(np.uint8)
+    xd = torch.as_tensor(x).to(torch.bfloat16).reshape(-1).cuda()
+    ld = torch.as_tensor(labels).reshape(-1).cuda()
+    net = Hh.hwfv1_skipnet_create(7)
+    l0, _ = Hh.hwfv1_skipnet_gradients(net, xd, ld, nimg, H, W)
+    Hh.hwfv1_skipnet_train(net, xd, ld, nimg, H, W, batch=8, epochs=40, lr=3e-3, seed=1)
+    l1, _ = Hh.hwfv1_skipnet_gradients(net, xd, ld, nimg, H, W)
+    print("training loss %.4f -> %.4f" % (l0, l1))
+    assert l1 < 0.6 * l0
+    Hh.hwfv1_skipnet_destroy(net)
+
+
+def _closure_labels(T, L):
+    """Training labels from the oracle's threshold flags (row-major per level):
+    close the flags upward and take, per level-(L-4) subtree, 1 + the deepest
+    flagged level, minus (L-4)."""
+    Ls = L - 4
+    C = [None] * L
+    for n in range(L - 1, -1, -1):
+        s = 1 << n
+        t = T[oracle.level_start(n): oracle.level_start(n) + s * s].reshape(s, s).astype(bool)
+        if n + 1 < L:
+            ch = C[n + 1]
+            t = t | ch[0::2, 0::2] | ch[1::2, 0::2] | ch[0::2, 1::2] | ch[1::2, 1::2]
+        C[n] = t
+    S = 1 << Ls
+    lab = np.zeros((S, S), np.uint8)
+    for n in range(Ls, L):
+        w = 1 << (n - Ls)
+        blk = C[n].reshape(S, w, S, w).any(axis=(1, 3))
+        lab[blk] = n + 1 - Ls
+    return lab
+
+
+def test_features_and_labels_match_oracle():
+    import torch
+    from paper_2206_05761_gb300.sim import Simulation
+    L, Ls = 7, 3
+    p, f = synth.bumpy_dam_break(L=L, eps=1e-3, seed=5)
+    sim = Simulation(p, f)
+    ref = oracle.State(p, f)
+    for _ in range(4):
+        sim.step()
+        ref.step()
+    # features: level-Ls scaling coefficients of the current state over s_max
+    s = 1 << Ls
+    exp = np.zeros((s, s, 4))
+    for q, fine in enumerate((ref.h, ref.qx, ref.qy, ref.z)):
+        hier, _ = oracle.encode(L, fine)
+        exp[..., q] = oracle.level(hier, Ls) / oracle.smax(L, fine)
+    exp_bf = torch.as_tensor(exp.astype(np.float32)).to(torch.bfloat16).float().numpy()
+    res = ref.step(want=("T",))
+    sim.encode()
+    sim.flag()
+    assert np.array_equal(sim.features(), exp_bf)
+    assert np.array_equal(sim.labels(), _closure_labels(res["T"], L))
+    sim.close()
+
+
+def test_learned_mode_with_gate_open_equals_plain():
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    from paper_2206_05761_gb300.sim import Simulation
+    p, f = synth.bumpy_dam_break(L=7, eps=1e-3, seed=6)
+    a = Simulation(p, f)
+    b = Simulation(p, f)
+    net = Hh.hwfv1_skipnet_create(3)
+    b.set_skipnet(net, audit_K=4, margin=-1.0)
+    a.advance(max_steps=15)
+    b.advance(max_steps=15)
+    ga, gb = a.fields(), b.fields()
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k])
+    assert np.array_equal(a.leaves(), b.leaves())
+    a.close()
+    b.close()
+    Hh.hwfv1_skipnet_destroy(net)
