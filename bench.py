@@ -31,12 +31,14 @@ UNIT = "steps/s"
 def parse():
     a = argparse.ArgumentParser()
     a.add_argument("--gpus", type=int, default=1)
-    a.add_argument("--steps", type=int, default=200)
+    a.add_argument("--steps", type=int, default=2000)
     a.add_argument("--warmup", type=int, default=20)
     a.add_argument("--impl", default="ours", choices=["ours", "reference"])
     a.add_argument("--precision", type=int, default=64, choices=[64, 32])
     a.add_argument("--L", type=int, default=12)
-    a.add_argument("--spinup", type=int, default=200, help="untimed steps before warm-up")
+    a.add_argument("--t-spin", type=float, default=1800.0,
+                   help="simulated seconds run before the timed window (the hydrograph peak)")
+    a.add_argument("--t-full", type=float, default=3600.0, help="end of the whole-run measurement")
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--no-ensemble", action="store_true")
     a.add_argument("--no-learned", action="store_true")
@@ -52,7 +54,9 @@ def workload(L):
 def config_dict(args, extra=None):
     d = {"workload": "terrain_flood", "L": args.L, "finest_cells": 1 << (2 * args.L),
          "domain_m": 10000.0, "eps": 1e-3, "manning_n": 0.03, "inflow_peak_m3s": 500.0,
-         "precision": args.precision, "spinup_steps": args.spinup,
+         "precision": args.precision, "simulated_s": 3600.0,
+         "window": "K steps from the state at t=%.0f s (hydrograph peak), reached from the dry "
+                   "start at t=0 by the GPU path" % args.t_spin,
          "l2_policy": "state (>1 GB) larger than L2; no flush",
          "parallelism": "replicas" if args.gpus > 1 else "single"}
     if extra:
@@ -77,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -134,31 +138,78 @@ def roofline_terms(L, M, precision):
     }
 
 
+def advance_to(sim, t_end, chunk=2000):
+    """Advance to t_end in chunks sized from the current dt (each chunk ends
+    with one host read of the time, so no idle step is launched past t_end)."""
+    while True:
+        t, dt, _ = sim.time()
+        if t >= t_end:
+            return
+        est = int((t_end - t) / dt) + 1
+        sim.advance(t_end=t_end, max_steps=max(1, min(chunk, est)))
+
+
+def spin_up(args, stream):
+    """The workload from t = 0: the state at t_spin (host float64 arrays,
+    time, dt) and, run on to t_full, the whole-run statistics."""
+    import torch
+    from paper_2206_05761_gb300.sim import Simulation
+    p, f = workload(args.L)
+    sim = Simulation(p, f, args.precision, stream=stream)
+    sim.counters()                               # captures the step graph
+    out = {}
+    halves = []
+    for t_end in (args.t_spin, args.t_full):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0 = sim.counters()
+        e0.record(stream)
+        advance_to(sim, t_end)
+        e1.record(stream)
+        stream.synchronize()
+        c1 = sim.counters()
+        halves.append((e0.elapsed_time(e1), [x1 - x0 for x0, x1 in zip(c0, c1)]))
+        if not out:
+            t, dt, n = sim.time()
+            out = {"fields": sim.fields(), "t": t, "dt": dt, "steps": n, "z": f["z"]}
+    ms = sum(h[0] for h in halves)
+    tot = [sum(h[1][i] for h in halves) for i in range(4)]
+    out["full_run"] = {
+        "t_end_s": args.t_full, "steps": tot[0], "device_s": ms / 1e3,
+        "steps_per_s": tot[0] / (ms / 1e3), "mean_leaves": tot[1] / max(tot[0], 1),
+        "active_fraction": tot[2] / max(tot[1], 1), "wet_fraction": tot[3] / max(tot[1], 1),
+        "note": "t = 0 to t_end_s in one run, host reads the time every <= 2000 steps"}
+    sim.close()
+    return p, out
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
     from paper_2206_05761_gb300 import hwfv1 as H
 
     torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
-    p, f = workload(args.L)
-    N = 1 << (2 * args.L)
     stream = torch.cuda.Stream()
     dev = torch.device("cuda")
+    p, snap = spin_up(args, stream)
+    N = 1 << (2 * args.L)
+    t_s, dt_s = snap["t"], snap["dt"]
+    state = {"z": snap["z"], **snap["fields"]}
 
-    # ---- end-to-end through the C ABI with host buffers -----------------
-    host = {k: torch.from_numpy(np.ascontiguousarray(f[k]).reshape(-1)).pin_memory()
+    # ---- end-to-end through the C ABI with host buffers: the state at t_spin
+    # from pinned host memory -> init -> K steps -> fields back to the host
+    host = {k: torch.from_numpy(np.ascontiguousarray(state[k]).reshape(-1)).pin_memory()
             for k in ("z", "h", "qx", "qy")}
     outs = {k: torch.empty(N, dtype=torch.float64).pin_memory() for k in ("h", "qx", "qy")}
     dbufs = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("z", "h", "qx", "qy")}
     spec = H.make_problem(p, args.precision)
-    e2e_steps = args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for k in dbufs:
             dbufs[k].copy_(host[k], non_blocking=True)
     hd = H.hwfv1_init(spec, dbufs["z"], dbufs["h"], dbufs["qx"], dbufs["qy"], stream)
-    H.hwfv1_advance(hd, float("inf"), args.spinup + e2e_steps)
+    H.hwfv1_set_time(hd, t_s, dt_s)
+    H.hwfv1_advance(hd, float("inf"), args.steps)
     H.hwfv1_get_fields(hd, dbufs["h"], dbufs["qx"], dbufs["qy"])
     with torch.cuda.stream(stream):
         for k in outs:
@@ -166,16 +217,14 @@ def run_ours(args, rank, world):
     stream.synchronize()
     t_e2e = time.perf_counter() - t0
     H.hwfv1_destroy(hd)
-    e2e_total_steps = args.spinup + e2e_steps
 
-    # ---- device-timed steps (fresh start from the initial fields) --------
+    # ---- device-timed steps from the same state, resident in HBM ----------
     with torch.cuda.stream(stream):
         for k in dbufs:
             dbufs[k].copy_(host[k], non_blocking=True)
     stream.synchronize()
     hd = H.hwfv1_init(spec, dbufs["z"], dbufs["h"], dbufs["qx"], dbufs["qy"], stream)
-    if args.spinup:
-        H.hwfv1_advance(hd, float("inf"), args.spinup)
+    H.hwfv1_set_time(hd, t_s, dt_s)
     H.hwfv1_advance(hd, float("inf"), max(args.warmup, 3))
     stream.synchronize()
     # per-phase timing on the library's stream (CUDA events)
@@ -202,23 +251,25 @@ def run_ours(args, rank, world):
     clk = ClockSampler(torch.cuda.current_device())
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # profiler range = the timed region (for ncu --profile-from-start off)
+    torch.cuda.profiler.start()
     with torch.cuda.stream(stream):
         e0.record(stream)
         H.hwfv1_advance(hd, float("inf"), args.steps)
         e1.record(stream)
     stream.synchronize()
+    torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     t_now, dt_now, nsteps = H.hwfv1_get_time(hd)
-    M_last, smax = H.hwfv1_get_stats(hd)
     c1 = H.hwfv1_get_counters(hd)
     H.hwfv1_destroy(hd)
     ph = {k: statistics.median(v) for k, v in phases.items()}
-    return dict(ms=ms, e2e_s=t_e2e, e2e_steps=e2e_total_steps, phases_ms=ph,
-                M_mean=float(sum(Ms) / len(Ms)), M_last=M_last, t=t_now, dt=dt_now,
-                clocks=clocks, N=N, timed_steps=c1[0] - c0[0], timed_leaf_updates=c1[1] - c0[1],
-                timed_wet_updates=c1[2] - c0[2], kernels_per_step=c1[3])
+    return dict(ms=ms, e2e_s=t_e2e, phases_ms=ph, M_mean=float(sum(Ms) / len(Ms)), t=t_now, dt=dt_now,
+                t_start=t_s, dt_start=dt_s, spin_steps=snap["steps"], full_run=snap["full_run"], snapshot=state,
+                problem=p, clocks=clocks, N=N, timed_steps=c1[0] - c0[0], timed_leaf_updates=c1[1] - c0[1],
+                timed_active_updates=c1[2] - c0[2], timed_wet_updates=c1[3] - c0[3], kernels_per_step=c1[4])
 
 
 def run_ensemble(args, steps=50):
@@ -314,7 +365,7 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
         e1.record(stream)
         stream.synchronize()
         ms = e0.elapsed_time(e1)
-        n, lu, wu, kps = sim.counters()
+        n, lu, au, wu, kps = sim.counters()
         t = sim.time()[0]
         fl = sim.fields()
         sim.close()
@@ -359,15 +410,15 @@ def combine_ranks(ms, e2e_s, world, device="cuda"):
     return float(t[0]), float(t[1])
 
 
-def time_precision(args, precision, steps=100):
-    """Device-timed steps/s of the same workload in another precision."""
-    import numpy as np
+def time_precision(args, precision, p, state, t_s, dt_s, steps):
+    """Device-timed steps/s of the same window in another precision."""
     import torch
     from paper_2206_05761_gb300.sim import Simulation
-    p, f = workload(args.L)
     stream = torch.cuda.Stream()
-    sim = Simulation(p, f, precision, stream=stream)
-    sim.advance(max_steps=args.spinup + max(args.warmup, 3))
+    sim = Simulation(p, state, precision, stream=stream)
+    sim.set_time(t_s, dt_s)
+    sim.advance(max_steps=max(args.warmup, 3))
+    sim.counters()
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -390,16 +441,15 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline(args, sample_steps):
+def cpu_baseline(args, p, state, t_s, dt_s, sample_steps):
     import oracle
-    p, f = workload(args.L)
-    st = oracle.State(p, f)
+    st = oracle.State(p, state, t=t_s, dt=dt_s)
     t0 = time.perf_counter()
     st.run(max_steps=sample_steps)
     el = time.perf_counter() - t0
     return {"value": sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d oracle steps of the same L=%d workload from t=0 (single-threaded C, %.1f s)"
-                      % (sample_steps, args.L, el)}
+            "sample": "%d oracle steps of the same L=%d workload from the same t=%.0f s state "
+                      "(single-threaded C, %.1f s)" % (sample_steps, args.L, t_s, el)}
 
 
 def main():
@@ -409,11 +459,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # the oracle (single-threaded C) on the same workload; a step takes
-        # seconds at L = 12, so the timed sample is bounded to ~2 minutes
+        # the oracle (single-threaded C) on the same window: the state at
+        # t_spin comes from the GPU path (untimed; the oracle would need many
+        # hours to get there); a step takes seconds at L = 12, so the timed
+        # sample is bounded to ~2 minutes
         import oracle
         p, f = workload(args.L)
-        st = oracle.State(p, f)
+        t_s = 0.0
+        try:
+            import torch
+            if torch.cuda.is_available():
+                p, snap = spin_up(args, torch.cuda.Stream())
+                f = {"z": snap["z"], **snap["fields"]}
+                t_s = snap["t"]
+                st = oracle.State(p, f, t=t_s, dt=snap["dt"])
+            else:
+                st = oracle.State(p, f)
+        except Exception:
+            st = oracle.State(p, f)
         t0 = time.perf_counter()
         st.run(max_steps=1)                      # one warm-up step
         per = time.perf_counter() - t0
@@ -422,12 +485,12 @@ def main():
         st.run(max_steps=k)
         el = time.perf_counter() - t1
         v = k / el
-        sample = ("%d oracle steps of the L=%d workload after 1 warm-up step "
-                  "(single-threaded C, %.1f s)" % (k, args.L, el))
+        sample = ("%d oracle steps of the L=%d workload from the t=%.0f s state after 1 warm-up "
+                  "step (single-threaded C, %.1f s)" % (k, args.L, t_s, el))
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
                "steps": k, "warmup": 1, "ms_per_step": 1e3 * el / k,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": config_dict(args, {"spinup_steps": 1}),
+               "data": "synthetic", "config": config_dict(args),
                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample},
                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -447,14 +510,14 @@ def main():
     # dominant kernel by live CUDA-event timing
     ph = r["phases_ms"]
     dom = max(ph, key=ph.get)
-    terms = roofline_terms(args.L, r["M_mean"], args.precision)
+    terms = roofline_terms(args.L, r["timed_active_updates"] / max(r["timed_steps"], 1), args.precision)
     alg = terms.get(dom)
     roof = None
     if alg:
         ach = alg / (ph[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": src}
-    e2e_val = world * r["e2e_steps"] / e2e_s
+    e2e_val = world * args.steps / e2e_s
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -463,22 +526,27 @@ def main():
         "leaf_updates_per_s": world * r["timed_leaf_updates"] / (ms / 1e3),
         "mean_leaves": r["timed_leaf_updates"] / max(r["timed_steps"], 1),
         "wet_fraction": r["timed_wet_updates"] / max(r["timed_leaf_updates"], 1),
+        "active_fraction": r["timed_active_updates"] / max(r["timed_leaf_updates"], 1),
         "phases_ms": ph, "roofline": roof,
         "e2e": {"value": e2e_val, "unit": UNIT,
-                "h2d_bytes_per_step": 4 * N * 8 / r["e2e_steps"],
-                "d2h_bytes_per_step": 3 * N * 8 / r["e2e_steps"],
-                "note": "host fields -> init -> %d steps -> fields back to host" % r["e2e_steps"]},
+                "h2d_bytes_per_step": 4 * N * 8 / args.steps,
+                "d2h_bytes_per_step": 3 * N * 8 / args.steps,
+                "note": "state at t=%.0f s in pinned host memory -> init -> %d steps -> fields back "
+                        "to the host" % (r["t_start"], args.steps)},
         "gpu_launches": r["kernels_per_step"] * r["timed_steps"],
-        "clocks": r["clocks"], "sim_time_s": r["t"],
+        "clocks": r["clocks"], "sim_time_s": [r["t_start"], r["t"]], "spinup_steps": r["spin_steps"],
+        "full_run": r["full_run"],
     }
     if world == 1:
-        out["other_precision"] = time_precision(args, 32 if args.precision == 64 else 64)
+        out["other_precision"] = time_precision(args, 32 if args.precision == 64 else 64, r["problem"],
+                                                r["snapshot"], r["t_start"], r["dt_start"], args.steps)
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_learned:
         out["learned"] = {k: run_learned(args, k) for k in ("columns", "bumpy")}
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, args.cpu_steps)
+        out["cpu_baseline"] = cpu_baseline(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"],
+                                           args.cpu_steps)
     print(json.dumps(out))
 
 

@@ -65,6 +65,13 @@ typedef enum {
 /* Regularisation switches (hwfv1_problem.flags). */
 #define HWFV1_REG_PREDICT 1u    /* children of a significant detail become significant */
 #define HWFV1_REG_CLOSE 2u      /* ancestors of a significant detail become significant */
+/* Execution switch (no counterpart in the paper; results are identical with
+ * and without it): update every leaf each step.  Without it, a step skips
+ * the tiles of 32 x 32 finest cells whose state is +0 in both state buffers
+ * and next to tiles at +0 (dry ground far from water): their update would
+ * reproduce the values already stored.  Skipping is off when eps < 1e-30
+ * (thresholds that round to 0 flag zero details). */
+#define HWFV1_FULL_SWEEP 4u
 
 /* Problem description.  The user inputs of Algorithm 3 are L and eps (t_end
  * is given to hwfv1_advance); CFL = 0.5 is the paper's choice (Sec. 2.1.3).
@@ -176,13 +183,15 @@ hwfv1_status hwfv1_set_time(hwfv1_handle* hd, double t, double dt);
 hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax3);
 
 /* Running counters (host outputs, any may be NULL; synchronises): steps
- * taken, leaves updated summed over those steps (sum of M, the work of
- * Sec. 2.3's leaf loop), the part of them that took the full FV1 update
- * (not entirely dry), and the number of kernels one captured step launches
- * (the learned step's when a network is attached; capturing the graph here
- * if no step has run yet).  No counterpart in the paper: diagnostics. */
+ * taken; leaves updated summed over those steps (sum of M, the work of
+ * Sec. 2.3's leaf loop); the part of them outside skipped quiescent tiles
+ * (see HWFV1_FULL_SWEEP), i.e. the leaves the kernels touched; the part
+ * that took the full FV1 update (not entirely dry); and the number of
+ * kernels one captured step launches (the learned step's when a network is
+ * attached; capturing the graph here if no step has run yet).  No
+ * counterpart in the paper: diagnostics. */
 hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates,
-                                int64_t* wet_updates, int64_t* kernels_per_step);
+                                int64_t* active_updates, int64_t* wet_updates, int64_t* kernels_per_step);
 
 /* Checkpoint: the finest h, hu, hv (Morton order, the handle's precision),
  * t, dt and the step count, written to a host buffer.  With host_buf NULL

@@ -44,7 +44,8 @@ hwfv1_status validate(const hwfv1_problem* s, std::string* msg) {
     if (!finite_pos(s->tol_h)) return spec_error("tol_h must be > 0", msg);
     if (!finite_pos(s->dt_max)) return spec_error("dt_max must be > 0", msg);
     if (s->precision != 64 && s->precision != 32) return spec_error("precision must be 64 or 32", msg);
-    if (s->flags & ~(HWFV1_REG_PREDICT | HWFV1_REG_CLOSE)) return spec_error("unknown flags", msg);
+    if (s->flags & ~(HWFV1_REG_PREDICT | HWFV1_REG_CLOSE | HWFV1_FULL_SWEEP))
+        return spec_error("unknown flags", msg);
     int inflow_sides = 0;
     for (int k = 0; k < 4; ++k) {
         if (s->bc[k] < HWFV1_BC_CLOSED || s->bc[k] > HWFV1_BC_INFLOW) return spec_error("bad boundary kind", msg);
@@ -165,10 +166,11 @@ hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax
     HWFV1_CHECK_HANDLE(hd);
     return from_engine(hd, hd->eng->get_stats(num_leaves, smax3));
 }
-hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates, int64_t* wet_updates,
-                                int64_t* kernels_per_step) {
+hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates,
+                                int64_t* active_updates, int64_t* wet_updates, int64_t* kernels_per_step) {
     HWFV1_CHECK_HANDLE(hd);
-    return from_engine(hd, hd->eng->get_counters(steps, leaf_updates, wet_updates, kernels_per_step));
+    return from_engine(hd, hd->eng->get_counters(steps, leaf_updates, active_updates, wet_updates,
+                                                 kernels_per_step));
 }
 hwfv1_status hwfv1_save(hwfv1_handle* hd, void* host_buf, size_t cap, size_t* used) {
     HWFV1_CHECK_HANDLE(hd);

@@ -80,7 +80,10 @@ static __global__ void __launch_bounds__(256) kb_flag(const DomainPlan<T>* P, co
     const int d = find_domain(base, D, blockIdx.x);
     const FlagArgs& f = P[d].flag;
     // the traversal that follows lists its decode tiles from zero
-    if (blockIdx.x == base[d] && threadIdx.x == 0) f.st->ndec = 0u;
+    if (blockIdx.x == base[d] && threadIdx.x == 0) {
+        f.st->ndec = 0u;
+        f.st->Mall = 0u;
+    }
     flag_body(f.Tb, f.Cb, f.Sbase, f.Sb, f.L, f.predict, f.close, f.st, domain_blk(base, d));
 }
 
@@ -88,21 +91,21 @@ template <typename T>
 static __global__ void __launch_bounds__(256) kb_trav_count(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
     const DomainPlan<T>& p = P[d];
-    trav_count_body(p.Sb, p.csum, p.dlist, p.L, p.kt, p.ntiles, p.st, domain_blk(base, d));
+    trav_count_body(p.Sb, p.csum, p.dlist, p.L, p.kt, p.ntiles, p.st, domain_blk(base, d), &p.st->Mall, Quiet());
 }
 
 template <typename T>
 static __global__ void __launch_bounds__(1024) kb_trav_scan(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
     const DomainPlan<T>& p = P[d];
-    trav_scan_body(p.csum, p.coffs, p.nct, p.st);
+    trav_scan_body(p.csum, p.coffs, p.nct, p.st, &p.st->M);
 }
 
 template <typename T>
 static __global__ void __launch_bounds__(256) kb_trav_write(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
     const DomainPlan<T>& p = P[d];
-    trav_write_body(p.Sb, p.coffs, p.leaves, p.L, p.kt, p.ntiles, p.st, domain_blk(base, d));
+    trav_write_body(p.Sb, p.coffs, p.leaves, p.L, p.kt, p.ntiles, p.st, domain_blk(base, d), nullptr);
 }
 
 template <typename T>
@@ -160,7 +163,11 @@ class BatchT final : public Batch {
         cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
         const int D = (int)specs_.size();
         for (int d = 0; d < D; ++d) {
-            auto* e = new EngineT<T>(specs_[d], stream_);
+            // the batched kernels update every tile (no quiescence bookkeeping),
+            // so a member never skips tiles, whichever path advances it
+            hwfv1_problem sd = specs_[d];
+            sd.flags |= HWFV1_FULL_SWEEP;
+            auto* e = new EngineT<T>(sd, stream_);
             doms_.push_back(e);
             const hwfv1_status s = e->init(z[d], h[d], qx[d], qy[d]);
             if (s != HWFV1_OK) return fail(s, "domain " + std::to_string(d) + ": " + e->err);

@@ -212,12 +212,14 @@ struct DevState {
     unsigned long long ticket;        // running tile ticket of the traversal
     uint32_t nwet;                    // leaves queued for the full FV1 update
     uint32_t ndec;                    // tiles listed for the decode kernel
+    uint32_t Mall;                    // leaves of the last traversal, skipped tiles included
     double rx0, ry0;                  // dt_use/lx, dt_use/ly (dt/dx_n = rx0 * 2^n)
     float rx0f, ry0f;                 // same, float arithmetic
     double thr[kMaxL * 3];            // eps*2^(n-L)*s_max,q for h, qx, qy
     float thrf[kMaxL * 3];            // same, float arithmetic (32-bit path)
     unsigned long long leaf_updates;  // leaves updated, summed over the steps taken
     unsigned long long wet_updates;   // of them, leaves that took the full FV1 update
+    unsigned long long act_updates;   // of them, leaves outside skipped (quiescent) tiles
 };
 
 enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };

@@ -75,6 +75,25 @@ class EngineT final : public Engine {
         if (!alloc(&counts_, (size_t)ntiles_ * 3 * sizeof(uint32_t))) return oom();
         offs_ = counts_ + ntiles_;
         dlist_ = counts_ + 2 * ntiles_;
+        // quiescent-tile bookkeeping: zf (two buffers), inlet, act
+        if (!alloc(&tilebytes_, (size_t)ntiles_ * 4)) return oom();
+        cudaMemsetAsync(tilebytes_, 0, (size_t)ntiles_ * 4, stream_);
+        quiet_on_ = !(spec_.flags & HWFV1_FULL_SWEEP) && spec_.eps >= 1e-30;
+        {
+            std::vector<uint8_t> inl(ntiles_, 0);
+            const int side = step_args().inflow_side;
+            if (side >= 0) {
+                const uint32_t last = (1u << (L_ - kt_)) - 1u;
+                for (int64_t pos = spec_.inflow_a0; pos < spec_.inflow_a1; ++pos) {
+                    const uint32_t tp = (uint32_t)(pos >> kt_);
+                    const uint32_t ti = side == 0 ? 0u : side == 1 ? last : tp;
+                    const uint32_t tj = side == 2 ? 0u : side == 3 ? last : tp;
+                    inl[morton2(ti, tj)] = 1;
+                }
+            }
+            cudaMemcpyAsync(tilebytes_ + 2 * ntiles_, inl.data(), ntiles_, cudaMemcpyHostToDevice, stream_);
+            cudaStreamSynchronize(stream_);
+        }
         if (!alloc(&st_, sizeof(DevState))) return oom();
         if (!alloc(&zaux_, 256)) return oom();
         if (!it_.empty()) {
@@ -135,7 +154,7 @@ class EngineT final : public Engine {
         if (num_leaves) {
             DevState s;
             if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
-            *num_leaves = s.M;
+            *num_leaves = s.Mall;
         }
         return check("traverse");
     }
@@ -227,6 +246,7 @@ class EngineT final : public Engine {
             k_rm_to_morton_cur<T><<<grid_for(N_), 256, 0, stream_>>>(
                 in[q], f_[0][q] + lvl_off(L_), f_[1][q] + lvl_off(L_), st_, L_);
         }
+        forget_quiet();
         reduce_state(/*set_dt=*/0);
         return check("set_fields");
     }
@@ -234,10 +254,27 @@ class EngineT final : public Engine {
     hwfv1_status get_leaves(uint32_t* out, int64_t cap, int64_t* n) override {
         DevState s;
         if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
-        if (n) *n = s.M;
+        if (n) *n = s.Mall;
         if (!out) return HWFV1_OK;
-        if (cap < (int64_t)s.M) return fail(HWFV1_ERR_INVALID_SPEC, "get_leaves: cap too small");
-        cudaMemcpyAsync(out, leaves_, sizeof(uint32_t) * s.M, cudaMemcpyDeviceToDevice, stream_);
+        if (cap < (int64_t)s.Mall) return fail(HWFV1_ERR_INVALID_SPEC, "get_leaves: cap too small");
+        if (s.Mall == s.M) {
+            cudaMemcpyAsync(out, leaves_, sizeof(uint32_t) * s.M, cudaMemcpyDeviceToDevice, stream_);
+        } else {
+            // the step's list leaves out skipped tiles: list every leaf of the
+            // current flags into `out` (no state changes)
+            const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
+            uint32_t* cnt = nullptr;
+            if (cudaMalloc(&cnt, ((size_t)2 * nct + 1) * sizeof(uint32_t)) != cudaSuccess) {
+                cudaGetLastError();
+                return oom();
+            }
+            k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, cnt, nullptr, L_, kt_, ntiles_, st_, nullptr, Quiet());
+            k_trav_scan<<<1, 1024, 0, stream_>>>(cnt, cnt + nct, nct, st_, cnt + 2 * nct);
+            k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, cnt + nct, out, L_, kt_, ntiles_, st_, nullptr);
+            const hwfv1_status r = check("get_leaves", true);
+            cudaFree(cnt);
+            return r;
+        }
         return check("get_leaves", true);
     }
 
@@ -285,7 +322,7 @@ class EngineT final : public Engine {
         return check("set_time", true);
     }
 
-    hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* wu, int64_t* kps) override {
+    hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* au, int64_t* wu, int64_t* kps) override {
         if (kps) {
             if (!exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
             *kps = skip_ ? kernels_learned_ : kernels_plain_;
@@ -294,6 +331,7 @@ class EngineT final : public Engine {
         if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
         if (steps) *steps = s.step;
         if (lu) *lu = (int64_t)s.leaf_updates;
+        if (au) *au = (int64_t)s.act_updates;
         if (wu) *wu = (int64_t)s.wet_updates;
         return HWFV1_OK;
     }
@@ -301,7 +339,7 @@ class EngineT final : public Engine {
     hwfv1_status get_stats(int64_t* M, double* smax3) override {
         DevState s;
         if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
-        if (M) *M = s.M;
+        if (M) *M = s.Mall;
         if (smax3)
             for (int q = 0; q < 3; ++q) smax3[q] = s.smax[q];
         return HWFV1_OK;
@@ -341,6 +379,7 @@ class EngineT final : public Engine {
         s.step = hd.step;
         s.err = 0;
         cudaMemcpyAsync(st_, &s, sizeof s, cudaMemcpyHostToDevice, stream_);
+        forget_quiet();
         reduce_state(/*set_dt=*/0);
         return check("load", true);
     }
@@ -427,18 +466,36 @@ class EngineT final : public Engine {
         a.Cb = Cb_;
         a.st = st_;
         a.L = L_;
+        if (quiet_on_) {
+            a.zf[0] = tilebytes_;
+            a.zf[1] = tilebytes_ + ntiles_;
+        }
         encode_passes(a);
     }
     void launch_flag() {
         k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
     }
     void launch_traverse() {
-        cudaMemsetAsync(&st_->ndec, 0, sizeof(uint32_t), stream_);
+        // ndec and Mall are adjacent
+        cudaMemsetAsync(&st_->ndec, 0, 2 * sizeof(uint32_t), stream_);
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
-        k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, counts_, dlist_, L_, kt_, ntiles_, st_);
-        k_trav_scan<<<1, 1024, 0, stream_>>>(counts_, offs_, nct, st_);
-        k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, offs_, leaves_, L_, kt_, ntiles_, st_);
+        const Quiet q = quiet();
+        k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, counts_, dlist_, L_, kt_, ntiles_, st_, &st_->Mall, q);
+        k_trav_scan<<<1, 1024, 0, stream_>>>(counts_, offs_, nct, st_, &st_->M);
+        k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, offs_, leaves_, L_, kt_, ntiles_, st_, q.act);
     }
+    Quiet quiet() const {
+        Quiet q;
+        if (quiet_on_) {
+            q.zf[0] = tilebytes_;
+            q.zf[1] = tilebytes_ + ntiles_;
+            q.inlet = tilebytes_ + 2 * ntiles_;
+            q.act = tilebytes_ + 3 * ntiles_;
+        }
+        return q;
+    }
+    // after the stored state changed outside a step: no tile is known quiescent
+    void forget_quiet() { cudaMemsetAsync(tilebytes_, 0, (size_t)ntiles_ * 2, stream_); }
     StepArgs<T> step_args() const {
         StepArgs<T> a;
         for (int b = 0; b < 2; ++b)
@@ -487,6 +544,7 @@ class EngineT final : public Engine {
         a.tol = (T)spec_.tol_h;
         a.L = L_;
         a.kt = kt_;
+        a.q = quiet();
         return a;
     }
     void launch_decode() {
@@ -609,6 +667,8 @@ class EngineT final : public Engine {
     uint32_t* leaves_ = nullptr;
     uint32_t* wet_ = nullptr;
     uint32_t *counts_ = nullptr, *offs_ = nullptr, *dlist_ = nullptr;
+    uint8_t* tilebytes_ = nullptr;      // per tile: zf of buffer 0, zf of buffer 1, inlet, act
+    bool quiet_on_ = false;
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;

@@ -32,8 +32,8 @@ class Engine {
     virtual hwfv1_status get_time(double* t, double* dt, int64_t* step) = 0;
     virtual hwfv1_status set_time(double t, double dt) = 0;
     virtual hwfv1_status get_stats(int64_t* M, double* smax3) = 0;
-    virtual hwfv1_status get_counters(int64_t* steps, int64_t* leaf_updates, int64_t* wet_updates,
-                                      int64_t* kernels_per_step) = 0;
+    virtual hwfv1_status get_counters(int64_t* steps, int64_t* leaf_updates, int64_t* active_updates,
+                                      int64_t* wet_updates, int64_t* kernels_per_step) = 0;
     virtual hwfv1_status save(void* buf, size_t cap, size_t* used) = 0;
     virtual hwfv1_status load(const void* buf, size_t n) = 0;
     // learned look-ahead (skipnet.cu); net == nullptr turns it off

@@ -132,7 +132,15 @@ struct EncodeArgs {
     uint32_t* Cb;         // upward closure of the threshold flags
     const DevState* st;   // NULL: buffer 0, always active
     int L, ls, k;         // source level ls; produces levels ls-1 .. ls-k
+    // Quiescent tiles (first pass only, its tiles are the traversal's):
+    // zf[b][t] = 1 when every value of buffer b in tile t, levels ls-k..ls,
+    // is +0.  NULL: no skipping.
+    uint8_t* zf[2] = {nullptr, nullptr};
 };
+
+// the value is +0 (all bits clear)
+__device__ __forceinline__ bool pos_zero(double x) { return __double_as_longlong(x) == 0ll; }
+__device__ __forceinline__ bool pos_zero(float x) { return __float_as_int(x) == 0; }
 
 // One CTA encodes one tile: the 4^k cells of level ls under one level-(ls-k)
 // cell, k <= 5 levels in one pass.  The first level reads four children
@@ -141,6 +149,11 @@ template <typename T, int NF>
 __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, int kk, uint32_t bid) {
     if (a.st && !a.st->active) return;
     const int par = a.st ? (int)a.st->cur : 0;
+    // A tile known to hold only +0 encodes to +0 with no significant detail
+    // (thresholds are > 0 whenever skipping is on): what is stored is
+    // already the result, and the cleared flag words stay clear.
+    const bool quiet = a.zf[0] != nullptr && ls == a.L;
+    if (quiet && a.zf[par][bid]) return;
     __shared__ T sv0[NF][256];        // level ls-1 (and ls-3, ls-5)
     __shared__ T sv1[NF][64];         // level ls-2 (and ls-4)
     __shared__ uint32_t sc[2][8];
@@ -150,7 +163,7 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
     {   // level ls-1
         const bool act = tid < cnt;
         const uint32_t p = tile * cnt + tid;
-        bool tf = false;
+        bool tf = false, nz = false;
         uint32_t cchild = 0;
         T s[NF];
 #pragma unroll
@@ -161,6 +174,7 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
                 T c0, c1, c2, c3, dm;
                 T* fq = par ? a.f[1][q] : a.f[0][q];
                 Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
+                nz = nz || !(pos_zero(c0) && pos_zero(c1) && pos_zero(c2) && pos_zero(c3));
                 haar4<T>(c0, c1, c2, c3, s[q], dm);
                 tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
                 fq[lvl_off(n) + p] = s[q];
@@ -176,6 +190,10 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
 #pragma unroll
         for (int q = 0; q < NF; ++q) sv0[q][tid] = s[q];
         if (lane == 0) sc[0][warp] = cball;
+        if (quiet) {   // all finest values +0 => every coarser value written is +0
+            const int any = __syncthreads_or(nz ? 1 : 0);
+            if (tid == 0) a.zf[par][tile] = any ? 0 : 1;
+        }
     }
     for (int j = 2; j <= kk; ++j) {
         __syncthreads();
@@ -470,49 +488,100 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t v) {
     return x - v;
 }
 
-// Traversal, pass 1: leaves per CTA (8 tiles); tiles holding a leaf of more
-// than 16 finest cells are listed for the decode kernel.
+// Quiescent-tile skipping.  A traversal tile (level L-kt) is skipped in a
+// step when every h, qx, qy value of both state buffers in it (levels
+// L-kt..L) is +0, the same holds in the current buffer for its four edge
+// neighbours, no inflow cell lies in it and no leaf coarser than the tile
+// covers it.  Every leaf of such a tile then sees depth +0 at itself and at
+// its same-level neighbours, so the update gives (+0, +0, +0) -- which the
+// destination buffer already holds, at every level of the tile.  Its leaves
+// are counted but not listed, updated or decoded, and its encode is a no-op.
+// A tile covered by a coarser leaf is processed (act = kActCovered) but
+// keeps its zf mark of the destination buffer: the decode kernel skips its
+// writes when that leaf's new value is +0 and clears the mark otherwise.
+struct Quiet {
+    uint8_t* zf[2] = {nullptr, nullptr};   // per state buffer and tile: all +0 (NULL: off)
+    const uint8_t* inlet = nullptr;        // tiles holding inflow cells
+    uint8_t* act = nullptr;                // per tile: 0 skipped, kActOwn or kActCovered
+};
+constexpr uint8_t kActOwn = 1, kActCovered = 2;
+
+// Traversal, pass 1: leaves per CTA (8 tiles) -- those of processed tiles
+// into csum, all of them into *mall (if given); tiles holding a leaf of more
+// than 16 finest cells are listed for the decode kernel (if dlist is given).
 __device__ __forceinline__ void trav_count_body(const uint32_t* __restrict__ Sb, uint32_t* __restrict__ csum,
                                                 uint32_t* __restrict__ dlist, int L, int kt, uint32_t ntiles,
-                                                DevState* st, Blk B) {
+                                                DevState* st, Blk B, uint32_t* mall, const Quiet& q) {
     if (!st->active) return;
     __shared__ TileBits tbs[kTilesPerCta];
-    __shared__ uint32_t wsum[kTilesPerCta];
+    __shared__ uint32_t wsum[kTilesPerCta], wall[kTilesPerCta];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t tile = B.id * kTilesPerCta + warp;
-    uint32_t total = 0u;
+    uint32_t total = 0u, total_all = 0u;
     if (tile < ntiles) {
         TileBits& tb = tbs[warp];
         warp_tile_bits(Sb, L, kt, tile, tb);
+        bool skip = false;
+        if (q.zf[0] != nullptr) {
+            if (lane == 0) {
+                const int Lr = L - kt;
+                const uint32_t cur = st->cur;
+                const uint8_t* X = q.zf[cur];
+                uint8_t* Y = q.zf[cur ^ 1u];
+                const bool covered = tb.l0 < Lr;
+                skip = !covered && X[tile] && Y[tile] && !q.inlet[tile];
+                if (skip) {
+                    const uint32_t lm = (1u << (2 * Lr)) - 1u;
+                    const uint32_t xs = tile & kXBits & lm, ys = tile & kYBits & lm;
+                    if (xs != 0u) skip = skip && X[mort_xm(tile)];
+                    if (xs != (kXBits & lm)) skip = skip && X[mort_xp(tile)];
+                    if (ys != 0u) skip = skip && X[mort_ym(tile)];
+                    if (ys != (kYBits & lm)) skip = skip && X[mort_yp(tile)];
+                }
+                q.act[tile] = skip ? 0 : (covered ? kActCovered : kActOwn);
+                if (!skip && !covered && Y[tile]) Y[tile] = 0;     // the step writes into it
+            }
+            skip = __shfl_sync(0xffffffffu, skip ? 1 : 0, 0) != 0;
+        }
         int lv[kGroupsPerLane];
         const uint32_t c = lane_heads(tb, L, kt, tile, lv);
         bool big = false;
 #pragma unroll
         for (int e = 0; e < kGroupsPerLane; ++e) big = big || (lv[e] >= 0 && needs_decode_kernel(lv[e], L));
-        total = warp_sum(c);
-        if (__any_sync(0xffffffffu, big) && lane == 0) {
+        total_all = warp_sum(c);
+        total = skip ? 0u : total_all;
+        if (dlist && !skip && __any_sync(0xffffffffu, big) && lane == 0) {
             const uint32_t pos = atomicAdd(&st->ndec, 1u);
             dlist[pos] = tile;           // one entry per tile at most
         }
     }
-    if (lane == 0) wsum[warp] = total;
+    if (lane == 0) {
+        wsum[warp] = total;
+        wall[warp] = total_all;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t s = 0u;
-        for (int w = 0; w < kTilesPerCta; ++w) s += wsum[w];
+        uint32_t s = 0u, sa = 0u;
+        for (int w = 0; w < kTilesPerCta; ++w) {
+            s += wsum[w];
+            sa += wall[w];
+        }
         csum[B.id] = s;
+        if (mall && sa) atomicAdd(mall, sa);
     }
 }
 static __global__ void __launch_bounds__(256) k_trav_count(const uint32_t* __restrict__ Sb,
                                                            uint32_t* __restrict__ csum,
                                                            uint32_t* __restrict__ dlist, int L, int kt,
-                                                           uint32_t ntiles, DevState* st) {
-    trav_count_body(Sb, csum, dlist, L, kt, ntiles, st, this_blk());
+                                                           uint32_t ntiles, DevState* st, uint32_t* mall,
+                                                           Quiet q) {
+    trav_count_body(Sb, csum, dlist, L, kt, ntiles, st, this_blk(), mall, q);
 }
 
-// Traversal, pass 2: exclusive scan of the per-CTA counts (one CTA); M = total.
+// Traversal, pass 2: exclusive scan of the per-CTA counts (one CTA); the
+// total goes to *total_out.
 __device__ __forceinline__ void trav_scan_body(const uint32_t* __restrict__ counts, uint32_t* __restrict__ offs,
-                                               uint32_t n, DevState* st) {
+                                               uint32_t n, DevState* st, uint32_t* total_out) {
     if (!st->active) return;
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     const uint32_t b = threadIdx.x * per, e = min(n, b + per);
@@ -524,27 +593,28 @@ __device__ __forceinline__ void trav_scan_body(const uint32_t* __restrict__ coun
         offs[i] = run;
         run += counts[i];
     }
-    if (threadIdx.x == 0) st->M = total;
+    if (threadIdx.x == 0) *total_out = total;
 }
 static __global__ void __launch_bounds__(1024) k_trav_scan(const uint32_t* __restrict__ counts,
                                                            uint32_t* __restrict__ offs, uint32_t n,
-                                                           DevState* st) {
-    trav_scan_body(counts, offs, n, st);
+                                                           DevState* st, uint32_t* total_out) {
+    trav_scan_body(counts, offs, n, st, total_out);
 }
 
 // Traversal, pass 3: each warp writes its tile's leaves in Z-order, 32
 // consecutive groups per round (lane t takes group 32r + t), so the stores
-// of a round are contiguous.
+// of a round are contiguous.  With `act`, only the processed tiles.
 __device__ __forceinline__ void trav_write_body(const uint32_t* __restrict__ Sb, const uint32_t* __restrict__ coffs,
                                                 uint32_t* __restrict__ leaves, int L, int kt, uint32_t ntiles,
-                                                const DevState* st, Blk B) {
+                                                const DevState* st, Blk B, const uint8_t* act) {
     if (!st->active) return;
     __shared__ TileBits tbs[kTilesPerCta];
     __shared__ uint32_t wsum[kTilesPerCta];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t tile = B.id * kTilesPerCta + warp;
+    const bool on = tile < ntiles && (act == nullptr || act[tile] != 0);
     uint32_t total = 0u;
-    if (tile < ntiles) {
+    if (on) {
         TileBits& tb = tbs[warp];
         warp_tile_bits(Sb, L, kt, tile, tb);
         int lv[kGroupsPerLane];
@@ -552,7 +622,7 @@ __device__ __forceinline__ void trav_write_body(const uint32_t* __restrict__ Sb,
     }
     if (lane == 0) wsum[warp] = total;
     __syncthreads();
-    if (tile >= ntiles) return;
+    if (!on) return;
     const TileBits& tb = tbs[warp];
     uint32_t base = __ldg(coffs + B.id);
     for (uint32_t w = 0; w < warp; ++w) base += wsum[w];
@@ -578,8 +648,9 @@ __device__ __forceinline__ void trav_write_body(const uint32_t* __restrict__ Sb,
 static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __restrict__ Sb,
                                                            const uint32_t* __restrict__ coffs,
                                                            uint32_t* __restrict__ leaves, int L, int kt,
-                                                           uint32_t ntiles, const DevState* st) {
-    trav_write_body(Sb, coffs, leaves, L, kt, ntiles, st, this_blk());
+                                                           uint32_t ntiles, const DevState* st,
+                                                           const uint8_t* act) {
+    trav_write_body(Sb, coffs, leaves, L, kt, ntiles, st, this_blk(), act);
 }
 
 // ---------------------------------------------------------------------------
@@ -1001,6 +1072,7 @@ struct DecodeArgs {
     DevState* st;
     T tol;
     int L, kt;
+    Quiet q;                  // quiescent-tile marks (zf NULL: off)
 };
 
 // Decode-back of the leaves of more than 16 finest cells, over the tiles the
@@ -1024,6 +1096,17 @@ __device__ __forceinline__ void decode_body(const DecodeArgs<T>& a, Blk B) {
         const uint32_t tile = a.dlist[d];
         __syncthreads();                            // tb reused across tiles
         load_tile_bits(a.Sb, a.L, a.kt, tile, tb);
+        if (a.q.zf[0] != nullptr && a.q.act[tile] == kActCovered) {
+            // one coarser leaf covers the whole tile: when its new value is
+            // (+0, +0, +0) and the tile already holds +0, nothing changes
+            const int lc = group_level(tb, a.L, a.kt, 0);
+            const uint64_t sc = lvl_off(lc) + (((uint64_t)tile << (2 * a.kt)) >> (2 * (a.L - lc)));
+            const bool zero = pos_zero(fh[sc]) && pos_zero(fqx[sc]) && pos_zero(fqy[sc]);
+            uint8_t* Y = a.q.zf[nxt];
+            if (zero && Y[tile]) continue;           // uniform over the CTA
+            __syncthreads();                         // every thread has read Y[tile]
+            if (threadIdx.x == 0) Y[tile] = 0;
+        }
         const int l = act ? group_level(tb, a.L, a.kt, g) : a.L;
         if (!needs_decode_kernel(l, a.L)) continue;
         const uint32_t m0 = (tile << (2 * a.kt)) + 4u * g;
@@ -1133,7 +1216,8 @@ __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
             !isfinite(st->smax[2]))
             st->err |= kErrNonFinite;
         st->step += 1;
-        st->leaf_updates += st->M;
+        st->leaf_updates += st->Mall;
+        st->act_updates += st->M;
         st->wet_updates += st->nwet;
         st->cur ^= 1u;
     }

@@ -23,7 +23,7 @@ STATUS = {0: "HWFV1_OK", 1: "HWFV1_ERR_INVALID_SPEC", 2: "HWFV1_ERR_OOM", 3: "HW
           4: "HWFV1_ERR_NONFINITE", 5: "HWFV1_ERR_NEG_DEPTH", 6: "HWFV1_ERR_TIMEOUT",
           7: "HWFV1_ERR_STATE"}
 BC = {"closed": 0, "transmissive": 1, "inflow": 2}
-REG_PREDICT, REG_CLOSE = 1, 2
+REG_PREDICT, REG_CLOSE, FULL_SWEEP = 1, 2, 4
 
 
 class Hwfv1Error(RuntimeError):
@@ -75,7 +75,7 @@ def lib():
                                          C.POINTER(C.c_int64)]
             L.hwfv1_set_time.argtypes = [_H, C.c_double, C.c_double]
             L.hwfv1_get_stats.argtypes = [_H, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
-            L.hwfv1_get_counters.argtypes = [_H] + [C.POINTER(C.c_int64)] * 4
+            L.hwfv1_get_counters.argtypes = [_H] + [C.POINTER(C.c_int64)] * 5
             L.hwfv1_save.argtypes = [_H, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
             L.hwfv1_load.argtypes = [_H, C.c_void_p, C.c_size_t]
             L.hwfv1_last_error.argtypes = [_H]
@@ -166,7 +166,8 @@ def make_problem(p, precision=64):
         s.inflow_Q = C.cast(q, C.POINTER(C.c_double))
         s.inflow_n = n
         s.inflow_a0, s.inflow_a1 = inf["a0"], inf["a1"]
-    s.flags = (REG_PREDICT if p.get("reg_predict", True) else 0) | (REG_CLOSE if p.get("reg_close", True) else 0)
+    s.flags = ((REG_PREDICT if p.get("reg_predict", True) else 0) | (REG_CLOSE if p.get("reg_close", True) else 0)
+               | (FULL_SWEEP if p.get("full_sweep", False) else 0))
     return s
 
 
@@ -252,8 +253,8 @@ def hwfv1_get_stats(hd):
 
 
 def hwfv1_get_counters(hd):
-    """(steps, leaf_updates, wet_updates, kernels_per_step)."""
-    v = [C.c_int64() for _ in range(4)]
+    """(steps, leaf_updates, active_updates, wet_updates, kernels_per_step)."""
+    v = [C.c_int64() for _ in range(5)]
     _check(lib().hwfv1_get_counters(hd, *[C.byref(x) for x in v]), "hwfv1_get_counters", hd)
     return tuple(x.value for x in v)
 

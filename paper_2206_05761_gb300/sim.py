@@ -90,7 +90,7 @@ class Simulation:
         return H.hwfv1_get_stats(self.hd)
 
     def counters(self):
-        """(steps, leaf_updates, wet_updates, kernels_per_step)."""
+        """(steps, leaf_updates, active_updates, wet_updates, kernels_per_step)."""
         return H.hwfv1_get_counters(self.hd)
 
     def save(self):

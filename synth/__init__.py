@@ -89,6 +89,18 @@ def circular_dam_break(L=6, eps=1e-3, radius=0.25, h_in=2.0, h_out=1.0):
     return p, _fields(p, eta, z)
 
 
+def dry_bed_dam_break(L=8, eps=1e-3, x1=0.2, y1=0.3, h0=1.0, relief=0.0, seed=7):
+    """A block of still water (free surface h0 over x < x1, y < y1) released
+    onto dry ground (h = 0 elsewhere), closed walls, no friction.  The bed is
+    flat, or with relief > 0 a seeded 1/f^2 surface of that relief (rough
+    ground: its details keep the tree fine everywhere)."""
+    p = problem(L, eps=eps, bc=("closed",) * 4)
+    x, y = centres(p)
+    z = np.zeros_like(x) if relief <= 0 else spectral_dem(1 << L, seed, relief)
+    eta = np.where((x < x1) & (y < y1), h0, 0.0)
+    return p, _fields(p, eta, z)
+
+
 def columns_dam_break(L=8, eps=1e-3, seed=0, k=3, h_out=1.0):
     """k seeded circular water columns collapsing on a flat bed: centres
     U[0.2, 0.8]^2, radii U[0.05, 0.15], depths U[1.3, 2.0] over h_out, at rest,

@@ -188,9 +188,9 @@ def test_counters_sum_the_leaf_updates():
     sim.advance(max_steps=25)
     for _ in range(25):
         ref.step()
-    steps, lu, wu, kps = sim.counters()
+    steps, lu, au, wu, kps = sim.counters()
     assert steps == 25 and lu == ref.leaf_updates
-    assert 0 < wu <= lu and 0 < kps < 64
+    assert 0 < wu <= au <= lu and 0 < kps < 64
     sim.close()
 
 
@@ -282,19 +282,55 @@ def test_float32_path_errors_stated():
 
 def test_full_size_terrain_flood_L12_bench_launch_path():
     # the bench workload at full size (4096 x 4096, 10 km, eps 1e-3, Manning
-    # 0.03, inflow) with its channel flowing, advanced one step through the
-    # same graph-replay path bench.py times, against one oracle step
+    # 0.03, inflow) with its channel flowing, advanced three steps through
+    # the same graph-replay path bench.py times (dry tiles skipped from the
+    # second step on), against three oracle steps
     p, f = synth.terrain_flood(L=12, fill=2.0, fill_q=1.0)
     sim = _sim(p, f)
     ref = oracle.State(p, f)
     t, dt, _ = sim.time()
     assert dt == ref.dt
-    sim.advance(max_steps=1)
+    sim.advance(max_steps=3)
+    ref.step()
+    ref.step()
     res = ref.step(want=("leaves",))
     lv = sim.leaves()
     assert len(lv) == res["num_leaves"] and np.array_equal(lv, res["leaves"])
     _compare_fields(sim, ref, exact=False)
     t, dt, steps = sim.time()
-    assert steps == 1 and t == ref.t
+    assert steps == 3 and abs(t - ref.t) <= RTOL_FRICTION * ref.t
     assert abs(dt - ref.dt) <= RTOL_FRICTION * ref.dt
+    n, lu, au, wu, kps = sim.counters()
+    assert lu == ref.leaf_updates and au < lu
     sim.close()
+
+
+@pytest.mark.parametrize("relief", [0.0, 0.05])
+def test_quiescent_tile_skipping_is_exact(relief):
+    # water released onto dry ground: most 32 x 32 tiles hold +0 in both
+    # state buffers; leaves, fields and time must equal the oracle's and the
+    # full sweep's bit for bit.  On the flat bed the dry ground is covered by
+    # leaves coarser than a tile (its encode and decode writes are skipped);
+    # on rough ground the dry tiles hold their own fine leaves (skipped)
+    p, f = synth.dry_bed_dam_break(L=8, eps=1e-3, relief=relief)
+    sim = _sim(p, f)
+    full = _sim(dict(p, full_sweep=True), f)
+    ref = oracle.State(p, f)
+    for chunk in range(6):
+        sim.advance(max_steps=10)
+        full.advance(max_steps=10)
+        for _ in range(9):
+            ref.step()
+        res = ref.step(want=("leaves",))
+        assert np.array_equal(sim.leaves(), res["leaves"]), "chunk %d" % chunk
+        assert np.array_equal(full.leaves(), res["leaves"]), "chunk %d" % chunk
+        _compare_fields(sim, ref)
+        _compare_fields(full, ref)
+        assert sim.time()[:2] == (ref.t, ref.dt)
+    _, lu, au, _, _ = sim.counters()
+    _, lu_f, au_f, _, _ = full.counters()
+    assert lu == lu_f == ref.leaf_updates and au_f == lu_f
+    if relief > 0:
+        assert au < 0.5 * lu
+    sim.close()
+    full.close()
