@@ -39,6 +39,9 @@ def parse():
     a.add_argument("--t-spin", type=float, default=1800.0,
                    help="simulated seconds run before the timed window (the hydrograph peak)")
     a.add_argument("--t-full", type=float, default=3600.0, help="end of the whole-run measurement")
+    a.add_argument("--fill", type=float, default=0.0,
+                   help="start with the channel this deep (m, 1 m^2/s eastward) instead of dry; "
+                        "a wet-channel case for profiling with --t-spin 0")
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--no-ensemble", action="store_true")
     a.add_argument("--no-learned", action="store_true")
@@ -46,9 +49,9 @@ def parse():
     return a.parse_args()
 
 
-def workload(L):
+def workload(L, fill=0.0):
     import synth
-    return synth.terrain_flood(L=L)
+    return synth.terrain_flood(L=L, fill=fill, fill_q=1.0 if fill > 0 else 0.0)
 
 
 def config_dict(args, extra=None):
@@ -59,6 +62,8 @@ def config_dict(args, extra=None):
                    "start at t=0 by the GPU path" % args.t_spin,
          "l2_policy": "state (>1 GB) larger than L2; no flush",
          "parallelism": "replicas" if args.gpus > 1 else "single"}
+    if args.fill > 0:
+        d["fill_m"] = args.fill
     if extra:
         d.update(extra)
     return d
@@ -154,7 +159,7 @@ def spin_up(args, stream):
     time, dt) and, run on to t_full, the whole-run statistics."""
     import torch
     from paper_2206_05761_gb300.sim import Simulation
-    p, f = workload(args.L)
+    p, f = workload(args.L, args.fill)
     sim = Simulation(p, f, args.precision, stream=stream)
     sim.counters()                               # captures the step graph
     out = {}
@@ -175,7 +180,7 @@ def spin_up(args, stream):
     tot = [sum(h[1][i] for h in halves) for i in range(4)]
     out["full_run"] = {
         "t_end_s": args.t_full, "steps": tot[0], "device_s": ms / 1e3,
-        "steps_per_s": tot[0] / (ms / 1e3), "mean_leaves": tot[1] / max(tot[0], 1),
+        "steps_per_s": tot[0] / max(ms / 1e3, 1e-9), "mean_leaves": tot[1] / max(tot[0], 1),
         "active_fraction": tot[2] / max(tot[1], 1), "wet_fraction": tot[3] / max(tot[1], 1),
         "note": "t = 0 to t_end_s in one run, host reads the time every <= 2000 steps"}
     sim.close()
@@ -464,7 +469,7 @@ def main():
         # hours to get there); a step takes seconds at L = 12, so the timed
         # sample is bounded to ~2 minutes
         import oracle
-        p, f = workload(args.L)
+        p, f = workload(args.L, args.fill)
         t_s = 0.0
         try:
             import torch

@@ -205,7 +205,6 @@ struct DevState {
     unsigned long long rmin_bits;     // min CFL bound over updated leaves
     unsigned long long max_bits[3];   // max |h|, |qx|, |qy| of the new state
     long long step;
-    uint32_t M;                       // leaves of the last traversal
     uint32_t active;                  // t < t_end
     uint32_t cur;                     // which state buffer holds the state
     uint32_t err;                     // latched device error bits
@@ -213,13 +212,19 @@ struct DevState {
     uint32_t nwet;                    // leaves queued for the full FV1 update
     uint32_t ndec;                    // tiles listed for the decode kernel
     uint32_t Mall;                    // leaves of the last traversal, skipped tiles included
+    uint32_t M;                       // leaves in the step's list (processed tiles); ndec, Mall
+                                      // and M are adjacent (cleared together)
     double rx0, ry0;                  // dt_use/lx, dt_use/ly (dt/dx_n = rx0 * 2^n)
     float rx0f, ry0f;                 // same, float arithmetic
     double thr[kMaxL * 3];            // eps*2^(n-L)*s_max,q for h, qx, qy
     float thrf[kMaxL * 3];            // same, float arithmetic (32-bit path)
+    double thr4[kMaxL * 3];           // 4 * thr where thr >= 2^-1020, else -1
+    float thr4f[kMaxL * 3];           // 4 * thrf where thrf >= 2^-124, else -1
     unsigned long long leaf_updates;  // leaves updated, summed over the steps taken
     unsigned long long wet_updates;   // of them, leaves that took the full FV1 update
     unsigned long long act_updates;   // of them, leaves outside skipped (quiescent) tiles
+    uint32_t enc_ticket;              // finished CTAs of the fused last encode passes
+    uint32_t dec_ticket;              // finished CTAs of the fused decode + finish
 };
 
 enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };

@@ -95,7 +95,7 @@ class EngineT final : public Engine {
             cudaStreamSynchronize(stream_);
         }
         if (!alloc(&st_, sizeof(DevState))) return oom();
-        if (!alloc(&zaux_, 256)) return oom();
+        if (!alloc(&zaux_, kZauxBytes)) return oom();
         if (!it_.empty()) {
             if (!alloc(&it_d_, it_.size() * sizeof(double))) return oom();
             if (!alloc(&iq_d_, iq_.size() * sizeof(double))) return oom();
@@ -120,14 +120,17 @@ class EngineT final : public Engine {
         // bed: s_max, thresholds, one-off encode and its static flags
         unsigned long long* zmax = reinterpret_cast<unsigned long long*>(zaux_);
         double* smax_z = reinterpret_cast<double*>(zaux_ + 8);
-        double* thr_zd = reinterpret_cast<double*>(zaux_ + 16);     // up to 14 doubles
-        float* thr_zf = reinterpret_cast<float*>(zaux_ + 16 + 8 * kMaxL);
+        double* thr_zd = reinterpret_cast<double*>(zaux_ + kZThrD);
+        float* thr_zf = reinterpret_cast<float*>(zaux_ + kZThrF);
         k_maxabs<T><<<g, 256, 0, stream_>>>(z_ + lvl_off(L_), N_, zmax);
-        k_z_thresholds<<<1, 32, 0, stream_>>>(zmax, thr_zd, thr_zf, smax_z, L_, spec_.eps, st_);
+        k_z_thresholds<<<1, 32, 0, stream_>>>(zmax, thr_zd, thr_zf, reinterpret_cast<double*>(zaux_ + kZThr4D),
+                                              reinterpret_cast<float*>(zaux_ + kZThr4F), smax_z, L_, spec_.eps,
+                                              st_);
         {
             EncodeArgs<T, 1> a;
             a.f[0][0] = a.f[1][0] = z_;
             a.thr = thr_z();
+            a.thr4 = thr4_z();
             a.Tb = Tz_;
             a.Cb = Cz_;
             a.st = nullptr;
@@ -136,6 +139,10 @@ class EngineT final : public Engine {
         }
         k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tz_, Cz_, nullptr, Sz_, L_, predict(), close(),
                                                        nullptr);
+        // leaf count of each tile holding the bed's flags alone (skipped tiles)
+        if (!alloc(&scount_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
+        k_static_counts<<<(ntiles_ + kTilesPerCta - 1) / kTilesPerCta, 256, 0, stream_>>>(Sz_, L_, kt_, ntiles_,
+                                                                                       scount_);
         // initial state scalars
         reduce_state(/*set_dt=*/1);
         return check("init", true);
@@ -257,11 +264,10 @@ class EngineT final : public Engine {
         if (n) *n = s.Mall;
         if (!out) return HWFV1_OK;
         if (cap < (int64_t)s.Mall) return fail(HWFV1_ERR_INVALID_SPEC, "get_leaves: cap too small");
-        if (s.Mall == s.M) {
-            cudaMemcpyAsync(out, leaves_, sizeof(uint32_t) * s.M, cudaMemcpyDeviceToDevice, stream_);
-        } else {
-            // the step's list leaves out skipped tiles: list every leaf of the
-            // current flags into `out` (no state changes)
+        {
+            // the step's list is in Z-order within tiles only and leaves out
+            // skipped tiles: list every leaf of the current flags into `out`
+            // in Z-order (no state changes)
             const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
             uint32_t* cnt = nullptr;
             if (cudaMalloc(&cnt, ((size_t)2 * nct + 1) * sizeof(uint32_t)) != cudaSuccess) {
@@ -275,7 +281,6 @@ class EngineT final : public Engine {
             cudaFree(cnt);
             return r;
         }
-        return check("get_leaves", true);
     }
 
     hwfv1_status get_flags(int which, uint32_t* out, int64_t cap_words) override {
@@ -392,6 +397,7 @@ class EngineT final : public Engine {
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) p.enc.f[b][q] = f_[b][q];
         p.enc.thr = thr_dyn();
+        p.enc.thr4 = thr4_dyn();
         p.enc.Tb = Tb_;
         p.enc.Cb = Cb_;
         p.enc.st = st_;
@@ -443,15 +449,31 @@ class EngineT final : public Engine {
     int close() const { return (spec_.flags & HWFV1_REG_CLOSE) ? 1 : 0; }
     const T* thr_z() const;
     const T* thr_dyn() const;
+    const T* thr4_z() const;
+    const T* thr4_dyn() const;
+    // aux buffer: z max bits, s_max of z, bed thresholds (thr, 4 thr) per precision
+    static constexpr size_t kZThrD = 16, kZThrF = kZThrD + 8 * kMaxL, kZThr4D = 256,
+                            kZThr4F = kZThr4D + 8 * kMaxL, kZauxBytes = 512;
 
+    // Passes of up to five levels from L down to 0.  With `ticket`, the
+    // final one-CTA pass runs in the last CTA of the pass before it.
     template <int NF>
-    void encode_passes(EncodeArgs<T, NF> a) {
+    void encode_passes(EncodeArgs<T, NF> a, uint32_t* ticket = nullptr) {
         int ls = L_;
         while (ls > 0) {
             const int k = ls < 5 ? ls : 5;
             a.ls = ls;
             a.k = k;
-            k_encode<T, NF><<<1u << (2 * (ls - k)), 256, 0, stream_>>>(a);
+            const uint32_t nb = 1u << (2 * (ls - k));
+            const int ls2 = ls - k, k2 = ls2 < 5 ? ls2 : 5;
+            if (ls == L_ && a.zf[0] != nullptr && nb > (uint32_t)nsm_ * 8u) {
+                k_encode_tiles<T, NF><<<nsm_ * 8, 256, 0, stream_>>>(a, nb);
+            } else if (ticket && ls2 > 0 && ls2 == k2) {      // next pass is the last (one CTA)
+                k_encode_tail<T, NF><<<nb, 256, 0, stream_>>>(a, ls2, k2, ticket);
+                break;                                     // levels ls2-1 .. 0 done too
+            } else {
+                k_encode<T, NF><<<nb, 256, 0, stream_>>>(a);
+            }
             ls -= k;
         }
     }
@@ -462,6 +484,7 @@ class EngineT final : public Engine {
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.thr = thr_dyn();
+        a.thr4 = thr4_dyn();
         a.Tb = Tb_;
         a.Cb = Cb_;
         a.st = st_;
@@ -470,19 +493,19 @@ class EngineT final : public Engine {
             a.zf[0] = tilebytes_;
             a.zf[1] = tilebytes_ + ntiles_;
         }
-        encode_passes(a);
+        encode_passes(a, &st_->enc_ticket);
     }
     void launch_flag() {
         k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
     }
-    void launch_traverse() {
-        // ndec and Mall are adjacent
-        cudaMemsetAsync(&st_->ndec, 0, 2 * sizeof(uint32_t), stream_);
+    // `learned`: the flags come from the learned look-ahead, whose skipped
+    // tiles need not hold the bed's static flags alone (no cached counts)
+    void launch_traverse(bool learned = false) {
+        cudaMemsetAsync(&st_->ndec, 0, 3 * sizeof(uint32_t), stream_);     // ndec, Mall, M
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
-        const Quiet q = quiet();
-        k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, counts_, dlist_, L_, kt_, ntiles_, st_, &st_->Mall, q);
-        k_trav_scan<<<1, 1024, 0, stream_>>>(counts_, offs_, nct, st_, &st_->M);
-        k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, offs_, leaves_, L_, kt_, ntiles_, st_, q.act);
+        const uint32_t grid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
+        k_trav_fused<<<grid, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
+                                                learned ? nullptr : scount_);
     }
     Quiet quiet() const {
         Quiet q;
@@ -521,6 +544,7 @@ class EngineT final : public Engine {
     Phys<T> phys() const {
         Phys<T> P;
         P.g = (T)spec_.g;
+        P.hg = P.g * (T)0.5;                 // exact
         P.tol = (T)spec_.tol_h;
         P.nM = (T)spec_.manning_n;
         P.cfl = (T)spec_.cfl;
@@ -548,8 +572,7 @@ class EngineT final : public Engine {
         return a;
     }
     void launch_decode() {
-        k_decode<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(decode_args());
-        k_finish<<<1, 64, 0, stream_>>>(st_, fin_args());
+        k_decode_finish<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(decode_args(), fin_args());
     }
     void launch_step_all() {
         launch_encode();
@@ -573,7 +596,7 @@ class EngineT final : public Engine {
         k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
         k_flag_learned<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
                                                               close(), st_);
-        launch_traverse();
+        launch_traverse(/*learned=*/true);
         launch_fv1();
         launch_decode();
     }
@@ -668,6 +691,7 @@ class EngineT final : public Engine {
     uint32_t* wet_ = nullptr;
     uint32_t *counts_ = nullptr, *offs_ = nullptr, *dlist_ = nullptr;
     uint8_t* tilebytes_ = nullptr;      // per tile: zf of buffer 0, zf of buffer 1, inlet, act
+    uint32_t* scount_ = nullptr;        // per tile: leaves when it holds the bed's flags alone
     bool quiet_on_ = false;
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;
@@ -687,11 +711,27 @@ class EngineT final : public Engine {
 
 template <>
 inline const double* EngineT<double>::thr_z() const {
-    return reinterpret_cast<const double*>(zaux_ + 16);
+    return reinterpret_cast<const double*>(zaux_ + kZThrD);
 }
 template <>
 inline const float* EngineT<float>::thr_z() const {
-    return reinterpret_cast<const float*>(zaux_ + 16 + 8 * kMaxL);
+    return reinterpret_cast<const float*>(zaux_ + kZThrF);
+}
+template <>
+inline const double* EngineT<double>::thr4_z() const {
+    return reinterpret_cast<const double*>(zaux_ + kZThr4D);
+}
+template <>
+inline const float* EngineT<float>::thr4_z() const {
+    return reinterpret_cast<const float*>(zaux_ + kZThr4F);
+}
+template <>
+inline const double* EngineT<double>::thr4_dyn() const {
+    return st_->thr4;
+}
+template <>
+inline const float* EngineT<float>::thr4_dyn() const {
+    return st_->thr4f;
 }
 template <>
 inline const double* EngineT<double>::thr_dyn() const {

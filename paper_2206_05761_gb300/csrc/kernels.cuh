@@ -27,11 +27,22 @@ template <> struct Vec4<double> {
         reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
         reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
     }
+    // through L2 only: for data other CTAs of the same kernel wrote
+    static __device__ __forceinline__ void load_cg(const double* p, double& a, double& b, double& c,
+                                                   double& d) {
+        const double2 u = __ldcg(reinterpret_cast<const double2*>(p));
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+        a = u.x; b = u.y; c = v.x; d = v.y;
+    }
 };
 template <> struct Vec4<float> {
     static __device__ __forceinline__ void load(const float* p, float& a, float& b, float& c,
                                                 float& d) {
         const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+        a = u.x; b = u.y; c = u.z; d = u.w;
+    }
+    static __device__ __forceinline__ void load_cg(const float* p, float& a, float& b, float& c, float& d) {
+        const float4 u = __ldcg(reinterpret_cast<const float4*>(p));
         a = u.x; b = u.y; c = u.z; d = u.w;
     }
     static __device__ __forceinline__ void store(float* p, float a, float b, float c, float d) {
@@ -78,6 +89,70 @@ __device__ __forceinline__ double absval(double x) {
 }
 __device__ __forceinline__ float absval(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
 
+// ---------------------------------------------------------------------------
+// Exact replacements of FP64 (FP32) instructions by integer ones, on a GPU
+// whose FP64 pipe is the bottleneck.  Each returns the bits the IEEE
+// operation returns (NaN inputs aside, which the state checks report).
+// ---------------------------------------------------------------------------
+// x * 2^k for k in {-2, -1, 1}: an exponent step when input and result are
+// normal numbers; otherwise the IEEE product (inline PTX, so that it is not
+// executed when the integer path applies).
+template <int K>
+__device__ __forceinline__ double pow2_scale(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e + K >= 1 && e + K <= 0x7FE && e >= 1 && e <= 0x7FE) return __longlong_as_double(b + ((long long)K << 52));
+    double r;
+    if (K == -2) asm volatile("mul.rn.f64 %0, %1, 0d3FD0000000000000;" : "=d"(r) : "d"(x));
+    else if (K == -1) asm volatile("mul.rn.f64 %0, %1, 0d3FE0000000000000;" : "=d"(r) : "d"(x));
+    else asm volatile("mul.rn.f64 %0, %1, 0d4000000000000000;" : "=d"(r) : "d"(x));
+    return r;
+}
+template <int K>
+__device__ __forceinline__ float pow2_scale(float x) {
+    const int b = __float_as_int(x);
+    const int e = (b >> 23) & 0xFF;
+    if (e + K >= 1 && e + K <= 0xFE && e >= 1 && e <= 0xFE) return __int_as_float(b + (K << 23));
+    float r;
+    if (K == -2) asm volatile("mul.rn.f32 %0, %1, 0f3E800000;" : "=f"(r) : "f"(x));
+    else if (K == -1) asm volatile("mul.rn.f32 %0, %1, 0f3F000000;" : "=f"(r) : "f"(x));
+    else asm volatile("mul.rn.f32 %0, %1, 0f40000000;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <typename T> __device__ __forceinline__ T quarter(T x) { return pow2_scale<-2>(x); }
+template <typename T> __device__ __forceinline__ T half(T x) { return pow2_scale<-1>(x); }
+template <typename T> __device__ __forceinline__ T twice(T x) { return pow2_scale<1>(x); }
+
+// Integer key with the order of the IEEE comparison (+0 and -0 equal).
+__device__ __forceinline__ long long ord_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ int ord_key(float x) {
+    const int b = __float_as_int(x);
+    return b >= 0 ? b : -(b & 0x7FFFFFFF);
+}
+// a < b ? a : b and a > b ? a : b (the IEEE selections, which pick b on ties)
+template <typename T> __device__ __forceinline__ T sel_min(T a, T b) { return ord_key(a) < ord_key(b) ? a : b; }
+template <typename T> __device__ __forceinline__ T sel_max(T a, T b) { return ord_key(a) > ord_key(b) ? a : b; }
+// x >= 0 and x <= 0 (true for either zero)
+template <typename T> __device__ __forceinline__ bool ge_zero(T x) { return ord_key(x) >= 0; }
+template <typename T> __device__ __forceinline__ bool le_zero(T x) { return ord_key(x) <= 0; }
+// x is finite (not inf or NaN)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool finite_bits(float x) { return (__float_as_int(x) & 0x7F800000) != 0x7F800000; }
+// x > 0, false for NaN as in IEEE
+__device__ __forceinline__ bool gt_zero(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool gt_zero(float x) {
+    const int b = __float_as_int(x);
+    return b > 0 && b <= 0x7F800000;
+}
+
 // A block of a (possibly batched) launch: its index among the blocks given
 // to one domain and their number.  Single-domain launches use blockIdx.x and
 // gridDim.x; batched launches (batch.cuh) map a flat grid onto domains.
@@ -92,18 +167,28 @@ __device__ __forceinline__ Blk this_blk() { return Blk{blockIdx.x, gridDim.x}; }
 // scaling by 0.25 and rounding commute with max.  Four equal children give
 // s = c0 and dmax = 0 in every arithmetic, so that case skips the sums.
 template <typename T>
-__device__ __forceinline__ void haar4(T c0, T c1, T c2, T c3, T& s, T& dmax) {
+__device__ __forceinline__ void haar4(T c0, T c1, T c2, T c3, T& s, T& dmax4) {
     if (same4<T>(c0, c1, c2, c3)) {
         s = c0;
-        dmax = T(0);
+        dmax4 = T(0);
         return;
     }
     const T a = c0 + c2, b = c1 + c3, d = c0 - c2, e = c1 - c3;
-    s = T(0.25) * (a + b);
+    s = quarter(a + b);
     const T da = absval(d + e), db = absval(a - b), dg = absval(d - e);
-    T m = da > db ? da : db;
-    m = m > dg ? m : dg;
-    dmax = T(0.25) * m;
+    // the largest |detail| times 4: details are a quarter of these sums, an
+    // exact scaling that passes_thr compares against 4 * threshold
+    dmax4 = sel_max(sel_max(da, db), dg);
+}
+
+// max|d| >= thr for the three details d = m4/4 of a parent: compared as
+// m4 >= thr4 = 4 thr when thr >= 2^-1020 (then m4/4 is exact, or both
+// sides of the original comparison are below thr); thr4 < 0 marks the
+// other thresholds, compared as written.
+template <typename T>
+__device__ __forceinline__ bool passes_thr(T m4, T thr, T thr4) {
+    if (ge_zero(thr4)) return ge_nonneg(m4, thr4);      // m4 is never -0
+    return ge_nonneg(T(0.25) * m4, thr);
 }
 
 // Write the per-thread flag of `cnt` consecutive parents (codes base..) of
@@ -128,6 +213,7 @@ template <typename T, int NF>
 struct EncodeArgs {
     T* f[2][NF];          // hierarchy of each quantity, per state buffer
     const T* thr;         // threshold of level n, quantity q at thr[n*NF + q]
+    const T* thr4;        // 4 * thr where exact comparisons allow it, else -1
     uint32_t* Tb;         // threshold flags
     uint32_t* Cb;         // upward closure of the threshold flags
     const DevState* st;   // NULL: buffer 0, always active
@@ -145,7 +231,9 @@ __device__ __forceinline__ bool pos_zero(float x) { return __float_as_int(x) == 
 // One CTA encodes one tile: the 4^k cells of level ls under one level-(ls-k)
 // cell, k <= 5 levels in one pass.  The first level reads four children
 // per thread with 128-bit loads; the next levels work from shared memory.
-template <typename T, int NF>
+// CG: read the source level and the closure bits through L2 only (the tail
+// pass reads what other CTAs of the same launch wrote).
+template <typename T, int NF, bool CG = false>
 __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, int kk, uint32_t bid) {
     if (a.st && !a.st->active) return;
     const int par = a.st ? (int)a.st->cur : 0;
@@ -153,7 +241,8 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
     // (thresholds are > 0 whenever skipping is on): what is stored is
     // already the result, and the cleared flag words stay clear.
     const bool quiet = a.zf[0] != nullptr && ls == a.L;
-    if (quiet && a.zf[par][bid]) return;
+    uint8_t* const zfp = par ? a.zf[1] : a.zf[0];   // (no dynamic index into parameters)
+    if (quiet && zfp[bid]) return;
     __shared__ T sv0[NF][256];        // level ls-1 (and ls-3, ls-5)
     __shared__ T sv1[NF][64];         // level ls-2 (and ls-4)
     __shared__ uint32_t sc[2][8];
@@ -173,15 +262,17 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
             for (int q = 0; q < NF; ++q) {
                 T c0, c1, c2, c3, dm;
                 T* fq = par ? a.f[1][q] : a.f[0][q];
-                Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
+                if (CG) Vec4<T>::load_cg(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
+                else Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
                 nz = nz || !(pos_zero(c0) && pos_zero(c1) && pos_zero(c2) && pos_zero(c3));
                 haar4<T>(c0, c1, c2, c3, s[q], dm);
-                tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
+                tf = tf || passes_thr(dm, a.thr[n * NF + q], a.thr4[n * NF + q]);
                 fq[lvl_off(n) + p] = s[q];
             }
             if (ls < a.L) {
                 const uint32_t cb = 4u * p;
-                cchild = (__ldg(a.Cb + word_off(ls) + (cb >> 5)) >> (cb & 31u)) & 0xFu;
+                const uint32_t* cw = a.Cb + word_off(ls) + (cb >> 5);
+                cchild = ((CG ? __ldcg(cw) : __ldg(cw)) >> (cb & 31u)) & 0xFu;
             }
         }
         const bool cf = act && (tf || cchild);
@@ -192,7 +283,7 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
         if (lane == 0) sc[0][warp] = cball;
         if (quiet) {   // all finest values +0 => every coarser value written is +0
             const int any = __syncthreads_or(nz ? 1 : 0);
-            if (tid == 0) a.zf[par][tile] = any ? 0 : 1;
+            if (tid == 0) zfp[tile] = any ? 0 : 1;
         }
     }
     for (int j = 2; j <= kk; ++j) {
@@ -214,7 +305,7 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
                 T* fq = par ? a.f[1][q] : a.f[0][q];
                 const T* r = rbuf ? sv1[q] : sv0[q];
                 haar4<T>(r[4 * tid], r[4 * tid + 1], r[4 * tid + 2], r[4 * tid + 3], s[q], dm);
-                tf = tf || ge_nonneg(dm, a.thr[n * NF + q]);   // dm is never -0
+                tf = tf || passes_thr(dm, a.thr[n * NF + q], a.thr4[n * NF + q]);
                 fq[lvl_off(n) + p] = s[q];
             }
             cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
@@ -233,6 +324,49 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
 template <typename T, int NF>
 static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
     encode_body<T, NF>(a, a.ls, a.k, blockIdx.x);
+}
+
+// A pass followed, in its last CTA to finish, by the final one-CTA pass
+// (levels ls2-1 .. 0), saving a launch; ticket counts the finished CTAs and
+// is reset by the last one.
+template <typename T, int NF>
+static __global__ void __launch_bounds__(256) k_encode_tail(EncodeArgs<T, NF> a, int ls2, int k2,
+                                                            uint32_t* ticket) {
+    encode_body<T, NF>(a, a.ls, a.k, blockIdx.x);
+    __threadfence();                     // this CTA's coefficients and bits are visible
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *ticket = 0u;
+    encode_body<T, NF, true>(a, ls2, k2, 0u);
+}
+
+// The same pass with a fixed grid striding over the tiles when quiescent
+// tiles are skipped: the CTA reads the marks of all its tiles at once (one
+// per thread) and encodes only the unmarked ones.
+template <typename T, int NF>
+static __global__ void __launch_bounds__(256) k_encode_tiles(EncodeArgs<T, NF> a, uint32_t ntiles) {
+    if (a.st && !a.st->active) return;
+    __shared__ uint32_t todo[256];
+    __shared__ uint32_t ntodo;
+    const int par = a.st ? (int)a.st->cur : 0;
+    const uint8_t* zf = par ? a.zf[1] : a.zf[0];
+    for (uint32_t t0 = blockIdx.x; t0 < ntiles; t0 += 256u * gridDim.x) {
+        if (threadIdx.x == 0) ntodo = 0u;
+        __syncthreads();
+        const uint32_t t = t0 + threadIdx.x * gridDim.x;
+        if (t < ntiles && !zf[t]) todo[atomicAdd(&ntodo, 1u)] = t;
+        __syncthreads();
+        const uint32_t n = ntodo;
+        __syncthreads();                 // every thread has read ntodo before it is reset
+        for (uint32_t i = 0; i < n; ++i) {
+            encode_body<T, NF>(a, a.ls, a.k, todo[i]);
+            __syncthreads();             // shared memory is reused by the next tile
+        }
+    }
 }
 
 // Clear bit arrays before an encode (the partial words are OR-ed into).
@@ -526,8 +660,8 @@ __device__ __forceinline__ void trav_count_body(const uint32_t* __restrict__ Sb,
             if (lane == 0) {
                 const int Lr = L - kt;
                 const uint32_t cur = st->cur;
-                const uint8_t* X = q.zf[cur];
-                uint8_t* Y = q.zf[cur ^ 1u];
+                const uint8_t* X = cur ? q.zf[1] : q.zf[0];
+                uint8_t* Y = cur ? q.zf[0] : q.zf[1];
                 const bool covered = tb.l0 < Lr;
                 skip = !covered && X[tile] && Y[tile] && !q.inlet[tile];
                 if (skip) {
@@ -653,6 +787,120 @@ static __global__ void __launch_bounds__(256) k_trav_write(const uint32_t* __res
     trav_write_body(Sb, coffs, leaves, L, kt, ntiles, st, this_blk(), act);
 }
 
+// Leaf count of every tile when its root cell is significant and its own
+// levels hold only the bed's static flags (what a skipped tile holds in the
+// plain step): one warp per tile, run once after the bed is flagged.
+static __global__ void __launch_bounds__(256) k_static_counts(const uint32_t* __restrict__ Sz, int L, int kt,
+                                                              uint32_t ntiles, uint32_t* __restrict__ out) {
+    __shared__ TileBits tbs[kTilesPerCta];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t tile = blockIdx.x * kTilesPerCta + warp;
+    if (tile >= ntiles) return;                  // whole warp
+    TileBits& tb = tbs[warp];
+    warp_tile_bits(Sz, L, kt, tile, tb);
+    if (lane == 0) tb.l0 = L - kt + 1;
+    __syncwarp();
+    int lv[kGroupsPerLane];
+    const uint32_t c = warp_sum(lane_heads(tb, L, kt, tile, lv));
+    if (lane == 0) out[tile] = c;
+}
+
+// Traversal in one pass (the step's own list; get_leaves lists in Z-order
+// with the three kernels above): a warp per tile, a fixed grid striding over
+// the tiles.  Per tile: the skip decision, its leaf count into *mall (for a
+// skipped tile from scount when given), its decode-list entry, and -- if it
+// is processed -- its leaves, appended at a position taken with one atomic
+// on st->M.  The list is therefore in Z-order within a tile only; nothing
+// downstream depends on the order (every leaf's update is independent and
+// the reductions are integer min/max).
+__device__ __forceinline__ void trav_fused_body(const uint32_t* __restrict__ Sb, uint32_t* __restrict__ dlist,
+                                                uint32_t* __restrict__ leaves, int L, int kt, uint32_t ntiles,
+                                                DevState* st, const Quiet& q, const uint32_t* scount) {
+    if (!st->active) return;
+    __shared__ TileBits tbs[kTilesPerCta];
+    __shared__ uint32_t wall[kTilesPerCta];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const int Lr = L - kt;
+    const uint32_t cur = st->cur;
+    const uint8_t* X = cur ? q.zf[1] : q.zf[0];
+    uint8_t* Y = cur ? q.zf[0] : q.zf[1];
+    const uint32_t lm = (1u << (2 * Lr)) - 1u;
+    uint32_t sum_all = 0u;
+    for (uint32_t tile = blockIdx.x * kTilesPerCta + warp; tile < ntiles; tile += gridDim.x * kTilesPerCta) {
+        TileBits& tb = tbs[warp];
+        __syncwarp();                            // tb reused across tiles
+        warp_tile_bits(Sb, L, kt, tile, tb);
+        bool skip = false;
+        if (X != nullptr) {
+            // the seven marks of the decision, one per lane, read together
+            const uint32_t xs = tile & kXBits & lm, ys = tile & kYBits & lm;
+            bool ok = true;
+            if (lane == 0) ok = X[tile] != 0;
+            else if (lane == 1) ok = Y[tile] != 0;
+            else if (lane == 2) ok = q.inlet[tile] == 0;
+            else if (lane == 3) ok = xs == 0u || X[mort_xm(tile)] != 0;
+            else if (lane == 4) ok = xs == (kXBits & lm) || X[mort_xp(tile)] != 0;
+            else if (lane == 5) ok = ys == 0u || X[mort_ym(tile)] != 0;
+            else if (lane == 6) ok = ys == (kYBits & lm) || X[mort_yp(tile)] != 0;
+            const uint32_t b = __ballot_sync(0xffffffffu, ok);
+            const bool covered = tb.l0 < Lr;
+            skip = !covered && (b & 0x7Fu) == 0x7Fu;
+            if (lane == 0) {
+                q.act[tile] = skip ? 0 : (covered ? kActCovered : kActOwn);
+                if (!skip && !covered && (b & 2u)) Y[tile] = 0;     // the step writes into it
+            }
+        }
+        if (skip && scount) {                    // uniform over the warp
+            sum_all += tb.l0 == Lr ? 1u : __ldg(scount + tile);
+            continue;
+        }
+        int lv[kGroupsPerLane];
+        const uint32_t c = lane_heads(tb, L, kt, tile, lv);
+        const uint32_t total = warp_sum(c);
+        sum_all += total;
+        if (skip) continue;
+        bool big = false;
+#pragma unroll
+        for (int e = 0; e < kGroupsPerLane; ++e) big = big || (lv[e] >= 0 && needs_decode_kernel(lv[e], L));
+        if (__any_sync(0xffffffffu, big) && lane == 0) dlist[atomicAdd(&st->ndec, 1u)] = tile;
+        uint32_t base = 0u;
+        if (lane == 0 && total) base = atomicAdd(&st->M, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const uint32_t ngroups = 1u << (2 * (kt - 1));
+        for (uint32_t r = 0; r * 32u < ngroups; ++r) {
+            const uint32_t g = r * 32u + lane;
+            int l = L;
+            uint32_t cc = 0u;
+            const uint32_t m0 = (tile << (2 * kt)) + 4u * g;
+            if (g < ngroups) {
+                l = group_level(tb, L, kt, g);
+                cc = l == L ? 4u : ((m0 & ((1u << (2 * (L - l))) - 1u)) == 0u ? 1u : 0u);
+            }
+            const uint32_t pos = base + warp_excl(cc);
+            if (cc == 4u) {
+                Vec4<uint32_t>::store_u(leaves + pos, ((uint32_t)L << kLeafShift) | m0);
+            } else if (cc == 1u) {
+                leaves[pos] = ((uint32_t)l << kLeafShift) | (m0 >> (2 * (L - l)));
+            }
+            base += warp_sum(cc);
+        }
+    }
+    if (lane == 0) wall[warp] = sum_all;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0u;
+        for (int w = 0; w < kTilesPerCta; ++w) s += wall[w];
+        if (s) atomicAdd(&st->Mall, s);
+    }
+}
+static __global__ void __launch_bounds__(256) k_trav_fused(const uint32_t* __restrict__ Sb,
+                                                           uint32_t* __restrict__ dlist,
+                                                           uint32_t* __restrict__ leaves, int L, int kt,
+                                                           uint32_t ntiles, DevState* st, Quiet q,
+                                                           const uint32_t* scount) {
+    trav_fused_body(Sb, dlist, leaves, L, kt, ntiles, st, q, scount);
+}
+
 // ---------------------------------------------------------------------------
 // FV1 update of one cell (Eq. 1-2; the L_c reading: hydrostatic
 // reconstruction, HLL, Audusse bed source, Manning friction)
@@ -663,6 +911,7 @@ struct Cell { T h, qx, qy, z; };
 template <typename T>
 struct Phys {
     T g, tol, nM, cfl, dxL, dyL;
+    T hg;                    // g / 2 (exact): the first product of every g h^2 / 2
 };
 
 template <typename T>
@@ -679,43 +928,48 @@ __device__ __forceinline__ void velocity(const Cell<T>& c, T tol, T& u, T& v) {
 
 // HLL flux across a face with normal from L to R; F = (mass, normal
 // momentum, tangential momentum), hLs/hRs the reconstructed depths.
+//
+// Every comparison, selection and power-of-two scaling below is done on the
+// bit patterns (is_zero, ge_nonneg, sel_min/sel_max, ge_zero/le_zero,
+// half/quarter/twice): the same results as the IEEE operations the oracle
+// performs, without occupying the FP64 pipe.
 template <typename T>
-__device__ __forceinline__ void hll_face(T g, T tol, T hL, T zL, T unL, T utL, T hR, T zR, T unR,
+__device__ __forceinline__ void hll_face(T g, T hg, T tol, T hL, T zL, T unL, T utL, T hR, T zR, T unR,
                                          T utR, T F[3], T& hLs_o, T& hRs_o) {
-    const T zf = zL > zR ? zL : zR;
+    const T zf = sel_max(zR, zL);                       // zL > zR ? zL : zR
     const T dL = (hL + zL) - zf;
     const T dR = (hR + zR) - zf;
-    const T hLs = dL >= tol ? dL : T(0);
-    const T hRs = dR >= tol ? dR : T(0);
+    const T hLs = ge_nonneg(dL, tol) ? dL : T(0);        // tol > 0
+    const T hRs = ge_nonneg(dR, tol) ? dR : T(0);
     hLs_o = hLs;
     hRs_o = hRs;
-    if (hLs == T(0) && hRs == T(0)) {
+    if (is_zero(hLs) && is_zero(hRs)) {
         F[0] = F[1] = F[2] = T(0);
         return;
     }
     const T aL = sqrt(g * hLs), aR = sqrt(g * hRs);
     T SL, SR;
-    if (hLs > T(0) && hRs > T(0)) {
-        const T us = T(0.5) * (unL + unR) + aL - aR;
-        const T as = T(0.5) * (aL + aR) + T(0.25) * (unL - unR);
+    if (!is_zero(hLs) && !is_zero(hRs)) {
+        const T us = half(unL + unR) + aL - aR;
+        const T as = half(aL + aR) + quarter(unL - unR);
         const T a1 = unL - aL, a2 = us - as;
         const T b1 = unR + aR, b2 = us + as;
-        SL = a1 < a2 ? a1 : a2;
-        SR = b1 > b2 ? b1 : b2;
-    } else if (hLs == T(0)) {
-        SL = unR - T(2) * aR;
+        SL = sel_min(a1, a2);
+        SR = sel_max(b1, b2);
+    } else if (is_zero(hLs)) {
+        SL = unR - twice(aR);
         SR = unR + aR;
     } else {
         SL = unL - aL;
-        SR = unL + T(2) * aL;
+        SR = unL + twice(aL);
     }
     const T qnL = hLs * unL, qtL = hLs * utL;
     const T qnR = hRs * unR, qtR = hRs * utR;
-    const T FL0 = qnL, FL1 = qnL * unL + T(0.5) * g * hLs * hLs, FL2 = qnL * utL;
-    const T FR0 = qnR, FR1 = qnR * unR + T(0.5) * g * hRs * hRs, FR2 = qnR * utR;
-    if (SL >= T(0)) {
+    const T FL0 = qnL, FL1 = qnL * unL + hg * hLs * hLs, FL2 = qnL * utL;
+    const T FR0 = qnR, FR1 = qnR * unR + hg * hRs * hRs, FR2 = qnR * utR;
+    if (ge_zero(SL)) {
         F[0] = FL0; F[1] = FL1; F[2] = FL2;
-    } else if (SR <= T(0)) {
+    } else if (le_zero(SR)) {
         F[0] = FR0; F[1] = FR1; F[2] = FR2;
     } else {
         const T inv = T(1) / (SR - SL);
@@ -730,10 +984,10 @@ template <typename T>
 __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
                                             const Cell<T>& W, const Cell<T>& E, const Cell<T>& S,
                                             const Cell<T>& N, bool inlet, T dh, T out[3]) {
-    const T g = P.g, tol = P.tol;
+    const T g = P.g, hg = P.hg, tol = P.tol;
     T FW[3], FE[3], GS[3], GN[3];
     T hW_R, hE_L, hS_R, hN_L, dummy;
-    if (C.h == T(0) && W.h == T(0) && E.h == T(0) && S.h == T(0) && N.h == T(0)) {
+    if (is_zero(C.h) && is_zero(W.h) && is_zero(E.h) && is_zero(S.h) && is_zero(N.h)) {
         // all five cells dry with zero depth: every reconstructed depth is 0
         // and every face flux is 0 (what the general path computes)
 #pragma unroll
@@ -746,19 +1000,19 @@ __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, 
         velocity(E, tol, uE, vE);
         velocity(S, tol, uS, vS);
         velocity(N, tol, uN, vN);
-        hll_face(g, tol, W.h, W.z, uW, vW, C.h, C.z, uC, vC, FW, dummy, hW_R);
-        hll_face(g, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hE_L, dummy);
-        hll_face(g, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
-        hll_face(g, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hN_L, dummy);
+        hll_face(g, hg, tol, W.h, W.z, uW, vW, C.h, C.z, uC, vC, FW, dummy, hW_R);
+        hll_face(g, hg, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hE_L, dummy);
+        hll_face(g, hg, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
+        hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hN_L, dummy);
     }
-    const T bx = T(0.5) * g * (hW_R * hW_R - hE_L * hE_L);
-    const T by = T(0.5) * g * (hS_R * hS_R - hN_L * hN_L);
+    const T bx = hg * (hW_R * hW_R - hE_L * hE_L);
+    const T by = hg * (hS_R * hS_R - hN_L * hN_L);
     T h = C.h - rx * (FE[0] - FW[0]) - ry * (GN[0] - GS[0]);
     T qx = C.qx - rx * ((FE[1] - FW[1]) + bx) - ry * (GN[2] - GS[2]);
     T qy = C.qy - rx * (FE[2] - FW[2]) - ry * ((GN[1] - GS[1]) + by);
     if (inlet) h = h + dh;
-    h = h > T(0) ? h : T(0);
-    if (h < tol) {
+    h = gt_zero(h) ? h : T(0);
+    if (!ge_nonneg(h, tol)) {                           // h < tol (tol > 0)
         qx = T(0);
         qy = T(0);
     } else if (P.nM > T(0)) {
@@ -784,7 +1038,7 @@ __device__ __forceinline__ T cfl_bound(const Phys<T>& P, T h, T qx, T qy) {
     const T u = absval(qx * rh), v = absval(qy * rh);
     const T a = sqrt(P.g * h);
     const T rx = P.dxL / (u + a), ry = P.dyL / (v + a);
-    return rx < ry ? rx : ry;
+    return sel_min(rx, ry);
 }
 
 template <typename T>
@@ -1028,10 +1282,10 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
                     T z0, z1, z2, z3;
                     Vec4<T>::load(src.z + fo + e, z0, z1, z2, z3);
                     const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
-                    hf[0] = d0 > T(0) ? d0 : T(0);
-                    hf[1] = d1 > T(0) ? d1 : T(0);
-                    hf[2] = d2 > T(0) ? d2 : T(0);
-                    hf[3] = d3 > T(0) ? d3 : T(0);
+                    hf[0] = gt_zero(d0) ? d0 : T(0);
+                    hf[1] = gt_zero(d1) ? d1 : T(0);
+                    hf[2] = gt_zero(d2) ? d2 : T(0);
+                    hf[3] = gt_zero(d3) ? d3 : T(0);
                 } else {
                     hf[0] = hf[1] = hf[2] = hf[3] = hl;
                 }
@@ -1049,7 +1303,8 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
             const unsigned long long b2 = abs_obits(out[2]);
             mqy = b2 > mqy ? b2 : mqy;
         }
-        if (!(isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]))) atomicOr(&st->err, kErrNonFinite);
+        if (!(finite_bits(out[0]) && finite_bits(out[1]) && finite_bits(out[2])))
+            atomicOr(&st->err, kErrNonFinite);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
     block_max3_u64(mh, mqx, mqy, st->max_bits);
@@ -1081,10 +1336,12 @@ struct DecodeArgs {
 template <typename T>
 __device__ __forceinline__ void decode_body(const DecodeArgs<T>& a, Blk B) {
     DevState* st = a.st;
-    if (!st->active) return;
-    const uint32_t nd = st->ndec;
+    // the state is read through L2 only: k_decode_finish's last CTA reads
+    // what the other CTAs' atomics wrote and must not find stale L1 lines
+    if (!__ldcg(&st->active)) return;
+    const uint32_t nd = __ldcg(&st->ndec);
     if (B.id >= nd) return;                   // whole block idle
-    const int nxt = (int)st->cur ^ 1;
+    const int nxt = (int)__ldcg(&st->cur) ^ 1;
     __shared__ TileBits tb;
     T* const fh = nxt ? a.f[1][0] : a.f[0][0];
     T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
@@ -1102,7 +1359,7 @@ __device__ __forceinline__ void decode_body(const DecodeArgs<T>& a, Blk B) {
             const int lc = group_level(tb, a.L, a.kt, 0);
             const uint64_t sc = lvl_off(lc) + (((uint64_t)tile << (2 * a.kt)) >> (2 * (a.L - lc)));
             const bool zero = pos_zero(fh[sc]) && pos_zero(fqx[sc]) && pos_zero(fqy[sc]);
-            uint8_t* Y = a.q.zf[nxt];
+            uint8_t* Y = nxt ? a.q.zf[1] : a.q.zf[0];
             if (zero && Y[tile]) continue;           // uniform over the CTA
             __syncthreads();                         // every thread has read Y[tile]
             if (threadIdx.x == 0) Y[tile] = 0;
@@ -1120,10 +1377,10 @@ __device__ __forceinline__ void decode_body(const DecodeArgs<T>& a, Blk B) {
             T z0, z1, z2, z3;
             Vec4<T>::load(a.z + fo, z0, z1, z2, z3);
             const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
-            hf[0] = d0 > T(0) ? d0 : T(0);
-            hf[1] = d1 > T(0) ? d1 : T(0);
-            hf[2] = d2 > T(0) ? d2 : T(0);
-            hf[3] = d3 > T(0) ? d3 : T(0);
+            hf[0] = gt_zero(d0) ? d0 : T(0);
+            hf[1] = gt_zero(d1) ? d1 : T(0);
+            hf[2] = gt_zero(d2) ? d2 : T(0);
+            hf[3] = gt_zero(d3) ? d3 : T(0);
         } else {
             hf[0] = hf[1] = hf[2] = hf[3] = hl;
         }
@@ -1171,11 +1428,19 @@ __device__ inline double inflow_Q(const FinishArgs& a, double t) {
 // Thresholds, timestep clamp and inflow volume of the step about to run.
 // Called by every thread of a one-block launch after s_max is final; the
 // (level, quantity) thresholds are spread over the threads.
+// 4 thr for passes_thr when the comparison against it is exact, else -1
+__device__ __forceinline__ double thr4_of(double t) { return t >= 0x1p-1020 ? ldexp(t, 2) : -1.0; }
+__device__ __forceinline__ float thr4_of(float t) { return t >= 0x1p-124f ? ldexpf(t, 2) : -1.0f; }
+
 __device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
     for (int k = threadIdx.x; k < 3 * a.L; k += blockDim.x) {
         const int n = k / 3, q = k - 3 * n;
-        st->thr[n * 3 + q] = ldexp(a.eps, n - a.L) * st->smax[q];
-        st->thrf[n * 3 + q] = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
+        const double td = ldexp(a.eps, n - a.L) * st->smax[q];
+        const float tf = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
+        st->thr[n * 3 + q] = td;
+        st->thrf[n * 3 + q] = tf;
+        st->thr4[n * 3 + q] = thr4_of(td);
+        st->thr4f[n * 3 + q] = thr4_of(tf);
     }
     if (threadIdx.x != 0) return;
     st->active = st->t < st->t_end ? 1u : 0u;
@@ -1228,6 +1493,23 @@ static __global__ void k_finish(DevState* st, FinishArgs a) {
     finish_body(st, a);
 }
 
+// Decode-back followed, in its last CTA to finish, by the time advance (one
+// launch instead of two).  decode_body reads the state through L2 only, so
+// the last CTA sees every other CTA's reductions after the fence.
+template <typename T>
+static __global__ void __launch_bounds__(256) k_decode_finish(DecodeArgs<T> a, FinishArgs fa) {
+    decode_body<T>(a, this_blk());
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(&a.st->dec_ticket, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) a.st->dec_ticket = 0u;
+    finish_body(a.st, fa);
+}
+
 // Set t_end (hwfv1_advance) and recompute the step scalars.
 __device__ __forceinline__ void set_tend_body(DevState* st, const FinishArgs& a, double t_end) {
     if (threadIdx.x == 0) st->t_end = t_end;
@@ -1254,7 +1536,8 @@ static __global__ void k_init_state(DevState* st, FinishArgs a, int set_dt) {
 
 // z thresholds for the one-off bed encode
 static __global__ void k_z_thresholds(const unsigned long long* zmax_bits, double* thr_d, float* thr_f,
-                               double* smax_z, int L, double eps, DevState* st) {
+                                      double* thr4_d, float* thr4_f, double* smax_z, int L, double eps,
+                                      DevState* st) {
     if (threadIdx.x != 0) return;
     const double s = smax_of(*zmax_bits);
     *smax_z = s;
@@ -1262,6 +1545,8 @@ static __global__ void k_z_thresholds(const unsigned long long* zmax_bits, doubl
     for (int n = 0; n < L; ++n) {
         thr_d[n] = ldexp(eps, n - L) * s;
         thr_f[n] = ldexpf((float)eps, n - L) * (float)s;
+        thr4_d[n] = thr4_of(thr_d[n]);
+        thr4_f[n] = thr4_of(thr_f[n]);
     }
 }
 
