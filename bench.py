@@ -127,20 +127,46 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
-def roofline_terms(L, M, precision):
-    """Algorithmic bytes of one launch of each kernel."""
-    N = 1 << (2 * L)
-    P = (N - 1) // 3
-    b = 8 if precision == 64 else 4
-    return {
-        # read finest h, qx, qy; write every coarser level of them; flag bits
-        "encode": 3 * b * N + 3 * b * P + 2 * P / 8,
-        # leaf id + own 4 values + 3 new values (neighbours served from L2)
-        "fv1": M * (4 + 4 * b + 3 * b),
-        # every finest cell under a coarser leaf: written 3 values + its bed
-        "decode": None,
-        "traverse": 3 * P / 8 * 2 + 4 * M,
-    }
+# Algorithmic work of the wet-leaf update (k_fv1_wet), per wet leaf whose
+# four faces are wet on both sides: FP64 operations of the arithmetic as
+# written (every add, multiply, divide, square and cube root counts 1; the
+# comparisons and power-of-two scalings run as integer operations): 5
+# velocities x 3, 4 HLL faces x 56, bed source 8, update 20, friction 18,
+# CFL bound 9.
+FV1_WET_FLOP_PER_LEAF = 294
+# The FP64 pipe issues 2 thread-instructions per cycle per SM (ncu's peak for
+# DFMA); the update may use no FMA (each operation is rounded on its own, as
+# in the oracle), so its peak is one FLOP per instruction: 152 SMs x 2 x
+# 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one k_fv1_wet launch in the timed window (mean over the
+# launches of the ncu capture summarised in
+# profiles/fv1_wet_terrain_flood_L12_f64.md), valid while kernels.cuh has
+# this SHA-256.
+FV1_WET_TRAFFIC = {"kernels_sha256": "8ed88a0a50e8e847c7280bc898e4d92a72522076812cfd67a874585941305f1e",
+                   "bytes_per_launch": 3304770}
+
+
+def kernels_sha256():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2206_05761_gb300", "csrc", "kernels.cuh"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def roofline(kernel, ms, r, args, pk, src):
+    """Roofline of the dominant kernel from its live duration."""
+    if kernel == "k_fv1_wet" and args.precision == 64:
+        flop = FV1_WET_FLOP_PER_LEAF * r["wet_per_step"]
+        ach = flop / (ms / 1e3) / 1e12
+        traffic = (FV1_WET_TRAFFIC["bytes_per_launch"]
+                   if FV1_WET_TRAFFIC["kernels_sha256"] == kernels_sha256() else None)
+        return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "units_per_launch": r["wet_per_step"], "flop_per_unit": FV1_WET_FLOP_PER_LEAF,
+                "peak_source": "derived: FP64 pipe, 2 instructions/clk/SM x 152 SMs x 2.07 GHz, "
+                               "1 FLOP per instruction (no FMA)"}
+    return {"kernel": kernel, "bound": None, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": None, "traffic": None, "peak_source": src}
 
 
 def advance_to(sim, t_end, chunk=2000):
@@ -232,22 +258,15 @@ def run_ours(args, rank, world):
     H.hwfv1_set_time(hd, t_s, dt_s)
     H.hwfv1_advance(hd, float("inf"), max(args.warmup, 3))
     stream.synchronize()
-    # per-phase timing on the library's stream (CUDA events)
-    phases = {"encode": [], "flag": [], "traverse": [], "fv1": [], "decode": []}
-    Ms = []
-    for _ in range(5):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-        with torch.cuda.stream(stream):
-            ev[0].record(stream)
-            H.hwfv1_encode(hd); ev[1].record(stream)
-            H.hwfv1_flag(hd); ev[2].record(stream)
-            H.hwfv1_traverse(hd); ev[3].record(stream)
-            H.hwfv1_step(hd); ev[4].record(stream)
-            H.hwfv1_decode(hd); ev[5].record(stream)
-        stream.synchronize()
-        for i, k in enumerate(phases):
-            phases[k].append(ev[i].elapsed_time(ev[i + 1]))
-        Ms.append(H.hwfv1_get_stats(hd)[0])
+    # per-kernel timing: steps launched kernel by kernel with CUDA events on
+    # the library's stream between the launches (median of 7)
+    kern, wet = {}, []
+    for _ in range(7):
+        w0 = H.hwfv1_get_counters(hd)[3]
+        for name, t in H.hwfv1_profile_step(hd):
+            kern.setdefault(name, []).append(t)
+        wet.append(H.hwfv1_get_counters(hd)[3] - w0)
+    Ms = [H.hwfv1_get_stats(hd)[0]]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -270,8 +289,8 @@ def run_ours(args, rank, world):
     t_now, dt_now, nsteps = H.hwfv1_get_time(hd)
     c1 = H.hwfv1_get_counters(hd)
     H.hwfv1_destroy(hd)
-    ph = {k: statistics.median(v) for k, v in phases.items()}
-    return dict(ms=ms, e2e_s=t_e2e, phases_ms=ph, M_mean=float(sum(Ms) / len(Ms)), t=t_now, dt=dt_now,
+    ph = {k: statistics.median(v) for k, v in kern.items()}
+    return dict(ms=ms, e2e_s=t_e2e, kernels_ms=ph, wet_per_step=statistics.median(wet), M_mean=float(sum(Ms) / len(Ms)), t=t_now, dt=dt_now,
                 t_start=t_s, dt_start=dt_s, spin_steps=snap["steps"], full_run=snap["full_run"], snapshot=state,
                 problem=p, clocks=clocks, N=N, timed_steps=c1[0] - c0[0], timed_leaf_updates=c1[1] - c0[1],
                 timed_active_updates=c1[2] - c0[2], timed_wet_updates=c1[3] - c0[3], kernels_per_step=c1[4])
@@ -513,15 +532,9 @@ def main():
     b = 8 if args.precision == 64 else 4
     pk, src = peaks()
     # dominant kernel by live CUDA-event timing
-    ph = r["phases_ms"]
+    ph = r["kernels_ms"]
     dom = max(ph, key=ph.get)
-    terms = roofline_terms(args.L, r["timed_active_updates"] / max(r["timed_steps"], 1), args.precision)
-    alg = terms.get(dom)
-    roof = None
-    if alg:
-        ach = alg / (ph[dom] / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": src}
+    roof = roofline(dom, ph[dom], r, args, pk, src)
     e2e_val = world * args.steps / e2e_s
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -532,7 +545,7 @@ def main():
         "mean_leaves": r["timed_leaf_updates"] / max(r["timed_steps"], 1),
         "wet_fraction": r["timed_wet_updates"] / max(r["timed_leaf_updates"], 1),
         "active_fraction": r["timed_active_updates"] / max(r["timed_leaf_updates"], 1),
-        "phases_ms": ph, "roofline": roof,
+        "kernels_ms": ph, "roofline": roof,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * 8 / args.steps,
                 "d2h_bytes_per_step": 3 * N * 8 / args.steps,

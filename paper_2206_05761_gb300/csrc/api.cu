@@ -166,6 +166,11 @@ hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax
     HWFV1_CHECK_HANDLE(hd);
     return from_engine(hd, hd->eng->get_stats(num_leaves, smax3));
 }
+hwfv1_status hwfv1_profile_step(hwfv1_handle* hd, float* ms, const char** names, int32_t cap, int32_t* n) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (cap < 0) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->profile_step(ms, names, cap, n));
+}
 hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates,
                                 int64_t* active_updates, int64_t* wet_updates, int64_t* kernels_per_step) {
     HWFV1_CHECK_HANDLE(hd);

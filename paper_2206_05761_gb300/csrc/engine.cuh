@@ -327,6 +327,35 @@ class EngineT final : public Engine {
         return check("set_time", true);
     }
 
+    // One plain step launched kernel by kernel with an event after every
+    // launch; durations in launch order.
+    hwfv1_status profile_step(float* ms, const char** names, int32_t cap, int32_t* n) override {
+        std::vector<std::pair<const char*, cudaEvent_t>> ev;
+        cudaEvent_t e0;
+        if (cudaEventCreate(&e0) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "event");
+        cudaEventRecord(e0, stream_);
+        prof_ = &ev;
+        launch_step_all();
+        prof_ = nullptr;
+        hwfv1_status r = check("profile_step", true);
+        int32_t k = 0;
+        cudaEvent_t prev = e0;
+        for (auto& p : ev) {
+            float t = 0.f;
+            if (r == HWFV1_OK && cudaEventElapsedTime(&t, prev, p.second) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "event");
+            if (k < cap) {
+                if (ms) ms[k] = t;
+                if (names) names[k] = p.first;
+            }
+            ++k;
+            prev = p.second;
+        }
+        for (auto& p : ev) cudaEventDestroy(p.second);
+        cudaEventDestroy(e0);
+        if (n) *n = k;
+        return r;
+    }
+
     hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* au, int64_t* wu, int64_t* kps) override {
         if (kps) {
             if (!exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
@@ -468,11 +497,14 @@ class EngineT final : public Engine {
             const int ls2 = ls - k, k2 = ls2 < 5 ? ls2 : 5;
             if (ls == L_ && a.zf[0] != nullptr && nb > (uint32_t)nsm_ * 8u) {
                 k_encode_tiles<T, NF><<<nsm_ * 8, 256, 0, stream_>>>(a, nb);
+                mark("k_encode_tiles");
             } else if (ticket && ls2 > 0 && ls2 == k2) {      // next pass is the last (one CTA)
                 k_encode_tail<T, NF><<<nb, 256, 0, stream_>>>(a, ls2, k2, ticket);
+                mark("k_encode_tail");
                 break;                                     // levels ls2-1 .. 0 done too
             } else {
                 k_encode<T, NF><<<nb, 256, 0, stream_>>>(a);
+                mark("k_encode");
             }
             ls -= k;
         }
@@ -480,6 +512,7 @@ class EngineT final : public Engine {
 
     void launch_encode() {
         k_clear_words<<<grid_for(2 * (uint64_t)words_), 256, 0, stream_>>>(Tb_, 2 * words_, st_);
+        mark("k_clear_words");
         EncodeArgs<T, 3> a;
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
@@ -497,15 +530,25 @@ class EngineT final : public Engine {
     }
     void launch_flag() {
         k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
+        mark("k_flag");
     }
     // `learned`: the flags come from the learned look-ahead, whose skipped
     // tiles need not hold the bed's static flags alone (no cached counts)
     void launch_traverse(bool learned = false) {
         cudaMemsetAsync(&st_->ndec, 0, 3 * sizeof(uint32_t), stream_);     // ndec, Mall, M
+        mark("memset");
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
         const uint32_t grid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
         k_trav_fused<<<grid, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
                                                 learned ? nullptr : scount_);
+        mark("k_trav_fused");
+    }
+    void mark(const char* name) {
+        if (!prof_) return;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, stream_);
+        prof_->push_back({name, e});
     }
     Quiet quiet() const {
         Quiet q;
@@ -555,7 +598,9 @@ class EngineT final : public Engine {
     void launch_fv1() {
         const StepArgs<T> a = step_args();
         k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+        mark("k_fv1_dry");
         k_fv1_wet<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+        mark("k_fv1_wet");
     }
     DecodeArgs<T> decode_args() const {
         DecodeArgs<T> a;
@@ -573,6 +618,7 @@ class EngineT final : public Engine {
     }
     void launch_decode() {
         k_decode_finish<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(decode_args(), fin_args());
+        mark("k_decode_finish");
     }
     void launch_step_all() {
         launch_encode();
@@ -693,6 +739,7 @@ class EngineT final : public Engine {
     uint8_t* tilebytes_ = nullptr;      // per tile: zf of buffer 0, zf of buffer 1, inlet, act
     uint32_t* scount_ = nullptr;        // per tile: leaves when it holds the bed's flags alone
     bool quiet_on_ = false;
+    std::vector<std::pair<const char*, cudaEvent_t>>* prof_ = nullptr;   // profile_step's events
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;

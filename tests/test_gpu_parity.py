@@ -194,6 +194,26 @@ def test_counters_sum_the_leaf_updates():
     sim.close()
 
 
+def test_profiled_step_is_an_ordinary_step():
+    # hwfv1_profile_step launches the plain step kernel by kernel with events
+    # in between: same state as one oracle step, every kernel listed
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    prof = Hh.hwfv1_profile_step(sim.hd)
+    names = [n for n, _ in prof]
+    assert names[0] == "k_clear_words" and names[-1] == "k_decode_finish"
+    for k in ("k_flag", "k_trav_fused", "k_fv1_dry", "k_fv1_wet"):
+        assert k in names
+    assert all(t >= 0.0 for _, t in prof)
+    res = ref.step(want=("leaves",))
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    _compare_fields(sim, ref)
+    assert sim.time()[:3] == (ref.t, ref.dt, 1)
+    sim.close()
+
+
 def test_advance_stops_at_t_end():
     p, f = synth.circular_dam_break(L=5, eps=1e-3)
     sim = _sim(p, f)
