@@ -139,12 +139,12 @@ FV1_WET_FLOP_PER_LEAF = 294
 # in the oracle), so its peak is one FLOP per instruction: 152 SMs x 2 x
 # 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
-# DRAM traffic of one k_fv1_wet launch in the timed window (mean over the
-# launches of the ncu capture summarised in
-# profiles/fv1_wet_terrain_flood_L12_f64.md), valid while kernels.cuh has
-# this SHA-256.
-FV1_WET_TRAFFIC = {"kernels_sha256": "8ed88a0a50e8e847c7280bc898e4d92a72522076812cfd67a874585941305f1e",
-                   "bytes_per_launch": 3304770}
+# DRAM traffic of the wet-leaf update (k_fv1_faces + k_fv1_update) of one
+# step in the timed window: mean over the launches of the ncu capture
+# summarised in profiles/terrain_flood_L12_f64_launches.md, valid while
+# kernels.cuh has this SHA-256.
+FV1_WET_TRAFFIC = {"kernels_sha256": "36ea356f331f15c4d3abf9e78034e1ce1b95f0bad9cb6d19330d13f8c8bc1fa4",
+                   "bytes_per_launch": 3225268 + 9874467}
 
 
 def kernels_sha256():
@@ -155,11 +155,16 @@ def kernels_sha256():
 
 def roofline(kernel, ms, r, args, pk, src):
     """Roofline of the dominant kernel from its live duration."""
-    if kernel == "k_fv1_wet" and args.precision == 64:
+    ph = r["kernels_ms"]
+    if kernel in ("k_fv1_faces", "k_fv1_update") and args.precision == 64:
+        # the two phases of one update: one unit of work
+        kernel, ms = "k_fv1_faces+k_fv1_update", ph["k_fv1_faces"] + ph["k_fv1_update"]
+    if kernel in ("k_fv1_wet", "k_fv1_faces+k_fv1_update") and args.precision == 64:
         flop = FV1_WET_FLOP_PER_LEAF * r["wet_per_step"]
         ach = flop / (ms / 1e3) / 1e12
         traffic = (FV1_WET_TRAFFIC["bytes_per_launch"]
-                   if FV1_WET_TRAFFIC["kernels_sha256"] == kernels_sha256() else None)
+                   if FV1_WET_TRAFFIC["kernels_sha256"] == kernels_sha256() and kernel != "k_fv1_wet"
+                   else None)
         return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "units_per_launch": r["wet_per_step"], "flop_per_unit": FV1_WET_FLOP_PER_LEAF,

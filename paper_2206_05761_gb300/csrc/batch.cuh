@@ -167,7 +167,7 @@ class BatchT final : public Batch {
             // so a member never skips tiles, whichever path advances it
             hwfv1_problem sd = specs_[d];
             sd.flags |= HWFV1_FULL_SWEEP;
-            auto* e = new EngineT<T>(sd, stream_);
+            auto* e = new EngineT<T>(sd, stream_, /*batched=*/true);
             doms_.push_back(e);
             const hwfv1_status s = e->init(z[d], h[d], qx[d], qy[d]);
             if (s != HWFV1_OK) return fail(s, "domain " + std::to_string(d) + ": " + e->err);

@@ -223,6 +223,7 @@ struct DevState {
     unsigned long long leaf_updates;  // leaves updated, summed over the steps taken
     unsigned long long wet_updates;   // of them, leaves that took the full FV1 update
     unsigned long long act_updates;   // of them, leaves outside skipped (quiescent) tiles
+    uint32_t epoch;                   // completed steps (never reset; tags the face stamps)
     uint32_t enc_ticket;              // finished CTAs of the fused last encode passes
     uint32_t dec_ticket;              // finished CTAs of the fused decode + finish
 };

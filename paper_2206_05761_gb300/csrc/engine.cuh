@@ -1,6 +1,7 @@
 // engine.cuh -- host side of one HWFV1 simulation: device buffers, the
 // launch sequence of a timestep, CUDA-graph replay, checkpoints.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -30,7 +31,10 @@ inline int64_t count_kernel_nodes(cudaGraph_t g) {
 template <typename T>
 class EngineT final : public Engine {
    public:
-    EngineT(const hwfv1_problem& s, cudaStream_t stream) : spec_(s), stream_(stream) {
+    // batched: a member of a BatchT, whose own kernels run its steps (no
+    // shared-face buffers)
+    EngineT(const hwfv1_problem& s, cudaStream_t stream, bool batched = false)
+        : spec_(s), stream_(stream), batched_(batched) {
         L_ = s.L;
         N_ = 1ull << (2 * L_);
         H_ = hier_size(L_);
@@ -75,6 +79,15 @@ class EngineT final : public Engine {
         if (!alloc(&counts_, (size_t)ntiles_ * 3 * sizeof(uint32_t))) return oom();
         offs_ = counts_ + ntiles_;
         dlist_ = counts_ + 2 * ntiles_;
+        // shared faces of the wet-leaf update: 10 values per queued leaf, a
+        // stamp per hierarchy cell.  Float64 only: in float32 the arithmetic
+        // saved costs less than the extra launch and face traffic.
+        if (!batched_ && sizeof(T) == 8) {
+            fcap_ = (uint32_t)std::min<uint64_t>(N_, 1ull << 22);
+            if (!alloc(&face_, (size_t)fcap_ * 10 * sizeof(T))) return oom();
+            if (!alloc(&mark_, H_ * sizeof(unsigned long long))) return oom();
+            cudaMemsetAsync(mark_, 0, H_ * sizeof(unsigned long long), stream_);
+        }
         // quiescent-tile bookkeeping: zf (two buffers), inlet, act
         if (!alloc(&tilebytes_, (size_t)ntiles_ * 4)) return oom();
         cudaMemsetAsync(tilebytes_, 0, (size_t)ntiles_ * 4, stream_);
@@ -582,6 +595,9 @@ class EngineT final : public Engine {
         }
         a.a0 = spec_.inflow_a0;
         a.a1 = spec_.inflow_a1;
+        a.face = face_;
+        a.fcap = fcap_;
+        a.mark = mark_;
         return a;
     }
     Phys<T> phys() const {
@@ -599,8 +615,15 @@ class EngineT final : public Engine {
         const StepArgs<T> a = step_args();
         k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
         mark("k_fv1_dry");
-        k_fv1_wet<T><<<grid_for(N_), 256, 0, stream_>>>(a);
-        mark("k_fv1_wet");
+        if (face_) {
+            k_fv1_faces<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+            mark("k_fv1_faces");
+            k_fv1_update<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+            mark("k_fv1_update");
+        } else {
+            k_fv1_wet<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+            mark("k_fv1_wet");
+        }
     }
     DecodeArgs<T> decode_args() const {
         DecodeArgs<T> a;
@@ -737,6 +760,10 @@ class EngineT final : public Engine {
     uint32_t* wet_ = nullptr;
     uint32_t *counts_ = nullptr, *offs_ = nullptr, *dlist_ = nullptr;
     uint8_t* tilebytes_ = nullptr;      // per tile: zf of buffer 0, zf of buffer 1, inlet, act
+    bool batched_ = false;
+    T* face_ = nullptr;                 // shared faces (10 x fcap_)
+    uint32_t fcap_ = 0;
+    unsigned long long* mark_ = nullptr;   // per hierarchy cell: (epoch + 1) << 32 | queue slot
     uint32_t* scount_ = nullptr;        // per tile: leaves when it holds the bed's flags alone
     bool quiet_on_ = false;
     std::vector<std::pair<const char*, cudaEvent_t>>* prof_ = nullptr;   // profile_step's events

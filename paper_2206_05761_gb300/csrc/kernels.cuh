@@ -979,6 +979,11 @@ __device__ __forceinline__ void hll_face(T g, T hg, T tol, T hL, T zL, T unL, T 
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+                                                  const T FW[3], const T FE[3], const T GS[3], const T GN[3],
+                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3]);
+
 // New (h, qx, qy) of a cell of size dx x dy: rx = dt/dx, ry = dt/dy.
 template <typename T>
 __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
@@ -1005,6 +1010,16 @@ __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, 
         hll_face(g, hg, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
         hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hN_L, dummy);
     }
+    cell_update_faces(P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out);
+}
+
+// The update of cell_update from its four face fluxes and its own
+// reconstructed depths at them (hW_R, hE_L, hS_R, hN_L).
+template <typename T>
+__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+                                                  const T FW[3], const T FE[3], const T GS[3], const T GN[3],
+                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3]) {
+    const T g = P.g, hg = P.hg, tol = P.tol;
     const T bx = hg * (hW_R * hW_R - hE_L * hE_L);
     const T by = hg * (hS_R * hS_R - hN_L * hN_L);
     T h = C.h - rx * (FE[0] - FW[0]) - ry * (GN[0] - GS[0]);
@@ -1054,6 +1069,12 @@ struct StepArgs {
     int bc_ref[4];           // 1: the side reflects (closed or inflow)
     int inflow_side;         // -1: none
     int a0, a1;
+    // shared faces (k_fv1_faces / k_fv1_update): 10 arrays of fcap values
+    // (east face F0..F2, h*_L, h*_R, then the north face's), and a stamp per
+    // hierarchy cell ((epoch + 1) << 32 | queue slot)
+    T* face = nullptr;
+    uint32_t fcap = 0;
+    unsigned long long* mark = nullptr;
 };
 
 template <typename T>
@@ -1206,6 +1227,66 @@ static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
     fv1_dry_body<T>(a, this_blk());
 }
 
+// CFL bound, write-back (with the prolongation of leaves of 4 or 16 finest
+// cells) and reductions of one updated wet leaf.
+template <typename T>
+__device__ __forceinline__ void wet_leaf_store(const StepArgs<T>& a, DevState* st, const T* z, T* oh, T* oqx,
+                                               T* oqy, int n, uint32_t code, uint64_t iC, const Cell<T>& C,
+                                               const T out[3], unsigned long long& rmin, unsigned long long& mh,
+                                               unsigned long long& mqx, unsigned long long& mqy) {
+    const T r = cfl_bound(a.P, out[0], out[1], out[2]);
+    const unsigned long long rb = obits((double)r);
+    rmin = rb < rmin ? rb : rmin;
+    if (n == a.L || needs_decode_kernel(n, a.L)) {
+        oh[iC] = out[0];
+        oqx[iC] = out[1];
+        oqy[iC] = out[2];
+        if (n == a.L) {
+            const unsigned long long b0 = abs_obits(out[0]);
+            mh = b0 > mh ? b0 : mh;
+            const unsigned long long b1 = abs_obits(out[1]);
+            mqx = b1 > mqx ? b1 : mqx;
+            const unsigned long long b2 = abs_obits(out[2]);
+            mqy = b2 > mqy ? b2 : mqy;
+        }
+    } else {
+        // decode-back of a leaf of 4 or 16 finest cells (as k_decode does)
+        const uint64_t fo = lvl_off(a.L) + ((uint64_t)code << (2 * (a.L - n)));
+        const uint32_t cnt = 1u << (2 * (a.L - n));
+        const T hl = out[0];
+        const bool restore = ge_nonneg(hl, a.P.tol);
+        const T eta = restore ? hl + C.z : T(0);
+        for (uint32_t e = 0; e < cnt; e += 4) {
+            T hf[4];
+            if (restore) {
+                T z0, z1, z2, z3;
+                Vec4<T>::load(z + fo + e, z0, z1, z2, z3);
+                const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
+                hf[0] = gt_zero(d0) ? d0 : T(0);
+                hf[1] = gt_zero(d1) ? d1 : T(0);
+                hf[2] = gt_zero(d2) ? d2 : T(0);
+                hf[3] = gt_zero(d3) ? d3 : T(0);
+            } else {
+                hf[0] = hf[1] = hf[2] = hf[3] = hl;
+            }
+            Vec4<T>::store(oh + fo + e, hf[0], hf[1], hf[2], hf[3]);
+            Vec4<T>::store(oqx + fo + e, out[1], out[1], out[1], out[1]);
+            Vec4<T>::store(oqy + fo + e, out[2], out[2], out[2], out[2]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned long long b = abs_obits(hf[q]);
+                mh = b > mh ? b : mh;
+            }
+        }
+        const unsigned long long b1 = abs_obits(out[1]);
+        mqx = b1 > mqx ? b1 : mqx;
+        const unsigned long long b2 = abs_obits(out[2]);
+        mqy = b2 > mqy ? b2 : mqy;
+    }
+    if (!(finite_bits(out[0]) && finite_bits(out[1]) && finite_bits(out[2])))
+        atomicOr(&st->err, kErrNonFinite);
+}
+
 // FV1, second kernel: the full update (Eq. 2 with the L_c reading) of every
 // queued leaf, with the CFL and s_max reductions.
 template <typename T>
@@ -1254,57 +1335,7 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
         }
         T out[3];
         cell_update(a.P, rx, ry, dt, C, W, E, S, N, inlet, dh, out);
-        const T r = cfl_bound(a.P, out[0], out[1], out[2]);
-        const unsigned long long rb = obits((double)r);
-        rmin = rb < rmin ? rb : rmin;
-        if (n == a.L || needs_decode_kernel(n, a.L)) {
-            oh[iC] = out[0];
-            oqx[iC] = out[1];
-            oqy[iC] = out[2];
-            if (n == a.L) {
-                const unsigned long long b0 = abs_obits(out[0]);
-                mh = b0 > mh ? b0 : mh;
-                const unsigned long long b1 = abs_obits(out[1]);
-                mqx = b1 > mqx ? b1 : mqx;
-                const unsigned long long b2 = abs_obits(out[2]);
-                mqy = b2 > mqy ? b2 : mqy;
-            }
-        } else {
-            // decode-back of a leaf of 4 or 16 finest cells (as k_decode does)
-            const uint64_t fo = lvl_off(a.L) + ((uint64_t)code << (2 * (a.L - n)));
-            const uint32_t cnt = 1u << (2 * (a.L - n));
-            const T hl = out[0];
-            const bool restore = ge_nonneg(hl, a.P.tol);
-            const T eta = restore ? hl + C.z : T(0);
-            for (uint32_t e = 0; e < cnt; e += 4) {
-                T hf[4];
-                if (restore) {
-                    T z0, z1, z2, z3;
-                    Vec4<T>::load(src.z + fo + e, z0, z1, z2, z3);
-                    const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
-                    hf[0] = gt_zero(d0) ? d0 : T(0);
-                    hf[1] = gt_zero(d1) ? d1 : T(0);
-                    hf[2] = gt_zero(d2) ? d2 : T(0);
-                    hf[3] = gt_zero(d3) ? d3 : T(0);
-                } else {
-                    hf[0] = hf[1] = hf[2] = hf[3] = hl;
-                }
-                Vec4<T>::store(oh + fo + e, hf[0], hf[1], hf[2], hf[3]);
-                Vec4<T>::store(oqx + fo + e, out[1], out[1], out[1], out[1]);
-                Vec4<T>::store(oqy + fo + e, out[2], out[2], out[2], out[2]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const unsigned long long b = abs_obits(hf[q]);
-                    mh = b > mh ? b : mh;
-                }
-            }
-            const unsigned long long b1 = abs_obits(out[1]);
-            mqx = b1 > mqx ? b1 : mqx;
-            const unsigned long long b2 = abs_obits(out[2]);
-            mqy = b2 > mqy ? b2 : mqy;
-        }
-        if (!(finite_bits(out[0]) && finite_bits(out[1]) && finite_bits(out[2])))
-            atomicOr(&st->err, kErrNonFinite);
+        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
     block_max3_u64(mh, mqx, mqy, st->max_bits);
@@ -1312,6 +1343,171 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
     fv1_wet_body<T>(a, this_blk());
+}
+
+// The same update in two kernels that compute every face between two queued
+// leaves of one level once.  Phase 1: each queued leaf computes its east and
+// north faces (it is their left side) and stamps its cell.  Phase 2: a
+// queued leaf whose west (south) same-level neighbour carries this step's
+// stamp takes that neighbour's east (north) face -- the same call with the
+// same operands, so the same bits -- and computes only its other faces.
+template <typename T>
+__device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
+    DevState* st = a.st;
+    if (!st->active) return;
+    const uint32_t nq = st->nwet;
+    if (nq > a.fcap || B.id * blockDim.x >= nq) return;
+    const int par = (int)st->cur;
+    CellSrc<T> src;
+    src.h = par ? a.f[1][0] : a.f[0][0];
+    src.qx = par ? a.f[1][1] : a.f[0][1];
+    src.qy = par ? a.f[1][2] : a.f[0][2];
+    src.z = a.z;
+    const T g = a.P.g, hg = a.P.hg, tol = a.P.tol;
+    const unsigned long long stamp = (unsigned long long)(st->epoch + 1u) << 32;
+    const uint32_t cap = a.fcap;
+    for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
+        const uint32_t pk = __ldg(a.leaves + a.wet[w]);
+        const int n = (int)(pk >> kLeafShift);
+        const uint32_t code = pk & kCodeMask;
+        const uint32_t i = compact16(code), j = compact16(code >> 1);
+        const uint32_t last = (1u << n) - 1u;
+        const uint64_t base = lvl_off(n);
+        const uint64_t iC = base + code;
+        const Cell<T> C = fetch(src, iC);
+        const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
+        const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
+        T uC, vC, uE, vE, uN, vN;
+        velocity(C, tol, uC, vC);
+        velocity(E, tol, uE, vE);
+        velocity(N, tol, uN, vN);
+        T FE[3], GN[3], hEL, hER, hNL, hNR;
+        hll_face(g, hg, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hEL, hER);
+        hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hNL, hNR);
+        T* f = a.face + w;
+        f[0 * (size_t)cap] = FE[0];
+        f[1 * (size_t)cap] = FE[1];
+        f[2 * (size_t)cap] = FE[2];
+        f[3 * (size_t)cap] = hEL;
+        f[4 * (size_t)cap] = hER;
+        f[5 * (size_t)cap] = GN[0];
+        f[6 * (size_t)cap] = GN[1];
+        f[7 * (size_t)cap] = GN[2];
+        f[8 * (size_t)cap] = hNL;
+        f[9 * (size_t)cap] = hNR;
+        a.mark[iC] = stamp | w;
+    }
+}
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_faces(StepArgs<T> a) {
+    fv1_faces_body<T>(a, this_blk());
+}
+
+template <typename T>
+__device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
+    DevState* st = a.st;
+    if (!st->active) return;
+    const uint32_t nq = st->nwet;
+    if (nq > a.fcap) {                            // no room for the faces: one pass
+        fv1_wet_body<T>(a, B);
+        return;
+    }
+    if (B.id * blockDim.x >= nq) return;          // whole block idle
+    const int par = (int)st->cur, nxt = par ^ 1;
+    const T dt = (T)st->dt_use;
+    const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
+    const T Qdt = (T)st->Qdt;
+    CellSrc<T> src;
+    src.h = par ? a.f[1][0] : a.f[0][0];
+    src.qx = par ? a.f[1][1] : a.f[0][1];
+    src.qy = par ? a.f[1][2] : a.f[0][2];
+    src.z = a.z;
+    T* const oh = nxt ? a.f[1][0] : a.f[0][0];
+    T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
+    T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
+    const T g = a.P.g, hg = a.P.hg, tol = a.P.tol;
+    const uint32_t tag = st->epoch + 1u;
+    const uint32_t cap = a.fcap;
+    const T* F = a.face;
+    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0;
+    for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
+        const uint32_t pk = __ldg(a.leaves + a.wet[w]);
+        const int n = (int)(pk >> kLeafShift);
+        const uint32_t code = pk & kCodeMask;
+        const uint32_t i = compact16(code), j = compact16(code >> 1);
+        const uint32_t last = (1u << n) - 1u;
+        const uint64_t base = lvl_off(n);
+        const uint64_t iC = base + code;
+        const Cell<T> C = fetch(src, iC);
+        T FE[3], GN[3], FW[3], GS[3], hE_L, hN_L, hW_R, hS_R;
+        FE[0] = F[0 * (size_t)cap + w];
+        FE[1] = F[1 * (size_t)cap + w];
+        FE[2] = F[2 * (size_t)cap + w];
+        hE_L = F[3 * (size_t)cap + w];
+        GN[0] = F[5 * (size_t)cap + w];
+        GN[1] = F[6 * (size_t)cap + w];
+        GN[2] = F[7 * (size_t)cap + w];
+        hN_L = F[8 * (size_t)cap + w];
+        bool haveW = false, haveS = false;
+        if (i > 0) {
+            const unsigned long long m = __ldg(a.mark + base + morton2(i - 1, j));
+            if ((uint32_t)(m >> 32) == tag) {
+                const uint32_t v = (uint32_t)m;
+                FW[0] = F[0 * (size_t)cap + v];
+                FW[1] = F[1 * (size_t)cap + v];
+                FW[2] = F[2 * (size_t)cap + v];
+                hW_R = F[4 * (size_t)cap + v];
+                haveW = true;
+            }
+        }
+        if (j > 0) {
+            const unsigned long long m = __ldg(a.mark + base + morton2(i, j - 1));
+            if ((uint32_t)(m >> 32) == tag) {
+                const uint32_t v = (uint32_t)m;
+                GS[0] = F[5 * (size_t)cap + v];
+                GS[1] = F[6 * (size_t)cap + v];
+                GS[2] = F[7 * (size_t)cap + v];
+                hS_R = F[9 * (size_t)cap + v];
+                haveS = true;
+            }
+        }
+        if (!(haveW && haveS)) {
+            T uC, vC, dummy;
+            velocity(C, tol, uC, vC);
+            if (!haveW) {
+                const Cell<T> W = i > 0 ? fetch(src, base + morton2(i - 1, j)) : ghost(C, a.bc_ref[0], true);
+                T uW, vW;
+                velocity(W, tol, uW, vW);
+                hll_face(g, hg, tol, W.h, W.z, uW, vW, C.h, C.z, uC, vC, FW, dummy, hW_R);
+            }
+            if (!haveS) {
+                const Cell<T> S = j > 0 ? fetch(src, base + morton2(i, j - 1)) : ghost(C, a.bc_ref[2], false);
+                T uS, vS;
+                velocity(S, tol, uS, vS);
+                hll_face(g, hg, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
+            }
+        }
+        const T scale = (T)(1u << n);
+        const T rx = rx0 * scale, ry = ry0 * scale;
+        int64_t lo = 0, hi = 0;
+        const bool inlet = inlet_range(a, n, i, j, last, lo, hi);
+        T dh = T(0);
+        if (inlet) {
+            const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
+            const T inv2n = T(1) / scale;
+            const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
+            dh = (Qdt * frac) / (dxn * dyn);
+        }
+        T out[3];
+        cell_update_faces(a.P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out);
+        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy);
+    }
+    block_atomic_u64<false>(rmin, &st->rmin_bits);
+    block_max3_u64(mh, mqx, mqy, st->max_bits);
+}
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_update(StepArgs<T> a) {
+    fv1_update_body<T>(a, this_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -1481,6 +1677,7 @@ __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
             !isfinite(st->smax[2]))
             st->err |= kErrNonFinite;
         st->step += 1;
+        st->epoch += 1u;
         st->leaf_updates += st->Mall;
         st->act_updates += st->M;
         st->wet_updates += st->nwet;

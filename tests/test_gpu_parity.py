@@ -204,7 +204,7 @@ def test_profiled_step_is_an_ordinary_step():
     prof = Hh.hwfv1_profile_step(sim.hd)
     names = [n for n, _ in prof]
     assert names[0] == "k_clear_words" and names[-1] == "k_decode_finish"
-    for k in ("k_flag", "k_trav_fused", "k_fv1_dry", "k_fv1_wet"):
+    for k in ("k_flag", "k_trav_fused", "k_fv1_dry", "k_fv1_faces", "k_fv1_update"):
         assert k in names
     assert all(t >= 0.0 for _, t in prof)
     res = ref.step(want=("leaves",))
@@ -323,6 +323,13 @@ def test_full_size_terrain_flood_L12_bench_launch_path():
     n, lu, au, wu, kps = sim.counters()
     assert lu == ref.leaf_updates and au < lu
     sim.close()
+
+
+def test_full_size_wet_domain_one_step():
+    # 4096 x 4096 bumpy dam-break: about 16 M wet leaves, more than the
+    # shared-face buffer holds, so the update takes its one-pass form
+    p, f = synth.bumpy_dam_break(L=12, eps=1e-3)
+    one_step_parity(p, f)
 
 
 @pytest.mark.parametrize("relief", [0.0, 0.05])
