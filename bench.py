@@ -461,6 +461,28 @@ def time_precision(args, precision, p, state, t_s, dt_s, steps):
             "dtype": "f32" if precision == 32 else "f64"}
 
 
+def time_uniform(args, p, state, t_s, dt_s, steps):
+    """Uniform FV1 on the finest grid (the paper's GPU-FV1 comparison
+    solver) on the same window: device-timed steps/s."""
+    import torch
+    from paper_2206_05761_gb300.sim import Simulation
+    stream = torch.cuda.Stream()
+    sim = Simulation(p, state, args.precision, stream=stream)
+    sim.set_time(t_s, dt_s)
+    sim.advance_uniform(max_steps=max(args.warmup, 3))
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.advance_uniform(max_steps=steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = sim.time()[0]
+    sim.close()
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "sim_time_s": [t_s, t], "leaves": 1 << (2 * args.L)}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -563,6 +585,10 @@ def main():
     if world == 1:
         out["other_precision"] = time_precision(args, 32 if args.precision == 64 else 64, r["problem"],
                                                 r["snapshot"], r["t_start"], r["dt_start"], args.steps)
+    if world == 1:
+        u = time_uniform(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"], args.steps)
+        u["hwfv1_speedup"] = value / u["value"]
+        out["uniform_fv1"] = u
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_learned:

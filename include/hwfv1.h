@@ -145,6 +145,15 @@ hwfv1_status hwfv1_decode(hwfv1_handle* hd);
  * Does not synchronise. */
 hwfv1_status hwfv1_advance(hwfv1_handle* hd, double t_end, int64_t max_steps);
 
+/* The same time loop with uniform FV1 on the finest grid: every finest cell
+ * is updated from its four finest neighbours every step, with no encode,
+ * flag, traversal or decode (eps plays no part).  This is the GPU-FV1
+ * solver the paper compares HWFV1 against (Sec. 3); it reproduces HWFV1
+ * with eps = 0.  The state stays the finest fields, so the two loops can be
+ * mixed on one handle.  Allocates a list of the 4^L finest cells on first
+ * use.  Does not synchronise. */
+hwfv1_status hwfv1_advance_uniform(hwfv1_handle* hd, double t_end, int64_t max_steps);
+
 /* Current finest fields h, hu, hv (device, row-major float64, 4^L each;
  * any pointer may be NULL). */
 hwfv1_status hwfv1_get_fields(hwfv1_handle* hd, double* h, double* qx, double* qy);

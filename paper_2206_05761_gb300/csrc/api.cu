@@ -131,6 +131,11 @@ hwfv1_status hwfv1_advance(hwfv1_handle* hd, double t_end, int64_t max_steps) {
     if (std::isnan(t_end)) return HWFV1_ERR_INVALID_SPEC;
     return from_engine(hd, hd->eng->advance(t_end, max_steps));
 }
+hwfv1_status hwfv1_advance_uniform(hwfv1_handle* hd, double t_end, int64_t max_steps) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (std::isnan(t_end)) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->advance_uniform(t_end, max_steps));
+}
 hwfv1_status hwfv1_get_fields(hwfv1_handle* hd, double* h, double* qx, double* qy) {
     HWFV1_CHECK_HANDLE(hd);
     return from_engine(hd, hd->eng->get_fields(h, qx, qy));

@@ -49,6 +49,7 @@ class EngineT final : public Engine {
     ~EngineT() override {
         if (exec_) cudaGraphExecDestroy(exec_);
         if (exec_learned_) cudaGraphExecDestroy(exec_learned_);
+        if (exec_uniform_) cudaGraphExecDestroy(exec_uniform_);
         skipwork_free(&skw_);
         for (void* p : allocs_) cudaFree(p);
         if (own_stream_) cudaStreamDestroy(stream_);
@@ -209,6 +210,43 @@ class EngineT final : public Engine {
             }
         }
         return check("advance");
+    }
+
+    // Uniform FV1 on the finest grid (eps plays no part): the comparison
+    // solver of the paper's Sec. 3 (GPU-FV1), on the same kernels.
+    hwfv1_status advance_uniform(double t_end, int64_t max_steps) override {
+        if (max_steps < 0) return fail(HWFV1_ERR_INVALID_SPEC, "max_steps < 0");
+        if (!uniform_leaves_) {
+            if (!alloc(&uniform_leaves_, N_ * sizeof(uint32_t))) return oom();
+            k_fill_finest_leaves<<<grid_for(N_), 256, 0, stream_>>>(uniform_leaves_, L_, N_);
+        }
+        // uniform steps keep no quiescence marks: forget them for later
+        // adaptive steps
+        forget_quiet();
+        k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), t_end);
+        if (max_steps == 0) return check("advance_uniform");
+        const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
+        if (use_graph && !exec_uniform_) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return fail(HWFV1_ERR_CUDA, "graph capture begin");
+            launch_step_uniform();
+            if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph capture end");
+            const cudaError_t e = cudaGraphInstantiate(&exec_uniform_, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                exec_uniform_ = nullptr;
+                return fail(HWFV1_ERR_CUDA, "graph instantiate");
+            }
+        }
+        for (int64_t s = 0; s < max_steps; ++s) {
+            if (use_graph) {
+                if (cudaGraphLaunch(exec_uniform_, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
+            } else {
+                launch_step_uniform();
+            }
+        }
+        return check("advance_uniform");
     }
 
     hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin) override {
@@ -611,8 +649,9 @@ class EngineT final : public Engine {
         P.dyL = (T)std::ldexp(spec_.ly, -L_);
         return P;
     }
-    void launch_fv1() {
-        const StepArgs<T> a = step_args();
+    void launch_fv1(const uint32_t* leaves = nullptr) {
+        StepArgs<T> a = step_args();
+        if (leaves) a.leaves = leaves;
         k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
         mark("k_fv1_dry");
         if (face_) {
@@ -642,6 +681,11 @@ class EngineT final : public Engine {
     void launch_decode() {
         k_decode_finish<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(decode_args(), fin_args());
         mark("k_decode_finish");
+    }
+    void launch_step_uniform() {
+        k_set_uniform<<<1, 32, 0, stream_>>>(st_, (uint32_t)N_);
+        launch_fv1(uniform_leaves_);
+        launch_decode();
     }
     void launch_step_all() {
         launch_encode();
@@ -780,6 +824,8 @@ class EngineT final : public Engine {
     __nv_bfloat16* feat_ = nullptr;
     uint8_t* phat_ = nullptr;
     cudaGraphExec_t exec_learned_ = nullptr;
+    cudaGraphExec_t exec_uniform_ = nullptr;
+    uint32_t* uniform_leaves_ = nullptr;   // every finest cell as a leaf (uniform FV1)
     int64_t kernels_plain_ = 0, kernels_learned_ = 0;   // kernel nodes of the captured step graphs
 };
 

@@ -24,6 +24,7 @@ class Engine {
     virtual hwfv1_status step() = 0;
     virtual hwfv1_status decode() = 0;
     virtual hwfv1_status advance(double t_end, int64_t max_steps) = 0;
+    virtual hwfv1_status advance_uniform(double t_end, int64_t max_steps) = 0;
     virtual hwfv1_status get_fields(double* h, double* qx, double* qy) = 0;
     virtual hwfv1_status set_fields(const double* h, const double* qx, const double* qy) = 0;
     virtual hwfv1_status get_leaves(uint32_t* out, int64_t cap, int64_t* n) = 0;

@@ -1510,6 +1510,19 @@ static __global__ void __launch_bounds__(256) k_fv1_update(StepArgs<T> a) {
     fv1_update_body<T>(a, this_blk());
 }
 
+// Uniform FV1 (every finest cell a leaf): the fixed leaf list in Z-order ...
+static __global__ void k_fill_finest_leaves(uint32_t* leaves, int L, uint64_t N) {
+    for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < N; m += (uint64_t)gridDim.x * blockDim.x)
+        leaves[m] = ((uint32_t)L << kLeafShift) | (uint32_t)m;
+}
+// ... and the step's list counts (no tile is skipped, none needs decoding).
+static __global__ void k_set_uniform(DevState* st, uint32_t N) {
+    if (threadIdx.x != 0 || !st->active) return;
+    st->M = N;
+    st->Mall = N;
+    st->ndec = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // Decode-back (Eq. 4 with zero details below leaves, free surface restored
 // on wet coarse leaves), tile-parallel like the traversal.

@@ -66,6 +66,7 @@ def lib():
                 getattr(L, "hwfv1_" + name).argtypes = [_H]
             L.hwfv1_traverse.argtypes = [_H, C.POINTER(C.c_int64)]
             L.hwfv1_advance.argtypes = [_H, C.c_double, C.c_int64]
+            L.hwfv1_advance_uniform.argtypes = [_H, C.c_double, C.c_int64]
             L.hwfv1_get_fields.argtypes = [_H, _dp, _dp, _dp]
             L.hwfv1_set_fields.argtypes = [_H, _dp, _dp, _dp]
             L.hwfv1_get_leaves.argtypes = [_H, _dp, C.c_int64, C.POINTER(C.c_int64)]
@@ -117,7 +118,7 @@ def lib():
 
 def exported_symbols():
     return ["hwfv1_init", "hwfv1_encode", "hwfv1_flag", "hwfv1_traverse", "hwfv1_step",
-            "hwfv1_decode", "hwfv1_advance", "hwfv1_get_fields", "hwfv1_set_fields",
+            "hwfv1_decode", "hwfv1_advance", "hwfv1_advance_uniform", "hwfv1_get_fields", "hwfv1_set_fields",
             "hwfv1_get_leaves", "hwfv1_get_flags", "hwfv1_get_level", "hwfv1_get_time",
             "hwfv1_set_time", "hwfv1_get_stats", "hwfv1_get_counters", "hwfv1_profile_step", "hwfv1_save", "hwfv1_load",
             "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version", "hwfv1_traverse_noalloc",
@@ -261,6 +262,10 @@ def hwfv1_profile_step(hd, cap=64):
     n = C.c_int32()
     _check(lib().hwfv1_profile_step(hd, ms, names, cap, C.byref(n)), "hwfv1_profile_step", hd)
     return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
+
+
+def hwfv1_advance_uniform(hd, t_end=float("inf"), max_steps=1):
+    _check(lib().hwfv1_advance_uniform(hd, float(t_end), int(max_steps)), "hwfv1_advance_uniform", hd)
 
 
 def hwfv1_get_counters(hd):

@@ -51,6 +51,10 @@ class Simulation:
     def advance(self, t_end=float("inf"), max_steps=1):
         H.hwfv1_advance(self.hd, t_end, max_steps)
 
+    def advance_uniform(self, t_end=float("inf"), max_steps=1):
+        """Uniform FV1 on the finest grid (the GPU-FV1 comparison solver)."""
+        H.hwfv1_advance_uniform(self.hd, t_end, max_steps)
+
     # -- results ------------------------------------------------------------
     def fields(self):
         h, qx, qy = self._bufs

@@ -361,3 +361,52 @@ def test_quiescent_tile_skipping_is_exact(relief):
         assert au < 0.5 * lu
     sim.close()
     full.close()
+
+
+def test_uniform_fv1_matches_oracle():
+    # hwfv1_advance_uniform: uniform FV1 on the finest grid (the comparison
+    # solver), against the oracle's uniform step, bit for bit
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    for chunk in range(4):
+        sim.advance_uniform(max_steps=5)
+        for _ in range(5):
+            ref.fv1_step()
+        _compare_fields(sim, ref)
+        t, dt, steps = sim.time()
+        assert (t, dt, steps) == (ref.t, ref.dt, ref.steps)
+    sim.close()
+
+
+def test_uniform_fv1_with_friction_and_inflow():
+    p, f = synth.terrain_flood(L=8, fill=2.0, fill_q=1.0)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    sim.advance_uniform(max_steps=6)
+    for _ in range(6):
+        ref.fv1_step()
+    _compare_fields(sim, ref, exact=False)
+    sim.close()
+
+
+def test_uniform_and_adaptive_steps_mix():
+    # adaptive steps (with quiescent tiles skipped), then uniform steps, then
+    # adaptive again on dry rough ground: the same as the oracle's sequence
+    p, f = synth.dry_bed_dam_break(L=8, eps=1e-3, relief=0.05)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    sim.advance(max_steps=8)
+    for _ in range(8):
+        ref.step()
+    sim.advance_uniform(max_steps=8)
+    for _ in range(8):
+        ref.fv1_step()
+    sim.advance(max_steps=8)
+    for _ in range(7):
+        ref.step()
+    res = ref.step(want=("leaves",))
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    _compare_fields(sim, ref)
+    assert sim.time()[:2] == (ref.t, ref.dt)
+    sim.close()
