@@ -212,8 +212,9 @@ struct DevState {
     uint32_t nwet;                    // leaves queued for the full FV1 update
     uint32_t ndec;                    // tiles listed for the decode kernel
     uint32_t Mall;                    // leaves of the last traversal, skipped tiles included
-    uint32_t M;                       // leaves in the step's list (processed tiles); ndec, Mall
-                                      // and M are adjacent (cleared together)
+    uint32_t M;                       // leaves in the step's list (processed tiles)
+    uint32_t nact;                    // tiles in the traversal's work list; ndec, Mall, M and
+                                      // nact are adjacent (cleared together)
     double rx0, ry0;                  // dt_use/lx, dt_use/ly (dt/dx_n = rx0 * 2^n)
     float rx0f, ry0f;                 // same, float arithmetic
     double thr[kMaxL * 3];            // eps*2^(n-L)*s_max,q for h, qx, qy

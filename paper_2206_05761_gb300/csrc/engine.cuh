@@ -91,6 +91,7 @@ class EngineT final : public Engine {
         }
         // quiescent-tile bookkeeping: zf (two buffers), inlet, act
         if (!alloc(&tilebytes_, (size_t)ntiles_ * 4)) return oom();
+        if (!alloc(&work_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
         cudaMemsetAsync(tilebytes_, 0, (size_t)ntiles_ * 4, stream_);
         quiet_on_ = !(spec_.flags & HWFV1_FULL_SWEEP) && spec_.eps >= 1e-30;
         {
@@ -171,6 +172,7 @@ class EngineT final : public Engine {
         return check("flag");
     }
     hwfv1_status traverse(int64_t* num_leaves) override {
+        cudaMemsetAsync(&st_->ndec, 0, 4 * sizeof(uint32_t), stream_);     // ndec, Mall, M, nact
         launch_traverse();
         if (num_leaves) {
             DevState s;
@@ -580,19 +582,27 @@ class EngineT final : public Engine {
         encode_passes(a, &st_->enc_ticket);
     }
     void launch_flag() {
-        k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_);
+        k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_,
+                                                       &st_->ndec);
         mark("k_flag");
     }
     // `learned`: the flags come from the learned look-ahead, whose skipped
-    // tiles need not hold the bed's static flags alone (no cached counts)
+    // tiles need not hold the bed's static flags alone (no cached counts).
+    // The four counters (ndec, Mall, M, nact) were cleared by the flag kernel.
     void launch_traverse(bool learned = false) {
-        cudaMemsetAsync(&st_->ndec, 0, 3 * sizeof(uint32_t), stream_);     // ndec, Mall, M
-        mark("memset");
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
         const uint32_t grid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
-        k_trav_fused<<<grid, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
-                                                learned ? nullptr : scount_);
-        mark("k_trav_fused");
+        if (quiet_on_) {
+            k_trav_classify<<<(ntiles_ + 255) / 256, 256, 0, stream_>>>(Sb_, L_, kt_, ntiles_, st_, quiet(),
+                                                                      learned ? nullptr : scount_, work_);
+            mark("k_trav_classify");
+            k_trav_list<<<nsm_ * 8, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, st_, work_);
+            mark("k_trav_list");
+        } else {
+            k_trav_fused<<<grid, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
+                                                    learned ? nullptr : scount_);
+            mark("k_trav_fused");
+        }
     }
     void mark(const char* name) {
         if (!prof_) return;
@@ -679,7 +689,10 @@ class EngineT final : public Engine {
         return a;
     }
     void launch_decode() {
-        k_decode_finish<T><<<grid_for((uint64_t)ntiles_ * 256), 256, 0, stream_>>>(decode_args(), fin_args());
+        // the decode list is short once quiescent tiles are skipped: 2 CTAs per SM
+        const int gd = quiet_on_ ? std::min(grid_for((uint64_t)ntiles_ * 256), nsm_ * 2)
+                                 : grid_for((uint64_t)ntiles_ * 256);
+        k_decode_finish<T><<<gd, 256, 0, stream_>>>(decode_args(), fin_args());
         mark("k_decode_finish");
     }
     void launch_step_uniform() {
@@ -708,7 +721,7 @@ class EngineT final : public Engine {
         skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
         k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
         k_flag_learned<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
-                                                              close(), st_);
+                                                              close(), st_, &st_->ndec);
         launch_traverse(/*learned=*/true);
         launch_fv1();
         launch_decode();
@@ -809,6 +822,7 @@ class EngineT final : public Engine {
     uint32_t fcap_ = 0;
     unsigned long long* mark_ = nullptr;   // per hierarchy cell: (epoch + 1) << 32 | queue slot
     uint32_t* scount_ = nullptr;        // per tile: leaves when it holds the bed's flags alone
+    uint32_t* work_ = nullptr;          // the traversal's list of tiles to treat one warp each
     bool quiet_on_ = false;
     std::vector<std::pair<const char*, cudaEvent_t>>* prof_ = nullptr;   // profile_step's events
     DevState* st_ = nullptr;

@@ -415,9 +415,12 @@ __device__ __forceinline__ void flag_body(const uint32_t* __restrict__ Tb, const
         Sb[w] = s;
     }
 }
+// zero4: the traversal's four counters (ndec, Mall, M, nact), cleared here
+// for the traversal that follows (NULL: none).
 static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
                               const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb, int L,
-                              int predict, int close, const DevState* st) {
+                              int predict, int close, const DevState* st, uint32_t* zero4 = nullptr) {
+    if (zero4 && blockIdx.x == 0 && threadIdx.x < 4u) zero4[threadIdx.x] = 0u;
     flag_body(Tb, Cb, Sbase, Sb, L, predict, close, st, this_blk());
 }
 
@@ -899,6 +902,113 @@ static __global__ void __launch_bounds__(256) k_trav_fused(const uint32_t* __res
                                                            uint32_t ntiles, DevState* st, Quiet q,
                                                            const uint32_t* scount) {
     trav_fused_body(Sb, dlist, leaves, L, kt, ntiles, st, q, scount);
+}
+
+// The traversal in two launches, for quiescent tiles: k_trav_classify
+// decides every tile with one thread (its root path and marks loaded at
+// once), counts a skipped tile from scount, and lists the others for
+// k_trav_list, which treats them one warp per tile as k_trav_fused does.
+// A list entry with bit 31 set is a skipped tile that is only counted (no
+// scount: the learned look-ahead's flags).
+static __global__ void __launch_bounds__(256) k_trav_classify(const uint32_t* __restrict__ Sb, int L, int kt,
+                                                              uint32_t ntiles, DevState* st, Quiet q,
+                                                              const uint32_t* scount, uint32_t* work) {
+    if (!st->active) return;
+    const int Lr = L - kt;
+    const uint32_t cur = st->cur;
+    const uint8_t* X = cur ? q.zf[1] : q.zf[0];
+    uint8_t* Y = cur ? q.zf[0] : q.zf[1];
+    const uint32_t lm = (1u << (2 * Lr)) - 1u;
+    uint32_t counted = 0u;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        // first insignificant cell on the root path (levels 0..Lr), else Lr+1
+        uint32_t bits[kMaxL];
+#pragma unroll
+        for (int n = 0; n < kMaxL; ++n)
+            if (n <= Lr) bits[n] = sig_bit(Sb, n, t >> (2 * (Lr - n)));
+        int l0 = Lr + 1;
+#pragma unroll
+        for (int n = kMaxL - 1; n >= 0; --n)
+            if (n <= Lr && !bits[n]) l0 = n;
+        const bool covered = l0 < Lr;
+        const uint32_t xs = t & kXBits & lm, ys = t & kYBits & lm;
+        const bool xw = xs == 0u || X[mort_xm(t)], xe = xs == (kXBits & lm) || X[mort_xp(t)];
+        const bool ysn = ys == 0u || X[mort_ym(t)], yn = ys == (kYBits & lm) || X[mort_yp(t)];
+        const bool yset = Y[t] != 0;
+        const bool skip = !covered && X[t] && yset && !q.inlet[t] && xw && xe && ysn && yn;
+        q.act[t] = skip ? 0 : (covered ? kActCovered : kActOwn);
+        if (!skip && !covered && yset) Y[t] = 0;          // the step writes into it
+        if (skip && scount) {
+            counted += l0 == Lr ? 1u : __ldg(scount + t);
+        } else {
+            // warp-aggregated append to the work list
+            const uint32_t m = __activemask();
+            const uint32_t lane = threadIdx.x & 31u, leader = __ffs(m) - 1u;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&st->nact, (uint32_t)__popc(m));
+            base = __shfl_sync(m, base, leader);
+            work[base + __popc(m & ((1u << lane) - 1u))] = t | (skip ? 0x80000000u : 0u);
+        }
+    }
+    // leaves of the skipped tiles: one atomic per block
+    __shared__ uint32_t red[8];
+    uint32_t v = warp_sum(counted);
+    if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0u;
+        for (uint32_t w = 0; w < blockDim.x / 32u; ++w) s += red[w];
+        if (s) atomicAdd(&st->Mall, s);
+    }
+}
+
+// One CTA per listed tile, one thread per 4-cell group: its leaf count, a
+// block scan for the positions, one atomic on st->M for the tile's base.
+static __global__ void __launch_bounds__(256) k_trav_list(const uint32_t* __restrict__ Sb,
+                                                          uint32_t* __restrict__ dlist,
+                                                          uint32_t* __restrict__ leaves, int L, int kt,
+                                                          DevState* st, const uint32_t* __restrict__ work) {
+    if (!st->active) return;
+    __shared__ TileBits tb;
+    __shared__ uint32_t sbase;
+    const uint32_t nact = st->nact;
+    const uint32_t g = threadIdx.x;
+    const uint32_t ngroups = 1u << (2 * (kt - 1));
+    uint32_t sum_all = 0u;                        // thread 0's running count
+    for (uint32_t e = blockIdx.x; e < nact; e += gridDim.x) {
+        const uint32_t item = __ldg(work + e);
+        const uint32_t tile = item & 0x7FFFFFFFu;
+        const bool count_only = (item >> 31) != 0u;
+        __syncthreads();                          // tb and sbase reused across tiles
+        load_tile_bits(Sb, L, kt, tile, tb);
+        int l = L;
+        uint32_t c = 0u;
+        const uint32_t m0 = (tile << (2 * kt)) + 4u * g;
+        if (g < ngroups) {
+            l = group_level(tb, L, kt, g);
+            c = l == L ? 4u : ((m0 & ((1u << (2 * (L - l))) - 1u)) == 0u ? 1u : 0u);
+        }
+        const bool big = g < ngroups && needs_decode_kernel(l, L);
+        uint32_t total;
+        const uint32_t pos = block_excl_scan(c, &total);
+        const int anybig = __syncthreads_or(big ? 1 : 0);
+        if (threadIdx.x == 0) {
+            sum_all += total;
+            if (!count_only) {
+                sbase = total ? atomicAdd(&st->M, total) : 0u;
+                if (anybig) dlist[atomicAdd(&st->ndec, 1u)] = tile;
+            }
+        }
+        if (count_only) continue;                 // uniform over the CTA
+        __syncthreads();
+        const uint32_t p = sbase + pos;
+        if (c == 4u) {
+            Vec4<uint32_t>::store_u(leaves + p, ((uint32_t)L << kLeafShift) | m0);
+        } else if (c == 1u) {
+            leaves[p] = ((uint32_t)l << kLeafShift) | (m0 >> (2 * (L - l)));
+        }
+    }
+    if (threadIdx.x == 0 && sum_all) atomicAdd(&st->Mall, sum_all);
 }
 
 // ---------------------------------------------------------------------------
@@ -1968,7 +2078,8 @@ static __global__ void k_predict(const float* __restrict__ logits, int Ls, float
 static __global__ void k_flag_learned(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
                                       const uint32_t* __restrict__ Tz, const uint32_t* __restrict__ Cz,
                                       uint32_t* __restrict__ Sb, const uint8_t* __restrict__ phat, int L, int Ls,
-                                      int predict, int close, const DevState* st) {
+                                      int predict, int close, const DevState* st, uint32_t* zero4 = nullptr) {
+    if (zero4 && blockIdx.x == 0 && threadIdx.x < 4u) zero4[threadIdx.x] = 0u;   // as k_flag
     if (st && !st->active) return;
     const uint32_t total = bits_words(L);
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {

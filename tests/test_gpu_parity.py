@@ -204,7 +204,7 @@ def test_profiled_step_is_an_ordinary_step():
     prof = Hh.hwfv1_profile_step(sim.hd)
     names = [n for n, _ in prof]
     assert names[0] == "k_clear_words" and names[-1] == "k_decode_finish"
-    for k in ("k_flag", "k_trav_fused", "k_fv1_dry", "k_fv1_faces", "k_fv1_update"):
+    for k in ("k_flag", "k_trav_classify", "k_trav_list", "k_fv1_dry", "k_fv1_faces", "k_fv1_update"):
         assert k in names
     assert all(t >= 0.0 for _, t in prof)
     res = ref.step(want=("leaves",))
