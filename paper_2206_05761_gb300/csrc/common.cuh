@@ -221,6 +221,8 @@ struct DevState {
     float thrf[kMaxL * 3];            // same, float arithmetic (32-bit path)
     double thr4[kMaxL * 3];           // 4 * thr where thr >= 2^-1020, else -1
     float thr4f[kMaxL * 3];           // 4 * thrf where thrf >= 2^-124, else -1
+    float thr4lo[kMaxL * 3];          // thr4 rounded down / up to float where thr4 >= 2^-100,
+    float thr4hi[kMaxL * 3];          // else -1 (the float pre-check of the encode)
     unsigned long long leaf_updates;  // leaves updated, summed over the steps taken
     unsigned long long wet_updates;   // of them, leaves that took the full FV1 update
     unsigned long long act_updates;   // of them, leaves outside skipped (quiescent) tiles

@@ -480,6 +480,10 @@ class EngineT final : public Engine {
             for (int q = 0; q < 3; ++q) p.enc.f[b][q] = f_[b][q];
         p.enc.thr = thr_dyn();
         p.enc.thr4 = thr4_dyn();
+        if (sizeof(T) == 8) {
+            p.enc.thr4lo = st_->thr4lo;
+            p.enc.thr4hi = st_->thr4hi;
+        }
         p.enc.Tb = Tb_;
         p.enc.Cb = Cb_;
         p.enc.st = st_;
@@ -571,6 +575,10 @@ class EngineT final : public Engine {
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.thr = thr_dyn();
         a.thr4 = thr4_dyn();
+        if (sizeof(T) == 8) {           // float pre-check of the details (float64 only)
+            a.thr4lo = st_->thr4lo;
+            a.thr4hi = st_->thr4hi;
+        }
         a.Tb = Tb_;
         a.Cb = Cb_;
         a.st = st_;

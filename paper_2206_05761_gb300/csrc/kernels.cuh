@@ -191,6 +191,42 @@ __device__ __forceinline__ bool passes_thr(T m4, T thr, T thr4) {
     return ge_nonneg(T(0.25) * m4, thr);
 }
 
+// The parent of four doubles and its threshold decision, the details
+// decided in float where that is conclusive.  With c' the children rounded
+// to float, the float m4' of the same sums satisfies
+// |m4' - m4| <= 2^-20 S + 2^-120, S = sum |c'| (three roundings of 2^-24 S
+// each on the float side, two of 2^-53 S on the double side, and 2^-150 per
+// input below the float range, with room to spare).  Compared with directed
+// roundings against thr4 rounded down and up, a decision taken in float is
+// the one the double comparison m4 >= thr4 takes; otherwise (or for values
+// outside the float range) the details are computed in double.
+__device__ __forceinline__ bool float_finite(float x) { return (__float_as_int(x) & 0x7F800000) != 0x7F800000; }
+__device__ __forceinline__ void haar4_pre(double c0, double c1, double c2, double c3, double thr, double thr4,
+                                          float lo, float hi, double& s, bool& flag) {
+    if (same4<double>(c0, c1, c2, c3)) {
+        s = c0;
+        flag = passes_thr(0.0, thr, thr4);
+        return;
+    }
+    const double a = c0 + c2, b = c1 + c3;
+    s = quarter(a + b);
+    if (lo >= 0.0f) {
+        const float f0 = (float)c0, f1 = (float)c1, f2 = (float)c2, f3 = (float)c3;
+        const float af = f0 + f2, bf = f1 + f3, df = f0 - f2, ef = f1 - f3;
+        const float m = fmaxf(fmaxf(fabsf(df + ef), fabsf(af - bf)), fabsf(df - ef));
+        const float S = __fadd_ru(__fadd_ru(fabsf(f0), fabsf(f1)), __fadd_ru(fabsf(f2), fabsf(f3)));
+        const float E = __fadd_ru(__fmul_ru(S, 0x1p-20f), 0x1p-120f);
+        if (float_finite(m) && float_finite(E)) {
+            if (__fsub_rd(m, E) >= hi) { flag = true; return; }
+            if (__fadd_ru(m, E) < lo) { flag = false; return; }
+        }
+    }
+    const double d = c0 - c2, e = c1 - c3;
+    const double m4 = sel_max(sel_max(absval(d + e), absval(a - b)), absval(d - e));
+    flag = passes_thr(m4, thr, thr4);
+}
+
+
 // Write the per-thread flag of `cnt` consecutive parents (codes base..) of
 // level n.  Full words are stored; a partial word (cnt < 32) is OR-ed into
 // a word cleared before the pass.  Called by every thread of the block.
@@ -214,6 +250,8 @@ struct EncodeArgs {
     T* f[2][NF];          // hierarchy of each quantity, per state buffer
     const T* thr;         // threshold of level n, quantity q at thr[n*NF + q]
     const T* thr4;        // 4 * thr where exact comparisons allow it, else -1
+    const float* thr4lo = nullptr;   // float bounds of thr4 for the pre-check (NULL: none)
+    const float* thr4hi = nullptr;
     uint32_t* Tb;         // threshold flags
     uint32_t* Cb;         // upward closure of the threshold flags
     const DevState* st;   // NULL: buffer 0, always active
@@ -223,6 +261,27 @@ struct EncodeArgs {
     // is +0.  NULL: no skipping.
     uint8_t* zf[2] = {nullptr, nullptr};
 };
+
+// Parent coefficient of quantity slot idx = n*NF + q and its part of the
+// parent's threshold flag tf (an OR over the quantities).  Once tf is set
+// the remaining quantities need their parent only.
+template <typename T, int NF>
+__device__ __forceinline__ void parent_coef(const EncodeArgs<T, NF>& a, int idx, T c0, T c1, T c2, T c3, T& s,
+                                            bool& tf) {
+    if constexpr (sizeof(T) == 8) {
+        if (a.thr4lo != nullptr) {
+            if (tf) {
+                s = same4<T>(c0, c1, c2, c3) ? c0 : quarter((c0 + c2) + (c1 + c3));
+                return;
+            }
+            haar4_pre(c0, c1, c2, c3, a.thr[idx], a.thr4[idx], a.thr4lo[idx], a.thr4hi[idx], s, tf);
+            return;
+        }
+    }
+    T dm;
+    haar4<T>(c0, c1, c2, c3, s, dm);
+    tf = tf || passes_thr(dm, a.thr[idx], a.thr4[idx]);
+}
 
 // the value is +0 (all bits clear)
 __device__ __forceinline__ bool pos_zero(double x) { return __double_as_longlong(x) == 0ll; }
@@ -260,13 +319,12 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
         if (act) {
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
-                T c0, c1, c2, c3, dm;
+                T c0, c1, c2, c3;
                 T* fq = par ? a.f[1][q] : a.f[0][q];
                 if (CG) Vec4<T>::load_cg(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
                 else Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
                 nz = nz || !(pos_zero(c0) && pos_zero(c1) && pos_zero(c2) && pos_zero(c3));
-                haar4<T>(c0, c1, c2, c3, s[q], dm);
-                tf = tf || passes_thr(dm, a.thr[n * NF + q], a.thr4[n * NF + q]);
+                parent_coef(a, n * NF + q, c0, c1, c2, c3, s[q], tf);
                 fq[lvl_off(n) + p] = s[q];
             }
             if (ls < a.L) {
@@ -301,11 +359,9 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
         if (act) {
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
-                T dm;
                 T* fq = par ? a.f[1][q] : a.f[0][q];
                 const T* r = rbuf ? sv1[q] : sv0[q];
-                haar4<T>(r[4 * tid], r[4 * tid + 1], r[4 * tid + 2], r[4 * tid + 3], s[q], dm);
-                tf = tf || passes_thr(dm, a.thr[n * NF + q], a.thr4[n * NF + q]);
+                parent_coef(a, n * NF + q, r[4 * tid], r[4 * tid + 1], r[4 * tid + 2], r[4 * tid + 3], s[q], tf);
                 fq[lvl_off(n) + p] = s[q];
             }
             cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
@@ -1758,8 +1814,12 @@ __device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
         const float tf = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
         st->thr[n * 3 + q] = td;
         st->thrf[n * 3 + q] = tf;
-        st->thr4[n * 3 + q] = thr4_of(td);
+        const double t4 = thr4_of(td);
+        st->thr4[n * 3 + q] = t4;
         st->thr4f[n * 3 + q] = thr4_of(tf);
+        const bool pre = t4 >= 0x1p-100;
+        st->thr4lo[n * 3 + q] = pre ? __double2float_rd(t4) : -1.0f;
+        st->thr4hi[n * 3 + q] = pre ? __double2float_ru(t4) : -1.0f;
     }
     if (threadIdx.x != 0) return;
     st->active = st->t < st->t_end ? 1u : 0u;
