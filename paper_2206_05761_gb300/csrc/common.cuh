@@ -141,6 +141,7 @@ __device__ __forceinline__ void block_atomic_u64(unsigned long long v, unsigned 
 __device__ __forceinline__ void block_max3_u64(unsigned long long a, unsigned long long b,
                                                unsigned long long c, unsigned long long* dst) {
     __shared__ unsigned long long red3[3][32];
+    __syncthreads();          // a previous call's readers are done with red3
     a = warp_max_u64(a);
     b = warp_max_u64(b);
     c = warp_max_u64(c);
@@ -203,6 +204,8 @@ struct DevState {
     double Qdt;                       // Q(t) * dt_use of the current step
     double smax[4];                   // s_max of h, qx, qy, z
     unsigned long long rmin_bits;     // min CFL bound over updated leaves
+    unsigned long long speed_bits[3]; // max |u|+sqrt(gh), |v|+sqrt(gh) over updated wet leaves
+                                      // (float64 updates; the bound is formed in the finish)
     unsigned long long max_bits[3];   // max |h|, |qx|, |qy| of the new state
     long long step;
     uint32_t active;                  // t < t_end

@@ -1148,7 +1148,8 @@ __device__ __forceinline__ void hll_face(T g, T hg, T tol, T hL, T zL, T unL, T 
 template <typename T>
 __device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
                                                   const T FW[3], const T FE[3], const T GS[3], const T GN[3],
-                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3]);
+                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3],
+                                                  T* rh_out = nullptr);
 
 // New (h, qx, qy) of a cell of size dx x dy: rx = dt/dx, ry = dt/dy.
 template <typename T>
@@ -1180,11 +1181,14 @@ __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, 
 }
 
 // The update of cell_update from its four face fluxes and its own
-// reconstructed depths at them (hW_R, hE_L, hS_R, hN_L).
+// reconstructed depths at them (hW_R, hE_L, hS_R, hN_L).  rh_out (if given)
+// receives 1/h of the new depth when the friction step formed it, else 0.
 template <typename T>
 __device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
                                                   const T FW[3], const T FE[3], const T GS[3], const T GN[3],
-                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3]) {
+                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3],
+                                                  T* rh_out) {
+    if (rh_out) *rh_out = T(0);
     const T g = P.g, hg = P.hg, tol = P.tol;
     const T bx = hg * (hW_R * hW_R - hE_L * hE_L);
     const T by = hg * (hS_R * hS_R - hN_L * hN_L);
@@ -1198,6 +1202,7 @@ __device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, 
         qy = T(0);
     } else if (P.nM > T(0)) {
         const T rh = T(1) / h;
+        if (rh_out) *rh_out = rh;
         const T u = qx * rh, v = qy * rh;
         const T speed = sqrt(u * u + v * v);
         const T nM = P.nM;
@@ -1399,10 +1404,25 @@ template <typename T>
 __device__ __forceinline__ void wet_leaf_store(const StepArgs<T>& a, DevState* st, const T* z, T* oh, T* oqx,
                                                T* oqy, int n, uint32_t code, uint64_t iC, const Cell<T>& C,
                                                const T out[3], unsigned long long& rmin, unsigned long long& mh,
-                                               unsigned long long& mqx, unsigned long long& mqy) {
-    const T r = cfl_bound(a.P, out[0], out[1], out[2]);
-    const unsigned long long rb = obits((double)r);
-    rmin = rb < rmin ? rb : rmin;
+                                               unsigned long long& mqx, unsigned long long& mqy,
+                                               unsigned long long* spd = nullptr, T rh_known = T(0)) {
+    if (sizeof(T) == 8 && spd != nullptr) {
+        // float64: the CFL speeds of the leaf (the divisions are formed once
+        // per step from their maxima, cfl_rmin); the same operations as
+        // cfl_bound up to the division, reusing the friction step's 1/h
+        if (ge_nonneg(out[0], a.P.tol)) {
+            const T rh = is_zero(rh_known) ? T(1) / out[0] : rh_known;
+            const T u = absval(out[1] * rh), v = absval(out[2] * rh);
+            const T aa = sqrt(a.P.g * out[0]);
+            const unsigned long long bx = abs_obits(u + aa), by = abs_obits(v + aa);
+            spd[0] = bx > spd[0] ? bx : spd[0];
+            spd[1] = by > spd[1] ? by : spd[1];
+        }
+    } else {
+        const T r = cfl_bound(a.P, out[0], out[1], out[2]);
+        const unsigned long long rb = obits((double)r);
+        rmin = rb < rmin ? rb : rmin;
+    }
     if (n == a.L || needs_decode_kernel(n, a.L)) {
         oh[iC] = out[0];
         oqx[iC] = out[1];
@@ -1473,7 +1493,7 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
     T* const oh = nxt ? a.f[1][0] : a.f[0][0];
     T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
-    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0;
+    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0, spd[2] = {0ull, 0ull};
     for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
         const uint32_t k = a.wet[w];
         const uint32_t pk = __ldg(a.leaves + k);
@@ -1501,10 +1521,11 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
         }
         T out[3];
         cell_update(a.P, rx, ry, dt, C, W, E, S, N, inlet, dh, out);
-        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy);
+        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
     block_max3_u64(mh, mqx, mqy, st->max_bits);
+    block_max3_u64(spd[0], spd[1], 0ull, st->speed_bits);
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
@@ -1595,7 +1616,7 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
     const uint32_t tag = st->epoch + 1u;
     const uint32_t cap = a.fcap;
     const T* F = a.face;
-    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0;
+    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0, spd[2] = {0ull, 0ull};
     for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
         const uint32_t pk = __ldg(a.leaves + a.wet[w]);
         const int n = (int)(pk >> kLeafShift);
@@ -1664,12 +1685,13 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
             const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
             dh = (Qdt * frac) / (dxn * dyn);
         }
-        T out[3];
-        cell_update_faces(a.P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out);
-        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy);
+        T out[3], rh;
+        cell_update_faces(a.P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out, &rh);
+        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd, rh);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
     block_max3_u64(mh, mqx, mqy, st->max_bits);
+    block_max3_u64(spd[0], spd[1], 0ull, st->speed_bits);
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_update(StepArgs<T> a) {
@@ -1834,9 +1856,26 @@ __device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
     st->Qdt = inflow_Q(a, st->t) * dt_use;
     st->rmin_bits = kInfBits;
     st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
+    st->speed_bits[0] = st->speed_bits[1] = st->speed_bits[2] = 0ull;
 }
 
 // next timestep: CFL * (min CFL bound), capped at dt_max (+inf when dry)
+// The step's CFL bound: the min of the bounds reduced as such and of
+// dx_L / max(|u|+sqrt(gh)) and dy_L / max(|v|+sqrt(gh)) over the wet leaves
+// whose speeds were reduced instead.  A correctly rounded division is
+// monotone in its divisor, so dx_L divided by the largest speed is exactly
+// the smallest of the per-leaf quotients dx_L/(|u|+sqrt(gh)) (Sec. 2.1.3 CFL).
+__device__ inline double cfl_rmin(const DevState* st, const FinishArgs& a) {
+    double r = from_obits(st->rmin_bits);
+    if (st->speed_bits[0] != 0ull) {
+        const double rx = ldexp(a.lx, -a.L) / __longlong_as_double((long long)st->speed_bits[0]);
+        const double ry = ldexp(a.ly, -a.L) / __longlong_as_double((long long)st->speed_bits[1]);
+        const double rr = rx < ry ? rx : ry;
+        r = rr < r ? rr : r;
+    }
+    return r;
+}
+
 __device__ inline double dt_from(const FinishArgs& a, double r) {
     const double dt = a.cfl * r;
     return dt < a.dt_max ? dt : a.dt_max;
@@ -1854,7 +1893,7 @@ __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
     __syncthreads();                 // every thread has read `active`
     if (threadIdx.x == 0) {
         st->t = st->t + st->dt_use;
-        st->dt = dt_from(a, from_obits(st->rmin_bits));
+        st->dt = dt_from(a, cfl_rmin(st, a));
         for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
         if (!isfinite(st->dt) || !isfinite(st->smax[0]) || !isfinite(st->smax[1]) ||
             !isfinite(st->smax[2]))
@@ -1964,6 +2003,7 @@ static __global__ void k_reset_red(DevState* st) {
     if (threadIdx.x != 0) return;
     st->rmin_bits = kInfBits;
     st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
+    st->speed_bits[0] = st->speed_bits[1] = st->speed_bits[2] = 0ull;
 }
 
 template <typename T>
