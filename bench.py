@@ -428,54 +428,11 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
             "audit_K": 10, "margin": 0.02}
 
 
-def run_pseudo2d(args, L=10, eps=1e-3, t_end=10.0, dt_sample=0.5):
-    """Pseudo-2D dam-break of Sec. 3.2 (50 m x 25 m, 6 m / 2 m, open sides)
-    from t = 0 to t_end: per dt_sample interval the mean leaves and device
-    ms per step of HWFV1, and the HWFV1 / uniform FV1 speed-up in simulated
-    seconds per second (the paper's speed-up as the flow goes from vigorous
-    to smooth)."""
-    import torch
-    import synth
-    from paper_2206_05761_gb300.sim import Simulation
-    p, f = synth.pseudo_2d_dam_break(L=L, eps=eps)
-    stream = torch.cuda.Stream()
-
-    def series(uniform):
-        sim = Simulation(p, f, args.precision, stream=stream)
-        sim.counters()
-        rows, tt = [], 0.0
-        while tt < t_end - 1e-12:
-            t1 = min(t_end, tt + dt_sample)
-            c0 = sim.counters()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            while sim.time()[0] < t1:
-                t, dt, _ = sim.time()
-                k = max(1, min(2000, int((t1 - t) / dt) + 1))
-                (sim.advance_uniform if uniform else sim.advance)(t_end=t1, max_steps=k)
-            e1.record(stream)
-            stream.synchronize()
-            c1 = sim.counters()
-            n = c1[0] - c0[0]
-            rows.append({"t": t1, "steps": n, "ms": e0.elapsed_time(e1),
-                         "mean_leaves": (c1[1] - c0[1]) / max(n, 1)})
-            tt = t1
-        sim.close()
-        return rows
-
-    a = series(False)
-    u = series(True)
-    out = []
-    for ra, ru in zip(a, u):
-        out.append({"t": ra["t"], "hwfv1_mean_leaves": round(ra["mean_leaves"]),
-                    "hwfv1_ms_per_step": ra["ms"] / max(ra["steps"], 1),
-                    "uniform_ms_per_step": ru["ms"] / max(ru["steps"], 1),
-                    "speedup": ru["ms"] / ra["ms"]})
-    ms_a, ms_u = sum(r["ms"] for r in a), sum(r["ms"] for r in u)
-    return {"workload": "pseudo-2D dam-break, 50 m x 25 m, 6 m / 2 m, L=%d (%dx%d), eps=%g, 0-%g s"
-                        % (L, 1 << L, 1 << L, eps, t_end),
-            "finest_cells": 1 << (2 * L), "hwfv1_s": ms_a / 1e3, "uniform_s": ms_u / 1e3,
-            "speedup": ms_u / ms_a, "series": out}
+def run_pseudo2d(args):
+    """Pseudo-2D dam-break of Sec. 3.2, HWFV1 vs uniform FV1 over 10 s at
+    L=10 (paper_2206_05761_gb300.scenarios)."""
+    from paper_2206_05761_gb300 import scenarios
+    return scenarios.pseudo2d(L=10, eps=1e-3, t_end=10.0, dt_sample=0.5, precision=args.precision)
 
 
 def combine_ranks(ms, e2e_s, world, device="cuda"):

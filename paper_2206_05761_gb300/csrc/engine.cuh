@@ -525,6 +525,11 @@ class EngineT final : public Engine {
 
    private:
     // ---- launch helpers -------------------------------------------------
+    // blocks of 64 threads for the wet-leaf kernels: 16 per SM at most
+    int wet_grid() const {
+        const uint64_t g = (N_ + 63) / 64, cap = (uint64_t)nsm_ * 16;
+        return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+    }
     int grid_for(uint64_t n) const {
         uint64_t g = (n + 255) / 256;
         const uint64_t cap = (uint64_t)nsm_ * 8;
@@ -673,12 +678,15 @@ class EngineT final : public Engine {
         k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
         mark("k_fv1_dry");
         if (face_) {
-            k_fv1_faces<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+            // 64-thread blocks: a short queue spreads over every SM's FP64 units
+            // (one warp-wide FP64 instruction holds a sub-partition's unit for
+            // tens of cycles, so few warps per unit means a shorter chain)
+            k_fv1_faces<T><<<wet_grid(), 64, 0, stream_>>>(a);
             mark("k_fv1_faces");
-            k_fv1_update<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+            k_fv1_update<T><<<wet_grid(), 64, 0, stream_>>>(a);
             mark("k_fv1_update");
         } else {
-            k_fv1_wet<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+            k_fv1_wet<T><<<wet_grid(), 64, 0, stream_>>>(a);
             mark("k_fv1_wet");
         }
     }
@@ -698,7 +706,7 @@ class EngineT final : public Engine {
     }
     void launch_decode() {
         // the decode list is short once quiescent tiles are skipped: 2 CTAs per SM
-        const int gd = quiet_on_ ? std::min(grid_for((uint64_t)ntiles_ * 256), nsm_ * 2)
+        const int gd = quiet_on_ ? std::min(grid_for((uint64_t)ntiles_ * 256), nsm_ * 4)
                                  : grid_for((uint64_t)ntiles_ * 256);
         k_decode_finish<T><<<gd, 256, 0, stream_>>>(decode_args(), fin_args());
         mark("k_decode_finish");
