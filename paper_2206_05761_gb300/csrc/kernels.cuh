@@ -262,25 +262,31 @@ struct EncodeArgs {
     uint8_t* zf[2] = {nullptr, nullptr};
 };
 
-// Parent coefficient of quantity slot idx = n*NF + q and its part of the
-// parent's threshold flag tf (an OR over the quantities).  Once tf is set
-// the remaining quantities need their parent only.
-template <typename T, int NF>
-__device__ __forceinline__ void parent_coef(const EncodeArgs<T, NF>& a, int idx, T c0, T c1, T c2, T c3, T& s,
-                                            bool& tf) {
+// The thresholds of one level and quantity (thr, 4 thr, and 4 thr's float
+// bounds, lo < 0 when the float pre-check is off).
+template <typename T>
+struct Thr {
+    T thr, thr4;
+    float lo, hi;
+};
+
+// Parent coefficient of one quantity and its part of the parent's threshold
+// flag tf (an OR over the quantities).  Once tf is set the remaining
+// quantities need their parent only.
+template <typename T>
+__device__ __forceinline__ void parent_coef(const Thr<T>& h, T c0, T c1, T c2, T c3, T& s, bool& tf) {
     if constexpr (sizeof(T) == 8) {
-        if (a.thr4lo != nullptr) {
-            if (tf) {
-                s = same4<T>(c0, c1, c2, c3) ? c0 : quarter((c0 + c2) + (c1 + c3));
-                return;
-            }
-            haar4_pre(c0, c1, c2, c3, a.thr[idx], a.thr4[idx], a.thr4lo[idx], a.thr4hi[idx], s, tf);
+        // haar4_pre with lo < 0 is haar4 + passes_thr
+        if (tf) {
+            s = same4<T>(c0, c1, c2, c3) ? c0 : quarter((c0 + c2) + (c1 + c3));
             return;
         }
+        haar4_pre(c0, c1, c2, c3, h.thr, h.thr4, h.lo, h.hi, s, tf);
+        return;
     }
     T dm;
     haar4<T>(c0, c1, c2, c3, s, dm);
-    tf = tf || passes_thr(dm, a.thr[idx], a.thr4[idx]);
+    tf = tf || passes_thr(dm, h.thr, h.thr4);
 }
 
 // the value is +0 (all bits clear)
@@ -305,6 +311,7 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
     __shared__ T sv0[NF][256];        // level ls-1 (and ls-3, ls-5)
     __shared__ T sv1[NF][64];         // level ls-2 (and ls-4)
     __shared__ uint32_t sc[2][8];
+    __shared__ Thr<T> sthr[5][NF];    // thresholds of the pass's levels (one load each)
     const uint32_t tile = bid, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     uint32_t cnt = 1u << (2 * (kk - 1));
     int n = ls - 1;
@@ -316,21 +323,44 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
         T s[NF];
 #pragma unroll
         for (int q = 0; q < NF; ++q) s[q] = T(0);
+        // every load first (the stores below could alias them for the
+        // compiler, which would then serialise load, compute and store per
+        // quantity), with the thresholds of all the pass's levels, then the
+        // parents, then the stores
+        T c[NF][4];
         if (act) {
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
-                T c0, c1, c2, c3;
-                T* fq = par ? a.f[1][q] : a.f[0][q];
-                if (CG) Vec4<T>::load_cg(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
-                else Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c0, c1, c2, c3);
-                nz = nz || !(pos_zero(c0) && pos_zero(c1) && pos_zero(c2) && pos_zero(c3));
-                parent_coef(a, n * NF + q, c0, c1, c2, c3, s[q], tf);
-                fq[lvl_off(n) + p] = s[q];
+                const T* fq = par ? a.f[1][q] : a.f[0][q];
+                if (CG) Vec4<T>::load_cg(fq + lvl_off(ls) + 4ull * p, c[q][0], c[q][1], c[q][2], c[q][3]);
+                else Vec4<T>::load(fq + lvl_off(ls) + 4ull * p, c[q][0], c[q][1], c[q][2], c[q][3]);
             }
             if (ls < a.L) {
                 const uint32_t cb = 4u * p;
                 const uint32_t* cw = a.Cb + word_off(ls) + (cb >> 5);
                 cchild = ((CG ? __ldcg(cw) : __ldg(cw)) >> (cb & 31u)) & 0xFu;
+            }
+        }
+        if (tid < (uint32_t)(kk * NF)) {
+            const int j = tid / NF, q = tid - j * NF, idx = (ls - 1 - j) * NF + q;
+            Thr<T> h;
+            h.thr = a.thr[idx];
+            h.thr4 = a.thr4[idx];
+            h.lo = a.thr4lo ? a.thr4lo[idx] : -1.0f;
+            h.hi = a.thr4hi ? a.thr4hi[idx] : -1.0f;
+            sthr[j][q] = h;
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                nz = nz || !(pos_zero(c[q][0]) && pos_zero(c[q][1]) && pos_zero(c[q][2]) && pos_zero(c[q][3]));
+                parent_coef(sthr[0][q], c[q][0], c[q][1], c[q][2], c[q][3], s[q], tf);
+            }
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                T* fq = par ? a.f[1][q] : a.f[0][q];
+                fq[lvl_off(n) + p] = s[q];
             }
         }
         const bool cf = act && (tf || cchild);
@@ -357,14 +387,21 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
 #pragma unroll
         for (int q = 0; q < NF; ++q) s[q] = T(0);
         if (act) {
+            T c[NF][4];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                const T* r = rbuf ? sv1[q] : sv0[q];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c[q][k] = r[4 * tid + k];
+            }
+            cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) parent_coef(sthr[j - 1][q], c[q][0], c[q][1], c[q][2], c[q][3], s[q], tf);
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
                 T* fq = par ? a.f[1][q] : a.f[0][q];
-                const T* r = rbuf ? sv1[q] : sv0[q];
-                parent_coef(a, n * NF + q, r[4 * tid], r[4 * tid + 1], r[4 * tid + 2], r[4 * tid + 3], s[q], tf);
                 fq[lvl_off(n) + p] = s[q];
             }
-            cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
         }
         const bool cf = act && (tf || cchild);
         put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
@@ -1232,7 +1269,7 @@ struct StepArgs {
     T* f[2][3];              // h, qx, qy hierarchies of the two state buffers
     const T* z;              // bed hierarchy
     const uint32_t* leaves;
-    uint32_t* wet;           // leaves that need the full update
+    uint32_t* wet;           // packed leaves that need the full update
     DevState* st;
     Phys<T> P;
     T lx, ly;
@@ -1340,7 +1377,7 @@ __device__ __forceinline__ bool dry5(const T* __restrict__ h, const DryProbe& d)
 // iteration, so many independent loads are in flight.
 template <typename T>
 __device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T* oh, T* oqx, T* oqy,
-                                           const DryProbe& d, bool dry, uint32_t k) {
+                                           const DryProbe& d, bool dry, uint32_t pk) {
     if (dry && a.inflow_side >= 0) {
         int64_t lo, hi;
         dry = !inlet_range(a, d.n, compact16(d.code), compact16(d.code >> 1), (1u << d.n) - 1u, lo, hi);
@@ -1367,7 +1404,7 @@ __device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T
         uint32_t base_pos = 0;
         if (lane == leader) base_pos = atomicAdd(&st->nwet, (uint32_t)__popc(m));
         base_pos = __shfl_sync(m, base_pos, leader);
-        a.wet[base_pos + __popc(m & ((1u << lane) - 1u))] = k;
+        a.wet[base_pos + __popc(m & ((1u << lane) - 1u))] = pk;   // the packed leaf
     }
 }
 
@@ -1385,12 +1422,13 @@ __device__ __forceinline__ void fv1_dry_body(const StepArgs<T>& a, Blk B) {
     for (uint32_t k = B.id * blockDim.x + threadIdx.x; k < M; k += 2u * stride) {
         const uint32_t k2 = k + stride;
         const bool two = k2 < M;
-        const DryProbe d1 = dry_probe(__ldg(a.leaves + k));
-        const DryProbe d2 = dry_probe(two ? __ldg(a.leaves + k2) : 0u);
+        const uint32_t p1 = __ldg(a.leaves + k), p2 = two ? __ldg(a.leaves + k2) : 0u;
+        const DryProbe d1 = dry_probe(p1);
+        const DryProbe d2 = dry_probe(p2);
         const bool y1 = dry5(hsrc, d1);
         const bool y2 = two && dry5(hsrc, d2);
-        dry_finish(a, st, oh, oqx, oqy, d1, y1, k);
-        if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, k2);
+        dry_finish(a, st, oh, oqx, oqy, d1, y1, p1);
+        if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, p2);
     }
 }
 template <typename T>
@@ -1495,8 +1533,7 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
     unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0, spd[2] = {0ull, 0ull};
     for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
-        const uint32_t k = a.wet[w];
-        const uint32_t pk = __ldg(a.leaves + k);
+        const uint32_t pk = a.wet[w];            // the queue holds packed leaves
         const int n = (int)(pk >> kLeafShift);
         const uint32_t code = pk & kCodeMask;
         const uint32_t i = compact16(code), j = compact16(code >> 1);
@@ -1554,7 +1591,7 @@ __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
     const unsigned long long stamp = (unsigned long long)(st->epoch + 1u) << 32;
     const uint32_t cap = a.fcap;
     for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
-        const uint32_t pk = __ldg(a.leaves + a.wet[w]);
+        const uint32_t pk = a.wet[w];
         const int n = (int)(pk >> kLeafShift);
         const uint32_t code = pk & kCodeMask;
         const uint32_t i = compact16(code), j = compact16(code >> 1);
@@ -1618,7 +1655,7 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
     const T* F = a.face;
     unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0, spd[2] = {0ull, 0ull};
     for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
-        const uint32_t pk = __ldg(a.leaves + a.wet[w]);
+        const uint32_t pk = a.wet[w];
         const int n = (int)(pk >> kLeafShift);
         const uint32_t code = pk & kCodeMask;
         const uint32_t i = compact16(code), j = compact16(code >> 1);
