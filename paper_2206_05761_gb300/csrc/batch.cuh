@@ -114,6 +114,20 @@ static __global__ void __launch_bounds__(256) kb_fv1_dry(const DomainPlan<T>* P,
     fv1_dry_body<T>(P[d].step, domain_blk(base, d));
 }
 
+// the shared-face pair of the single-domain path (float64; float32 domains
+// have no face buffer and take the one-pass update inside kb_fv1_update)
+template <typename T>
+static __global__ void __launch_bounds__(256) kb_fv1_faces(const DomainPlan<T>* P, const uint32_t* base, int D) {
+    const int d = find_domain(base, D, blockIdx.x);
+    fv1_faces_body<T>(P[d].step, domain_blk(base, d));
+}
+
+template <typename T>
+static __global__ void __launch_bounds__(256) kb_fv1_update(const DomainPlan<T>* P, const uint32_t* base, int D) {
+    const int d = find_domain(base, D, blockIdx.x);
+    fv1_update_body<T>(P[d].step, domain_blk(base, d));
+}
+
 template <typename T>
 static __global__ void __launch_bounds__(256) kb_fv1_wet(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
@@ -294,6 +308,7 @@ class BatchT final : public Batch {
         cudaMemcpyAsync(d_bases_, bases.data(), sizeof(uint32_t) * bases.size(), cudaMemcpyHostToDevice, stream_);
         launches_ = 0;
         for (int k = 0; k < BK_KINDS; ++k) launches_ += total_[k] > 0 ? 1 : 0;
+        if (total_[BK_WET] > 0) launches_ += 1;        // the wet update is two kernels
         return check("batch plan", true);
     }
 
@@ -310,7 +325,8 @@ class BatchT final : public Batch {
         kb_trav_scan<T><<<total_[BK_TSCAN], 1024, 0, stream_>>>(d_plans_, base(BK_TSCAN), D);
         kb_trav_write<T><<<total_[BK_TWRITE], 256, 0, stream_>>>(d_plans_, base(BK_TWRITE), D);
         kb_fv1_dry<T><<<total_[BK_DRY], 256, 0, stream_>>>(d_plans_, base(BK_DRY), D);
-        kb_fv1_wet<T><<<total_[BK_WET], 256, 0, stream_>>>(d_plans_, base(BK_WET), D);
+        kb_fv1_faces<T><<<total_[BK_WET], 256, 0, stream_>>>(d_plans_, base(BK_WET), D);
+        kb_fv1_update<T><<<total_[BK_WET], 256, 0, stream_>>>(d_plans_, base(BK_WET), D);
         kb_decode<T><<<total_[BK_DEC], 256, 0, stream_>>>(d_plans_, base(BK_DEC), D);
         kb_finish<T><<<D, 64, 0, stream_>>>(d_plans_, D);
     }

@@ -83,7 +83,7 @@ class EngineT final : public Engine {
         // shared faces of the wet-leaf update: 10 values per queued leaf, a
         // stamp per hierarchy cell.  Float64 only: in float32 the arithmetic
         // saved costs less than the extra launch and face traffic.
-        if (!batched_ && sizeof(T) == 8) {
+        if (sizeof(T) == 8) {
             fcap_ = (uint32_t)std::min<uint64_t>(N_, 1ull << 22);
             if (!alloc(&face_, (size_t)fcap_ * 10 * sizeof(T))) return oom();
             if (!alloc(&mark_, H_ * sizeof(unsigned long long))) return oom();
