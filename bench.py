@@ -382,10 +382,10 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     p, f = make(test_seed)
     stream = torch.cuda.Stream()
 
-    def timed(net_, t_end, max_steps):
+    def timed(net_, t_end, max_steps, every=1):
         sim = Simulation(p, f, args.precision, stream=stream)
         if net_ is not None:
-            sim.set_skipnet(net_, audit_K=10, margin=0.02)
+            sim.set_skipnet(net_, audit_K=10, margin=0.02, predict_every=every)
         sim.counters()                        # captures the step graph (untimed)
         sim.advance(max_steps=0)
         stream.synchronize()
@@ -404,11 +404,12 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     plain = timed(None, float("inf"), steps)
     # the learned run's step count to the same simulated time, then a timed
     # run of exactly that many steps (no idle launches after t_end)
-    n_l = timed(net, plain["t"], 4 * steps)["steps"]
-    lrn = timed(net, plain["t"], n_l)
+    runs = {}
+    for every in (1, 4):
+        n_l = timed(net, plain["t"], 4 * steps, every)["steps"]
+        runs[every] = timed(net, plain["t"], n_l, every)
     H.hwfv1_skipnet_destroy(net)
     cell = 1.0 / (1 << (2 * L))
-    d = float(np.abs(lrn["h"] - plain["h"]).sum() * cell)
 
     def rep(r):
         return {"steps": r["steps"], "ms": r["ms"], "steps_per_s": r["steps"] / (r["ms"] / 1e3),
@@ -418,10 +419,14 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     return {"workload": "%s dam-break L=%d eps=1e-3 (train seeds %d..%d, held-out seed %d)"
                         % (kind, L, min(train_seeds), max(train_seeds), test_seed),
             "finest_cells": 1 << (2 * L), "sim_time_s": plain["t"],
-            "plain": rep(plain), "learned": rep(lrn),
-            "speedup_sim_time": (plain["ms"] / lrn["ms"]) if lrn["t"] >= plain["t"] * (1 - 1e-12) else None,
-            "leaves_ratio": (lrn["lu"] / lrn["steps"]) / (plain["lu"] / plain["steps"]),
-            "l1_depth_learned_vs_plain_m": d, "held_out_under_prediction": under,
+            "plain": rep(plain),
+            "learned": {"predict_every_%d" % e: dict(
+                rep(r),
+                speedup_sim_time=(plain["ms"] / r["ms"]) if r["t"] >= plain["t"] * (1 - 1e-12) else None,
+                leaves_ratio=(r["lu"] / r["steps"]) / (plain["lu"] / plain["steps"]),
+                l1_depth_learned_vs_plain_m=float(np.abs(r["h"] - plain["h"]).sum() * cell))
+                for e, r in runs.items()},
+            "held_out_under_prediction": under,
             "training": {"images": int(8 * 20 * len(train_seeds)), "image_px": 1 << (L - 4),
                          "last_batch_loss": loss, "collect_s": t_collect, "train_s": t_train,
                          "epochs": 6, "batch": 8, "augment": "8 symmetries of the square"},

@@ -267,9 +267,12 @@ void hwfv1_skipnet_destroy(hwfv1_skipnet* net);
 /* Use `net` (NULL: stop) for the look-ahead of hwfv1_advance: a subtree may
  * refine only above the smallest level whose predicted cumulative
  * probability reaches 1 - margin (margin < 0 keeps every level, which equals
- * the plain method); every audit_K-th step is exact.  Needs L >= 6.  The
- * network must outlive its use. */
-hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin);
+ * the plain method); every audit_K-th step is exact.  The network runs on
+ * every predict_every-th learned step (>= 1) and the steps in between reuse
+ * its last predicted levels.  Needs L >= 6.  The network must outlive its
+ * use. */
+hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin,
+                               int32_t predict_every);
 /* CNN input of the current state (device output, bf16 bits, 4 x 4^(L-4)
  * values, channels last, row j of subtrees major); call after hwfv1_encode. */
 hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap);

@@ -200,9 +200,11 @@ void hwfv1_destroy(hwfv1_handle* hd) {
     delete hd;
 }
 
-hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin) {
+hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin,
+                               int32_t predict_every) {
     HWFV1_CHECK_HANDLE(hd);
-    return from_engine(hd, hd->eng->set_skipnet(net ? net->net : nullptr, audit_K, margin));
+    if (predict_every < 1) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->set_skipnet(net ? net->net : nullptr, audit_K, margin, predict_every));
 }
 hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap) {
     HWFV1_CHECK_HANDLE(hd);

@@ -49,6 +49,7 @@ class EngineT final : public Engine {
     ~EngineT() override {
         if (exec_) cudaGraphExecDestroy(exec_);
         if (exec_learned_) cudaGraphExecDestroy(exec_learned_);
+        if (exec_reuse_) cudaGraphExecDestroy(exec_reuse_);
         if (exec_uniform_) cudaGraphExecDestroy(exec_uniform_);
         skipwork_free(&skw_);
         for (void* p : allocs_) cudaFree(p);
@@ -195,20 +196,25 @@ class EngineT final : public Engine {
         k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), t_end);
         if (max_steps == 0) return check("advance");
         const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
-        if (use_graph && !exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
-        if (use_graph && skip_ && !exec_learned_ && capture(&exec_learned_, true) != HWFV1_OK)
+        if (use_graph && !exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        if (use_graph && skip_ && !exec_learned_ && capture(&exec_learned_, kStepLearned) != HWFV1_OK)
+            return HWFV1_ERR_CUDA;
+        if (use_graph && skip_ && every_ > 1 && !exec_reuse_ && capture(&exec_reuse_, kStepReuse) != HWFV1_OK)
             return HWFV1_ERR_CUDA;
         for (int64_t s = 0; s < max_steps; ++s) {
             // with the learned look-ahead every audit_K-th step is an exact
-            // (plain) step
-            const bool learned = skip_ && (lstep_++ % audit_K_) != 0;
+            // (plain) step; of the learned steps after it, every every_-th
+            // runs the network and the others reuse its predicted levels
+            int kind = kStepPlain;
+            if (skip_) {
+                const int64_t pos = lstep_++ % audit_K_;
+                if (pos != 0) kind = ((pos - 1) % every_) == 0 ? kStepLearned : kStepReuse;
+            }
             if (use_graph) {
-                if (cudaGraphLaunch(learned ? exec_learned_ : exec_, stream_) != cudaSuccess)
-                    return fail(HWFV1_ERR_CUDA, "graph launch");
-            } else if (learned) {
-                launch_step_learned();
+                cudaGraphExec_t g = kind == kStepPlain ? exec_ : kind == kStepLearned ? exec_learned_ : exec_reuse_;
+                if (cudaGraphLaunch(g, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
             } else {
-                launch_step_all();
+                launch_step(kind);
             }
         }
         return check("advance");
@@ -251,15 +257,17 @@ class EngineT final : public Engine {
         return check("advance_uniform");
     }
 
-    hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin) override {
-        if (net && (L_ < 6 || audit_K < 1)) return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead needs L >= 6, K >= 1");
+    hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin, int predict_every) override {
+        if (net && (L_ < 6 || audit_K < 1 || predict_every < 1))
+            return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead needs L >= 6, K >= 1, predict_every >= 1");
         skip_ = net;
         audit_K_ = audit_K < 1 ? 1 : audit_K;
+        every_ = predict_every < 1 ? 1 : predict_every;
         margin_ = margin;
         lstep_ = 0;
-        if (exec_learned_) {
-            cudaGraphExecDestroy(exec_learned_);
-            exec_learned_ = nullptr;
+        for (cudaGraphExec_t* g : {&exec_learned_, &exec_reuse_}) {
+            if (*g) cudaGraphExecDestroy(*g);
+            *g = nullptr;
         }
         if (!net) return HWFV1_OK;
         const uint64_t npx = 1ull << (2 * (L_ - 4));
@@ -269,8 +277,9 @@ class EngineT final : public Engine {
         // capture both step graphs now (capturing runs nothing), so that the
         // first advance does not pay for it
         if (std::getenv("HWFV1_NO_GRAPH") == nullptr) {
-            if (!exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
-            if (capture(&exec_learned_, true) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (!exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (capture(&exec_learned_, kStepLearned) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (every_ > 1 && capture(&exec_reuse_, kStepReuse) != HWFV1_OK) return HWFV1_ERR_CUDA;
         }
         return HWFV1_OK;
     }
@@ -411,7 +420,7 @@ class EngineT final : public Engine {
 
     hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* au, int64_t* wu, int64_t* kps) override {
         if (kps) {
-            if (!exec_ && capture(&exec_, false) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (!exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
             *kps = skip_ ? kernels_learned_ : kernels_plain_;
         }
         DevState s;
@@ -729,27 +738,36 @@ class EngineT final : public Engine {
         k_features<T><<<grid_for(n), 256, 0, stream_>>>(
             f_[0][0], f_[1][0], f_[0][1], f_[1][1], f_[0][2], f_[1][2], z_, st_, smax_z, L_ - 4, out);
     }
-    // one step with the learned look-ahead in place of R1
-    void launch_step_learned() {
+    // one step with the learned look-ahead in place of R1; predict = false
+    // reuses the levels the network predicted last
+    void launch_step_learned(bool predict_now = true) {
         launch_encode();
-        launch_features(feat_);
-        const int S = 1 << (L_ - 4);
-        skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
-        k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+        if (predict_now) {
+            launch_features(feat_);
+            const int S = 1 << (L_ - 4);
+            skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
+            k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+        }
         k_flag_learned<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
                                                               close(), st_, &st_->ndec);
         launch_traverse(/*learned=*/true);
         launch_fv1();
         launch_decode();
     }
-    hwfv1_status capture(cudaGraphExec_t* out, bool learned) {
+    enum { kStepPlain = 0, kStepLearned = 1, kStepReuse = 2 };
+    void launch_step(int kind) {
+        if (kind == kStepPlain) launch_step_all();
+        else launch_step_learned(kind == kStepLearned);
+    }
+    hwfv1_status capture(cudaGraphExec_t* out, int kind) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(HWFV1_ERR_CUDA, "graph capture begin");
-        if (learned) launch_step_learned();
-        else launch_step_all();
+        launch_step(kind);
         if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph capture end");
-        (learned ? kernels_learned_ : kernels_plain_) = count_kernel_nodes(g);
+        const int64_t nk = count_kernel_nodes(g);
+        if (kind == kStepPlain) kernels_plain_ = nk;
+        else if (kind == kStepLearned) kernels_learned_ = nk;
         const cudaError_t e = cudaGraphInstantiate(out, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
@@ -848,12 +866,14 @@ class EngineT final : public Engine {
     // learned look-ahead
     SkipNet* skip_ = nullptr;
     int audit_K_ = 10;
+    int every_ = 1;        // the network runs on every every_-th learned step
     float margin_ = 0.02f;
     int64_t lstep_ = 0;
     SkipWork skw_;
     __nv_bfloat16* feat_ = nullptr;
     uint8_t* phat_ = nullptr;
     cudaGraphExec_t exec_learned_ = nullptr;
+    cudaGraphExec_t exec_reuse_ = nullptr;   // learned step on the last prediction
     cudaGraphExec_t exec_uniform_ = nullptr;
     uint32_t* uniform_leaves_ = nullptr;   // every finest cell as a leaf (uniform FV1)
     int64_t kernels_plain_ = 0, kernels_learned_ = 0;   // kernel nodes of the captured step graphs

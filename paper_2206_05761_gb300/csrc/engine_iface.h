@@ -39,7 +39,7 @@ class Engine {
     virtual hwfv1_status save(void* buf, size_t cap, size_t* used) = 0;
     virtual hwfv1_status load(const void* buf, size_t n) = 0;
     // learned look-ahead (skipnet.cu); net == nullptr turns it off
-    virtual hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin) = 0;
+    virtual hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin, int predict_every) = 0;
     virtual hwfv1_status get_features(uint16_t* out, int64_t cap) = 0;
     virtual hwfv1_status get_labels(uint8_t* out, int64_t cap) = 0;
     std::string err;

@@ -107,7 +107,7 @@ def lib():
                                               C.c_int32, C.c_float, C.c_uint32, C.POINTER(C.c_double)]
             L.hwfv1_skipnet_destroy.argtypes = [C.c_void_p]
             L.hwfv1_skipnet_destroy.restype = None
-            L.hwfv1_set_skipnet.argtypes = [_H, C.c_void_p, C.c_int32, C.c_float]
+            L.hwfv1_set_skipnet.argtypes = [_H, C.c_void_p, C.c_int32, C.c_float, C.c_int32]
             L.hwfv1_get_features.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_get_labels.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_destroy.argtypes = [_H]
@@ -428,8 +428,9 @@ def hwfv1_skipnet_destroy(net):
     lib().hwfv1_skipnet_destroy(net)
 
 
-def hwfv1_set_skipnet(hd, net, audit_K=10, margin=0.02):
-    _check(lib().hwfv1_set_skipnet(hd, net, int(audit_K), float(margin)), "hwfv1_set_skipnet", hd)
+def hwfv1_set_skipnet(hd, net, audit_K=10, margin=0.02, predict_every=1):
+    _check(lib().hwfv1_set_skipnet(hd, net, int(audit_K), float(margin), int(predict_every)),
+           "hwfv1_set_skipnet", hd)
 
 
 def hwfv1_get_features(hd, out):

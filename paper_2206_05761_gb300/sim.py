@@ -123,8 +123,8 @@ class Simulation:
     def labels_dev(self, out):
         H.hwfv1_get_labels(self.hd, out)
 
-    def set_skipnet(self, net, audit_K=10, margin=0.02):
-        H.hwfv1_set_skipnet(self.hd, net, audit_K, margin)
+    def set_skipnet(self, net, audit_K=10, margin=0.02, predict_every=1):
+        H.hwfv1_set_skipnet(self.hd, net, audit_K, margin, predict_every)
 
     def close(self):
         if self.hd is not None:

@@ -14,11 +14,11 @@ pytestmark = pytest.mark.gpu
 L = 8
 
 
-def _run(p, f, t_end, net=None, audit_K=10, margin=0.02, max_steps=20000):
+def _run(p, f, t_end, net=None, audit_K=10, margin=0.02, max_steps=20000, every=1):
     from paper_2206_05761_gb300.sim import Simulation
     sim = Simulation(p, f)
     if net is not None:
-        sim.set_skipnet(net, audit_K=audit_K, margin=margin)
+        sim.set_skipnet(net, audit_K=audit_K, margin=margin, predict_every=every)
     ms = []
     while sim.time()[0] < t_end and len(ms) < max_steps:
         sim.advance(t_end=t_end, max_steps=1)
@@ -66,3 +66,41 @@ def test_learned_run_uses_fewer_leaves_at_bounded_cost(trained):
     print("L1 depth: |learned - plain| = %.3e, |plain - uniform| = %.3e" % (d_lp, d_pu))
     assert ml < mp
     assert d_lp <= 2.0 * d_pu + 1e-12
+
+
+def test_learned_run_reusing_predictions(trained):
+    """The network on every 3rd learned step, its levels reused in between."""
+    net, _ = trained
+    t_end = 0.25
+    p, f = synth.columns_dam_break(L=L, eps=1e-3, seed=200)
+    fp, mp, _ = _run(p, f, t_end)
+    fl, ml, _ = _run(p, f, t_end, net=net, every=3)
+    pu, fu = synth.columns_dam_break(L=L, eps=0.0, seed=200)
+    fu_, _, _ = _run(pu, fu, t_end)
+    cell = 1.0 / (1 << (2 * L))
+    d_lp = np.abs(fl["h"] - fp["h"]).sum() * cell
+    d_pu = np.abs(fp["h"] - fu_["h"]).sum() * cell
+    print("reuse 3: mean leaves %.0f (%.3f of plain); L1 |learned - plain| = %.3e, |plain - uniform| = %.3e"
+          % (ml, ml / mp, d_lp, d_pu))
+    assert ml < mp
+    assert d_lp <= 2.0 * d_pu + 1e-12
+
+
+def test_reuse_schedule_same_with_and_without_graphs(trained, monkeypatch):
+    """The captured step graphs and the direct launches pick the same kind of
+    step (exact, predicting, reusing) in the same order."""
+    from paper_2206_05761_gb300.sim import Simulation
+    net, _ = trained
+    p, f = synth.columns_dam_break(L=L, eps=1e-3, seed=201)
+    out = []
+    for graphs in (True, False):
+        if not graphs:
+            monkeypatch.setenv("HWFV1_NO_GRAPH", "1")
+        sim = Simulation(p, f)
+        sim.set_skipnet(net, audit_K=5, margin=0.02, predict_every=2)
+        sim.advance(max_steps=23)
+        out.append((sim.fields(), sim.leaves()))
+        sim.close()
+    for k in out[0][0]:
+        assert np.array_equal(out[0][0][k], out[1][0][k])
+    assert np.array_equal(out[0][1], out[1][1])

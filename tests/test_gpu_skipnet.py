@@ -146,14 +146,15 @@ def test_features_and_labels_match_oracle():
     sim.close()
 
 
-def test_learned_mode_with_gate_open_equals_plain():
+@pytest.mark.parametrize("every", [1, 3])
+def test_learned_mode_with_gate_open_equals_plain(every):
     from paper_2206_05761_gb300 import hwfv1 as Hh
     from paper_2206_05761_gb300.sim import Simulation
     p, f = synth.bumpy_dam_break(L=7, eps=1e-3, seed=6)
     a = Simulation(p, f)
     b = Simulation(p, f)
     net = Hh.hwfv1_skipnet_create(3)
-    b.set_skipnet(net, audit_K=4, margin=-1.0)
+    b.set_skipnet(net, audit_K=4, margin=-1.0, predict_every=every)
     a.advance(max_steps=15)
     b.advance(max_steps=15)
     ga, gb = a.fields(), b.fields()
