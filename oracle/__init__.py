@@ -50,7 +50,8 @@ class Problem(C.Structure):
                 ("bc", C.c_int * 4),
                 ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
                 ("manning_n", C.c_double), ("tol_h", C.c_double), ("dt_max", C.c_double),
-                ("inflow_t", C.POINTER(C.c_double)), ("inflow_Q", C.POINTER(C.c_double))]
+                ("inflow_t", C.POINTER(C.c_double)), ("inflow_Q", C.POINTER(C.c_double)),
+                ("flux_match", C.c_int)]
 
 
 class StepOut(C.Structure):
@@ -121,6 +122,7 @@ def make_problem(p):
     s.L = p["L"]
     s.reg_predict = int(p["reg_predict"])
     s.reg_close = int(p["reg_close"])
+    s.flux_match = int(p.get("flux_match", False))
     for k in range(4):
         s.bc[k] = BC[p["bc"][k]]
     s.eps, s.cfl, s.g = p["eps"], p["cfl"], p["g"]
@@ -296,7 +298,7 @@ class State:
         rc = lib().orc_hwfv1_step(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy),
                                   _d(self.z), self.t, dt, C.byref(o))
         if rc:
-            raise MemoryError("oracle step failed")
+            raise RuntimeError("oracle step failed (%d)" % rc)
         if "T" in res:
             res["T"] = res["T"][:P]
         if "S" in res:

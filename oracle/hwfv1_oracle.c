@@ -68,13 +68,28 @@
  *           Q(t)*dt*(covered inlet length / inlet length) on every leaf that
  *           touches the inlet, Q piecewise linear in t, taken at the start
  *           of the step.
+ *  R-match  (optional, flux_match = 1; the conservative variant the paper
+ *           leaves out of its same-level rule, Sec. 2.1.3) a face of a leaf
+ *           whose same-level neighbour is refined (significant after R2, so
+ *           smaller leaves lie on the other side) does not use that
+ *           neighbour's coarse coefficient: its flux and the leaf's own
+ *           reconstructed depth squared (the bed source term's face value)
+ *           are the averages, 0.5*(first half + second half), of those of
+ *           its two half faces one level finer, recursively, down to the
+ *           half faces whose neighbour cell is a leaf.  Such a half face is
+ *           evaluated between the same-level cells on both sides of it, the
+ *           call the smaller leaf makes for the same face, so every face
+ *           between leaves of two levels carries one flux from both sides
+ *           (mass is conserved up to rounding), and a still free surface
+ *           stays still.  Needs R2 (a significant cell then has only
+ *           significant ancestors).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_VERSION 1
+#define ORC_VERSION 2
 
 /* ------------------------------------------------------------------------ */
 /* Problem description (a plain C struct mirrored by oracle/__init__.py).   */
@@ -93,6 +108,7 @@ typedef struct {
     double eps, cfl, g, manning_n, tol_h, dt_max;
     const double* inflow_t;
     const double* inflow_Q;
+    int flux_match;          /* R-match on/off                             */
 } orc_problem;
 
 int orc_version(void) { return ORC_VERSION; }
@@ -451,35 +467,43 @@ static orc_cell ghost(const orc_problem* p, int s, orc_cell c) {
     return c;
 }
 
-/* One FV1 forward-Euler update (Eq. 2) of the cell (n, i, j) of size
- * dx x dy from its state C and the same-level neighbour states W, E, S, N
- * (ghosts already applied).  dh_in is the inflow depth added this step
- * (0 when the cell is not on an inlet); `inlet` says whether it is. */
-static void cell_update(const orc_problem* p, double dx, double dy, double dt,
-                        orc_cell C, orc_cell W, orc_cell E, orc_cell S, orc_cell N,
-                        int inlet, double dh_in, double out[3]) {
+/* One face of a cell, seen from the cell: side s (W, E, S, N) between the
+ * cell state C and the state X across the face.  F receives the face flux
+ * in the order of cell_update (x faces (h, qx, qy), y faces (h, qy, qx)),
+ * own2 the square of the cell's own reconstructed depth at the face. */
+static void face_of(const orc_problem* p, int s, orc_cell C, orc_cell X, double F[3], double* own2) {
     double g = p->g, tol = p->tol_h;
-    double uC, vC, uW, vW, uE, vE, uS, vS, uN, vN;
+    double uC, vC, uX, vX, hl, hr, zf;
     velocity(&C, tol, &uC, &vC);
-    velocity(&W, tol, &uW, &vW);
-    velocity(&E, tol, &uE, &vE);
-    velocity(&S, tol, &uS, &vS);
-    velocity(&N, tol, &uN, &vN);
+    velocity(&X, tol, &uX, &vX);
+    if (s == ORC_W) {               /* X on the left, normal u */
+        hll_face(g, tol, X.h, X.z, uX, vX, C.h, C.z, uC, vC, F, &hl, &hr, &zf);
+        *own2 = hr * hr;
+    } else if (s == ORC_E) {        /* X on the right, normal u */
+        hll_face(g, tol, C.h, C.z, uC, vC, X.h, X.z, uX, vX, F, &hl, &hr, &zf);
+        *own2 = hl * hl;
+    } else if (s == ORC_S) {        /* X below, normal v */
+        hll_face(g, tol, X.h, X.z, vX, uX, C.h, C.z, vC, uC, F, &hl, &hr, &zf);
+        *own2 = hr * hr;
+    } else {                        /* X above, normal v */
+        hll_face(g, tol, C.h, C.z, vC, uC, X.h, X.z, vX, uX, F, &hl, &hr, &zf);
+        *own2 = hl * hl;
+    }
+}
 
-    /* x faces: normal velocity u, tangential v; flux order (h, qx, qy) */
-    double FW[3], FE[3], hW_L, hW_R, zfW, hE_L, hE_R, zfE;
-    hll_face(g, tol, W.h, W.z, uW, vW, C.h, C.z, uC, vC, FW, &hW_L, &hW_R, &zfW);
-    hll_face(g, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, &hE_L, &hE_R, &zfE);
-    /* y faces: normal velocity v, tangential u; returned flux order is
-     * (h, qy, qx) */
-    double GS[3], GN[3], hS_L, hS_R, zfS, hN_L, hN_R, zfN;
-    hll_face(g, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, &hS_L, &hS_R, &zfS);
-    hll_face(g, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, &hN_L, &hN_R, &zfN);
-
+/* One FV1 forward-Euler update (Eq. 2) of a cell of size dx x dy from its
+ * state C, its four face fluxes (order of face_of) and the squares of its
+ * own reconstructed depths at them.  dh_in is the inflow depth added this
+ * step (0 when the cell is not on an inlet); `inlet` says whether it is. */
+static void cell_update_faces(const orc_problem* p, double dx, double dy, double dt, orc_cell C,
+                              const double FW[3], const double FE[3], const double GS[3],
+                              const double GN[3], double hW2, double hE2, double hS2, double hN2,
+                              int inlet, double dh_in, double out[3]) {
+    double g = p->g, tol = p->tol_h;
     double rx = dt / dx, ry = dt / dy;
     /* bed slope from the cell's own reconstructed face depths */
-    double bx = 0.5 * g * (hW_R * hW_R - hE_L * hE_L);
-    double by = 0.5 * g * (hS_R * hS_R - hN_L * hN_L);
+    double bx = 0.5 * g * (hW2 - hE2);
+    double by = 0.5 * g * (hS2 - hN2);
 
     double h = C.h - rx * (FE[0] - FW[0]) - ry * (GN[0] - GS[0]);
     double qx = C.qx - rx * ((FE[1] - FW[1]) + bx) - ry * (GN[2] - GS[2]);
@@ -502,6 +526,19 @@ static void cell_update(const orc_problem* p, double dx, double dy, double dt,
     out[0] = h;
     out[1] = qx;
     out[2] = qy;
+}
+
+/* The update of a cell from its state and its four same-level neighbour
+ * states W, E, S, N (ghosts already applied). */
+static void cell_update(const orc_problem* p, double dx, double dy, double dt,
+                        orc_cell C, orc_cell W, orc_cell E, orc_cell S, orc_cell N,
+                        int inlet, double dh_in, double out[3]) {
+    double FW[3], FE[3], GS[3], GN[3], hW2, hE2, hS2, hN2;
+    face_of(p, ORC_W, C, W, FW, &hW2);
+    face_of(p, ORC_E, C, E, FE, &hE2);
+    face_of(p, ORC_S, C, S, GS, &hS2);
+    face_of(p, ORC_N, C, N, GN, &hN2);
+    cell_update_faces(p, dx, dy, dt, C, FW, FE, GS, GN, hW2, hE2, hS2, hN2, inlet, dh_in, out);
 }
 
 /* Read the same-level cell (n, i, j) from the hierarchies. */
@@ -536,20 +573,75 @@ static double inflow_depth(const orc_problem* p, int n, int64_t i, int64_t j, do
     return ((Q * dt) * frac) / (dx * dy);
 }
 
-/* FV1 update of one leaf (n, i, j) using same-level neighbours from the
- * hierarchies (Sec. 2.1.3, Fig. 3). */
-static void leaf_update(const orc_problem* p, const double* const* hier4, int n, int64_t i,
-                        int64_t j, double t, double dt, double out[3]) {
-    double dx = ldexp(p->lx, -n), dy = ldexp(p->ly, -n);
+/* Whether the cell (n, i, j) is refined: below the finest level and
+ * significant after regularisation. */
+static int refined(const orc_problem* p, const uint8_t* S, int n, int64_t i, int64_t j) {
+    return n < p->L && S[level_start(n) + rm(n, i, j)];
+}
+
+/* R-match: the face on side s of the cell (n, i, j) whose neighbour cell
+ * (n, ni, nj) across that face is refined.  The face splits into two half
+ * faces one level finer; on each, the own-side cell and the neighbour
+ * cell are the level-(n+1) children that touch it (own side: the children
+ * of (n, i, j) next to the face; neighbour side: those of (n, ni, nj)).
+ * A half face whose neighbour child is refined again is split again. */
+static void matched_face(const orc_problem* p, const double* const* hier4, const uint8_t* S, int s,
+                         int n, int64_t i, int64_t j, int64_t ni, int64_t nj, double F[3],
+                         double* own2) {
+    double Fa[3], Fb[3], oa, ob;
+    for (int half = 0; half < 2; ++half) {
+        int64_t ci, cj, cni, cnj;            /* children at level n+1 */
+        if (s == ORC_W || s == ORC_E) {      /* x face: the halves go up in j */
+            ci = 2 * i + (s == ORC_E ? 1 : 0);
+            cni = 2 * ni + (s == ORC_E ? 0 : 1);
+            cj = cnj = 2 * j + half;
+        } else {                             /* y face: the halves go along i */
+            cj = 2 * j + (s == ORC_N ? 1 : 0);
+            cnj = 2 * nj + (s == ORC_N ? 0 : 1);
+            ci = cni = 2 * i + half;
+        }
+        double* Fh = half ? Fb : Fa;
+        double* oh = half ? &ob : &oa;
+        if (refined(p, S, n + 1, cni, cnj))
+            matched_face(p, hier4, S, s, n + 1, ci, cj, cni, cnj, Fh, oh);
+        else
+            face_of(p, s, fetch(hier4, n + 1, ci, cj), fetch(hier4, n + 1, cni, cnj), Fh, oh);
+    }
+    for (int k = 0; k < 3; ++k) F[k] = 0.5 * (Fa[k] + Fb[k]);
+    *own2 = 0.5 * (oa + ob);
+}
+
+/* One face of the leaf (n, i, j) on side s: the ghost at the domain edge,
+ * else the same-level neighbour (Sec. 2.1.3, Fig. 3), or with R-match the
+ * averaged finer faces when that neighbour is refined. */
+static void leaf_face(const orc_problem* p, const double* const* hier4, const uint8_t* S, int s,
+                      int n, int64_t i, int64_t j, orc_cell C, double F[3], double* own2) {
     int64_t last = side(n) - 1;
+    int64_t ni = i + (s == ORC_E) - (s == ORC_W), nj = j + (s == ORC_N) - (s == ORC_S);
+    if (ni < 0 || ni > last || nj < 0 || nj > last) {
+        face_of(p, s, C, ghost(p, s, C), F, own2);
+    } else if (p->flux_match && refined(p, S, n, ni, nj)) {
+        matched_face(p, hier4, S, s, n, i, j, ni, nj, F, own2);
+    } else {
+        face_of(p, s, C, fetch(hier4, n, ni, nj), F, own2);
+    }
+}
+
+/* FV1 update of one leaf (n, i, j) using same-level neighbours from the
+ * hierarchies (Sec. 2.1.3, Fig. 3); S the regularised flags (read by
+ * R-match only). */
+static void leaf_update(const orc_problem* p, const double* const* hier4, const uint8_t* S, int n,
+                        int64_t i, int64_t j, double t, double dt, double out[3]) {
+    double dx = ldexp(p->lx, -n), dy = ldexp(p->ly, -n);
     orc_cell C = fetch(hier4, n, i, j);
-    orc_cell W = i > 0 ? fetch(hier4, n, i - 1, j) : ghost(p, ORC_W, C);
-    orc_cell E = i < last ? fetch(hier4, n, i + 1, j) : ghost(p, ORC_E, C);
-    orc_cell S = j > 0 ? fetch(hier4, n, i, j - 1) : ghost(p, ORC_S, C);
-    orc_cell N = j < last ? fetch(hier4, n, i, j + 1) : ghost(p, ORC_N, C);
+    double FW[3], FE[3], GS[3], GN[3], hW2, hE2, hS2, hN2;
+    leaf_face(p, hier4, S, ORC_W, n, i, j, C, FW, &hW2);
+    leaf_face(p, hier4, S, ORC_E, n, i, j, C, FE, &hE2);
+    leaf_face(p, hier4, S, ORC_S, n, i, j, C, GS, &hS2);
+    leaf_face(p, hier4, S, ORC_N, n, i, j, C, GN, &hN2);
     int inlet;
     double dh = inflow_depth(p, n, i, j, dx, dy, t, dt, &inlet);
-    cell_update(p, dx, dy, dt, C, W, E, S, N, inlet, dh, out);
+    cell_update_faces(p, dx, dy, dt, C, FW, FE, GS, GN, hW2, hE2, hS2, hN2, inlet, dh, out);
 }
 
 /* CFL bound of one cell state (R-cfl): min(dx/(|u|+a), dy/(|v|+a)) with
@@ -609,6 +701,7 @@ typedef struct {
 int orc_hwfv1_step(const orc_problem* p, double* h, double* qx, double* qy, const double* z,
                    double t, double dt, orc_step_out* o) {
     int L = p->L;
+    if (p->flux_match && !p->reg_close) return 2;     /* R-match needs R2 */
     int64_t N = side(L) * side(L), P = level_start(L), H = N + P;
     double* hier[4];
     double* det[4];
@@ -635,7 +728,7 @@ int orc_hwfv1_step(const orc_problem* p, double* h, double* qx, double* qy, cons
         int n = (int)(leaves[k] >> 28);
         uint32_t i, j;
         orc_demorton(leaves[k] & 0x0FFFFFFFu, &i, &j);
-        leaf_update(p, (const double* const*)hier, n, i, j, t, dt, newU + 3 * k);
+        leaf_update(p, (const double* const*)hier, S, n, i, j, t, dt, newU + 3 * k);
     }
     /* R-cfl over the updated leaves */
     double rmin = INFINITY;

@@ -26,18 +26,20 @@ BC = {"closed": 0, "transmissive": 1, "inflow": 2}
 
 def problem(L, lx=1.0, ly=1.0, x0=0.0, y0=0.0, eps=1e-3, cfl=0.5, g=9.80665,
             manning_n=0.0, tol_h=1e-3, dt_max=1.0, bc=("closed",) * 4,
-            inflow=None, reg_predict=True, reg_close=True):
+            inflow=None, reg_predict=True, reg_close=True, flux_match=False):
     """Problem description: domain, maximum level L, threshold eps, CFL,
     gravity, Manning n, wet/dry tolerance, boundary kinds (W, E, S, N) and an
     optional inflow ``{"a0": first finest cell, "a1": end, "t": [...],
-    "Q": [...]}`` on the side whose kind is ``"inflow"``."""
+    "Q": [...]}`` on the side whose kind is ``"inflow"``; ``flux_match`` selects
+    the conservative variant with matched fluxes at resolution changes."""
     bc = tuple(bc)
     assert len(bc) == 4 and all(b in BC for b in bc)
     assert sum(b == "inflow" for b in bc) <= 1
     return dict(L=int(L), lx=float(lx), ly=float(ly), x0=float(x0), y0=float(y0),
                 eps=float(eps), cfl=float(cfl), g=float(g), manning_n=float(manning_n),
                 tol_h=float(tol_h), dt_max=float(dt_max), bc=bc, inflow=inflow,
-                reg_predict=bool(reg_predict), reg_close=bool(reg_close))
+                reg_predict=bool(reg_predict), reg_close=bool(reg_close),
+                flux_match=bool(flux_match))
 
 
 def centres(p):
