@@ -72,6 +72,19 @@ typedef enum {
  * reproduce the values already stored.  Skipping is off when eps < 1e-30
  * (thresholds that round to 0 flag zero details). */
 #define HWFV1_FULL_SWEEP 4u
+/* Conservative variant (a switch of this library; the paper's update uses
+ * the same-level neighbour on every face, Sec. 2.1.3, which does not
+ * conserve mass where the resolution changes).  A face of a leaf whose
+ * same-level neighbour is refined (smaller leaves lie behind it) takes, for
+ * its flux and for the leaf's own reconstructed depth squared in the bed
+ * source term, the average of its two halves one level finer, recursively,
+ * down to the half faces whose neighbour cell is a leaf; each such half face
+ * is evaluated between the two same-level cells that touch it, as the
+ * smaller leaf evaluates it.  Both sides of every face then carry one flux:
+ * mass is conserved up to rounding on closed domains whose finest depths
+ * hand a leaf's volume down unchanged.  Needs HWFV1_REG_CLOSE; single
+ * domains only (not hwfv1_batch_init, not with hwfv1_set_skipnet). */
+#define HWFV1_FLUX_MATCH 8u
 
 /* Problem description.  The user inputs of Algorithm 3 are L and eps (t_end
  * is given to hwfv1_advance); CFL = 0.5 is the paper's choice (Sec. 2.1.3).

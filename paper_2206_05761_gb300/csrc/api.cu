@@ -44,8 +44,10 @@ hwfv1_status validate(const hwfv1_problem* s, std::string* msg) {
     if (!finite_pos(s->tol_h)) return spec_error("tol_h must be > 0", msg);
     if (!finite_pos(s->dt_max)) return spec_error("dt_max must be > 0", msg);
     if (s->precision != 64 && s->precision != 32) return spec_error("precision must be 64 or 32", msg);
-    if (s->flags & ~(HWFV1_REG_PREDICT | HWFV1_REG_CLOSE | HWFV1_FULL_SWEEP))
+    if (s->flags & ~(HWFV1_REG_PREDICT | HWFV1_REG_CLOSE | HWFV1_FULL_SWEEP | HWFV1_FLUX_MATCH))
         return spec_error("unknown flags", msg);
+    if ((s->flags & HWFV1_FLUX_MATCH) && !(s->flags & HWFV1_REG_CLOSE))
+        return spec_error("HWFV1_FLUX_MATCH needs HWFV1_REG_CLOSE", msg);
     int inflow_sides = 0;
     for (int k = 0; k < 4; ++k) {
         if (s->bc[k] < HWFV1_BC_CLOSED || s->bc[k] > HWFV1_BC_INFLOW) return spec_error("bad boundary kind", msg);
@@ -231,6 +233,7 @@ hwfv1_status hwfv1_batch_init(const hwfv1_problem* specs, int32_t n, const doubl
         const hwfv1_status s = validate(specs + d, &msg);
         if (s != HWFV1_OK) return s;
         if (specs[d].precision != specs[0].precision) return HWFV1_ERR_INVALID_SPEC;
+        if (specs[d].flags & HWFV1_FLUX_MATCH) return HWFV1_ERR_INVALID_SPEC;
         if (!z[d] || !h[d] || !qx[d] || !qy[d]) return HWFV1_ERR_INVALID_SPEC;
     }
     hwfv1_batch* bt = new (std::nothrow) hwfv1_batch;

@@ -260,6 +260,8 @@ class EngineT final : public Engine {
     hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin, int predict_every) override {
         if (net && (L_ < 6 || audit_K < 1 || predict_every < 1))
             return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead needs L >= 6, K >= 1, predict_every >= 1");
+        if (net && (spec_.flags & HWFV1_FLUX_MATCH))
+            return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead with HWFV1_FLUX_MATCH");
         skip_ = net;
         audit_K_ = audit_K < 1 ? 1 : audit_K;
         every_ = predict_every < 1 ? 1 : predict_every;
@@ -668,6 +670,8 @@ class EngineT final : public Engine {
         a.face = face_;
         a.fcap = fcap_;
         a.mark = mark_;
+        a.Sb = Sb_;
+        a.fm = (spec_.flags & HWFV1_FLUX_MATCH) ? 1 : 0;
         return a;
     }
     Phys<T> phys() const {
@@ -683,10 +687,16 @@ class EngineT final : public Engine {
     }
     void launch_fv1(const uint32_t* leaves = nullptr) {
         StepArgs<T> a = step_args();
-        if (leaves) a.leaves = leaves;
+        if (leaves) {
+            a.leaves = leaves;
+            a.fm = 0;            // every leaf on the finest level: nothing to match
+        }
         k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
         mark("k_fv1_dry");
-        if (face_) {
+        if (a.fm) {
+            k_fv1_match<T><<<wet_grid(), 64, 0, stream_>>>(a);
+            mark("k_fv1_match");
+        } else if (face_) {
             // 64-thread blocks: a short queue spreads over every SM's FP64 units
             // (one warp-wide FP64 instruction holds a sub-partition's unit for
             // tens of cycles, so few warps per unit means a shorter chain)

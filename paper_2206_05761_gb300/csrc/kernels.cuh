@@ -1217,18 +1217,19 @@ __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, 
     cell_update_faces(P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out);
 }
 
-// The update of cell_update from its four face fluxes and its own
-// reconstructed depths at them (hW_R, hE_L, hS_R, hN_L).  rh_out (if given)
-// receives 1/h of the new depth when the friction step formed it, else 0.
+// The update from the four face fluxes and the squares of the cell's own
+// reconstructed depths at them (hW2, hE2, hS2, hN2: the bed source term's
+// face values).  rh_out (if given) receives 1/h of the new depth when the
+// friction step formed it, else 0.
 template <typename T>
-__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
-                                                  const T FW[3], const T FE[3], const T GS[3], const T GN[3],
-                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3],
-                                                  T* rh_out) {
+__device__ __forceinline__ void cell_update_faces_sq(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+                                                     const T FW[3], const T FE[3], const T GS[3], const T GN[3],
+                                                     T hW2, T hE2, T hS2, T hN2, bool inlet, T dh, T out[3],
+                                                     T* rh_out = nullptr) {
     if (rh_out) *rh_out = T(0);
     const T g = P.g, hg = P.hg, tol = P.tol;
-    const T bx = hg * (hW_R * hW_R - hE_L * hE_L);
-    const T by = hg * (hS_R * hS_R - hN_L * hN_L);
+    const T bx = hg * (hW2 - hE2);
+    const T by = hg * (hS2 - hN2);
     T h = C.h - rx * (FE[0] - FW[0]) - ry * (GN[0] - GS[0]);
     T qx = C.qx - rx * ((FE[1] - FW[1]) + bx) - ry * (GN[2] - GS[2]);
     T qy = C.qy - rx * (FE[2] - FW[2]) - ry * ((GN[1] - GS[1]) + by);
@@ -1251,6 +1252,17 @@ __device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, 
     out[0] = h;
     out[1] = qx;
     out[2] = qy;
+}
+
+// The update of cell_update from its four face fluxes and its own
+// reconstructed depths at them (hW_R, hE_L, hS_R, hN_L).
+template <typename T>
+__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+                                                  const T FW[3], const T FE[3], const T GS[3], const T GN[3],
+                                                  T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3],
+                                                  T* rh_out) {
+    cell_update_faces_sq(P, rx, ry, dt, C, FW, FE, GS, GN, hW_R * hW_R, hE_L * hE_L, hS_R * hS_R, hN_L * hN_L,
+                         inlet, dh, out, rh_out);
 }
 
 // CFL bound of an updated cell: min(dx/(|u|+a), dy/(|v|+a)), +inf if dry
@@ -1283,6 +1295,10 @@ struct StepArgs {
     T* face = nullptr;
     uint32_t fcap = 0;
     unsigned long long* mark = nullptr;
+    // matched fluxes at resolution changes (k_fv1_match): the regularised
+    // significance bits, which tell a refined same-level neighbour
+    const uint32_t* Sb = nullptr;
+    int fm = 0;
 };
 
 template <typename T>
@@ -1362,6 +1378,17 @@ __device__ __forceinline__ DryProbe dry_probe(uint32_t pk) {
     return d;
 }
 
+// Whether a same-level neighbour of the leaf is refined (significant after
+// the upward closure, so smaller leaves lie behind that face).
+__device__ __forceinline__ bool refined_nbr(const uint32_t* __restrict__ Sb, const DryProbe& d, int L) {
+    if (d.n >= L) return false;
+    const uint64_t base = lvl_off(d.n);
+    return (d.iW != d.iC && sig_bit(Sb, d.n, (uint32_t)(d.iW - base))) ||
+           (d.iE != d.iC && sig_bit(Sb, d.n, (uint32_t)(d.iE - base))) ||
+           (d.iS != d.iC && sig_bit(Sb, d.n, (uint32_t)(d.iS - base))) ||
+           (d.iN != d.iC && sig_bit(Sb, d.n, (uint32_t)(d.iN - base)));
+}
+
 template <typename T>
 __device__ __forceinline__ bool dry5(const T* __restrict__ h, const DryProbe& d) {
     const T a = __ldg(h + d.iC), b = __ldg(h + d.iW), c = __ldg(h + d.iE), e = __ldg(h + d.iS),
@@ -1425,8 +1452,14 @@ __device__ __forceinline__ void fv1_dry_body(const StepArgs<T>& a, Blk B) {
         const uint32_t p1 = __ldg(a.leaves + k), p2 = two ? __ldg(a.leaves + k2) : 0u;
         const DryProbe d1 = dry_probe(p1);
         const DryProbe d2 = dry_probe(p2);
-        const bool y1 = dry5(hsrc, d1);
-        const bool y2 = two && dry5(hsrc, d2);
+        bool y1 = dry5(hsrc, d1);
+        bool y2 = two && dry5(hsrc, d2);
+        if (a.fm) {
+            // with matched fluxes a face toward a refined neighbour averages
+            // finer faces: such a leaf takes the full update
+            y1 = y1 && !refined_nbr(a.Sb, d1, a.L);
+            y2 = y2 && !refined_nbr(a.Sb, d2, a.L);
+        }
         dry_finish(a, st, oh, oqx, oqy, d1, y1, p1);
         if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, p2);
     }
@@ -1567,6 +1600,174 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
     fv1_wet_body<T>(a, this_blk());
+}
+
+// ---------------------------------------------------------------------------
+// Matched fluxes at resolution changes (the conservative variant): a face of
+// a leaf whose same-level neighbour is refined takes, for its flux and for
+// the square of the leaf's own reconstructed depth, the average
+// half(first + second) of its two halves one level finer, recursively, down
+// to the half faces whose neighbour cell is not refined; such a half face
+// is evaluated between the two same-level cells that touch it -- the call
+// the smaller leaf on the other side makes for the same face, so both sides
+// carry one flux.
+// ---------------------------------------------------------------------------
+
+// One face of a cell seen from the cell: side s (0 W, 1 E, 2 S, 3 N) between
+// its state C and the state X across the face.  F in the order of
+// cell_update (x faces (h, qx, qy), y faces (h, qy, qx)), own2 the square of
+// the cell's own reconstructed depth at the face.
+template <typename T>
+__device__ __forceinline__ void face_of(const Phys<T>& P, int s, const Cell<T>& C, const Cell<T>& X, T F[3],
+                                        T& own2) {
+    T uC, vC, uX, vX, hl, hr;
+    velocity(C, P.tol, uC, vC);
+    velocity(X, P.tol, uX, vX);
+    if (s == 0) {
+        hll_face(P.g, P.hg, P.tol, X.h, X.z, uX, vX, C.h, C.z, uC, vC, F, hl, hr);
+        own2 = hr * hr;
+    } else if (s == 1) {
+        hll_face(P.g, P.hg, P.tol, C.h, C.z, uC, vC, X.h, X.z, uX, vX, F, hl, hr);
+        own2 = hl * hl;
+    } else if (s == 2) {
+        hll_face(P.g, P.hg, P.tol, X.h, X.z, vX, uX, C.h, C.z, vC, uC, F, hl, hr);
+        own2 = hr * hr;
+    } else {
+        hll_face(P.g, P.hg, P.tol, C.h, C.z, vC, uC, X.h, X.z, vX, uX, F, hl, hr);
+        own2 = hl * hl;
+    }
+}
+
+// The face on side s of the leaf (n, i, j) whose same-level neighbour is
+// refined.  Depth first over the halves (first half: lower j on x faces,
+// lower i on y faces): half r of level m lies between the own-side cell and
+// the neighbour cell of level m that touch it; a finished second half is
+// averaged with the pending first half of its level, one level up, until
+// the face itself is reached.  The walk visits each half face of the finite
+// tree once.
+template <typename T>
+__device__ __noinline__ void matched_face(const StepArgs<T>& a, const CellSrc<T>& src, int s, int n, uint32_t i,
+                                          uint32_t j, T F[3], T& own2) {
+    T pend[kMaxL][4];                     // pending first halves, by level - n - 1
+    int m = n + 1;
+    uint32_t r = 0u;
+    for (;;) {
+        const bool xf = s <= 1;
+        uint32_t oi, oj, ni, nj;
+        for (;;) {
+            const int k = m - n;
+            if (xf) {
+                oi = s == 0 ? (i << k) : ((i + 1u) << k) - 1u;
+                ni = s == 0 ? (i << k) - 1u : ((i + 1u) << k);
+                oj = nj = (j << k) + r;
+            } else {
+                oj = s == 2 ? (j << k) : ((j + 1u) << k) - 1u;
+                nj = s == 2 ? (j << k) - 1u : ((j + 1u) << k);
+                oi = ni = (i << k) + r;
+            }
+            if (m >= a.L || !sig_bit(a.Sb, m, morton2(ni, nj))) break;
+            ++m;                                  // the neighbour cell is refined: split
+            r <<= 1;
+        }
+        const uint64_t base = lvl_off(m);
+        T v[4];
+        face_of(a.P, s, fetch(src, base + morton2(oi, oj)), fetch(src, base + morton2(ni, nj)), v, v[3]);
+        while (r & 1u) {                          // a second half: close its pair
+            const T* p = pend[m - n - 1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = half(p[q] + v[q]);
+            --m;
+            r >>= 1;
+        }
+        if (m == n) {
+            F[0] = v[0];
+            F[1] = v[1];
+            F[2] = v[2];
+            own2 = v[3];
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pend[m - n - 1][q] = v[q];
+        r += 1u;                                  // on to its second half
+    }
+}
+
+// One face of a queued leaf: the ghost at the domain edge, the matched face
+// toward a refined neighbour, else the same-level neighbour.
+template <typename T>
+__device__ __forceinline__ void leaf_face(const StepArgs<T>& a, const CellSrc<T>& src, int s, int n, uint32_t i,
+                                          uint32_t j, uint32_t last, const Cell<T>& C, T F[3], T& own2) {
+    const bool edge = (s == 0 && i == 0u) || (s == 1 && i == last) || (s == 2 && j == 0u) ||
+                      (s == 3 && j == last);
+    if (edge) {
+        face_of(a.P, s, C, ghost(C, a.bc_ref[s], s <= 1), F, own2);
+        return;
+    }
+    const uint32_t ni = s == 0 ? i - 1u : (s == 1 ? i + 1u : i);
+    const uint32_t nj = s == 2 ? j - 1u : (s == 3 ? j + 1u : j);
+    const uint32_t nc = morton2(ni, nj);
+    if (n < a.L && sig_bit(a.Sb, n, nc)) {
+        matched_face(a, src, s, n, i, j, F, own2);
+        return;
+    }
+    face_of(a.P, s, C, fetch(src, lvl_off(n) + nc), F, own2);
+}
+
+// FV1 with matched fluxes: the full update of every queued leaf.
+template <typename T>
+__device__ __forceinline__ void fv1_match_body(const StepArgs<T>& a, Blk B) {
+    DevState* st = a.st;
+    if (!st->active) return;
+    const uint32_t nq = st->nwet;
+    if (B.id * blockDim.x >= nq) return;          // whole block idle
+    const int par = (int)st->cur, nxt = par ^ 1;
+    const T dt = (T)st->dt_use;
+    const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
+    const T Qdt = (T)st->Qdt;
+    CellSrc<T> src;
+    src.h = par ? a.f[1][0] : a.f[0][0];
+    src.qx = par ? a.f[1][1] : a.f[0][1];
+    src.qy = par ? a.f[1][2] : a.f[0][2];
+    src.z = a.z;
+    T* const oh = nxt ? a.f[1][0] : a.f[0][0];
+    T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
+    T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
+    unsigned long long rmin = kInfBits, mh = 0, mqx = 0, mqy = 0, spd[2] = {0ull, 0ull};
+    for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < nq; w += B.n * blockDim.x) {
+        const uint32_t pk = a.wet[w];
+        const int n = (int)(pk >> kLeafShift);
+        const uint32_t code = pk & kCodeMask;
+        const uint32_t i = compact16(code), j = compact16(code >> 1);
+        const uint32_t last = (1u << n) - 1u;
+        const uint64_t iC = lvl_off(n) + code;
+        const Cell<T> C = fetch(src, iC);
+        T FW[3], FE[3], GS[3], GN[3], w2, e2, s2, n2;
+        leaf_face(a, src, 0, n, i, j, last, C, FW, w2);
+        leaf_face(a, src, 1, n, i, j, last, C, FE, e2);
+        leaf_face(a, src, 2, n, i, j, last, C, GS, s2);
+        leaf_face(a, src, 3, n, i, j, last, C, GN, n2);
+        const T scale = (T)(1u << n);
+        const T rx = rx0 * scale, ry = ry0 * scale;
+        int64_t lo = 0, hi = 0;
+        const bool inlet = inlet_range(a, n, i, j, last, lo, hi);
+        T dh = T(0);
+        if (inlet) {
+            const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
+            const T inv2n = T(1) / scale;
+            const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
+            dh = (Qdt * frac) / (dxn * dyn);
+        }
+        T out[3], rh;
+        cell_update_faces_sq(a.P, rx, ry, dt, C, FW, FE, GS, GN, w2, e2, s2, n2, inlet, dh, out, &rh);
+        wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd, rh);
+    }
+    block_atomic_u64<false>(rmin, &st->rmin_bits);
+    block_max3_u64(mh, mqx, mqy, st->max_bits);
+    block_max3_u64(spd[0], spd[1], 0ull, st->speed_bits);
+}
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fv1_match(StepArgs<T> a) {
+    fv1_match_body<T>(a, this_blk());
 }
 
 // The same update in two kernels that compute every face between two queued

@@ -23,7 +23,7 @@ STATUS = {0: "HWFV1_OK", 1: "HWFV1_ERR_INVALID_SPEC", 2: "HWFV1_ERR_OOM", 3: "HW
           4: "HWFV1_ERR_NONFINITE", 5: "HWFV1_ERR_NEG_DEPTH", 6: "HWFV1_ERR_TIMEOUT",
           7: "HWFV1_ERR_STATE"}
 BC = {"closed": 0, "transmissive": 1, "inflow": 2}
-REG_PREDICT, REG_CLOSE, FULL_SWEEP = 1, 2, 4
+REG_PREDICT, REG_CLOSE, FULL_SWEEP, FLUX_MATCH = 1, 2, 4, 8
 
 
 class Hwfv1Error(RuntimeError):
@@ -170,7 +170,8 @@ def make_problem(p, precision=64):
         s.inflow_n = n
         s.inflow_a0, s.inflow_a1 = inf["a0"], inf["a1"]
     s.flags = ((REG_PREDICT if p.get("reg_predict", True) else 0) | (REG_CLOSE if p.get("reg_close", True) else 0)
-               | (FULL_SWEEP if p.get("full_sweep", False) else 0))
+               | (FULL_SWEEP if p.get("full_sweep", False) else 0)
+               | (FLUX_MATCH if p.get("flux_match", False) else 0))
     return s
 
 

@@ -36,7 +36,8 @@ def test_problem_struct_layout():
 @pytest.mark.parametrize("field,value", [
     ("L", 0), ("L", 15), ("lx", 0.0), ("ly", -1.0), ("eps", -1e-3), ("eps", 1e-250),
     ("cfl", 0.0), ("cfl", 1.5), ("g", 0.0), ("manning_n", -0.1), ("tol_h", 0.0),
-    ("dt_max", 0.0), ("precision", 16), ("flags", 8)])
+    ("dt_max", 0.0), ("precision", 16), ("flags", 16),
+    ("flags", 8)])                 # flux matching without the upward closure
 def test_invalid_spec_rejected_without_gpu(field, value):
     p, _ = synth.circular_dam_break(L=3)
     s = H.make_problem(p)
