@@ -496,6 +496,52 @@ def time_uniform(args, p, state, t_s, dt_s, steps):
             "sim_time_s": [t_s, t], "leaves": 1 << (2 * args.L)}
 
 
+def time_flux_match(args, p, state, t_s, dt_s, steps):
+    """The conservative variant (HWFV1_FLUX_MATCH) on the same window, and
+    the volume drift of a closed, fully wet adaptive basin (wet mound,
+    L=10, 2000 steps) with and without it."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2206_05761_gb300.sim import Simulation
+    stream = torch.cuda.Stream()
+    pm = dict(p, flux_match=True)
+    sim = Simulation(pm, state, args.precision, stream=stream)
+    sim.set_time(t_s, dt_s)
+    sim.advance(max_steps=max(args.warmup, 3))
+    sim.counters()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.advance(max_steps=steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.close()
+    out = {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps}
+    pw, fw = synth.wet_mound(L=10, eps=1e-3)
+    cell = (pw["lx"] / 1024) * (pw["ly"] / 1024)
+    v0 = float(np.sum(fw["h"])) * cell
+    basin = {}
+    for fm in (False, True):
+        s = Simulation(dict(pw, flux_match=fm), fw, args.precision, stream=stream)
+        s.counters()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.advance(max_steps=2000)
+        b.record(stream)
+        stream.synchronize()
+        n, lu, _, _, _ = s.counters()
+        v = float(np.sum(s.fields()["h"])) * cell
+        basin["matched" if fm else "same_level"] = {
+            "volume_drift_rel": abs(v - v0) / v0, "steps_per_s": n / (a.elapsed_time(b) / 1e3),
+            "mean_leaves": lu / max(n, 1)}
+        s.close()
+    out["closed_wet_basin"] = dict(basin, workload="wet mound over humps, closed, L=10, eps=1e-3, 2000 steps")
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -602,6 +648,10 @@ def main():
         u = time_uniform(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"], args.steps)
         u["hwfv1_speedup"] = value / u["value"]
         out["uniform_fv1"] = u
+    if world == 1:
+        fm = time_flux_match(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"], args.steps)
+        fm["cost_vs_same_level"] = value / fm["value"]
+        out["flux_match"] = fm
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_pseudo2d:

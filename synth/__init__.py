@@ -14,7 +14,8 @@ Workloads (the paper's test cases, Sec. 3, replaced by seeded stand-ins):
 * ``terrain_flood`` -- a seeded 1/f^2 spectral DEM with a carved channel and
   an inflow hydrograph, standing in for the DEM-based tests of Sec. 3.3.
 * ``ensemble`` -- many independent bumpy dam-breaks of mixed depth L.
-* small fixtures for the pins: lake at rest, pseudo-2D dam-break (Sec. 3.2),
+* small fixtures for the pins: lake at rest, a wet mound in a closed basin,
+  pseudo-2D dam-break (Sec. 3.2),
   uniform frictional flow, a closed basin with inflow.
 """
 from __future__ import annotations
@@ -207,6 +208,16 @@ def lake_at_rest(L=6, eps=1e-3, seed=5, eta=1.0, wet=True):
     amp = (0.1, 0.6) if wet else (0.6, 1.4)
     z = gaussian_humps(p, rng, amp=amp)
     return p, _fields(p, np.full_like(z, eta), z)
+
+
+def wet_mound(L=6, eps=1e-3, seed=5, eta=1.0, mound=0.3):
+    """A raised free-surface mound released over seeded humps in a closed
+    basin, fully wet: the finest depths under a leaf hand its volume down
+    unchanged, so the volume changes only through the fluxes."""
+    p, f = lake_at_rest(L=L, eps=eps, seed=seed, eta=eta)
+    x, y = centres(p)
+    eta_m = eta + mound * np.exp(-((x - 0.3) ** 2 + (y - 0.6) ** 2) / 0.01)
+    return p, _fields(p, eta_m, f["z"])
 
 
 def pseudo_2d_dam_break(L=7, eps=0.0, h_up=6.0, h_down=2.0, dam_x=10.0):

@@ -24,10 +24,7 @@ def _closed_circle(L):
 
 
 def _wet_bumps(L):
-    p, f = synth.lake_at_rest(L=L, eps=1e-3)
-    x, y = synth.centres(p)
-    eta = 1.0 + 0.3 * np.exp(-((x - 0.3) ** 2 + (y - 0.6) ** 2) / 0.01)
-    f["h"] = np.ascontiguousarray(np.maximum(0.0, eta - f["z"]))
+    p, f = synth.wet_mound(L=L, eps=1e-3)
     return _fm(p), f
 
 

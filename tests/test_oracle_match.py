@@ -16,12 +16,7 @@ def _volume(st):
 
 
 def _wet_bumps(L=6):
-    """Closed basin, humps below a free surface with a raised mound: fully
-    wet, so the finest depths hand down a leaf's volume unchanged."""
-    p, f = synth.lake_at_rest(L=L, eps=1e-3)
-    x, y = synth.centres(p)
-    eta = 1.0 + 0.3 * np.exp(-((x - 0.3) ** 2 + (y - 0.6) ** 2) / 0.01)
-    f["h"] = np.ascontiguousarray(np.maximum(0.0, eta - f["z"]))
+    p, f = synth.wet_mound(L=L, eps=1e-3)
     assert f["h"].min() > 0.1
     return p, f
 
