@@ -66,6 +66,17 @@ __host__ __device__ inline uint32_t mort_xm(uint32_t c) { return (((c & kXBits) 
 __host__ __device__ inline uint32_t mort_yp(uint32_t c) { return (((c | kXBits) + 2u) & kYBits) | (c & kXBits); }
 __host__ __device__ inline uint32_t mort_ym(uint32_t c) { return (((c & kYBits) - 2u) & kYBits) | (c & kXBits); }
 
+// Programmatic dependent launch.  A kernel of the step launched with the
+// programmatic-serialisation attribute may be scheduled before the kernel
+// ahead of it in the stream has finished; pdl_wait, its first statement,
+// blocks until that kernel has completed and its writes are visible (an
+// ordinary launch returns at once).  pdl_launch_next lets the next kernel
+// be scheduled once every CTA of this grid has issued it or exited; every
+// CTA has then been placed, so the waiting CTAs of the next kernel only take
+// slots this grid no longer needs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // significance bit (n, code)
 __device__ __forceinline__ uint32_t sig_bit(const uint32_t* __restrict__ b, int n, uint32_t code) {
     return (__ldg(b + word_off(n) + (code >> 5)) >> (code & 31u)) & 1u;

@@ -95,6 +95,7 @@ class EngineT final : public Engine {
         if (!alloc(&work_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
         cudaMemsetAsync(tilebytes_, 0, (size_t)ntiles_ * 4, stream_);
         quiet_on_ = !(spec_.flags & HWFV1_FULL_SWEEP) && spec_.eps >= 1e-30;
+        pdl_ = std::getenv("HWFV1_NO_PDL") == nullptr;
         {
             std::vector<uint8_t> inl(ntiles_, 0);
             const int side = step_args().inflow_side;
@@ -153,8 +154,8 @@ class EngineT final : public Engine {
             a.L = L_;
             encode_passes(a);
         }
-        k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tz_, Cz_, nullptr, Sz_, L_, predict(), close(),
-                                                       nullptr);
+        lk(k_flag, grid_for(words_), 256, Tz_, Cz_, nullptr, Sz_, L_, predict(), close(),
+           (const DevState*)nullptr, (uint32_t*)nullptr);
         // leaf count of each tile holding the bed's flags alone (skipped tiles)
         if (!alloc(&scount_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
         k_static_counts<<<(ntiles_ + kTilesPerCta - 1) / kTilesPerCta, 256, 0, stream_>>>(Sz_, L_, kt_, ntiles_,
@@ -569,14 +570,14 @@ class EngineT final : public Engine {
             const uint32_t nb = 1u << (2 * (ls - k));
             const int ls2 = ls - k, k2 = ls2 < 5 ? ls2 : 5;
             if (ls == L_ && a.zf[0] != nullptr && nb > (uint32_t)nsm_ * 8u) {
-                k_encode_tiles<T, NF><<<nsm_ * 8, 256, 0, stream_>>>(a, nb);
+                lk(k_encode_tiles<T, NF>, nsm_ * 8, 256, a, nb);
                 mark("k_encode_tiles");
             } else if (ticket && ls2 > 0 && ls2 == k2) {      // next pass is the last (one CTA)
-                k_encode_tail<T, NF><<<nb, 256, 0, stream_>>>(a, ls2, k2, ticket);
+                lk(k_encode_tail<T, NF>, nb, 256, a, ls2, k2, ticket);
                 mark("k_encode_tail");
                 break;                                     // levels ls2-1 .. 0 done too
             } else {
-                k_encode<T, NF><<<nb, 256, 0, stream_>>>(a);
+                lk(k_encode<T, NF>, nb, 256, a);
                 mark("k_encode");
             }
             ls -= k;
@@ -584,7 +585,7 @@ class EngineT final : public Engine {
     }
 
     void launch_encode() {
-        k_clear_words<<<grid_for(2 * (uint64_t)words_), 256, 0, stream_>>>(Tb_, 2 * words_, st_);
+        lk(k_clear_words, grid_for(2 * (uint64_t)words_), 256, Tb_, 2 * words_, st_);
         mark("k_clear_words");
         EncodeArgs<T, 3> a;
         for (int b = 0; b < 2; ++b)
@@ -606,7 +607,7 @@ class EngineT final : public Engine {
         encode_passes(a, &st_->enc_ticket);
     }
     void launch_flag() {
-        k_flag<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_,
+        lk(k_flag, grid_for(words_), 256, Tb_, Cb_, Sz_, Sb_, L_, predict(), close(), st_,
                                                        &st_->ndec);
         mark("k_flag");
     }
@@ -617,16 +618,34 @@ class EngineT final : public Engine {
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
         const uint32_t grid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
         if (quiet_on_) {
-            k_trav_classify<<<(ntiles_ + 255) / 256, 256, 0, stream_>>>(Sb_, L_, kt_, ntiles_, st_, quiet(),
+            lk(k_trav_classify, (ntiles_ + 255) / 256, 256, Sb_, L_, kt_, ntiles_, st_, quiet(),
                                                                       learned ? nullptr : scount_, work_);
             mark("k_trav_classify");
-            k_trav_list<<<nsm_ * 8, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, st_, work_);
+            lk(k_trav_list, nsm_ * 8, 256, Sb_, dlist_, leaves_, L_, kt_, st_, work_);
             mark("k_trav_list");
         } else {
-            k_trav_fused<<<grid, 256, 0, stream_>>>(Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
+            lk(k_trav_fused, grid, 256, Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
                                                     learned ? nullptr : scount_);
             mark("k_trav_fused");
         }
+    }
+    // Launch of a kernel of the step chain with programmatic dependent launch:
+    // its CTAs may be placed while the kernel ahead of it drains, and wait
+    // in pdl_wait for its completion (captured into the step graph as a
+    // programmatic edge).  HWFV1_NO_PDL gives ordinary launches.
+    template <typename... KArgs, typename... Args>
+    void lk(void (*k)(KArgs...), uint32_t grid, uint32_t block, Args... args) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = stream_;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = pdl_ ? 1 : 0;
+        cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
     }
     void mark(const char* name) {
         if (!prof_) return;
@@ -691,21 +710,21 @@ class EngineT final : public Engine {
             a.leaves = leaves;
             a.fm = 0;            // every leaf on the finest level: nothing to match
         }
-        k_fv1_dry<T><<<grid_for(N_), 256, 0, stream_>>>(a);
+        lk(k_fv1_dry<T>, grid_for(N_), 256, a);
         mark("k_fv1_dry");
         if (a.fm) {
-            k_fv1_match<T><<<wet_grid(), 64, 0, stream_>>>(a);
+            lk(k_fv1_match<T>, wet_grid(), 64, a);
             mark("k_fv1_match");
         } else if (face_) {
             // 64-thread blocks: a short queue spreads over every SM's FP64 units
             // (one warp-wide FP64 instruction holds a sub-partition's unit for
             // tens of cycles, so few warps per unit means a shorter chain)
-            k_fv1_faces<T><<<wet_grid(), 64, 0, stream_>>>(a);
+            lk(k_fv1_faces<T>, wet_grid(), 64, a);
             mark("k_fv1_faces");
-            k_fv1_update<T><<<wet_grid(), 64, 0, stream_>>>(a);
+            lk(k_fv1_update<T>, wet_grid(), 64, a);
             mark("k_fv1_update");
         } else {
-            k_fv1_wet<T><<<wet_grid(), 64, 0, stream_>>>(a);
+            lk(k_fv1_wet<T>, wet_grid(), 64, a);
             mark("k_fv1_wet");
         }
     }
@@ -727,11 +746,11 @@ class EngineT final : public Engine {
         // the decode list is short once quiescent tiles are skipped: 2 CTAs per SM
         const int gd = quiet_on_ ? std::min(grid_for((uint64_t)ntiles_ * 256), nsm_ * 4)
                                  : grid_for((uint64_t)ntiles_ * 256);
-        k_decode_finish<T><<<gd, 256, 0, stream_>>>(decode_args(), fin_args());
+        lk(k_decode_finish<T>, gd, 256, decode_args(), fin_args());
         mark("k_decode_finish");
     }
     void launch_step_uniform() {
-        k_set_uniform<<<1, 32, 0, stream_>>>(st_, (uint32_t)N_);
+        lk(k_set_uniform, 1, 32, st_, (uint32_t)N_);
         launch_fv1(uniform_leaves_);
         launch_decode();
     }
@@ -758,7 +777,7 @@ class EngineT final : public Engine {
             skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
             k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
         }
-        k_flag_learned<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
+        lk(k_flag_learned, grid_for(words_), 256, Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
                                                               close(), st_, &st_->ndec);
         launch_traverse(/*learned=*/true);
         launch_fv1();
@@ -868,6 +887,7 @@ class EngineT final : public Engine {
     uint32_t* scount_ = nullptr;        // per tile: leaves when it holds the bed's flags alone
     uint32_t* work_ = nullptr;          // the traversal's list of tiles to treat one warp each
     bool quiet_on_ = false;
+    bool pdl_ = true;             // programmatic dependent launch in the step chain
     std::vector<std::pair<const char*, cudaEvent_t>>* prof_ = nullptr;   // profile_step's events
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;

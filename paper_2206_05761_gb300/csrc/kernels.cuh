@@ -119,6 +119,20 @@ __device__ __forceinline__ float pow2_scale(float x) {
     else asm volatile("mul.rn.f32 %0, %1, 0f40000000;" : "=f"(r) : "f"(x));
     return r;
 }
+// x * 2^n for 0 <= n <= 30: an exponent step when x and the result are
+// normal numbers, otherwise the IEEE product (the same bits either way).
+__device__ __forceinline__ double mul_pow2(double x, int n) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e >= 1 && e + n <= 0x7FE) return __longlong_as_double(b + ((long long)n << 52));
+    return x * (double)(1u << n);
+}
+__device__ __forceinline__ float mul_pow2(float x, int n) {
+    const int b = __float_as_int(x);
+    const int e = (b >> 23) & 0xFF;
+    if (e >= 1 && e + n <= 0xFE) return __int_as_float(b + (n << 23));
+    return x * (float)(1u << n);
+}
 template <typename T> __device__ __forceinline__ T quarter(T x) { return pow2_scale<-2>(x); }
 template <typename T> __device__ __forceinline__ T half(T x) { return pow2_scale<-1>(x); }
 template <typename T> __device__ __forceinline__ T twice(T x) { return pow2_scale<1>(x); }
@@ -191,15 +205,33 @@ __device__ __forceinline__ bool passes_thr(T m4, T thr, T thr4) {
     return ge_nonneg(T(0.25) * m4, thr);
 }
 
+// A float near a double, by integer instructions alone (a conversion
+// instruction would take the FP64 pipe): the significand truncated to 23
+// bits, so |f - x| <= 2^-23 |x| and |f| <= |x| in the normal float range;
+// +-0 when |x| < 2^-126; an infinity when |x| >= 2^128, or x is not finite.
+__device__ __forceinline__ float trunc_float(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    uint32_t f;
+    if (e <= 0) f = sign;
+    else if (e >= 255) f = sign | 0x7F800000u;
+    else f = sign | ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return __int_as_float((int)f);
+}
+
 // The parent of four doubles and its threshold decision, the details
-// decided in float where that is conclusive.  With c' the children rounded
-// to float, the float m4' of the same sums satisfies
-// |m4' - m4| <= 2^-20 S + 2^-120, S = sum |c'| (three roundings of 2^-24 S
-// each on the float side, two of 2^-53 S on the double side, and 2^-150 per
-// input below the float range, with room to spare).  Compared with directed
-// roundings against thr4 rounded down and up, a decision taken in float is
-// the one the double comparison m4 >= thr4 takes; otherwise (or for values
-// outside the float range) the details are computed in double.
+// decided in float where that is conclusive.  With c' = trunc_float(c) and
+// S = sum |c'|, the float m4' of the same sums satisfies
+// |m4' - m4| <= 2^-20 S + 2^-120: the inputs are off by at most 2^-23 |c|
+// (<= 2^-23 (1 + 2^-22) S in total) or 2^-126 each below the float range,
+// the float sums add two roundings of at most 2^-24 S each, the double side
+// two of 2^-53 S (about 2^-22 S + 2^-124 in all, with room to spare).
+// Compared with directed roundings against thr4 rounded down and up, a
+// decision taken in float is the one the double comparison m4 >= thr4
+// takes; otherwise (or for values outside the float range) the details are
+// computed in double.
 __device__ __forceinline__ bool float_finite(float x) { return (__float_as_int(x) & 0x7F800000) != 0x7F800000; }
 __device__ __forceinline__ void haar4_pre(double c0, double c1, double c2, double c3, double thr, double thr4,
                                           float lo, float hi, double& s, bool& flag) {
@@ -211,7 +243,7 @@ __device__ __forceinline__ void haar4_pre(double c0, double c1, double c2, doubl
     const double a = c0 + c2, b = c1 + c3;
     s = quarter(a + b);
     if (lo >= 0.0f) {
-        const float f0 = (float)c0, f1 = (float)c1, f2 = (float)c2, f3 = (float)c3;
+        const float f0 = trunc_float(c0), f1 = trunc_float(c1), f2 = trunc_float(c2), f3 = trunc_float(c3);
         const float af = f0 + f2, bf = f1 + f3, df = f0 - f2, ef = f1 - f3;
         const float m = fmaxf(fmaxf(fabsf(df + ef), fabsf(af - bf)), fabsf(df - ef));
         const float S = __fadd_ru(__fadd_ru(fabsf(f0), fabsf(f1)), __fadd_ru(fabsf(f2), fabsf(f3)));
@@ -416,6 +448,7 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
 
 template <typename T, int NF>
 static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
+    pdl_wait();
     encode_body<T, NF>(a, a.ls, a.k, blockIdx.x);
 }
 
@@ -425,6 +458,7 @@ static __global__ void __launch_bounds__(256) k_encode(EncodeArgs<T, NF> a) {
 template <typename T, int NF>
 static __global__ void __launch_bounds__(256) k_encode_tail(EncodeArgs<T, NF> a, int ls2, int k2,
                                                             uint32_t* ticket) {
+    pdl_wait();
     encode_body<T, NF>(a, a.ls, a.k, blockIdx.x);
     __threadfence();                     // this CTA's coefficients and bits are visible
     __syncthreads();
@@ -442,6 +476,7 @@ static __global__ void __launch_bounds__(256) k_encode_tail(EncodeArgs<T, NF> a,
 // per thread) and encodes only the unmarked ones.
 template <typename T, int NF>
 static __global__ void __launch_bounds__(256) k_encode_tiles(EncodeArgs<T, NF> a, uint32_t ntiles) {
+    pdl_wait();
     if (a.st && !a.st->active) return;
     __shared__ uint32_t todo[256];
     __shared__ uint32_t ntodo;
@@ -468,6 +503,7 @@ __device__ __forceinline__ void clear_body(uint32_t* w, uint32_t nwords, const D
     for (uint32_t i = B.id * blockDim.x + threadIdx.x; i < nwords; i += B.n * blockDim.x) w[i] = 0u;
 }
 static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, const DevState* st) {
+    pdl_wait();
     clear_body(w, nwords, st, this_blk());
 }
 
@@ -513,6 +549,7 @@ __device__ __forceinline__ void flag_body(const uint32_t* __restrict__ Tb, const
 static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
                               const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb, int L,
                               int predict, int close, const DevState* st, uint32_t* zero4 = nullptr) {
+    pdl_wait();
     if (zero4 && blockIdx.x == 0 && threadIdx.x < 4u) zero4[threadIdx.x] = 0u;
     flag_body(Tb, Cb, Sbase, Sb, L, predict, close, st, this_blk());
 }
@@ -994,6 +1031,7 @@ static __global__ void __launch_bounds__(256) k_trav_fused(const uint32_t* __res
                                                            uint32_t* __restrict__ leaves, int L, int kt,
                                                            uint32_t ntiles, DevState* st, Quiet q,
                                                            const uint32_t* scount) {
+    pdl_wait();
     trav_fused_body(Sb, dlist, leaves, L, kt, ntiles, st, q, scount);
 }
 
@@ -1006,6 +1044,7 @@ static __global__ void __launch_bounds__(256) k_trav_fused(const uint32_t* __res
 static __global__ void __launch_bounds__(256) k_trav_classify(const uint32_t* __restrict__ Sb, int L, int kt,
                                                               uint32_t ntiles, DevState* st, Quiet q,
                                                               const uint32_t* scount, uint32_t* work) {
+    pdl_wait();
     if (!st->active) return;
     const int Lr = L - kt;
     const uint32_t cur = st->cur;
@@ -1061,6 +1100,7 @@ static __global__ void __launch_bounds__(256) k_trav_list(const uint32_t* __rest
                                                           uint32_t* __restrict__ dlist,
                                                           uint32_t* __restrict__ leaves, int L, int kt,
                                                           DevState* st, const uint32_t* __restrict__ work) {
+    pdl_wait();
     if (!st->active) return;
     __shared__ TileBits tb;
     __shared__ uint32_t sbase;
@@ -1466,6 +1506,7 @@ __device__ __forceinline__ void fv1_dry_body(const StepArgs<T>& a, Blk B) {
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_dry(StepArgs<T> a) {
+    pdl_wait();
     fv1_dry_body<T>(a, this_blk());
 }
 
@@ -1578,12 +1619,12 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
         const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
         const Cell<T> S = j > 0 ? fetch(src, base + morton2(i, j - 1)) : ghost(C, a.bc_ref[2], false);
         const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
-        const T scale = (T)(1u << n);
-        const T rx = rx0 * scale, ry = ry0 * scale;
+        const T rx = mul_pow2(rx0, n), ry = mul_pow2(ry0, n);   // rx0 * 2^n, exact
         int64_t lo = 0, hi = 0;
         const bool inlet = inlet_range(a, n, i, j, last, lo, hi);
         T dh = T(0);
         if (inlet) {
+            const T scale = (T)(1u << n);
             const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
             const T inv2n = T(1) / scale;
             const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
@@ -1599,6 +1640,7 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_wet(StepArgs<T> a) {
+    pdl_wait();
     fv1_wet_body<T>(a, this_blk());
 }
 
@@ -1746,12 +1788,12 @@ __device__ __forceinline__ void fv1_match_body(const StepArgs<T>& a, Blk B) {
         leaf_face(a, src, 1, n, i, j, last, C, FE, e2);
         leaf_face(a, src, 2, n, i, j, last, C, GS, s2);
         leaf_face(a, src, 3, n, i, j, last, C, GN, n2);
-        const T scale = (T)(1u << n);
-        const T rx = rx0 * scale, ry = ry0 * scale;
+        const T rx = mul_pow2(rx0, n), ry = mul_pow2(ry0, n);   // rx0 * 2^n, exact
         int64_t lo = 0, hi = 0;
         const bool inlet = inlet_range(a, n, i, j, last, lo, hi);
         T dh = T(0);
         if (inlet) {
+            const T scale = (T)(1u << n);
             const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
             const T inv2n = T(1) / scale;
             const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
@@ -1767,6 +1809,7 @@ __device__ __forceinline__ void fv1_match_body(const StepArgs<T>& a, Blk B) {
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_match(StepArgs<T> a) {
+    pdl_wait();
     fv1_match_body<T>(a, this_blk());
 }
 
@@ -1825,6 +1868,7 @@ __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_faces(StepArgs<T> a) {
+    pdl_wait();
     fv1_faces_body<T>(a, this_blk());
 }
 
@@ -1912,12 +1956,12 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
                 hll_face(g, hg, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
             }
         }
-        const T scale = (T)(1u << n);
-        const T rx = rx0 * scale, ry = ry0 * scale;
+        const T rx = mul_pow2(rx0, n), ry = mul_pow2(ry0, n);   // rx0 * 2^n, exact
         int64_t lo = 0, hi = 0;
         const bool inlet = inlet_range(a, n, i, j, last, lo, hi);
         T dh = T(0);
         if (inlet) {
+            const T scale = (T)(1u << n);
             const T frac = (T)(hi - lo) / (T)(a.a1 - a.a0);
             const T inv2n = T(1) / scale;
             const T dxn = a.lx * inv2n, dyn = a.ly * inv2n;
@@ -1933,6 +1977,7 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
 }
 template <typename T>
 static __global__ void __launch_bounds__(256) k_fv1_update(StepArgs<T> a) {
+    pdl_wait();
     fv1_update_body<T>(a, this_blk());
 }
 
@@ -1943,6 +1988,7 @@ static __global__ void k_fill_finest_leaves(uint32_t* leaves, int L, uint64_t N)
 }
 // ... and the step's list counts (no tile is skipped, none needs decoding).
 static __global__ void k_set_uniform(DevState* st, uint32_t N) {
+    pdl_wait();
     if (threadIdx.x != 0 || !st->active) return;
     st->M = N;
     st->Mall = N;
@@ -2155,6 +2201,7 @@ static __global__ void k_finish(DevState* st, FinishArgs a) {
 // the last CTA sees every other CTA's reductions after the fence.
 template <typename T>
 static __global__ void __launch_bounds__(256) k_decode_finish(DecodeArgs<T> a, FinishArgs fa) {
+    pdl_wait();
     decode_body<T>(a, this_blk());
     __threadfence();
     __syncthreads();
@@ -2417,6 +2464,7 @@ static __global__ void k_flag_learned(const uint32_t* __restrict__ Tb, const uin
                                       const uint32_t* __restrict__ Tz, const uint32_t* __restrict__ Cz,
                                       uint32_t* __restrict__ Sb, const uint8_t* __restrict__ phat, int L, int Ls,
                                       int predict, int close, const DevState* st, uint32_t* zero4 = nullptr) {
+    pdl_wait();
     if (zero4 && blockIdx.x == 0 && threadIdx.x < 4u) zero4[threadIdx.x] = 0u;   // as k_flag
     if (st && !st->active) return;
     const uint32_t total = bits_words(L);

@@ -143,6 +143,39 @@ def test_regularisation_variants(predict, close):
     one_step_parity(p, f, pre_steps=2)
 
 
+def test_threshold_edges_decided_like_the_oracle():
+    # 2 x 2 blocks whose largest detail sits within a relative r of the
+    # level-(L-1) threshold (r from 1e-15 to 1e-3, both signs, both detail
+    # directions, several magnitudes): the float pre-check of the encode may
+    # decide only where its error bound allows, so every flag must equal the
+    # oracle's double decision
+    L = 6
+    p, f = synth.circular_dam_break(L=L, eps=1e-3)
+    p["bc"] = ("closed",) * 4
+    thr = p["eps"] * 0.5                                  # s_max = 1 (all h <= 1)
+    rs = [s * m for m in (1e-15, 1e-13, 1e-11, 1e-9, 1e-8, 1e-7, 3e-7, 1e-6, 1e-5, 1e-3) for s in (1, -1)]
+    xs = [1e-3, 0.01, 0.05, 0.3, 0.9]
+    h = np.zeros((1 << L, 1 << L))
+    k = 0
+    for pj in range(1 << (L - 1)):
+        for pi in range(1 << (L - 1)):
+            r = rs[k % len(rs)]
+            x = xs[(k // len(rs)) % len(xs)]
+            d = 2.0 * thr * (1.0 + r)
+            if (k // (len(rs) * len(xs))) % 2 == 0:       # detail beta: columns differ
+                blk = [[x, x + d], [x, x + d]]
+            else:                                         # detail alpha: rows differ
+                blk = [[x, x], [x + d, x + d]]
+            h[2 * pj: 2 * pj + 2, 2 * pi: 2 * pi + 2] = blk
+            k += 1
+    assert h.max() <= 1.0
+    f = dict(f, h=np.ascontiguousarray(h), qx=np.zeros_like(h), qy=np.zeros_like(h),
+             z=np.zeros_like(h))
+    res = one_step_parity(p, f)
+    T = res["T"][level_slice(L - 1)]
+    assert 0 < T.sum() < T.size                           # both decisions occur
+
+
 def test_all_dry_terrain():
     p, f = synth.terrain_flood(L=7)
     p["bc"] = ("closed",) * 4
