@@ -48,6 +48,7 @@ class EngineT final : public Engine {
     }
     ~EngineT() override {
         if (exec_) cudaGraphExecDestroy(exec_);
+        if (exec_multi_) cudaGraphExecDestroy(exec_multi_);
         if (exec_learned_) cudaGraphExecDestroy(exec_learned_);
         if (exec_reuse_) cudaGraphExecDestroy(exec_reuse_);
         if (exec_uniform_) cudaGraphExecDestroy(exec_uniform_);
@@ -202,7 +203,17 @@ class EngineT final : public Engine {
             return HWFV1_ERR_CUDA;
         if (use_graph && skip_ && every_ > 1 && !exec_reuse_ && capture(&exec_reuse_, kStepReuse) != HWFV1_OK)
             return HWFV1_ERR_CUDA;
-        for (int64_t s = 0; s < max_steps; ++s) {
+        int64_t s = 0;
+        if (use_graph && !skip_ && max_steps >= kMultiSteps) {
+            // kMultiSteps plain steps per graph launch: the kernels of
+            // consecutive steps follow each other as inside one step, without
+            // the gap between two graph launches.  A step after t_end does
+            // nothing, as with single-step launches.
+            if (!exec_multi_ && capture(&exec_multi_, kStepPlain, kMultiSteps) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            for (; s + kMultiSteps <= max_steps; s += kMultiSteps)
+                if (cudaGraphLaunch(exec_multi_, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
+        }
+        for (; s < max_steps; ++s) {
             // with the learned look-ahead every audit_K-th step is an exact
             // (plain) step; of the learned steps after it, every every_-th
             // runs the network and the others reuse its predicted levels
@@ -424,6 +435,9 @@ class EngineT final : public Engine {
     hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* au, int64_t* wu, int64_t* kps) override {
         if (kps) {
             if (!exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (!exec_multi_ && !skip_ && std::getenv("HWFV1_NO_GRAPH") == nullptr &&
+                capture(&exec_multi_, kStepPlain, kMultiSteps) != HWFV1_OK)
+                return HWFV1_ERR_CUDA;
             *kps = skip_ ? kernels_learned_ : kernels_plain_;
         }
         DevState s;
@@ -788,13 +802,14 @@ class EngineT final : public Engine {
         if (kind == kStepPlain) launch_step_all();
         else launch_step_learned(kind == kStepLearned);
     }
-    hwfv1_status capture(cudaGraphExec_t* out, int kind) {
+    static constexpr int kMultiSteps = 16;   // plain steps per graph in hwfv1_advance
+    hwfv1_status capture(cudaGraphExec_t* out, int kind, int nsteps = 1) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(HWFV1_ERR_CUDA, "graph capture begin");
-        launch_step(kind);
+        for (int k = 0; k < nsteps; ++k) launch_step(kind);
         if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph capture end");
-        const int64_t nk = count_kernel_nodes(g);
+        const int64_t nk = count_kernel_nodes(g) / nsteps;
         if (kind == kStepPlain) kernels_plain_ = nk;
         else if (kind == kStepLearned) kernels_learned_ = nk;
         const cudaError_t e = cudaGraphInstantiate(out, g, 0);
@@ -893,6 +908,7 @@ class EngineT final : public Engine {
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
+    cudaGraphExec_t exec_multi_ = nullptr;   // kMultiSteps plain steps
     // learned look-ahead
     SkipNet* skip_ = nullptr;
     int audit_K_ = 10;

@@ -211,6 +211,25 @@ def test_trajectory_circular_dam_break_100_steps():
     sim.close()
 
 
+def test_trajectory_in_multi_step_graphs():
+    # advances of 37 steps: two 16-step graph launches and five single-step
+    # ones each, against the oracle's loop
+    p, f = synth.circular_dam_break(L=6, eps=1e-3)
+    p["bc"] = ("closed",) * 4
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    for chunk in range(3):
+        sim.advance(max_steps=37)
+        for _ in range(36):
+            ref.step()
+        res = ref.step(want=("leaves",))
+        assert np.array_equal(sim.leaves(), res["leaves"]), "chunk %d" % chunk
+        _compare_fields(sim, ref)
+        t, dt, steps = sim.time()
+        assert t == ref.t and dt == ref.dt and steps == ref.steps
+    sim.close()
+
+
 def test_counters_sum_the_leaf_updates():
     # the running leaf-update count equals the oracle's sum of M over the
     # same steps; the captured step graph launches a positive, fixed number
