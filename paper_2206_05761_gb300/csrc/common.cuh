@@ -243,6 +243,8 @@ struct DevState {
     uint32_t epoch;                   // completed steps (never reset; tags the face stamps)
     uint32_t enc_ticket;              // finished CTAs of the fused last encode passes
     uint32_t dec_ticket;              // finished CTAs of the fused decode + finish
+    uint32_t ntodo;                   // tiles the first encode pass works on (listed by the
+                                      // clear kernel, reset by the encode's last CTA)
 };
 
 enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };

@@ -573,22 +573,25 @@ class EngineT final : public Engine {
                             kZThr4F = kZThr4D + 8 * kMaxL, kZauxBytes = 512;
 
     // Passes of up to five levels from L down to 0.  With `ticket`, the
-    // final one-CTA pass runs in the last CTA of the pass before it.
+    // final one-CTA pass runs in the last CTA of the pass before it.  With
+    // a.list, the first pass works on the listed tiles (k_encode_tiles).
     template <int NF>
     void encode_passes(EncodeArgs<T, NF> a, uint32_t* ticket = nullptr) {
         int ls = L_;
+        bool list_reset = a.list == nullptr;
         while (ls > 0) {
             const int k = ls < 5 ? ls : 5;
             a.ls = ls;
             a.k = k;
             const uint32_t nb = 1u << (2 * (ls - k));
             const int ls2 = ls - k, k2 = ls2 < 5 ? ls2 : 5;
-            if (ls == L_ && a.zf[0] != nullptr && nb > (uint32_t)nsm_ * 8u) {
-                lk(k_encode_tiles<T, NF>, nsm_ * 8, 256, a, nb);
+            if (ls == L_ && a.list != nullptr) {
+                lk(k_encode_tiles<T, NF>, nsm_ * 8, 256, a);
                 mark("k_encode_tiles");
             } else if (ticket && ls2 > 0 && ls2 == k2) {      // next pass is the last (one CTA)
                 lk(k_encode_tail<T, NF>, nb, 256, a, ls2, k2, ticket);
                 mark("k_encode_tail");
+                list_reset = true;                         // its last CTA resets the list
                 break;                                     // levels ls2-1 .. 0 done too
             } else {
                 lk(k_encode<T, NF>, nb, 256, a);
@@ -596,12 +599,20 @@ class EngineT final : public Engine {
             }
             ls -= k;
         }
+        if (!list_reset) cudaMemsetAsync(&st_->ntodo, 0, sizeof(uint32_t), stream_);
     }
 
+    // the first encode pass takes a tile list when quiescent tiles are
+    // skipped and there are more tiles than a grid of 8 CTAs per SM
+    bool tile_list() const { return quiet_on_ && ntiles_ > (uint32_t)nsm_ * 8u && L_ - kt_ > 0; }
+
     void launch_encode() {
-        lk(k_clear_words, grid_for(2 * (uint64_t)words_), 256, Tb_, 2 * words_, st_);
+        uint32_t* list = tile_list() ? work_ : nullptr;
+        lk(k_clear_words, grid_for(2 * (uint64_t)words_), 256, Tb_, 2 * words_, st_,
+           (const uint8_t*)tilebytes_, (const uint8_t*)(tilebytes_ + ntiles_), ntiles_, list);
         mark("k_clear_words");
         EncodeArgs<T, 3> a;
+        a.list = list;
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.thr = thr_dyn();

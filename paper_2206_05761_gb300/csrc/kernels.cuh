@@ -292,6 +292,8 @@ struct EncodeArgs {
     // zf[b][t] = 1 when every value of buffer b in tile t, levels ls-k..ls,
     // is +0.  NULL: no skipping.
     uint8_t* zf[2] = {nullptr, nullptr};
+    // the first pass's tiles (k_encode_tiles): list[0 .. st->ntodo)
+    const uint32_t* list = nullptr;
 };
 
 // The thresholds of one level and quantity (thr, 4 thr, and 4 thr's float
@@ -319,6 +321,79 @@ __device__ __forceinline__ void parent_coef(const Thr<T>& h, T c0, T c1, T c2, T
     T dm;
     haar4<T>(c0, c1, c2, c3, s, dm);
     tf = tf || passes_thr(dm, h.thr, h.thr4);
+}
+
+// The parents of all NF quantities of one cell and its threshold flag.  In
+// float64 the sums of every quantity come first (independent of one
+// another, so the FP64 pipe takes them back to back instead of one
+// quantity's chain after the other's), then the threshold decisions in
+// quantity order, with the float pre-check of haar4_pre and the same
+// shortcut: once a quantity has flagged the parent the others need their
+// parent only.  Every value is formed by the same operations as in
+// haar4_pre.
+template <typename T, int NF>
+__device__ __forceinline__ void parents_all(const Thr<T>* th, const T (&c)[NF][4], T (&s)[NF], bool& tf) {
+    if constexpr (sizeof(T) == 8) {
+        bool eq[NF];
+        T sa[NF], sb[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            eq[q] = same4<T>(c[q][0], c[q][1], c[q][2], c[q][3]);
+            sa[q] = T(0);
+            sb[q] = T(0);
+            if (!eq[q]) {
+                sa[q] = c[q][0] + c[q][2];
+                sb[q] = c[q][1] + c[q][3];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NF; ++q) s[q] = eq[q] ? c[q][0] : quarter(sa[q] + sb[q]);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            if (tf) break;
+            const Thr<T>& h = th[q];
+            if (eq[q]) {
+                tf = passes_thr(T(0), h.thr, h.thr4);
+                continue;
+            }
+            const T c0 = c[q][0], c1 = c[q][1], c2 = c[q][2], c3 = c[q][3];
+            bool decided = false;
+            if (h.lo >= 0.0f) {
+                const float f0 = trunc_float(c0), f1 = trunc_float(c1), f2 = trunc_float(c2), f3 = trunc_float(c3);
+                const float af = f0 + f2, bf = f1 + f3, df = f0 - f2, ef = f1 - f3;
+                const float m = fmaxf(fmaxf(fabsf(df + ef), fabsf(af - bf)), fabsf(df - ef));
+                const float S = __fadd_ru(__fadd_ru(fabsf(f0), fabsf(f1)), __fadd_ru(fabsf(f2), fabsf(f3)));
+                const float E = __fadd_ru(__fmul_ru(S, 0x1p-20f), 0x1p-120f);
+                if (float_finite(m) && float_finite(E)) {
+                    if (__fsub_rd(m, E) >= h.hi) {
+                        tf = true;
+                        decided = true;
+                    } else if (__fadd_ru(m, E) < h.lo) {
+                        decided = true;
+                    }
+                }
+            }
+            if (!decided) {
+                const T d = c0 - c2, e = c1 - c3;
+                const T m4 = sel_max(sel_max(absval(d + e), absval(sa[q] - sb[q])), absval(d - e));
+                tf = passes_thr(m4, h.thr, h.thr4);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) parent_coef(th[q], c[q][0], c[q][1], c[q][2], c[q][3], s[q], tf);
+    }
+}
+
+// Hierarchy of quantity q in the current state buffer (selects, so that the
+// parameter array is not indexed at run time).
+template <typename T, int NF>
+__device__ __forceinline__ T* quantity_ptr(const EncodeArgs<T, NF>& a, int par, uint32_t q) {
+    T* r = par ? a.f[1][0] : a.f[0][0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k)
+        if (q == (uint32_t)k) r = par ? a.f[1][k] : a.f[0][k];
+    return r;
 }
 
 // the value is +0 (all bits clear)
@@ -385,10 +460,9 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
         __syncthreads();
         if (act) {
 #pragma unroll
-            for (int q = 0; q < NF; ++q) {
+            for (int q = 0; q < NF; ++q)
                 nz = nz || !(pos_zero(c[q][0]) && pos_zero(c[q][1]) && pos_zero(c[q][2]) && pos_zero(c[q][3]));
-                parent_coef(sthr[0][q], c[q][0], c[q][1], c[q][2], c[q][3], s[q], tf);
-            }
+            parents_all<T, NF>(sthr[0], c, s, tf);
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
                 T* fq = par ? a.f[1][q] : a.f[0][q];
@@ -406,42 +480,38 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
             if (tid == 0) zfp[tile] = any ? 0 : 1;
         }
     }
+    // Levels of at most 64 parents: one thread per (quantity, parent), so
+    // that the quantities' FP64 work, which costs a full warp instruction
+    // however few lanes are active, runs in different warps side by side.
+    __shared__ uint8_t sflag[NF][64];
     for (int j = 2; j <= kk; ++j) {
         __syncthreads();
         n = ls - j;
         cnt >>= 2;
         const int rbuf = (j - 2) & 1, wbuf = (j - 1) & 1;   // level j-1 wrote buffer (j-2)&1
+        if (tid < NF * cnt) {
+            const uint32_t q = tid / cnt, pp = tid - q * cnt;
+            const T* r = rbuf ? sv1[q] : sv0[q];
+            const T c0 = r[4 * pp], c1 = r[4 * pp + 1], c2 = r[4 * pp + 2], c3 = r[4 * pp + 3];
+            T s = T(0);
+            bool f = false;
+            parent_coef(sthr[j - 1][q], c0, c1, c2, c3, s, f);
+            quantity_ptr(a, par, q)[lvl_off(n) + tile * cnt + pp] = s;
+            (wbuf ? sv1[q] : sv0[q])[pp] = s;              // the level read next (other buffer)
+            sflag[q][pp] = f ? 1 : 0;
+        }
+        __syncthreads();
         const bool act = tid < cnt;
-        const uint32_t p = tile * cnt + tid;
         bool tf = false;
         uint32_t cchild = 0;
-        T s[NF];
-#pragma unroll
-        for (int q = 0; q < NF; ++q) s[q] = T(0);
         if (act) {
-            T c[NF][4];
 #pragma unroll
-            for (int q = 0; q < NF; ++q) {
-                const T* r = rbuf ? sv1[q] : sv0[q];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) c[q][k] = r[4 * tid + k];
-            }
+            for (int q = 0; q < NF; ++q) tf = tf || sflag[q][tid] != 0;
             cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
-#pragma unroll
-            for (int q = 0; q < NF; ++q) parent_coef(sthr[j - 1][q], c[q][0], c[q][1], c[q][2], c[q][3], s[q], tf);
-#pragma unroll
-            for (int q = 0; q < NF; ++q) {
-                T* fq = par ? a.f[1][q] : a.f[0][q];
-                fq[lvl_off(n) + p] = s[q];
-            }
         }
         const bool cf = act && (tf || cchild);
         put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
         const uint32_t cball = put_bits(a.Cb, n, tile * cnt, cnt, cf);
-        if (tid < cnt) {
-#pragma unroll
-            for (int q = 0; q < NF; ++q) (wbuf ? sv1[q] : sv0[q])[tid] = s[q];
-        }
         if (lane == 0) sc[wbuf][warp] = cball;
     }
 }
@@ -467,44 +537,55 @@ static __global__ void __launch_bounds__(256) k_encode_tail(EncodeArgs<T, NF> a,
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x == 0) *ticket = 0u;
+    if (threadIdx.x == 0) {
+        *ticket = 0u;
+        // the tile list of the pass before (k_encode_tiles, done) starts
+        // empty next step
+        if (a.list) const_cast<DevState*>(a.st)->ntodo = 0u;
+    }
     encode_body<T, NF, true>(a, ls2, k2, 0u);
 }
 
-// The same pass with a fixed grid striding over the tiles when quiescent
-// tiles are skipped: the CTA reads the marks of all its tiles at once (one
-// per thread) and encodes only the unmarked ones.
+// The same pass with a fixed grid when quiescent tiles are skipped: the
+// tiles that are not marked quiescent were listed by k_clear_words, and CTA
+// b encodes list entries b, b + grid, ...: a step's active tiles, which
+// cluster where the water is, spread one per CTA.
 template <typename T, int NF>
-static __global__ void __launch_bounds__(256) k_encode_tiles(EncodeArgs<T, NF> a, uint32_t ntiles) {
+static __global__ void __launch_bounds__(256) k_encode_tiles(EncodeArgs<T, NF> a) {
     pdl_wait();
-    if (a.st && !a.st->active) return;
-    __shared__ uint32_t todo[256];
-    __shared__ uint32_t ntodo;
-    const int par = a.st ? (int)a.st->cur : 0;
-    const uint8_t* zf = par ? a.zf[1] : a.zf[0];
-    for (uint32_t t0 = blockIdx.x; t0 < ntiles; t0 += 256u * gridDim.x) {
-        if (threadIdx.x == 0) ntodo = 0u;
-        __syncthreads();
-        const uint32_t t = t0 + threadIdx.x * gridDim.x;
-        if (t < ntiles && !zf[t]) todo[atomicAdd(&ntodo, 1u)] = t;
-        __syncthreads();
-        const uint32_t n = ntodo;
-        __syncthreads();                 // every thread has read ntodo before it is reset
-        for (uint32_t i = 0; i < n; ++i) {
-            encode_body<T, NF>(a, a.ls, a.k, todo[i]);
-            __syncthreads();             // shared memory is reused by the next tile
-        }
+    if (!a.st->active) return;
+    const uint32_t n = *(volatile const uint32_t*)&a.st->ntodo;
+    for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
+        encode_body<T, NF>(a, a.ls, a.k, __ldg(a.list + e));
+        __syncthreads();                 // shared memory is reused by the next tile
     }
 }
 
-// Clear bit arrays before an encode (the partial words are OR-ed into).
+// Clear bit arrays before an encode (the partial words are OR-ed into),
+// and with `list`, list the tiles of the current state buffer that are not
+// marked quiescent (st->ntodo counts them; it is 0 on entry).
 __device__ __forceinline__ void clear_body(uint32_t* w, uint32_t nwords, const DevState* st, Blk B) {
     if (st && !st->active) return;
     for (uint32_t i = B.id * blockDim.x + threadIdx.x; i < nwords; i += B.n * blockDim.x) w[i] = 0u;
 }
-static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, const DevState* st) {
+static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, DevState* st, const uint8_t* zf0,
+                                     const uint8_t* zf1, uint32_t ntiles, uint32_t* list) {
     pdl_wait();
     clear_body(w, nwords, st, this_blk());
+    if (!list || !st->active) return;
+    const uint8_t* zf = st->cur ? zf1 : zf0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < ntiles; t0 += stride) {   // whole warps
+        const uint32_t t = t0 + threadIdx.x;
+        const bool todo = t < ntiles && !zf[t];
+        const uint32_t m = __ballot_sync(0xffffffffu, todo);
+        if (m == 0u) continue;
+        uint32_t base = 0u;
+        if (lane == 0) base = atomicAdd(&st->ntodo, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (todo) list[base + __popc(m & ((1u << lane) - 1u))] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
