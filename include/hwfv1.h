@@ -204,12 +204,13 @@ hwfv1_status hwfv1_set_time(hwfv1_handle* hd, double t, double dt);
  * number of leaves and the maxima of |h|, |hu|, |hv| used for s_max. */
 hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax3);
 
-/* One step (encode .. time advance, the plain step of hwfv1_advance)
- * launched kernel by kernel with a CUDA event recorded on the handle's
- * stream after every launch.  Writes the duration in ms of each launch
- * (from the previous event) to ms[0..cap) and its kernel name (static
+/* One step (encode .. time advance, the plain step of hwfv1_advance) with
+ * a CUDA event recorded after every kernel: the step is captured as a graph
+ * whose kernels are separated by event-record nodes (HWFV1_NO_GRAPH set:
+ * ordinary launches on the handle's stream).  Writes the duration in ms of
+ * each kernel (from the previous event) to ms[0..cap) and its name (static
  * strings owned by the library) to names[0..cap); either may be NULL;
- * *n = number of launches.  Advances the simulation by one step and
+ * *n = number of kernels.  Advances the simulation by one step and
  * synchronises.  No counterpart in the paper: diagnostics. */
 hwfv1_status hwfv1_profile_step(hwfv1_handle* hd, float* ms, const char** names, int32_t cap, int32_t* n);
 

@@ -405,15 +405,44 @@ class EngineT final : public Engine {
 
     // One plain step launched kernel by kernel with an event after every
     // launch; durations in launch order.
+    // One plain step with a CUDA event after every kernel.  The step is
+    // captured as a graph whose kernels are separated by event-record nodes
+    // (so the times are those of kernels in a graph, without the launch
+    // latency of separate stream launches); HWFV1_NO_GRAPH records the
+    // events between ordinary launches.
     hwfv1_status profile_step(float* ms, const char** names, int32_t cap, int32_t* n) override {
         std::vector<std::pair<const char*, cudaEvent_t>> ev;
         cudaEvent_t e0;
         if (cudaEventCreate(&e0) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "event");
-        cudaEventRecord(e0, stream_);
-        prof_ = &ev;
-        launch_step_all();
-        prof_ = nullptr;
-        hwfv1_status r = check("profile_step", true);
+        const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
+        hwfv1_status r = HWFV1_OK;
+        if (use_graph) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t x = nullptr;
+            if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                return fail(HWFV1_ERR_CUDA, "graph capture begin");
+            }
+            cudaEventRecordWithFlags(e0, stream_, cudaEventRecordExternal);
+            prof_ = &ev;
+            prof_external_ = true;
+            launch_step_all();
+            prof_ = nullptr;
+            prof_external_ = false;
+            if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "graph capture end");
+            if (r == HWFV1_OK && cudaGraphInstantiate(&x, g, 0) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "graph instantiate");
+            if (r == HWFV1_OK && cudaGraphLaunch(x, stream_) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "graph launch");
+            if (r == HWFV1_OK) r = check("profile_step", true);
+            else cudaStreamSynchronize(stream_);
+            if (x) cudaGraphExecDestroy(x);
+            if (g) cudaGraphDestroy(g);
+        } else {
+            cudaEventRecord(e0, stream_);
+            prof_ = &ev;
+            launch_step_all();
+            prof_ = nullptr;
+            r = check("profile_step", true);
+        }
         int32_t k = 0;
         cudaEvent_t prev = e0;
         for (auto& p : ev) {
@@ -676,7 +705,8 @@ class EngineT final : public Engine {
         if (!prof_) return;
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
-        cudaEventRecord(e, stream_);
+        if (prof_external_) cudaEventRecordWithFlags(e, stream_, cudaEventRecordExternal);
+        else cudaEventRecord(e, stream_);
         prof_->push_back({name, e});
     }
     Quiet quiet() const {
@@ -915,6 +945,7 @@ class EngineT final : public Engine {
     bool quiet_on_ = false;
     bool pdl_ = true;             // programmatic dependent launch in the step chain
     std::vector<std::pair<const char*, cudaEvent_t>>* prof_ = nullptr;   // profile_step's events
+    bool prof_external_ = false;          // events recorded as graph nodes (under capture)
     DevState* st_ = nullptr;
     char* zaux_ = nullptr;
     double *it_d_ = nullptr, *iq_d_ = nullptr;

@@ -483,7 +483,8 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
     // Levels of at most 64 parents: one thread per (quantity, parent), so
     // that the quantities' FP64 work, which costs a full warp instruction
     // however few lanes are active, runs in different warps side by side.
-    __shared__ uint8_t sflag[NF][64];
+    // The quantities' flags of a parent are the bytes of one word.
+    __shared__ uint32_t sflag[64];
     for (int j = 2; j <= kk; ++j) {
         __syncthreads();
         n = ls - j;
@@ -498,15 +499,14 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
             parent_coef(sthr[j - 1][q], c0, c1, c2, c3, s, f);
             quantity_ptr(a, par, q)[lvl_off(n) + tile * cnt + pp] = s;
             (wbuf ? sv1[q] : sv0[q])[pp] = s;              // the level read next (other buffer)
-            sflag[q][pp] = f ? 1 : 0;
+            reinterpret_cast<uint8_t*>(sflag)[4 * pp + q] = f ? 1 : 0;
         }
         __syncthreads();
         const bool act = tid < cnt;
         bool tf = false;
         uint32_t cchild = 0;
         if (act) {
-#pragma unroll
-            for (int q = 0; q < NF; ++q) tf = tf || sflag[q][tid] != 0;
+            tf = (sflag[tid] & (0xFFFFFFFFu >> (32 - 8 * NF))) != 0u;   // bytes 0 .. NF-1
             cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
         }
         const bool cf = act && (tf || cchild);
