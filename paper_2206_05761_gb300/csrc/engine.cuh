@@ -172,6 +172,7 @@ class EngineT final : public Engine {
     }
     hwfv1_status flag() override {
         launch_flag();
+        sb_valid_ = true;
         return check("flag");
     }
     hwfv1_status traverse(int64_t* num_leaves) override {
@@ -213,11 +214,12 @@ class EngineT final : public Engine {
             for (; s + kMultiSteps <= max_steps; s += kMultiSteps)
                 if (cudaGraphLaunch(exec_multi_, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
         }
+        int kind = kStepPlain;
         for (; s < max_steps; ++s) {
             // with the learned look-ahead every audit_K-th step is an exact
             // (plain) step; of the learned steps after it, every every_-th
             // runs the network and the others reuse its predicted levels
-            int kind = kStepPlain;
+            kind = kStepPlain;
             if (skip_) {
                 const int64_t pos = lstep_++ % audit_K_;
                 if (pos != 0) kind = ((pos - 1) % every_) == 0 ? kStepLearned : kStepReuse;
@@ -229,6 +231,8 @@ class EngineT final : public Engine {
                 launch_step(kind);
             }
         }
+        // a plain last step formed S on the spot: Sb_ is materialised on demand
+        sb_valid_ = kind != kStepPlain || !onfly_flags();
         return check("advance");
     }
 
@@ -350,6 +354,7 @@ class EngineT final : public Engine {
                 cudaGetLastError();
                 return oom();
             }
+            ensure_sig_words();
             k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, cnt, nullptr, L_, kt_, ntiles_, st_, nullptr, Quiet());
             k_trav_scan<<<1, 1024, 0, stream_>>>(cnt, cnt + nct, nct, st_, cnt + 2 * nct);
             k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, cnt + nct, out, L_, kt_, ntiles_, st_, nullptr);
@@ -361,6 +366,7 @@ class EngineT final : public Engine {
 
     hwfv1_status get_flags(int which, uint32_t* out, int64_t cap_words) override {
         if (cap_words < (int64_t)words_) return fail(HWFV1_ERR_INVALID_SPEC, "get_flags: cap too small");
+        if (which == 1) ensure_sig_words();
         if (which == 0)
             k_or_words<<<grid_for(words_), 256, 0, stream_>>>(Tb_, Tz_, out, words_);
         else if (which == 1)
@@ -638,7 +644,7 @@ class EngineT final : public Engine {
     void launch_encode() {
         uint32_t* list = tile_list() ? work_ : nullptr;
         lk(k_clear_words, grid_for(2 * (uint64_t)words_), 256, Tb_, 2 * words_, st_,
-           (const uint8_t*)tilebytes_, (const uint8_t*)(tilebytes_ + ntiles_), ntiles_, list);
+           (const uint8_t*)tilebytes_, (const uint8_t*)(tilebytes_ + ntiles_), ntiles_, list, &st_->ndec);
         mark("k_clear_words");
         EncodeArgs<T, 3> a;
         a.list = list;
@@ -665,17 +671,46 @@ class EngineT final : public Engine {
                                                        &st_->ndec);
         mark("k_flag");
     }
+    // Where the step's traversal and decode read S: the words of k_flag, or
+    // (onfly) words formed from the threshold, closure and bed flags on the
+    // spot, which spares the plain step the flag kernel.
+    SigSrc sig_src(bool onfly) const {
+        SigSrc s;
+        if (onfly) {
+            s.Tb = Tb_;
+            s.Cb = Cb_;
+            s.Sbase = Sz_;
+            s.predict = predict();
+            s.close = close();
+        } else {
+            s.Sb = Sb_;
+        }
+        return s;
+    }
+    // the plain step forms S on the spot (the fused traversal of the full
+    // sweep and the matched-flux kernels read the flag kernel's words)
+    bool onfly_flags() const { return quiet_on_ && !(spec_.flags & HWFV1_FLUX_MATCH); }
+    // materialise S for the readers of the words (listing, get_flags) when
+    // the last step formed it on the spot
+    void ensure_sig_words() {
+        if (sb_valid_) return;
+        lk(k_flag, grid_for(words_), 256, Tb_, Cb_, Sz_, Sb_, L_, predict(), close(),
+           (const DevState*)nullptr, (uint32_t*)nullptr);
+        sb_valid_ = true;
+    }
     // `learned`: the flags come from the learned look-ahead, whose skipped
     // tiles need not hold the bed's static flags alone (no cached counts).
-    // The four counters (ndec, Mall, M, nact) were cleared by the flag kernel.
-    void launch_traverse(bool learned = false) {
+    // The four counters (ndec, Mall, M, nact) were cleared by the flag or
+    // the clear kernel.
+    void launch_traverse(bool learned = false, bool onfly = false) {
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
         const uint32_t grid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
         if (quiet_on_) {
-            lk(k_trav_classify, (ntiles_ + 255) / 256, 256, Sb_, L_, kt_, ntiles_, st_, quiet(),
+            const SigSrc sg = sig_src(onfly && !learned);
+            lk(k_trav_classify, (ntiles_ + 255) / 256, 256, sg, L_, kt_, ntiles_, st_, quiet(),
                                                                       learned ? nullptr : scount_, work_);
             mark("k_trav_classify");
-            lk(k_trav_list, nsm_ * 8, 256, Sb_, dlist_, leaves_, L_, kt_, st_, work_);
+            lk(k_trav_list, nsm_ * 8, 256, sg, dlist_, leaves_, L_, kt_, st_, work_);
             mark("k_trav_list");
         } else {
             lk(k_trav_fused, grid, 256, Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, quiet(),
@@ -783,12 +818,12 @@ class EngineT final : public Engine {
             mark("k_fv1_wet");
         }
     }
-    DecodeArgs<T> decode_args() const {
+    DecodeArgs<T> decode_args(bool onfly = false) const {
         DecodeArgs<T> a;
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.z = z_;
-        a.Sb = Sb_;
+        a.Sb = sig_src(onfly);
         a.dlist = dlist_;
         a.st = st_;
         a.tol = (T)spec_.tol_h;
@@ -797,11 +832,11 @@ class EngineT final : public Engine {
         a.q = quiet();
         return a;
     }
-    void launch_decode() {
+    void launch_decode(bool onfly = false) {
         // the decode list is short once quiescent tiles are skipped: 2 CTAs per SM
         const int gd = quiet_on_ ? std::min(grid_for((uint64_t)ntiles_ * 256), nsm_ * 4)
                                  : grid_for((uint64_t)ntiles_ * 256);
-        lk(k_decode_finish<T>, gd, 256, decode_args(), fin_args());
+        lk(k_decode_finish<T>, gd, 256, decode_args(onfly), fin_args());
         mark("k_decode_finish");
     }
     void launch_step_uniform() {
@@ -810,11 +845,13 @@ class EngineT final : public Engine {
         launch_decode();
     }
     void launch_step_all() {
+        const bool onfly = onfly_flags();
         launch_encode();
-        launch_flag();
-        launch_traverse();
+        if (!onfly) launch_flag();
+        launch_traverse(false, onfly);
         launch_fv1();
-        launch_decode();
+        launch_decode(onfly);
+        sb_valid_ = !onfly;
     }
     void launch_features(__nv_bfloat16* out) {
         const uint32_t n = 1u << (2 * (L_ - 4));
@@ -837,6 +874,7 @@ class EngineT final : public Engine {
         launch_traverse(/*learned=*/true);
         launch_fv1();
         launch_decode();
+        sb_valid_ = true;
     }
     enum { kStepPlain = 0, kStepLearned = 1, kStepReuse = 2 };
     void launch_step(int kind) {
@@ -944,6 +982,7 @@ class EngineT final : public Engine {
     uint32_t* work_ = nullptr;          // the traversal's list of tiles to treat one warp each
     bool quiet_on_ = false;
     bool pdl_ = true;             // programmatic dependent launch in the step chain
+    bool sb_valid_ = true;        // Sb_ holds the S of the last step (else formed on the spot)
     std::vector<std::pair<const char*, cudaEvent_t>>* prof_ = nullptr;   // profile_step's events
     bool prof_external_ = false;          // events recorded as graph nodes (under capture)
     DevState* st_ = nullptr;

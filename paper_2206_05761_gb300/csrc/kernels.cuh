@@ -569,8 +569,11 @@ __device__ __forceinline__ void clear_body(uint32_t* w, uint32_t nwords, const D
     for (uint32_t i = B.id * blockDim.x + threadIdx.x; i < nwords; i += B.n * blockDim.x) w[i] = 0u;
 }
 static __global__ void k_clear_words(uint32_t* w, uint32_t nwords, DevState* st, const uint8_t* zf0,
-                                     const uint8_t* zf1, uint32_t ntiles, uint32_t* list) {
+                                     const uint8_t* zf1, uint32_t ntiles, uint32_t* list, uint32_t* zero4) {
     pdl_wait();
+    // the traversal's four counters (ndec, Mall, M, nact), for the step's
+    // traversal (no kernel in between uses them)
+    if (zero4 && blockIdx.x == 0 && threadIdx.x < 4u && st->active) zero4[threadIdx.x] = 0u;
     clear_body(w, nwords, st, this_blk());
     if (!list || !st->active) return;
     const uint8_t* zf = st->cur ? zf1 : zf0;
@@ -599,6 +602,28 @@ struct FlagArgs {
     DevState* st;
 };
 
+// Word lw of level n of S (the inputs are read-only in the caller).
+__device__ __forceinline__ uint32_t reg_word(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
+                                             const uint32_t* __restrict__ Sbase, int n, uint32_t lw, int predict,
+                                             int close) {
+    const uint32_t w = word_off(n) + lw;
+    uint32_t s = close ? __ldg(Cb + w) : __ldg(Tb + w);
+    if (Sbase) s |= __ldg(Sbase + w);
+    if (predict && n >= 1) {
+        uint32_t pb;
+        if (n >= 3) {
+            pb = expand4x8(__ldg(Tb + word_off(n - 1) + (lw >> 2)) >> (8u * (lw & 3u)));
+        } else if (n == 2) {   // 16 cells, parents are the 4 cells of level 1
+            pb = expand4x8(__ldg(Tb + word_off(1)) & 0xFu);
+        } else {               // level 1: the root's four children
+            pb = (__ldg(Tb + word_off(0)) & 1u) ? 0xFu : 0u;
+        }
+        s |= pb;
+    }
+    if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
+    return s;
+}
+
 __device__ __forceinline__ void flag_body(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
                                           const uint32_t* __restrict__ Sbase, uint32_t* __restrict__ Sb,
                                           int L, int predict, int close, const DevState* st, Blk B) {
@@ -607,23 +632,22 @@ __device__ __forceinline__ void flag_body(const uint32_t* __restrict__ Tb, const
     for (uint32_t w = B.id * blockDim.x + threadIdx.x; w < total; w += B.n * blockDim.x) {
         int n = 0;
         while (n + 1 < L && word_off(n + 1) <= w) ++n;
-        const uint32_t lw = w - word_off(n);
-        uint32_t s = (close ? Cb[w] : Tb[w]);
-        if (Sbase) s |= Sbase[w];
-        if (predict && n >= 1) {
-            uint32_t pb;
-            if (n >= 3) {
-                pb = expand4x8(Tb[word_off(n - 1) + (lw >> 2)] >> (8u * (lw & 3u)));
-            } else if (n == 2) {   // 16 cells, parents are the 4 cells of level 1
-                pb = expand4x8(Tb[word_off(1)] & 0xFu);
-            } else {               // level 1: the root's four children
-                pb = (Tb[word_off(0)] & 1u) ? 0xFu : 0u;
-            }
-            s |= pb;
-        }
-        if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
-        Sb[w] = s;
+        Sb[w] = reg_word(Tb, Cb, Sbase, n, w - word_off(n), predict, close);
     }
+}
+
+// Where a kernel reads S: the words k_flag wrote (Sb), or, with Sb NULL,
+// each word formed on the spot from the words k_flag would read.
+struct SigSrc {
+    const uint32_t* Sb = nullptr;
+    const uint32_t *Tb = nullptr, *Cb = nullptr, *Sbase = nullptr;
+    int predict = 1, close = 1;
+};
+__device__ __forceinline__ uint32_t s_word(const SigSrc& s, int n, uint32_t lw) {
+    return s.Sb ? __ldg(s.Sb + word_off(n) + lw) : reg_word(s.Tb, s.Cb, s.Sbase, n, lw, s.predict, s.close);
+}
+__device__ __forceinline__ uint32_t sig_bit(const SigSrc& s, int n, uint32_t code) {
+    return (s_word(s, n, code >> 5) >> (code & 31u)) & 1u;
 }
 // zero4: the traversal's four counters (ndec, Mall, M, nact), cleared here
 // for the traversal that follows (NULL: none).
@@ -716,8 +740,7 @@ struct TileBits {
 __device__ __forceinline__ int tb_slot(int j) { return j == 1 ? 0 : (j == 2 ? 1 : (j == 3 ? 2 : 4)); }
 
 // Called by the whole block; ends with __syncthreads.
-__device__ __forceinline__ void load_tile_bits(const uint32_t* __restrict__ Sb, int L, int kt,
-                                               uint32_t tile, TileBits& tb) {
+__device__ __forceinline__ void load_tile_bits(const SigSrc& Sb, int L, int kt, uint32_t tile, TileBits& tb) {
     const int Lr = L - kt;
     const int t = threadIdx.x;
     if (t < 32) {
@@ -738,14 +761,20 @@ __device__ __forceinline__ void load_tile_bits(const uint32_t* __restrict__ Sb, 
             const uint32_t cnt = 1u << (2 * j);
             const uint32_t first = tile * cnt;        // first code of the tile at level n
             if (cnt < 32u) {
-                v = (__ldg(Sb + word_off(n) + (first >> 5)) >> (first & 31u)) & ((1u << cnt) - 1u);
+                v = (s_word(Sb, n, first >> 5) >> (first & 31u)) & ((1u << cnt) - 1u);
             } else if ((uint32_t)idx * 32u < cnt) {
-                v = __ldg(Sb + word_off(n) + (first >> 5) + idx);
+                v = s_word(Sb, n, (first >> 5) + idx);
             }
         }
         tb.w[k] = v;
     }
     __syncthreads();
+}
+__device__ __forceinline__ void load_tile_bits(const uint32_t* __restrict__ Sb, int L, int kt, uint32_t tile,
+                                               TileBits& tb) {
+    SigSrc s;
+    s.Sb = Sb;
+    load_tile_bits(s, L, kt, tile, tb);
 }
 
 // leaf level of the thread's group of four finest cells (local group g)
@@ -1122,7 +1151,7 @@ static __global__ void __launch_bounds__(256) k_trav_fused(const uint32_t* __res
 // k_trav_list, which treats them one warp per tile as k_trav_fused does.
 // A list entry with bit 31 set is a skipped tile that is only counted (no
 // scount: the learned look-ahead's flags).
-static __global__ void __launch_bounds__(256) k_trav_classify(const uint32_t* __restrict__ Sb, int L, int kt,
+static __global__ void __launch_bounds__(256) k_trav_classify(SigSrc Sb, int L, int kt,
                                                               uint32_t ntiles, DevState* st, Quiet q,
                                                               const uint32_t* scount, uint32_t* work) {
     pdl_wait();
@@ -1177,7 +1206,7 @@ static __global__ void __launch_bounds__(256) k_trav_classify(const uint32_t* __
 
 // One CTA per listed tile, one thread per 4-cell group: its leaf count, a
 // block scan for the positions, one atomic on st->M for the tile's base.
-static __global__ void __launch_bounds__(256) k_trav_list(const uint32_t* __restrict__ Sb,
+static __global__ void __launch_bounds__(256) k_trav_list(SigSrc Sb,
                                                           uint32_t* __restrict__ dlist,
                                                           uint32_t* __restrict__ leaves, int L, int kt,
                                                           DevState* st, const uint32_t* __restrict__ work) {
@@ -2084,7 +2113,7 @@ template <typename T>
 struct DecodeArgs {
     T* f[2][3];
     const T* z;
-    const uint32_t* Sb;
+    SigSrc Sb;                // the step's regularised flags
     const uint32_t* dlist;    // tiles holding a leaf of more than 16 finest cells
     DevState* st;
     T tol;

@@ -256,11 +256,17 @@ def test_profiled_step_is_an_ordinary_step():
     prof = Hh.hwfv1_profile_step(sim.hd)
     names = [n for n, _ in prof]
     assert names[0] == "k_clear_words" and names[-1] == "k_decode_finish"
-    for k in ("k_flag", "k_trav_classify", "k_trav_list", "k_fv1_dry", "k_fv1_faces", "k_fv1_update"):
+    for k in ("k_encode_tail", "k_trav_classify", "k_trav_list", "k_fv1_dry", "k_fv1_faces", "k_fv1_update"):
         assert k in names
+    # the plain step forms the regularised flags inside the traversal
+    assert "k_flag" not in names
     assert all(t >= 0.0 for _, t in prof)
-    res = ref.step(want=("leaves",))
+    res = ref.step(want=("leaves", "S"))
     assert np.array_equal(sim.leaves(), res["leaves"])
+    # the flag words, formed on demand after such a step, are the oracle's S
+    S = _unpack(sim.flags(1), p["L"])
+    for n in range(p["L"]):
+        assert np.array_equal(S[n], rm_to_morton(res["S"][level_slice(n)], n)), "S level %d" % n
     _compare_fields(sim, ref)
     assert sim.time()[:3] == (ref.t, ref.dt, 1)
     sim.close()
