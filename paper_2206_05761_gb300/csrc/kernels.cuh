@@ -649,6 +649,40 @@ __device__ __forceinline__ uint32_t s_word(const SigSrc& s, int n, uint32_t lw) 
 __device__ __forceinline__ uint32_t sig_bit(const SigSrc& s, int n, uint32_t code) {
     return (s_word(s, n, code >> 5) >> (code & 31u)) & 1u;
 }
+// The bits S(n, tile >> 2(Lr-n)) of the root path of a tile, levels
+// 0..Lr, bit n of the result.  Formed on the spot, every word is loaded
+// before any is used: S(n,c) = Sbase(n,c) | (close ? C : T)(n,c) |
+// (predict ? T(n-1, c/4) : 0), the bit of reg_word's word.
+__device__ __forceinline__ uint32_t root_bits(const SigSrc& s, int Lr, uint32_t tile) {
+    uint32_t r = 0u;
+    if (s.Sb) {
+#pragma unroll
+        for (int n = 0; n < kMaxL; ++n)
+            if (n <= Lr) r |= sig_bit(s, n, tile >> (2 * (Lr - n))) << n;
+        return r;
+    }
+    const uint32_t* cw = s.close ? s.Cb : s.Tb;
+    uint32_t a[kMaxL], z[kMaxL], p[kMaxL];
+#pragma unroll
+    for (int n = 0; n < kMaxL; ++n) {
+        a[n] = z[n] = p[n] = 0u;
+        if (n <= Lr) {
+            const uint32_t c = tile >> (2 * (Lr - n));
+            a[n] = __ldg(cw + word_off(n) + (c >> 5));
+            if (s.Sbase) z[n] = __ldg(s.Sbase + word_off(n) + (c >> 5));
+            if (s.predict && n >= 1) p[n] = __ldg(s.Tb + word_off(n - 1) + ((c >> 2) >> 5));
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < kMaxL; ++n) {
+        if (n <= Lr) {
+            const uint32_t c = tile >> (2 * (Lr - n));
+            const uint32_t b = (((a[n] | z[n]) >> (c & 31u)) | (p[n] >> ((c >> 2) & 31u))) & 1u;
+            r |= b << n;
+        }
+    }
+    return r;
+}
 // zero4: the traversal's four counters (ndec, Mall, M, nact), cleared here
 // for the traversal that follows (NULL: none).
 static __global__ void k_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
@@ -1164,14 +1198,9 @@ static __global__ void __launch_bounds__(256) k_trav_classify(SigSrc Sb, int L, 
     uint32_t counted = 0u;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
         // first insignificant cell on the root path (levels 0..Lr), else Lr+1
-        uint32_t bits[kMaxL];
-#pragma unroll
-        for (int n = 0; n < kMaxL; ++n)
-            if (n <= Lr) bits[n] = sig_bit(Sb, n, t >> (2 * (Lr - n)));
-        int l0 = Lr + 1;
-#pragma unroll
-        for (int n = kMaxL - 1; n >= 0; --n)
-            if (n <= Lr && !bits[n]) l0 = n;
+        const uint32_t rb = root_bits(Sb, Lr, t);
+        const uint32_t zmask = ~rb & ((2u << Lr) - 1u);
+        const int l0 = zmask ? (__ffs(zmask) - 1) : Lr + 1;
         const bool covered = l0 < Lr;
         const uint32_t xs = t & kXBits & lm, ys = t & kYBits & lm;
         const bool xw = xs == 0u || X[mort_xm(t)], xe = xs == (kXBits & lm) || X[mort_xp(t)];
@@ -1630,7 +1659,7 @@ __device__ __forceinline__ void wet_leaf_store(const StepArgs<T>& a, DevState* s
                                                unsigned long long* spd = nullptr, T rh_known = T(0)) {
     if (sizeof(T) == 8 && spd != nullptr) {
         // float64: the CFL speeds of the leaf (the divisions are formed once
-        // per step from their maxima, cfl_rmin); the same operations as
+        // per step from their maxima, finish_body); the same operations as
         // cfl_bound up to the division, reusing the friction step's 1/h
         if (ge_nonneg(out[0], a.P.tol)) {
             const T rh = is_zero(rh_known) ? T(1) / out[0] : rh_known;
@@ -2223,11 +2252,13 @@ __device__ inline double inflow_Q(const FinishArgs& a, double t) {
 __device__ __forceinline__ double thr4_of(double t) { return t >= 0x1p-1020 ? ldexp(t, 2) : -1.0; }
 __device__ __forceinline__ float thr4_of(float t) { return t >= 0x1p-124f ? ldexpf(t, 2) : -1.0f; }
 
-__device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
+// With t, t_end, dt and s_max given (no reload of what the caller holds).
+__device__ inline void prepare_vals(DevState* st, const FinishArgs& a, double t, double t_end, double dt,
+                                    const double* smax) {
     for (int k = threadIdx.x; k < 3 * a.L; k += blockDim.x) {
         const int n = k / 3, q = k - 3 * n;
-        const double td = ldexp(a.eps, n - a.L) * st->smax[q];
-        const float tf = ldexpf((float)a.eps, n - a.L) * (float)st->smax[q];
+        const double td = ldexp(a.eps, n - a.L) * smax[q];
+        const float tf = ldexpf((float)a.eps, n - a.L) * (float)smax[q];
         st->thr[n * 3 + q] = td;
         st->thrf[n * 3 + q] = tf;
         const double t4 = thr4_of(td);
@@ -2237,39 +2268,38 @@ __device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
         st->thr4lo[n * 3 + q] = pre ? __double2float_rd(t4) : -1.0f;
         st->thr4hi[n * 3 + q] = pre ? __double2float_ru(t4) : -1.0f;
     }
-    if (threadIdx.x != 0) return;
-    st->active = st->t < st->t_end ? 1u : 0u;
-    double dt_use = st->dt;
-    if (st->t + dt_use > st->t_end) dt_use = st->t_end - st->t;
-    st->dt_use = dt_use;
-    st->rx0 = dt_use / a.lx;            // dt/dx_n = (dt/lx) * 2^n exactly
-    st->ry0 = dt_use / a.ly;
-    st->rx0f = (float)dt_use / (float)a.lx;
-    st->ry0f = (float)dt_use / (float)a.ly;
-    st->nwet = 0u;
-    st->Qdt = inflow_Q(a, st->t) * dt_use;
-    st->rmin_bits = kInfBits;
-    st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
-    st->speed_bits[0] = st->speed_bits[1] = st->speed_bits[2] = 0ull;
+    // the scalars: four independent tasks on lane 0 of different warps (a
+    // double division holds the FP64 pipe of its sub-partition for hundreds
+    // of cycles), each forming dt_use itself
+    if ((threadIdx.x & 31u) != 0u) return;
+    const int warp = (int)(threadIdx.x >> 5), nw = (int)((blockDim.x + 31u) >> 5);
+    double dt_use = dt;
+    if (t + dt_use > t_end) dt_use = t_end - t;
+    for (int task = warp; task < 4; task += nw) {
+        if (task == 0) {
+            st->active = t < t_end ? 1u : 0u;
+            st->dt_use = dt_use;
+            st->rx0f = (float)dt_use / (float)a.lx;
+            st->ry0f = (float)dt_use / (float)a.ly;
+            st->nwet = 0u;
+            st->rmin_bits = kInfBits;
+            st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
+            st->speed_bits[0] = st->speed_bits[1] = st->speed_bits[2] = 0ull;
+        } else if (task == 1) {
+            st->rx0 = dt_use / a.lx;            // dt/dx_n = (dt/lx) * 2^n exactly
+        } else if (task == 2) {
+            st->ry0 = dt_use / a.ly;
+        } else {
+            st->Qdt = inflow_Q(a, t) * dt_use;
+        }
+    }
+}
+__device__ inline void prepare_step(DevState* st, const FinishArgs& a) {
+    const double smax[3] = {st->smax[0], st->smax[1], st->smax[2]};
+    prepare_vals(st, a, st->t, st->t_end, st->dt, smax);
 }
 
 // next timestep: CFL * (min CFL bound), capped at dt_max (+inf when dry)
-// The step's CFL bound: the min of the bounds reduced as such and of
-// dx_L / max(|u|+sqrt(gh)) and dy_L / max(|v|+sqrt(gh)) over the wet leaves
-// whose speeds were reduced instead.  A correctly rounded division is
-// monotone in its divisor, so dx_L divided by the largest speed is exactly
-// the smallest of the per-leaf quotients dx_L/(|u|+sqrt(gh)) (Sec. 2.1.3 CFL).
-__device__ inline double cfl_rmin(const DevState* st, const FinishArgs& a) {
-    double r = from_obits(st->rmin_bits);
-    if (st->speed_bits[0] != 0ull) {
-        const double rx = ldexp(a.lx, -a.L) / __longlong_as_double((long long)st->speed_bits[0]);
-        const double ry = ldexp(a.ly, -a.L) / __longlong_as_double((long long)st->speed_bits[1]);
-        const double rr = rx < ry ? rx : ry;
-        r = rr < r ? rr : r;
-    }
-    return r;
-}
-
 __device__ inline double dt_from(const FinishArgs& a, double r) {
     const double dt = a.cfl * r;
     return dt < a.dt_max ? dt : a.dt_max;
@@ -2280,27 +2310,65 @@ __device__ inline double smax_of(unsigned long long bits) {
     return 1.0 > m ? 1.0 : m;
 }
 
-// One block: thread 0 advances the scalars, then all threads prepare the
-// next step.
+// One block advances the scalars, then prepares the next step.  The
+// independent parts run on lane 0 of different warps: the time and the
+// counters, the two CFL quotients (one division each), the three s_max;
+// then the timestep.  The step's CFL bound is the min of the bounds reduced
+// as such and of dx_L / max(|u|+sqrt(gh)) and dy_L / max(|v|+sqrt(gh)) over
+// the wet leaves whose speeds were reduced instead: a correctly rounded
+// division is monotone in its divisor, so dx_L divided by the largest speed
+// is exactly the smallest of the per-leaf quotients (Sec. 2.1.3 CFL).
 __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
     if (!st->active) return;
     __syncthreads();                 // every thread has read `active`
-    if (threadIdx.x == 0) {
-        st->t = st->t + st->dt_use;
-        st->dt = dt_from(a, cfl_rmin(st, a));
-        for (int q = 0; q < 3; ++q) st->smax[q] = smax_of(st->max_bits[q]);
-        if (!isfinite(st->dt) || !isfinite(st->smax[0]) || !isfinite(st->smax[1]) ||
-            !isfinite(st->smax[2]))
-            st->err |= kErrNonFinite;
-        st->step += 1;
-        st->epoch += 1u;
-        st->leaf_updates += st->Mall;
-        st->act_updates += st->M;
-        st->wet_updates += st->nwet;
-        st->cur ^= 1u;
+    // values handed between the parts through shared memory, so that
+    // nothing written here is read back from global memory
+    __shared__ double s_q[2], s_t, s_tend, s_dt, s_r, s_smax[3];
+    const int warp = (int)(threadIdx.x >> 5), nw = (int)((blockDim.x + 31u) >> 5);
+    const bool speeds = st->speed_bits[0] != 0ull;
+    if ((threadIdx.x & 31u) == 0u) {
+        for (int task = warp; task < 4; task += nw) {
+            if (task == 0) {
+                const double t = st->t + st->dt_use;
+                st->t = t;
+                s_t = t;
+                s_tend = st->t_end;
+                st->step += 1;
+                st->epoch += 1u;
+                st->leaf_updates += st->Mall;
+                st->act_updates += st->M;
+                st->wet_updates += st->nwet;
+                st->cur ^= 1u;
+            } else if (task == 1) {
+                if (speeds) s_q[0] = ldexp(a.lx, -a.L) / __longlong_as_double((long long)st->speed_bits[0]);
+                s_r = from_obits(st->rmin_bits);
+            } else if (task == 2) {
+                if (speeds) s_q[1] = ldexp(a.ly, -a.L) / __longlong_as_double((long long)st->speed_bits[1]);
+            } else {
+                for (int q = 0; q < 3; ++q) {
+                    const double m = smax_of(st->max_bits[q]);
+                    st->smax[q] = m;
+                    s_smax[q] = m;
+                }
+            }
+        }
     }
     __syncthreads();
-    prepare_step(st, a);
+    if (threadIdx.x == 0) {
+        double r = s_r;
+        if (speeds) {
+            const double rx = s_q[0], ry = s_q[1];
+            const double rr = rx < ry ? rx : ry;
+            r = rr < r ? rr : r;
+        }
+        const double dt = dt_from(a, r);
+        st->dt = dt;
+        s_dt = dt;
+        if (!isfinite(dt) || !isfinite(s_smax[0]) || !isfinite(s_smax[1]) || !isfinite(s_smax[2]))
+            st->err |= kErrNonFinite;
+    }
+    __syncthreads();
+    prepare_vals(st, a, s_t, s_tend, s_dt, s_smax);
 }
 static __global__ void k_finish(DevState* st, FinishArgs a) {
     finish_body(st, a);
