@@ -802,7 +802,14 @@ class EngineT final : public Engine {
         }
         lk(k_fv1_dry<T>, grid_for(N_), 256, a);
         mark("k_fv1_dry");
-        if (a.fm) {
+        if (a.fm && face_) {
+            // matched fluxes with shared faces: a face toward a refined
+            // neighbour takes the walk over its halves in either phase
+            lk(k_fv1_faces<T, true>, wet_grid(), 64, a);
+            mark("k_fv1_faces");
+            lk(k_fv1_update<T, true>, wet_grid(), 64, a);
+            mark("k_fv1_update");
+        } else if (a.fm) {
             lk(k_fv1_match<T>, wet_grid(), 64, a);
             mark("k_fv1_match");
         } else if (face_) {

@@ -1958,7 +1958,7 @@ static __global__ void __launch_bounds__(256) k_fv1_match(StepArgs<T> a) {
 // queued leaf whose west (south) same-level neighbour carries this step's
 // stamp takes that neighbour's east (north) face -- the same call with the
 // same operands, so the same bits -- and computes only its other faces.
-template <typename T>
+template <typename T, bool FM = false>
 __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
     DevState* st = a.st;
     if (!st->active) return;
@@ -1982,42 +1982,65 @@ __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
         const uint64_t base = lvl_off(n);
         const uint64_t iC = base + code;
         const Cell<T> C = fetch(src, iC);
-        const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
-        const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
-        T uC, vC, uE, vE, uN, vN;
-        velocity(C, tol, uC, vC);
-        velocity(E, tol, uE, vE);
-        velocity(N, tol, uN, vN);
-        T FE[3], GN[3], hEL, hER, hNL, hNR;
-        hll_face(g, hg, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hEL, hER);
-        hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hNL, hNR);
+        T FE[3], GN[3], hEL2, hER2 = T(0), hNL2, hNR2 = T(0);
+        // with matched fluxes, a face toward a refined neighbour is the walk
+        // over its finer halves (its other side belongs to no leaf)
+        const bool mE = FM && i < last && n < a.L && sig_bit(a.Sb, n, morton2(i + 1, j));
+        const bool mN = FM && j < last && n < a.L && sig_bit(a.Sb, n, morton2(i, j + 1));
+        if (FM && (mE || mN)) {
+            if (mE) matched_face(a, src, 1, n, i, j, FE, hEL2);
+            if (mN) matched_face(a, src, 3, n, i, j, GN, hNL2);
+        }
+        if (!(mE && mN)) {
+            const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
+            const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
+            T uC, vC, uE, vE, uN, vN;
+            velocity(C, tol, uC, vC);
+            if (!mE) {
+                velocity(E, tol, uE, vE);
+                T hEL, hER;
+                hll_face(g, hg, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hEL, hER);
+                hEL2 = hEL * hEL;
+                hER2 = hER * hER;
+            }
+            if (!mN) {
+                velocity(N, tol, uN, vN);
+                T hNL, hNR;
+                hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hNL, hNR);
+                hNL2 = hNL * hNL;
+                hNR2 = hNR * hNR;
+            }
+        }
+        // the face of both sides: flux, then the squares of the two
+        // reconstructed depths (the bed source terms of the two cells)
         T* f = a.face + w;
         f[0 * (size_t)cap] = FE[0];
         f[1 * (size_t)cap] = FE[1];
         f[2 * (size_t)cap] = FE[2];
-        f[3 * (size_t)cap] = hEL;
-        f[4 * (size_t)cap] = hER;
+        f[3 * (size_t)cap] = hEL2;
+        f[4 * (size_t)cap] = hER2;
         f[5 * (size_t)cap] = GN[0];
         f[6 * (size_t)cap] = GN[1];
         f[7 * (size_t)cap] = GN[2];
-        f[8 * (size_t)cap] = hNL;
-        f[9 * (size_t)cap] = hNR;
+        f[8 * (size_t)cap] = hNL2;
+        f[9 * (size_t)cap] = hNR2;
         a.mark[iC] = stamp | w;
     }
 }
-template <typename T>
+template <typename T, bool FM = false>
 static __global__ void __launch_bounds__(256) k_fv1_faces(StepArgs<T> a) {
     pdl_wait();
-    fv1_faces_body<T>(a, this_blk());
+    fv1_faces_body<T, FM>(a, this_blk());
 }
 
-template <typename T>
+template <typename T, bool FM = false>
 __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
     DevState* st = a.st;
     if (!st->active) return;
     const uint32_t nq = st->nwet;
     if (nq > a.fcap) {                            // no room for the faces: one pass
-        fv1_wet_body<T>(a, B);
+        if (FM) fv1_match_body<T>(a, B);
+        else fv1_wet_body<T>(a, B);
         return;
     }
     if (B.id * blockDim.x >= nq) return;          // whole block idle
@@ -2047,15 +2070,16 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
         const uint64_t base = lvl_off(n);
         const uint64_t iC = base + code;
         const Cell<T> C = fetch(src, iC);
-        T FE[3], GN[3], FW[3], GS[3], hE_L, hN_L, hW_R, hS_R;
+        // squares of the reconstructed depths of the cell at its faces
+        T FE[3], GN[3], FW[3], GS[3], hE2, hN2, hW2, hS2;
         FE[0] = F[0 * (size_t)cap + w];
         FE[1] = F[1 * (size_t)cap + w];
         FE[2] = F[2 * (size_t)cap + w];
-        hE_L = F[3 * (size_t)cap + w];
+        hE2 = F[3 * (size_t)cap + w];
         GN[0] = F[5 * (size_t)cap + w];
         GN[1] = F[6 * (size_t)cap + w];
         GN[2] = F[7 * (size_t)cap + w];
-        hN_L = F[8 * (size_t)cap + w];
+        hN2 = F[8 * (size_t)cap + w];
         bool haveW = false, haveS = false;
         if (i > 0) {
             const unsigned long long m = __ldg(a.mark + base + morton2(i - 1, j));
@@ -2064,7 +2088,7 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
                 FW[0] = F[0 * (size_t)cap + v];
                 FW[1] = F[1 * (size_t)cap + v];
                 FW[2] = F[2 * (size_t)cap + v];
-                hW_R = F[4 * (size_t)cap + v];
+                hW2 = F[4 * (size_t)cap + v];
                 haveW = true;
             }
         }
@@ -2075,24 +2099,34 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
                 GS[0] = F[5 * (size_t)cap + v];
                 GS[1] = F[6 * (size_t)cap + v];
                 GS[2] = F[7 * (size_t)cap + v];
-                hS_R = F[9 * (size_t)cap + v];
+                hS2 = F[9 * (size_t)cap + v];
                 haveS = true;
             }
+        }
+        if (FM && !haveW && i > 0 && n < a.L && sig_bit(a.Sb, n, morton2(i - 1, j))) {
+            matched_face(a, src, 0, n, i, j, FW, hW2);
+            haveW = true;
+        }
+        if (FM && !haveS && j > 0 && n < a.L && sig_bit(a.Sb, n, morton2(i, j - 1))) {
+            matched_face(a, src, 2, n, i, j, GS, hS2);
+            haveS = true;
         }
         if (!(haveW && haveS)) {
             T uC, vC, dummy;
             velocity(C, tol, uC, vC);
             if (!haveW) {
                 const Cell<T> W = i > 0 ? fetch(src, base + morton2(i - 1, j)) : ghost(C, a.bc_ref[0], true);
-                T uW, vW;
+                T uW, vW, hW_R;
                 velocity(W, tol, uW, vW);
                 hll_face(g, hg, tol, W.h, W.z, uW, vW, C.h, C.z, uC, vC, FW, dummy, hW_R);
+                hW2 = hW_R * hW_R;
             }
             if (!haveS) {
                 const Cell<T> S = j > 0 ? fetch(src, base + morton2(i, j - 1)) : ghost(C, a.bc_ref[2], false);
-                T uS, vS;
+                T uS, vS, hS_R;
                 velocity(S, tol, uS, vS);
                 hll_face(g, hg, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
+                hS2 = hS_R * hS_R;
             }
         }
         const T rx = mul_pow2(rx0, n), ry = mul_pow2(ry0, n);   // rx0 * 2^n, exact
@@ -2107,17 +2141,17 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
             dh = (Qdt * frac) / (dxn * dyn);
         }
         T out[3], rh;
-        cell_update_faces(a.P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out, &rh);
+        cell_update_faces_sq(a.P, rx, ry, dt, C, FW, FE, GS, GN, hW2, hE2, hS2, hN2, inlet, dh, out, &rh);
         wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd, rh);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
     block_max3_u64(mh, mqx, mqy, st->max_bits);
     block_max3_u64(spd[0], spd[1], 0ull, st->speed_bits);
 }
-template <typename T>
+template <typename T, bool FM = false>
 static __global__ void __launch_bounds__(256) k_fv1_update(StepArgs<T> a) {
     pdl_wait();
-    fv1_update_body<T>(a, this_blk());
+    fv1_update_body<T, FM>(a, this_blk());
 }
 
 // Uniform FV1 (every finest cell a leaf): the fixed leaf list in Z-order ...

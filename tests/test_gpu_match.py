@@ -93,13 +93,15 @@ def test_matched_with_quiescent_tiles_equals_full_sweep():
     full.close()
 
 
-def test_matched_profiled_step_names_the_kernel():
+def test_matched_profiled_step_is_an_ordinary_step():
+    # the shared-face kernels with the walk over finer halves, and the flag
+    # words they read, in a step launched kernel by kernel
     from paper_2206_05761_gb300 import hwfv1 as Hh
     p, f = _closed_circle(6)
     sim = _sim(p, f)
     ref = oracle.State(p, f)
     names = [n for n, _ in Hh.hwfv1_profile_step(sim.hd)]
-    assert "k_fv1_match" in names and "k_fv1_faces" not in names
+    assert "k_flag" in names and "k_fv1_faces" in names and "k_fv1_update" in names
     ref.step()
     _compare_fields(sim, ref)
     sim.close()
@@ -134,3 +136,10 @@ def test_matched_rejected_with_batches_and_learned_lookahead():
         sim.set_skipnet(net)
     H.hwfv1_skipnet_destroy(net)
     sim.close()
+
+
+def test_matched_full_size_wet_domain_one_step():
+    # 4096 x 4096 bumpy dam-break: more queued leaves than the shared-face
+    # buffer holds, so the matched update takes its one-pass form
+    p, f = synth.bumpy_dam_break(L=12, eps=1e-3)
+    one_step_parity(_fm(p), f)
