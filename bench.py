@@ -144,8 +144,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
 # step in the timed window: mean over the launches of the ncu capture
 # summarised in profiles/terrain_flood_L12_f64_launches.md, valid while
 # kernels.cuh has this SHA-256.
-FV1_WET_TRAFFIC = {"kernels_sha256": "1fc0c3e5128aac7e6d472ba7baf947bb5326df7a6b245062f99df3476691af58",
-                   "bytes_per_launch": 2888403 + 9537779}
+FV1_WET_TRAFFIC = {"kernels_sha256": "2787cfa90737a6403e967fb8a1a0ac7817b91e08219b65f5944aa8b3898ee5d4",
+                   "bytes_per_launch": 2889228 + 9536416}
 
 
 def kernels_sha256():

@@ -421,6 +421,31 @@ def test_quiescent_tile_skipping_is_exact(relief):
     full.close()
 
 
+def test_listed_encode_tiles_L11():
+    # 2048 x 2048, water released on rough dry ground: more tiles (4096)
+    # than the first encode pass has CTAs, so it works from the list of
+    # non-quiescent tiles; 16-step graphs; against the oracle and the full
+    # sweep
+    p, f = synth.dry_bed_dam_break(L=11, eps=1e-3, relief=0.05)
+    sim = _sim(p, f)
+    full = _sim(dict(p, full_sweep=True), f)
+    ref = oracle.State(p, f)
+    sim.advance(max_steps=17)
+    full.advance(max_steps=17)
+    for _ in range(16):
+        ref.step()
+    res = ref.step(want=("leaves",))
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    assert np.array_equal(full.leaves(), res["leaves"])
+    _compare_fields(sim, ref)
+    _compare_fields(full, ref)
+    assert sim.time()[:2] == (ref.t, ref.dt)
+    _, lu, au, _, _ = sim.counters()
+    assert au < 0.5 * lu
+    sim.close()
+    full.close()
+
+
 def test_uniform_fv1_matches_oracle():
     # hwfv1_advance_uniform: uniform FV1 on the finest grid (the comparison
     # solver), against the oracle's uniform step, bit for bit
