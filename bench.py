@@ -47,6 +47,10 @@ def parse():
     a.add_argument("--no-learned", action="store_true")
     a.add_argument("--no-pseudo2d", action="store_true")
     a.add_argument("--cpu-steps", type=int, default=2)
+    a.add_argument("--full-sweep", action="store_true",
+                   help="time the window with HWFV1_FULL_SWEEP (every tile encoded, updated and "
+                        "decoded): the MRA kernels at full size, for an ncu launch list")
+    a.add_argument("--no-mra", action="store_true")
     return a.parse_args()
 
 
@@ -65,6 +69,8 @@ def config_dict(args, extra=None):
          "parallelism": "replicas" if args.gpus > 1 else "single"}
     if args.fill > 0:
         d["fill_m"] = args.fill
+    if args.full_sweep:
+        d["full_sweep"] = True
     if extra:
         d.update(extra)
     return d
@@ -228,6 +234,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     dev = torch.device("cuda")
     p, snap = spin_up(args, stream)
+    if args.full_sweep:
+        p = dict(p, full_sweep=True)
     N = 1 << (2 * args.L)
     t_s, dt_s = snap["t"], snap["dt"]
     state = {"z": snap["z"], **snap["fields"]}
@@ -542,6 +550,55 @@ def time_flux_match(args, p, state, t_s, dt_s, steps):
     return out
 
 
+def run_mra(args, p, state, t_s, dt_s, steps=100):
+    """The MRA kernels at full size: the same window with HWFV1_FULL_SWEEP
+    (every tile encoded and every leaf updated and decoded).  Per kernel the
+    live time (hwfv1_profile_step, median of 5), its algorithmic bytes and
+    HBM GB/s against the measured copy bandwidth.  First encode pass: the
+    finest h, hu, hv read, levels L-1..L-5 written (24 B per cell read +
+    8 B written, float64) plus their threshold and closure bits; decode:
+    the finest cells under the leaves of more than 16 cells written (24 B
+    each; the bed reads of wet leaves not counted)."""
+    import numpy as np
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as H
+    from paper_2206_05761_gb300.sim import Simulation
+    stream = torch.cuda.Stream()
+    sim = Simulation(dict(p, full_sweep=True), state, args.precision, stream=stream)
+    sim.set_time(t_s, dt_s)
+    sim.advance(max_steps=3)
+    stream.synchronize()
+    kern = {}
+    for _ in range(5):
+        for name, t in H.hwfv1_profile_step(sim.hd):
+            kern.setdefault(name, []).append(t)
+    ph = {k: statistics.median(v) for k, v in kern.items()}
+    L, esz = args.L, 8 if args.precision == 64 else 4
+    N = 1 << (2 * L)
+    upper = sum(4.0 ** -k for k in range(1, 6))          # levels L-1 .. L-5 per finest cell
+    enc_bytes = N * (3 * esz * (1.0 + upper) + 2 * upper / 8.0)
+    lv = sim.leaves() >> 28
+    big = lv[(L - lv.astype(np.int64)) >= 3]
+    cells_big = int(np.sum(np.left_shift(np.ones(big.shape, dtype=np.int64), 2 * (L - big.astype(np.int64)))))
+    dec_bytes = cells_big * 3 * esz
+    pk, src = peaks()
+    out = {"workload": "terrain flood window at t=%.0f s with HWFV1_FULL_SWEEP" % t_s, "peak_gbs": pk["hbm_gbs"],
+           "peak_source": src, "kernels_ms": ph}
+    for name, b in (("k_encode", enc_bytes), ("k_decode_finish", dec_bytes)):
+        if name in ph and ph[name] > 0:
+            gbs = b / (ph[name] / 1e3) / 1e9
+            out[name] = {"algorithmic_bytes": int(b), "ms": ph[name], "gbs": gbs, "frac": gbs / pk["hbm_gbs"]}
+    out["decode_cells"] = cells_big
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.advance(max_steps=steps)
+    e1.record(stream)
+    stream.synchronize()
+    out["full_sweep_steps_per_s"] = steps / (e0.elapsed_time(e1) / 1e3)
+    sim.close()
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -652,6 +709,8 @@ def main():
         fm = time_flux_match(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"], args.steps)
         fm["cost_vs_same_level"] = value / fm["value"]
         out["flux_match"] = fm
+    if world == 1 and not args.no_mra:
+        out["mra"] = run_mra(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"])
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_pseudo2d:
