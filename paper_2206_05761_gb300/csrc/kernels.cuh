@@ -649,6 +649,18 @@ __device__ __forceinline__ uint32_t s_word(const SigSrc& s, int n, uint32_t lw) 
 __device__ __forceinline__ uint32_t sig_bit(const SigSrc& s, int n, uint32_t code) {
     return (s_word(s, n, code >> 5) >> (code & 31u)) & 1u;
 }
+// One bit of S formed without a branch on the level (lanes asking for
+// different levels issue the same loads together): Sbase(n,c) | (close ? C
+// : T)(n,c) | (predict ? T(n-1, c/4) : 0), the bit of reg_word's word.
+__device__ __forceinline__ uint32_t sig_bit_flat(const SigSrc& s, int n, uint32_t c) {
+    if (s.Sb) return (__ldg(s.Sb + word_off(n) + (c >> 5)) >> (c & 31u)) & 1u;
+    const uint32_t* cw = s.close ? s.Cb : s.Tb;
+    const uint32_t a = __ldg(cw + word_off(n) + (c >> 5));
+    const uint32_t z = s.Sbase ? __ldg(s.Sbase + word_off(n) + (c >> 5)) : 0u;
+    const bool par = s.predict && n >= 1;
+    const uint32_t p = par ? __ldg(s.Tb + word_off(par ? n - 1 : 0) + ((c >> 2) >> 5)) : 0u;
+    return ((((a | z) >> (c & 31u)) | (p >> ((c >> 2) & 31u))) & 1u);
+}
 // The bits S(n, tile >> 2(Lr-n)) of the root path of a tile, levels
 // 0..Lr, bit n of the result.  Formed on the spot, every word is loaded
 // before any is used: S(n,c) = Sbase(n,c) | (close ? C : T)(n,c) |
@@ -779,7 +791,7 @@ __device__ __forceinline__ void load_tile_bits(const SigSrc& Sb, int L, int kt, 
     const int t = threadIdx.x;
     if (t < 32) {
         bool zero = false;
-        if (t <= Lr) zero = sig_bit(Sb, t, tile >> (2 * (Lr - t))) == 0u;
+        if (t <= Lr) zero = sig_bit_flat(Sb, t, tile >> (2 * (Lr - t))) == 0u;
         const uint32_t z = __ballot_sync(0xffffffffu, zero);
         if (t == 0) tb.l0 = z ? (__ffs(z) - 1) : Lr + 1;
     } else if (t < 44) {
