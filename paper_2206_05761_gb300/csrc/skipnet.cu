@@ -84,6 +84,44 @@ __device__ __forceinline__ bf16 xcol(const bf16* __restrict__ X, const Img& g, i
     return X[((size_t)(b * g.H + y) * g.W + x) * g.cin + c];
 }
 
+// The im2col row of pixel p (k = tap * cin + c over the 3x3 taps, zero
+// outside the image and for k >= 9 cin) written to row `row` of the
+// core-matrix operand: the pixel's position is formed once, and each tap's
+// channels move as one 16-byte (cin % 8 == 0) or 8-byte (cin == 4) vector.
+__device__ __forceinline__ void im2col_row(const bf16* __restrict__ X, const Img& g, int p, uint32_t row,
+                                           uint8_t* sA, int kpad) {
+    const uint32_t kb = (uint32_t)kpad / 8u;
+    const int npix = g.B * g.H * g.W;
+    if (g.cin % 8 != 0 && g.cin != 4) {
+        for (int k = 0; k < kpad; ++k) put_bf16(sA, tc::core_off(row, k, kb), xcol(X, g, p, k));
+        return;
+    }
+    const bool inside = p < npix;
+    int b = 0, y = 0, x = 0;
+    if (inside) {
+        b = p / (g.H * g.W);
+        const int rem = p % (g.H * g.W);
+        y = rem / g.W;
+        x = rem % g.W;
+    }
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+        const bool ok = inside && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W;
+        const size_t at = ok ? ((size_t)(b * g.H + yy) * g.W + xx) * g.cin : 0;
+        if (g.cin == 4) {
+            const uint2 v = ok ? __ldg(reinterpret_cast<const uint2*>(X + at)) : make_uint2(0u, 0u);
+            *reinterpret_cast<uint2*>(sA + tc::core_off(row, tap * 4, kb)) = v;
+        } else {
+            for (int cb = 0; cb < g.cin / 8; ++cb) {
+                const uint4 v = ok ? __ldg(reinterpret_cast<const uint4*>(X + at) + cb) : make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4*>(sA + tc::core_off(row, tap * g.cin + cb * 8, kb)) = v;
+            }
+        }
+    }
+    for (int k = 9 * g.cin; k < kpad; ++k) put_bf16(sA, tc::core_off(row, k, kb), __float2bfloat16(0.f));
+}
+
 // Shared TMEM/mbarrier bookkeeping of one CTA (128 threads).
 struct TcCta {
     uint64_t bar;
@@ -139,7 +177,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, Im
     const int kb = kpad / 8;
     const int t = threadIdx.x;
     const int p = blockIdx.x * 128 + t;
-    for (int k = 0; k < kpad; ++k) put_bf16(sA, tc::core_off(t, k, kb), xcol(X, g, p, k));
+    im2col_row(X, g, p, (uint32_t)t, sA, kpad);
     const uint4* src = reinterpret_cast<const uint4*>(wf);
     for (int i = t; i < 2 * kpad; i += 128) reinterpret_cast<uint4*>(sB)[i] = src[i];
     tc_begin(s, 32);
