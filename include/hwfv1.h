@@ -214,6 +214,16 @@ hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax
  * synchronises.  No counterpart in the paper: diagnostics. */
 hwfv1_status hwfv1_profile_step(hwfv1_handle* hd, float* ms, const char** names, int32_t cap, int32_t* n);
 
+/* One plain step whose full update of the queued (wet) leaves, Eq. 2 on the
+ * leaf grid, is captured on its own and replayed `reps` (>= 1) times between
+ * two CUDA events on the handle's stream before the step goes on.  Every
+ * replay reads the same state and queue and writes the same values (leaf
+ * values of the next state, min/max reductions), so the simulation still
+ * advances by exactly one step.  *ms (host) = the mean time of one update,
+ * the kernels as they run inside the step's graph.  Synchronises.  No
+ * counterpart in the paper: diagnostics. */
+hwfv1_status hwfv1_profile_update(hwfv1_handle* hd, int32_t reps, float* ms);
+
 /* Running counters (host outputs, any may be NULL; synchronises): steps
  * taken; leaves updated summed over those steps (sum of M, the work of
  * Sec. 2.3's leaf loop); the part of them outside skipped quiescent tiles

@@ -178,6 +178,12 @@ hwfv1_status hwfv1_profile_step(hwfv1_handle* hd, float* ms, const char** names,
     if (cap < 0) return HWFV1_ERR_INVALID_SPEC;
     return from_engine(hd, hd->eng->profile_step(ms, names, cap, n));
 }
+
+hwfv1_status hwfv1_profile_update(hwfv1_handle* hd, int32_t reps, float* ms) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (reps < 1 || !ms) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->profile_update(reps, ms));
+}
 hwfv1_status hwfv1_get_counters(hwfv1_handle* hd, int64_t* steps, int64_t* leaf_updates,
                                 int64_t* active_updates, int64_t* wet_updates, int64_t* kernels_per_step) {
     HWFV1_CHECK_HANDLE(hd);

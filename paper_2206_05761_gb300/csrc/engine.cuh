@@ -467,6 +467,52 @@ class EngineT final : public Engine {
         return r;
     }
 
+    // One plain step whose full update of the queued leaves (the pair of
+    // shared-face kernels, or their one-pass form) is captured on its own and
+    // replayed `reps` times between two CUDA events before the step goes on:
+    // the update reads the current state and the queue and writes the next
+    // state's leaf values and min/max reductions, so every replay writes the
+    // same values.  *ms = the mean time of one update.
+    hwfv1_status profile_update(int32_t reps, float* ms) override {
+        if (reps < 1 || !ms) return fail(HWFV1_ERR_INVALID_SPEC, "profile_update: reps >= 1 and ms");
+        const bool onfly = onfly_flags();
+        launch_encode();
+        if (!onfly) launch_flag();
+        launch_traverse(false, onfly);
+        StepArgs<T> a = step_args();
+        lk(k_fv1_dry<T>, grid_for(N_), 256, a);
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        hwfv1_status r = HWFV1_OK;
+        if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(HWFV1_ERR_CUDA, "graph capture begin");
+        launch_wet(a);
+        if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "graph capture end");
+        if (r == HWFV1_OK && cudaGraphInstantiate(&x, g, 0) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "graph instantiate");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (r == HWFV1_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+            r = fail(HWFV1_ERR_CUDA, "event");
+        if (r == HWFV1_OK) {
+            cudaGraphLaunch(x, stream_);                  // once untimed
+            cudaEventRecord(e0, stream_);
+            for (int32_t k = 0; k < reps; ++k) cudaGraphLaunch(x, stream_);
+            cudaEventRecord(e1, stream_);
+            launch_decode(onfly);
+            sb_valid_ = !onfly;
+            r = check("profile_update", true);
+            float t = 0.f;
+            if (r == HWFV1_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "event");
+            *ms = t / (float)reps;
+        } else {
+            cudaStreamSynchronize(stream_);
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+
     hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* au, int64_t* wu, int64_t* kps) override {
         if (kps) {
             if (!exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
@@ -802,6 +848,10 @@ class EngineT final : public Engine {
         }
         lk(k_fv1_dry<T>, grid_for(N_), 256, a);
         mark("k_fv1_dry");
+        launch_wet(a);
+    }
+    // the full update of the queued leaves (after k_fv1_dry)
+    void launch_wet(const StepArgs<T>& a) {
         if (a.fm && face_) {
             // matched fluxes with shared faces: a face toward a refined
             // neighbour takes the walk over its halves in either phase

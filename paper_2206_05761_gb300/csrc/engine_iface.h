@@ -34,6 +34,7 @@ class Engine {
     virtual hwfv1_status set_time(double t, double dt) = 0;
     virtual hwfv1_status get_stats(int64_t* M, double* smax3) = 0;
     virtual hwfv1_status profile_step(float* ms, const char** names, int32_t cap, int32_t* n) = 0;
+    virtual hwfv1_status profile_update(int32_t reps, float* ms) = 0;
     virtual hwfv1_status get_counters(int64_t* steps, int64_t* leaf_updates, int64_t* active_updates,
                                       int64_t* wet_updates, int64_t* kernels_per_step) = 0;
     virtual hwfv1_status save(void* buf, size_t cap, size_t* used) = 0;

@@ -272,6 +272,25 @@ def test_profiled_step_is_an_ordinary_step():
     sim.close()
 
 
+def test_profiled_update_is_an_ordinary_step():
+    # hwfv1_profile_update replays the update of the queued leaves inside
+    # one step: the state after it is one oracle step, bit for bit
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    p, f = synth.bumpy_dam_break(L=7, eps=1e-3, seed=2)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    sim.advance(max_steps=3)
+    for _ in range(3):
+        ref.step()
+    ms = Hh.hwfv1_profile_update(sim.hd, reps=7)
+    assert ms > 0.0
+    res = ref.step(want=("leaves",))
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    _compare_fields(sim, ref)
+    assert sim.time()[:3] == (ref.t, ref.dt, 4)
+    sim.close()
+
+
 def test_advance_stops_at_t_end():
     p, f = synth.circular_dam_break(L=5, eps=1e-3)
     sim = _sim(p, f)
