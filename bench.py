@@ -8,7 +8,11 @@ encode + flag + regularise + traverse/compact + FV1 update + decode-back +
 time advance.  The state (about 1 GB) is larger than L2, so no flush is
 needed between steps.
 
-Prints one JSON line (see the design doc for every key).
+Prints one JSON line: steps/s of the timed window (value), the same through
+the C ABI with host buffers (e2e), the roofline of the wet-leaf update, the
+oracle's rate (cpu_baseline), clocks, and the side measurements (float32,
+uniform FV1, the conservative variant, the MRA at full size, the batched
+ensemble, the learned look-ahead, the pseudo-2D dam-break).
 """
 from __future__ import annotations
 
