@@ -569,8 +569,10 @@ def run_mra(args, p, state, t_s, dt_s, steps=100):
     (every tile encoded and every leaf updated and decoded).  Per kernel the
     live time (hwfv1_profile_step, median of 5), its algorithmic bytes and
     HBM GB/s against the measured copy bandwidth.  First encode pass: the
-    finest h, hu, hv read, levels L-1..L-5 written (24 B per cell read +
-    8 B written, float64) plus their threshold and closure bits; decode:
+    finest h, hu, hv read (24 B per cell, float64), its levels written (L-1
+    .. L-3 when there are more 1024-cell blocks than 8 CTAs per SM, the pass
+    then stopping three levels up; else L-1 .. L-5) plus their threshold
+    and closure bits; decode:
     the finest cells under the leaves of more than 16 cells written (24 B
     each; the bed reads of wet leaves not counted)."""
     import numpy as np
@@ -589,7 +591,9 @@ def run_mra(args, p, state, t_s, dt_s, steps=100):
     ph = {k: statistics.median(v) for k, v in kern.items()}
     L, esz = args.L, 8 if args.precision == 64 else 4
     N = 1 << (2 * L)
-    upper = sum(4.0 ** -k for k in range(1, 6))          # levels L-1 .. L-5 per finest cell
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    levels = 3 if L >= 8 and (1 << (2 * (L - 5))) > nsm * 8 else 5
+    upper = sum(4.0 ** -k for k in range(1, levels + 1))  # levels written per finest cell
     enc_bytes = N * (3 * esz * (1.0 + upper) + 2 * upper / 8.0)
     lv = sim.leaves() >> 28
     big = lv[(L - lv.astype(np.int64)) >= 3]

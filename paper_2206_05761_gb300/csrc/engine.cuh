@@ -661,10 +661,20 @@ class EngineT final : public Engine {
         int ls = L_;
         bool list_reset = a.list == nullptr;
         while (ls > 0) {
-            const int k = ls < 5 ? ls : 5;
+            int k = ls < 5 ? ls : 5;
+            a.span = 0;
+            // a first pass over every one of many tiles stops after three
+            // levels of each 1024-cell block: a shorter chain per CTA, and the
+            // block's two top levels move to the next pass, which reads 1/64
+            // of the data
+            if (ls == L_ && a.zf[0] == nullptr && a.list == nullptr && NF == 3 && ls >= 8 &&
+                (1u << (2 * (ls - 5))) > (uint32_t)nsm_ * 8u) {
+                k = 3;
+                a.span = 5;
+            }
             a.ls = ls;
             a.k = k;
-            const uint32_t nb = 1u << (2 * (ls - k));
+            const uint32_t nb = 1u << (2 * (ls - (a.span ? a.span : k)));
             const int ls2 = ls - k, k2 = ls2 < 5 ? ls2 : 5;
             if (ls == L_ && a.list != nullptr) {
                 lk(k_encode_tiles<T, NF>, nsm_ * 8, 256, a);

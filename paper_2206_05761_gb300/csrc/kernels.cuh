@@ -288,6 +288,7 @@ struct EncodeArgs {
     uint32_t* Cb;         // upward closure of the threshold flags
     const DevState* st;   // NULL: buffer 0, always active
     int L, ls, k;         // source level ls; produces levels ls-1 .. ls-k
+    int span = 0;         // a CTA covers 4^span cells of level ls (0: 4^k)
     // Quiescent tiles (first pass only, its tiles are the traversal's):
     // zf[b][t] = 1 when every value of buffer b in tile t, levels ls-k..ls,
     // is +0.  NULL: no skipping.
@@ -420,7 +421,10 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
     __shared__ uint32_t sc[2][8];
     __shared__ Thr<T> sthr[5][NF];    // thresholds of the pass's levels (one load each)
     const uint32_t tile = bid, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    uint32_t cnt = 1u << (2 * (kk - 1));
+    // parents of level ls-1 under the CTA (its block of 4^span cells of
+    // level ls; a pass may stop short of the block's top level)
+    const int span = (ls == a.ls && a.span > kk) ? a.span : kk;
+    uint32_t cnt = 1u << (2 * (span - 1));
     int n = ls - 1;
     {   // level ls-1
         const bool act = tid < cnt;

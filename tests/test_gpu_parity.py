@@ -402,6 +402,15 @@ def test_full_size_terrain_flood_L12_bench_launch_path():
     sim.close()
 
 
+def test_full_sweep_L12_encode_levels():
+    # every tile encoded (HWFV1_FULL_SWEEP) at 4096 x 4096: the first pass
+    # stops after three levels of each 1024-cell block and the next pass
+    # takes the block's top levels; every level, flag and leaf against the
+    # oracle
+    p, f = synth.terrain_flood(L=12, fill=2.0, fill_q=1.0)
+    one_step_parity(dict(p, full_sweep=True), f, exact=False)
+
+
 def test_full_size_wet_domain_one_step():
     # 4096 x 4096 bumpy dam-break: about 16 M wet leaves, more than the
     # shared-face buffer holds, so the update takes its one-pass form
