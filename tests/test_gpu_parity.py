@@ -112,6 +112,23 @@ def test_lake_at_rest_dry_humps():
     one_step_parity(p, f, pre_steps=3)
 
 
+@pytest.mark.parametrize("eta", [0.875, 1.78, 1.95])
+def test_lake_at_rest_table3_levels(eta):
+    # Table 3's free-surface levels over humps that partly emerge: 20 steps
+    # of the graph path against the oracle, bit for bit
+    p, f = synth.lake_at_rest(L=7, eps=1e-3, eta=eta, wet=False)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    sim.advance(max_steps=20)
+    for _ in range(19):
+        ref.step()
+    res = ref.step(want=("leaves",))
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    _compare_fields(sim, ref)
+    assert max(np.abs(ref.qx).max(), np.abs(ref.qy).max()) <= 1e-6
+    sim.close()
+
+
 def test_inflow_basin():
     p, f = synth.inflow_basin(L=6, eps=1e-3, q=0.01)
     one_step_parity(p, f, pre_steps=4)

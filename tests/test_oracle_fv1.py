@@ -234,3 +234,21 @@ def test_dry_bumpy_domain_stays_dry():
         levels = res["leaves"] >> 28
         assert levels.min() < p["L"]          # coarse dry leaves exist
     assert np.all(st.h == 0.0) and np.all(st.qx == 0.0) and np.all(st.qy == 0.0)
+
+
+@pytest.mark.parametrize("eta", [0.875, 1.78, 1.95])
+def test_lake_at_rest_at_table3_free_surface_levels(eta):
+    # Sec. 3.1, Table 3: still water at the three printed free-surface
+    # levels over humps up to 1.4 m (some emerge at the lowest level): the
+    # discharges stay at round-off where the domain is fully wet and small
+    # where humps emerge, and the free surface does not move
+    p, f = synth.lake_at_rest(L=6, eps=1e-3, eta=eta, wet=False)
+    st = oracle.State(p, f)
+    st.run(max_steps=150)
+    qmax = max(np.abs(st.qx).max(), np.abs(st.qy).max())
+    wet = f["h"] > 0
+    if wet.all():
+        assert qmax <= 1e-10
+    else:
+        assert qmax <= 1e-6
+    assert np.abs((st.h + st.z)[st.h > 1e-3] - eta).max() <= 1e-6
