@@ -69,10 +69,11 @@ def test_learned_run_uses_fewer_leaves_at_bounded_cost(trained):
     # drops vary from run to run): never more leaves, bounded error
     assert ml <= mp * 1.001
     assert d_lp <= 2.0 * d_pu + 1e-12
-    # a looser margin drops children for certain, at a bounded cost
-    fm, mm, _ = _run(p, f, t_end, net=net, margin=0.3)
+    # a looser margin (the median level) drops children for certain, at a
+    # bounded cost
+    fm, mm, _ = _run(p, f, t_end, net=net, margin=0.5)
     d_mp = np.abs(fm["h"] - fp["h"]).sum() * cell
-    print("margin 0.3: mean leaves %.0f (%.3f of plain), L1 |learned - plain| = %.3e" % (mm, mm / mp, d_mp))
+    print("margin 0.5: mean leaves %.0f (%.3f of plain), L1 |learned - plain| = %.3e" % (mm, mm / mp, d_mp))
     assert mm < mp
     assert d_mp <= 2.0 * d_pu + 1e-12
 
