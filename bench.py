@@ -154,7 +154,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
 # step in the timed window: mean over the launches of the ncu capture
 # summarised in profiles/terrain_flood_L12_f64_launches.md, valid while
 # kernels.cuh has this SHA-256.
-FV1_WET_TRAFFIC = {"kernels_sha256": "d778917e31b56a95a83365c5eb3c46e1a22fce832a70baa0d32991fee0d9f617",
+FV1_WET_TRAFFIC = {"kernels_sha256": "031354562575dbefa03d530bceae25ec30c3f939376f477f9f2bc300a6aa93a5",
                    "bytes_per_launch": 2889235 + 9541593}
 
 

@@ -2420,9 +2420,6 @@ __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
     __syncthreads();
     prepare_vals(st, a, s_t, s_tend, s_dt, s_smax);
 }
-static __global__ void k_finish(DevState* st, FinishArgs a) {
-    finish_body(st, a);
-}
 
 // Decode-back followed, in its last CTA to finish, by the time advance (one
 // launch instead of two).  decode_body reads the state through L2 only, so
