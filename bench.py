@@ -154,7 +154,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
 # step in the timed window: mean over the launches of the ncu capture
 # summarised in profiles/terrain_flood_L12_f64_launches.md, valid while
 # kernels.cuh has this SHA-256.
-FV1_WET_TRAFFIC = {"kernels_sha256": "031354562575dbefa03d530bceae25ec30c3f939376f477f9f2bc300a6aa93a5",
+FV1_WET_TRAFFIC = {"kernels_sha256": "ce2a3fd4fd7da561af9087d25c298342f2768235a8dda54771d7ef489200726c",
                    "bytes_per_launch": 2889235 + 9541593}
 
 

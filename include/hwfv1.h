@@ -13,7 +13,7 @@
  *                   (Eq. 1-2, Sec. 2.1.3, Sec. 2.2.3)
  *   hwfv1_decode    leaf values back onto the finest grid (Eq. 4 with zero
  *                   details below the leaves) and time advance with the new
- *                   CFL timestep (Algorithm 3 lines 8-9)
+ *                   CFL timestep (end of Algorithm 3's time loop)
  * hwfv1_advance runs that sequence for many steps.
  *
  * Conventions
@@ -117,7 +117,7 @@ typedef struct hwfv1_handle hwfv1_handle;
  * the handle's Morton-ordered hierarchy, encodes the static bed once, and
  * sets t = 0 and dt from the CFL condition on the initial state.  `stream`
  * is a cudaStream_t (NULL = legacy default stream).  Synchronises.
- * Initial discretisation: Algorithm 3 line 2. */
+ * Initial discretisation: the first step of Algorithm 3. */
 hwfv1_status hwfv1_init(const hwfv1_problem* spec, const double* z, const double* h,
                         const double* qx, const double* qy, void* stream,
                         hwfv1_handle** out);
@@ -148,8 +148,8 @@ hwfv1_status hwfv1_step(hwfv1_handle* hd);
 
 /* Decode-back: every finest cell under a coarser leaf takes the leaf's
  * discharges and free surface (Eq. 4 with zero details below leaves);
- * then t += dt and the next dt = CFL * (min CFL bound) (Algorithm 3 lines
- * 8-9), clamped so that no step passes the t_end of hwfv1_advance. */
+ * then t += dt and the next dt = CFL * (min CFL bound) (end of
+ * Algorithm 3's time loop), clamped so that no step passes the t_end of hwfv1_advance. */
 hwfv1_status hwfv1_decode(hwfv1_handle* hd);
 
 /* Run up to max_steps full steps (encode, flag, traverse, step, decode),
@@ -183,7 +183,7 @@ hwfv1_status hwfv1_set_fields(hwfv1_handle* hd, const double* h, const double* q
 hwfv1_status hwfv1_get_leaves(hwfv1_handle* hd, uint32_t* packed, int64_t cap, int64_t* n);
 
 /* Significance bits (device output).  which = 0: threshold flags of
- * h, hu, hv and z (Algorithm 1 line 8); 1: regularised flags used by the
+ * h, hu, hv and z (Algorithm 1's threshold test); 1: regularised flags used by the
  * traversal.  Level n (0..L-1) occupies words [w(n), w(n+1)) with w(n) = n
  * for n <= 3 and 3 + (4^n - 64)/96 above; bit b of word k of level n is
  * the parent with Morton code 32k + b.  `cap_words` must be >= w(L). */

@@ -240,7 +240,7 @@ void orc_decode_all(int L, const double* coarse0, const double* det, double* fin
 }
 
 /* ------------------------------------------------------------------------ */
-/* Significance: threshold flags (Sec. 2.1.2, Algorithm 1 lines 7-8) and    */
+/* Significance: threshold flags (Sec. 2.1.2, Algorithm 1's test) and       */
 /* regularisation (R1, R2).  Flags are bytes, level-major, row-major in a   */
 /* level, levels 0..L-1 (P = (4^L-1)/3 entries).                            */
 /* ------------------------------------------------------------------------ */
@@ -677,7 +677,7 @@ double orc_next_dt(const orc_problem* p, const double* h, const double* qx, cons
 }
 
 /* ------------------------------------------------------------------------ */
-/* One HWFV1 timestep (Algorithm 3, lines 4-9).                             */
+/* One HWFV1 timestep (Algorithm 3, the body of its time loop).             */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {

@@ -2274,7 +2274,7 @@ static __global__ void __launch_bounds__(256) k_decode(DecodeArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// Time advance and next-step scalars (Algorithm 3 lines 8-9)
+// Time advance and next-step scalars (Algorithm 3: t += dt, new CFL dt)
 // ---------------------------------------------------------------------------
 struct FinishArgs {
     const double* inflow_t;
