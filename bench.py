@@ -55,6 +55,10 @@ def parse():
                    help="time the window with HWFV1_FULL_SWEEP (every tile encoded, updated and "
                         "decoded): the MRA kernels at full size, for an ncu launch list")
     a.add_argument("--no-mra", action="store_true")
+    a.add_argument("--only", choices=["ensemble", "learned"],
+                   help="run only this side measurement, print its result, and bracket its timed "
+                        "region (the batched advance; the learned run predicting every step) "
+                        "with the profiler range, for an ncu launch list")
     return a.parse_args()
 
 
@@ -358,10 +362,14 @@ def run_ensemble(args, steps=50):
     choice = ens.autotune(trial_steps=2)
     ens.advance(max_steps=3)
     stream.synchronize()
+    if args.only == "ensemble":
+        torch.cuda.profiler.start()
     e0.record(stream)
     ens.advance(max_steps=steps)
     e1.record(stream)
     stream.synchronize()
+    if args.only == "ensemble":
+        torch.cuda.profiler.stop()
     batch_ms = e0.elapsed_time(e1)
     leaves = sum(ens.member_stats(d)[0] for d in range(len(cases)))
     lps = ens.launches_per_step()
@@ -404,7 +412,7 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     p, f = make(test_seed)
     stream = torch.cuda.Stream()
 
-    def timed(net_, t_end, max_steps, every=1):
+    def timed(net_, t_end, max_steps, every=1, profile=False):
         sim = Simulation(p, f, args.precision, stream=stream)
         if net_ is not None:
             sim.set_skipnet(net_, audit_K=10, margin=0.02, predict_every=every)
@@ -412,10 +420,14 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
         sim.advance(max_steps=0)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if profile:
+            torch.cuda.profiler.start()
         e0.record(stream)
         sim.advance(t_end=t_end, max_steps=max_steps)
         e1.record(stream)
         stream.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
         ms = e0.elapsed_time(e1)
         n, lu, au, wu, kps = sim.counters()
         t = sim.time()[0]
@@ -429,7 +441,7 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     runs = {}
     for every in (1, 4):
         n_l = timed(net, plain["t"], 4 * steps, every)["steps"]
-        runs[every] = timed(net, plain["t"], n_l, every)
+        runs[every] = timed(net, plain["t"], n_l, every, profile=(args.only == "learned" and every == 1))
     H.hwfv1_skipnet_destroy(net)
     cell = 1.0 / (1 << (2 * L))
 
@@ -680,6 +692,11 @@ def main():
                                 "sample": sample},
                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
+        return
+    if args.only is not None:
+        if rank == 0:
+            res = run_ensemble(args) if args.only == "ensemble" else {"bumpy": run_learned(args, "bumpy")}
+            print(json.dumps({args.only: res}))
         return
     if world > 1:
         import torch.distributed as dist
