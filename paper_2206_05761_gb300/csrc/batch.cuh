@@ -67,12 +67,16 @@ static __global__ void __launch_bounds__(256) kb_clear(const DomainPlan<T>* P, c
     clear_body(P[d].clear_w, P[d].clear_n, P[d].st, domain_blk(base, d));
 }
 
+// The bodies take their arguments from a local copy of the domain's plan:
+// read through the plan's global-memory address, every field would be
+// reloaded after each store the body makes (the store could alias it).
+
 template <typename T>
 static __global__ void __launch_bounds__(256) kb_encode(const DomainPlan<T>* P, const uint32_t* base, int D,
                                                         int pass) {
     const int d = find_domain(base, D, blockIdx.x);
-    const DomainPlan<T>& p = P[d];
-    encode_body<T, 3>(p.enc, p.ls[pass], p.kk[pass], blockIdx.x - base[d]);
+    const EncodeArgs<T, 3> a = P[d].enc;
+    encode_body<T, 3>(a, P[d].ls[pass], P[d].kk[pass], blockIdx.x - base[d]);
 }
 
 template <typename T>
@@ -111,33 +115,32 @@ static __global__ void __launch_bounds__(256) kb_trav_write(const DomainPlan<T>*
 template <typename T>
 static __global__ void __launch_bounds__(256) kb_fv1_dry(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
-    fv1_dry_body<T>(P[d].step, domain_blk(base, d));
+    const StepArgs<T> a = P[d].step;
+    fv1_dry_body<T>(a, domain_blk(base, d));
 }
 
 // the shared-face pair of the single-domain path (float64; float32 domains
-// have no face buffer and take the one-pass update inside kb_fv1_update)
+// have no face buffer and take the one-pass update inside kb_fv1_update),
+// launched, as there, in 64-thread blocks
 template <typename T>
-static __global__ void __launch_bounds__(256) kb_fv1_faces(const DomainPlan<T>* P, const uint32_t* base, int D) {
+static __global__ void __launch_bounds__(64) kb_fv1_faces(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
-    fv1_faces_body<T>(P[d].step, domain_blk(base, d));
+    const StepArgs<T> a = P[d].step;
+    fv1_faces_body<T>(a, domain_blk(base, d));
 }
 
 template <typename T>
-static __global__ void __launch_bounds__(256) kb_fv1_update(const DomainPlan<T>* P, const uint32_t* base, int D) {
+static __global__ void __launch_bounds__(64) kb_fv1_update(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
-    fv1_update_body<T>(P[d].step, domain_blk(base, d));
-}
-
-template <typename T>
-static __global__ void __launch_bounds__(256) kb_fv1_wet(const DomainPlan<T>* P, const uint32_t* base, int D) {
-    const int d = find_domain(base, D, blockIdx.x);
-    fv1_wet_body<T>(P[d].step, domain_blk(base, d));
+    const StepArgs<T> a = P[d].step;
+    fv1_update_body<T>(a, domain_blk(base, d));
 }
 
 template <typename T>
 static __global__ void __launch_bounds__(256) kb_decode(const DomainPlan<T>* P, const uint32_t* base, int D) {
     const int d = find_domain(base, D, blockIdx.x);
-    decode_body<T>(P[d].dec, domain_blk(base, d));
+    const DecodeArgs<T> a = P[d].dec;
+    decode_body<T>(a, domain_blk(base, d));
 }
 
 template <typename T>
@@ -289,7 +292,7 @@ class BatchT final : public Batch {
             const uint64_t N = 1ull << (2 * p.L);
             const uint32_t fb = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(1024, N / (256ull * fv1_cells)));
             set(BK_DRY, fb);
-            set(BK_WET, fb);
+            set(BK_WET, 4u * fb);                      // 64-thread blocks, as many threads
             set(BK_DEC, std::min<uint32_t>(p.ntiles, 64u));
             set(BK_FIN, 1u);
         }
@@ -325,8 +328,8 @@ class BatchT final : public Batch {
         kb_trav_scan<T><<<total_[BK_TSCAN], 1024, 0, stream_>>>(d_plans_, base(BK_TSCAN), D);
         kb_trav_write<T><<<total_[BK_TWRITE], 256, 0, stream_>>>(d_plans_, base(BK_TWRITE), D);
         kb_fv1_dry<T><<<total_[BK_DRY], 256, 0, stream_>>>(d_plans_, base(BK_DRY), D);
-        kb_fv1_faces<T><<<total_[BK_WET], 256, 0, stream_>>>(d_plans_, base(BK_WET), D);
-        kb_fv1_update<T><<<total_[BK_WET], 256, 0, stream_>>>(d_plans_, base(BK_WET), D);
+        kb_fv1_faces<T><<<total_[BK_WET], 64, 0, stream_>>>(d_plans_, base(BK_WET), D);
+        kb_fv1_update<T><<<total_[BK_WET], 64, 0, stream_>>>(d_plans_, base(BK_WET), D);
         kb_decode<T><<<total_[BK_DEC], 256, 0, stream_>>>(d_plans_, base(BK_DEC), D);
         kb_finish<T><<<D, 64, 0, stream_>>>(d_plans_, D);
     }

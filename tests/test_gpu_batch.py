@@ -69,3 +69,24 @@ def test_batch_t_end_per_member():
         g = ens.member_fields(d)
         assert np.array_equal(g["h"], ref.h)
     ens.close()
+
+
+def test_batch_float32_matches_single_domain_path():
+    # float32 members have no shared-face buffer: the batched update takes
+    # the one-pass kernel body; every member must equal the single-domain
+    # float32 run bit for bit (fields, leaves, time)
+    from paper_2206_05761_gb300.sim import Ensemble, Simulation
+    cases = _cases()[:4]
+    ens = Ensemble(cases, 32)
+    ens.advance(max_steps=15)
+    for d, (p, f) in enumerate(cases):
+        sim = Simulation(p, f, 32)
+        sim.advance(max_steps=15)
+        g, s = ens.member_fields(d), sim.fields()
+        for k in ("h", "qx", "qy"):
+            assert g[k].dtype == s[k].dtype
+            assert np.array_equal(g[k], s[k]), "member %d field %s" % (d, k)
+        assert np.array_equal(ens.member_leaves(d), sim.leaves()), "member %d leaves" % d
+        assert tuple(ens.member_time(d)) == tuple(sim.time())
+        sim.close()
+    ens.close()
