@@ -638,15 +638,22 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline(args, p, state, t_s, dt_s, sample_steps):
+def cpu_baseline(args, p, state, t_s, dt_s, min_steps, min_seconds=12.0, max_steps=30):
+    """The oracle from the window's start state: steps one at a time until
+    at least min_steps steps and min_seconds of CPU work (at most
+    max_steps)."""
     import oracle
     st = oracle.State(p, state, t=t_s, dt=dt_s)
+    n = 0
     t0 = time.perf_counter()
-    st.run(max_steps=sample_steps)
-    el = time.perf_counter() - t0
-    return {"value": sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    el = 0.0
+    while n < max_steps and (n < min_steps or el < min_seconds):
+        st.run(max_steps=1)
+        n += 1
+        el = time.perf_counter() - t0
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d oracle steps of the same L=%d workload from the same t=%.0f s state "
-                      "(single-threaded C, %.1f s)" % (sample_steps, args.L, t_s, el)}
+                      "(single-threaded C, %.1f s)" % (n, args.L, t_s, el)}
 
 
 def main():
