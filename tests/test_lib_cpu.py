@@ -62,3 +62,54 @@ def test_bad_inflow_rejected():
 def test_null_handle_is_state_error():
     assert H.lib().hwfv1_encode(None) == 7
     assert H.lib().hwfv1_last_error(None) == b"NULL handle"
+
+
+def _batch_init(specs, n, ptrs):
+    """hwfv1_batch_init on host-side descriptions; ptrs[d] is the field
+    pointer of member d (every field), or None.  Returns (status, handle)."""
+    arr = (H.Problem * max(len(specs), 1))(*specs)
+    fields = [(C.c_void_p * max(len(ptrs), 1))(*ptrs) for _ in range(4)]
+    out = C.c_void_p()
+    st = H.lib().hwfv1_batch_init(arr, n, *[C.cast(f, C.POINTER(C.c_void_p)) for f in fields], None, C.byref(out))
+    return st, out.value
+
+
+def _two(p=None):
+    p = p or synth.circular_dam_break(L=3)[0]
+    return [H.make_problem(p), H.make_problem(p)]
+
+
+# A real host buffer stands for a device field: validation fails before any
+# pointer is read.
+_BUF = (C.c_double * 64)()
+
+
+@pytest.mark.parametrize("case", ["empty", "mixed_precision", "flux_match", "null_field", "bad_member"])
+def test_batch_init_rejects_bad_descriptions_without_gpu(case):
+    specs, n, ptrs = _two(), 2, [C.addressof(_BUF)] * 2
+    if case == "empty":
+        n = 0
+    elif case == "mixed_precision":
+        specs[1].precision = 32
+    elif case == "flux_match":
+        specs[0].flags |= 8                  # HWFV1_FLUX_MATCH: single domains only
+    elif case == "null_field":
+        ptrs = [C.addressof(_BUF), None]
+    elif case == "bad_member":
+        specs[1].L = 0
+    st, hd = _batch_init(specs, n, ptrs)
+    assert st == 1 and not hd
+
+
+def test_batch_init_needs_an_output_pointer():
+    specs = _two()
+    arr = (H.Problem * 2)(*specs)
+    f = (C.c_void_p * 2)(C.addressof(_BUF), C.addressof(_BUF))
+    pp = C.cast(f, C.POINTER(C.c_void_p))
+    assert H.lib().hwfv1_batch_init(arr, 2, pp, pp, pp, pp, None, None) == 1
+
+
+def test_null_batch_is_state_error():
+    assert H.lib().hwfv1_batch_advance(None, 1.0, 1) == 7
+    assert H.lib().hwfv1_batch_launches_per_step(None) == 0
+    assert H.lib().hwfv1_batch_last_error(None) == b"NULL batch"
