@@ -113,3 +113,20 @@ def test_null_batch_is_state_error():
     assert H.lib().hwfv1_batch_advance(None, 1.0, 1) == 7
     assert H.lib().hwfv1_batch_launches_per_step(None) == 0
     assert H.lib().hwfv1_batch_last_error(None) == b"NULL batch"
+
+
+def test_network_parameter_count_matches_the_oracle_cnn():
+    # w1[16][4][3][3], b1[16], w2[16][16][3][3], b2[16], w3[5][16][3][3], b3[5]
+    import numpy as np
+    from oracle import cnn
+    params = cnn.init_params(np.random.default_rng(0))
+    assert H.hwfv1_skipnet_num_params() == sum(a.size for a in params) == 3637
+
+
+def test_null_network_arguments_are_rejected_without_gpu():
+    L = H.lib()
+    assert L.hwfv1_skipnet_create(1, None) == 1
+    assert L.hwfv1_skipnet_set_params(None, None, 0) == 1
+    assert L.hwfv1_skipnet_get_params(None, None, 0) == 1
+    assert L.hwfv1_skipnet_forward(None, None, 1, 8, 8, None) == 1
+    L.hwfv1_skipnet_destroy(None)              # a no-op
