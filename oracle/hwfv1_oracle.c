@@ -383,6 +383,16 @@ static void velocity(const orc_cell* c, double tol_h, double* u, double* v) {
     }
 }
 
+/* Two-rarefaction estimate of the star region between the two waves of a
+ * face with both sides wet (reading R-Lc): its normal velocity us and
+ * celerity as.  It is the exact star state of a Riemann problem whose two
+ * waves are rarefactions (the Riemann invariants u + 2a and u - 2a carry
+ * it across them). */
+void orc_star_estimate(double unL, double aL, double unR, double aR, double* us, double* as) {
+    *us = 0.5 * (unL + unR) + aL - aR;
+    *as = 0.5 * (aL + aR) + 0.25 * (unL - unR);
+}
+
 /* HLL flux across one face whose normal points from side L to side R.
  * un/ut are the normal/tangential velocities of each side; F receives
  * (mass, normal momentum, tangential momentum) fluxes.  hLs/hRs return the
@@ -406,8 +416,8 @@ static void hll_face(double g, double tol_h,
     double aL = sqrt(g * hLs), aR = sqrt(g * hRs);
     double SL, SR;
     if (hLs > 0.0 && hRs > 0.0) {               /* two-rarefaction estimate */
-        double us = 0.5 * (unL + unR) + aL - aR;
-        double as = 0.5 * (aL + aR) + 0.25 * (unL - unR);
+        double us, as;
+        orc_star_estimate(unL, aL, unR, aR, &us, &as);
         double a1 = unL - aL, a2 = us - as;
         double b1 = unR + aR, b2 = us + as;
         SL = a1 < a2 ? a1 : a2;

@@ -230,6 +230,16 @@ def pseudo_2d_dam_break(L=7, eps=0.0, h_up=6.0, h_down=2.0, dam_x=10.0):
     return p, _fields(p, eta, z)
 
 
+def ritter_dam_break(L=6, eps=0.0, h0=1.0, water="west", side_m=100.0):
+    """Dam break onto a dry flat bed (Ritter's problem): still water h0 on
+    one half of a square (``water`` = "west" or "east"), dry ground on the
+    other, transmissive sides.  Mirror images of each other."""
+    p = problem(L, lx=side_m, ly=side_m, eps=eps, bc=("transmissive",) * 4)
+    x, _ = centres(p)
+    wet = (x < 0.5 * side_m) if water == "west" else (x > 0.5 * side_m)
+    return p, _fields(p, np.where(wet, h0, 0.0), np.zeros_like(x))
+
+
 def uniform_flow(L=4, h=1.0, u=2.0, manning_n=0.03, eps=0.0):
     """Uniform depth and velocity on a flat bed with transmissive sides and
     Manning friction: the fluxes cancel and only friction acts."""

@@ -162,10 +162,12 @@ def test_hwfv1_dam_break_close_to_uniform():
     assert float(np.mean(np.abs(a.h - b.h))) < 2e-2
 
 
-def test_friction_decay_matches_closed_form():
+@pytest.mark.parametrize("h", [1.0, 2.5, 0.4])
+def test_friction_decay_matches_closed_form(h):
     # uniform flow on a flat bed: fluxes cancel and the semi-implicit Manning
     # step solves du/dt = -k u^2 exactly: 1/u(t) = 1/u0 + k t, k = g n^2 / h^(4/3)
-    h, u0, n = 1.0, 2.0, 0.03
+    # (depths other than 1 tell the Manning exponent apart)
+    u0, n = 2.0, 0.03
     p, f = synth.uniform_flow(L=4, h=h, u=u0, manning_n=n)
     st = oracle.State(p, f)
     st.run(max_steps=200)
@@ -189,6 +191,82 @@ def test_inflow_adds_exact_volume():
     st.run(max_steps=100)
     added = 0.01 * st.t
     assert abs(_volume(st) - v0 - added) <= 1e-12 * _volume(st)
+
+
+def test_inflow_follows_the_piecewise_linear_hydrograph():
+    # R-inflow: each step adds Q(t) dt at its start time t, Q interpolated
+    # linearly between the hydrograph's points (np.interp), and the closed
+    # basin loses nothing; the steps cross a breakpoint of the hydrograph
+    tq, Q = [0.0, 0.2, 1.0], [0.0, 0.03, 0.005]
+    p, f = synth.inflow_basin(L=5, eps=0.0, q=0.01)
+    p = dict(p, inflow=dict(p["inflow"], t=tq, Q=Q))
+    st = oracle.State(p, f)
+    v = _volume(st)
+    while st.t < 0.4:
+        t0 = st.t
+        st.step()
+        v_new = _volume(st)
+        assert abs((v_new - v) - np.interp(t0, tq, Q) * (st.t - t0)) <= 1e-12 * v_new
+        v = v_new
+
+
+def test_depths_stay_non_negative_when_a_cell_drains_through_two_faces():
+    # a shallow cell moving diagonally into dry ground at CFL 1 (u = v = 10
+    # m/s > sqrt(g h): every face upwinds) sends q dt / dx out through each
+    # of its east and north faces, more than it holds; its depth is clamped
+    # at zero and its discharges dropped
+    p = synth.problem(3, lx=8.0, ly=8.0, eps=0.0, cfl=1.0, bc=("transmissive",) * 4)
+    x, _ = synth.centres(p)
+    h = np.zeros_like(x)
+    h[3, 3] = 0.01
+    f = dict(h=h, qx=10.0 * h, qy=10.0 * h, z=np.zeros_like(x))
+    st = oracle.State(p, f)
+    dt, dx = st.dt, p["lx"] / 8
+    assert 0.01 - 2 * 0.1 * dt / dx < 0.0
+    st.step()
+    assert st.h.min() >= 0.0
+    assert st.h[3, 3] == 0.0 and st.qx[3, 3] == 0.0 and st.qy[3, 3] == 0.0
+
+
+def _ritter(x, t, h0, x0):
+    a0 = np.sqrt(G * h0)
+    xi = (x - x0) / t
+    return np.where(xi <= -a0, h0, np.where(xi >= 2 * a0, 0.0, (2 * a0 - xi) ** 2 / (9 * G)))
+
+
+def test_dry_bed_dam_break_mirror_and_ritter():
+    # Ritter's dam break onto a dry bed, with the water on the west and on
+    # the east: the two runs are mirror images (the HLL dry-bed speeds of a
+    # dry left side and of a dry right side agree), every row is the same
+    # (1D flow), and the depth converges to Ritter's solution
+    errs = []
+    for L in (6, 7):
+        out = {}
+        for water in ("west", "east"):
+            p, f = synth.ritter_dam_break(L=L, water=water)
+            st = oracle.State(p, f)
+            st.run(t_end=5.0, uniform=True)
+            assert st.t == 5.0
+            assert np.abs(st.h - st.h[0:1, :]).max() <= 1e-12
+            out[water] = st
+        w, e = out["west"], out["east"]
+        assert np.abs(w.h - e.h[:, ::-1]).max() <= 1e-12
+        assert np.abs(w.qx + e.qx[:, ::-1]).max() <= 1e-12
+        x, _ = synth.centres(w.p)
+        errs.append(float(np.mean(np.abs(w.h - _ritter(x, 5.0, 1.0, 50.0)))))
+    assert errs[1] < errs[0] / 1.3
+
+
+@pytest.mark.parametrize("us, as_, aL, aR", [(0.3, 2.0, 2.5, 3.0), (-1.2, 1.5, 1.7, 4.0), (2.0, 0.5, 3.0, 0.6)])
+def test_star_estimate_exact_for_two_rarefactions(us, as_, aL, aR):
+    # states joined to the star state (us, as) by a left and a right
+    # rarefaction (aL, aR >= as): u + 2a is carried across the left wave and
+    # u - 2a across the right one, so the exact star state is known; the
+    # two-rarefaction estimate must return it
+    uL = us + 2 * as_ - 2 * aL
+    uR = us - 2 * as_ + 2 * aR
+    e_us, e_as = oracle.star_estimate(uL, aL, uR, aR)
+    assert abs(e_us - us) <= 1e-14 * 8 and abs(e_as - as_) <= 1e-14 * 8
 
 
 def test_circular_dam_break_symmetry():
