@@ -20,8 +20,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "hwfv1_oracle.c")
-_OUT_DIR = os.path.join(_HERE, "_build")
+# HWFV1_ORACLE_SRC / HWFV1_ORACLE_BUILD_DIR point the loader at another copy
+# of the C source and build folder: the mutation test plants mistakes in
+# such a copy to show that the pins catch them.
+_SRC = os.environ.get("HWFV1_ORACLE_SRC") or os.path.join(_HERE, "hwfv1_oracle.c")
+_OUT_DIR = os.environ.get("HWFV1_ORACLE_BUILD_DIR") or os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liborc_hwfv1.so")
 _lock = threading.Lock()
 _lib = None
@@ -89,6 +92,7 @@ def lib():
             L.orc_leaves_dft.argtypes = [C.c_int, _u8p, C.POINTER(C.c_uint32), C.c_int64]
             L.orc_leaves_ptt.argtypes = [C.c_int, _u8p, C.POINTER(C.c_int64)]
             L.orc_hll_x.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp]
+            L.orc_star_estimate.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
             L.orc_cfl_rmin.restype = C.c_double
             L.orc_cfl_rmin.argtypes = [C.POINTER(Problem), _dp, _dp, _dp]
             L.orc_next_dt.restype = C.c_double
@@ -251,6 +255,14 @@ def hll_x(g, tol_h, left, right):
     F = np.empty(3)
     lib().orc_hll_x(float(g), float(tol_h), _d(a), _d(b), _d(F))
     return F
+
+
+def star_estimate(unL, aL, unR, aR):
+    """Two-rarefaction estimate (us, as) of the star region of a wet face
+    (hydrostatic reconstruction already applied: a = sqrt(g h*))."""
+    us, as_ = C.c_double(), C.c_double()
+    lib().orc_star_estimate(float(unL), float(aL), float(unR), float(aR), C.byref(us), C.byref(as_))
+    return us.value, as_.value
 
 
 class State:
