@@ -6,7 +6,8 @@ Eq. 3/4 (encode, decode), the threshold test, the regularisation, Algorithms
 inflow, CFL, the decode-back and the matched faces.  Every mutant must build
 and must fail at least one pin of tests/test_oracle_{mra,tree,fv1,match}.py.
 The mutants are built and run on the CPU, in the oracle's git-ignored build
-folder (no GPU)."""
+folder (no GPU).  The CNN oracle of the learned look-ahead gets the same
+treatment against its own pins, in this process."""
 import concurrent.futures as cf
 import os
 import shutil
@@ -103,3 +104,51 @@ def test_every_planted_mistake_fails_a_pin():
         res = list(ex.map(lambda m: _try(m, source), MUTANTS))
     bad = [(n, why) for n, why in res if why is not None]
     assert not bad, bad
+
+
+# The CNN oracle (oracle/cnn.py, numpy): mutants run in this process against
+# the pins of tests/test_oracle_cnn.py.
+CNN_MUTANTS = [
+    ("padding_offset", "    xp[:, :, 1:H + 1, 1:W + 1] = x\n    y = np.zeros", "    xp[:, :, 0:H, 0:W] = x\n    y = np.zeros"),
+    ("convolution_not_correlation", 'y += np.einsum("oc,bchw->bohw", w[:, :, di, dj], patch)',
+     'y += np.einsum("oc,bchw->bohw", w[:, :, 2 - di, 2 - dj], patch)'),
+    ("no_bias", "y = np.zeros((B, w.shape[0], H, W)) + b[None, :, None, None]", "y = np.zeros((B, w.shape[0], H, W))"),
+    ("no_first_relu", "a1 = np.maximum(z1, 0.0)", "a1 = z1"),
+    ("no_second_relu", "a2 = np.maximum(z2, 0.0)", "a2 = z2"),
+    ("softmax_over_all", "p = e / e.sum(axis=1, keepdims=True)", "p = e / e.sum()"),
+    ("loss_per_image", "loss = -np.sum(onehot * np.log(p)) / npix", "loss = -np.sum(onehot * np.log(p)) / B"),
+    ("dlogits_sign", "return loss, (p - onehot) / npix", "return loss, (onehot - p) / npix"),
+    ("dlogits_per_image", "return loss, (p - onehot) / npix", "return loss, (p - onehot) / B"),
+    ("no_second_relu_mask", "dz2 = da2 * (z2 > 0)", "dz2 = da2"),
+    ("no_first_relu_mask", "dz1 = da1 * (z1 > 0)", "dz1 = da1"),
+    ("weight_gradient_transposed", "            patch = xp[:, :, di:di + H, dj:dj + W]\n            dw[",
+     "            patch = xp[:, :, dj:dj + H, di:di + W]\n            dw["),
+    ("input_gradient_flipped", 'dxp[:, :, di:di + H, dj:dj + W] += np.einsum("oc,bohw->bchw", w[:, :, di, dj], dy)',
+     'dxp[:, :, di:di + H, dj:dj + W] += np.einsum("oc,bohw->bchw", w[:, :, 2 - di, 2 - dj], dy)'),
+    ("bias_gradient_scale", "db = dy.sum(axis=(0, 2, 3))", "db = dy.sum(axis=(0, 2, 3)) * 0.5"),
+    ("layer_input_before_relu", "da1, dw2, db2 = conv3x3_backward(a1, w2, dz2)", "da1, dw2, db2 = conv3x3_backward(z1, w2, dz2)"),
+]
+
+
+def test_every_planted_mistake_in_the_cnn_oracle_fails_a_pin(monkeypatch):
+    import types
+    import test_oracle_cnn as pins
+    with open(os.path.join(ROOT, "oracle", "cnn.py")) as fh:
+        source = fh.read()
+    checks = [getattr(pins, n) for n in sorted(dir(pins)) if n.startswith("test_")]
+    survivors = []
+    for name, before, after in CNN_MUTANTS:
+        assert source.count(before) == 1, "mutation site of %s not found once" % name
+        mod = types.ModuleType("cnn_mutant")
+        exec(compile(source.replace(before, after), "cnn_mutant", "exec"), mod.__dict__)
+        monkeypatch.setattr(pins, "cnn", mod)
+        caught = False
+        for check in checks:
+            try:
+                check()
+            except AssertionError:
+                caught = True
+                break
+        if not caught:
+            survivors.append(name)
+    assert not survivors, survivors
