@@ -28,7 +28,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "adaptive steps/s at L=12 (terrain flood, 4096x4096)"
+def metric(L):
+    return "adaptive steps/s at L=%d (terrain flood, %dx%d)" % (L, 1 << L, 1 << L)
 UNIT = "steps/s"
 
 
@@ -691,10 +692,13 @@ def main():
         v = k / el
         sample = ("%d oracle steps of the L=%d workload from the t=%.0f s state after 1 warm-up "
                   "step (single-threaded C, %.1f s)" % (k, args.L, t_s, el))
-        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+        cfg = config_dict(args)
+        if t_s == 0.0:
+            cfg["window"] = "K steps from the dry start at t=0 (no GPU here to reach the t=%.0f s state)" % args.t_spin
+        out = {"impl": "reference", "metric": metric(args.L), "value": v, "unit": UNIT, "n_gpus": 0,
                "steps": k, "warmup": 1, "ms_per_step": 1e3 * el / k,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": config_dict(args),
+               "data": "synthetic", "config": cfg,
                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample},
                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -722,7 +726,7 @@ def main():
     roof = roofline(dom, ph[dom], r, args, pk, src)
     e2e_val = world * args.steps / e2e_s
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric(args.L), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 64 else "f32",
         "data": "synthetic", "config": config_dict(args),
