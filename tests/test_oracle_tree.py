@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -170,3 +171,38 @@ def test_prediction_refines_one_level_below_threshold_tree():
     leaves = _unpack(L, oracle.leaves_dft(L, S))
     expect = [oracle.zindex(3, c) for c in range(16)] + [oracle.zindex(1, c) for c in (1, 2, 3)]
     assert leaves == expect
+
+
+def test_subtrees_under_leaves_on_a_flat_bed_encode_to_the_leaf_value():
+    # After a step, R-decode hands every leaf's new (h, hu, hv) to all the
+    # finest cells under it; on a flat bed the depth too is constant there.
+    # Re-encoding then gives the leaf's value at every level of its subtree
+    # (the average of four equal values is that value, bit for bit) and +0
+    # for every detail: the exactness an encode restricted to the tree
+    # relies on.
+    p, f = synth.pseudo_2d_dam_break(L=6, eps=1e-3)
+    st = oracle.State(p, f)
+    for _ in range(30):
+        st.step()
+    res = st.step(want=("leaves",))
+    L = p["L"]
+    checked = 0
+    for q in (st.h, st.qx, st.qy):
+        hier, det = oracle.encode(L, q)
+        for pk in res["leaves"]:
+            n, code = int(pk) >> 28, int(pk) & 0x0FFFFFFF
+            if n == L:
+                continue
+            i, j = oracle.demorton(code)
+            v = q[j << (L - n), i << (L - n)]
+            for m in range(n, L + 1):
+                w = 1 << (m - n)
+                blk = oracle.level(hier, m)[j * w:(j + 1) * w, i * w:(i + 1) * w]
+                assert np.all(blk.view(np.uint64) == np.float64(v).view(np.uint64))
+                if m < L:
+                    s = 1 << m
+                    rows = [oracle.level_start(m) + jj * s + ii
+                            for jj in range(j * w, (j + 1) * w) for ii in range(i * w, (i + 1) * w)]
+                    assert np.all(det[rows] == 0.0)
+            checked += 1
+    assert checked > 30
