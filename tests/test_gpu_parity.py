@@ -228,6 +228,36 @@ def test_trajectory_circular_dam_break_100_steps():
     sim.close()
 
 
+@pytest.mark.parametrize("water", ["west", "east"])
+def test_dry_bed_dam_break_trajectory(water):
+    # Ritter's dam break onto a dry flat bed, with the water on either side:
+    # the dry-bed HLL speeds of both orientations, 40 steps of the graph path
+    p, f = synth.ritter_dam_break(L=6, eps=1e-3, water=water)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    sim.advance(max_steps=40)
+    for _ in range(39):
+        ref.step()
+    res = ref.step(want=("leaves",))
+    assert np.array_equal(sim.leaves(), res["leaves"])
+    _compare_fields(sim, ref)
+    t, dt, steps = sim.time()
+    assert t == ref.t and dt == ref.dt and steps == 40
+    sim.close()
+
+
+def test_cell_draining_through_two_faces_is_clamped_like_the_oracle():
+    # CFL 1: a shallow cell moving diagonally into dry ground loses more than
+    # it holds in one step; both sides clamp its depth at zero
+    p = synth.problem(3, lx=8.0, ly=8.0, eps=0.0, cfl=1.0, bc=("transmissive",) * 4)
+    x, _ = synth.centres(p)
+    h = np.zeros_like(x)
+    h[3, 3] = 0.01
+    f = dict(h=h, qx=10.0 * h, qy=10.0 * h, z=np.zeros_like(x))
+    res = one_step_parity(p, f)
+    assert res["num_leaves"] == 64
+
+
 def test_trajectory_in_multi_step_graphs():
     # advances of 37 steps: two 16-step graph launches and five single-step
     # ones each, against the oracle's loop
