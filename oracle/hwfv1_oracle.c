@@ -44,7 +44,9 @@
  *           depths at its two faces (Audusse et al. 2004), which keeps a
  *           lake at rest still also next to dry ground; a face side with
  *           reconstructed depth below tol_h is dry (depth 0); cell
- *           velocities are q*(1/h) for h >= tol_h, else 0.
+ *           velocities are q*(1/h) for h >= tol_h, else 0.  After the
+ *           update a negative depth becomes 0 and a cell left below tol_h
+ *           loses its discharges.
  *  R-fric   Manning friction by semi-implicit splitting after the flux
  *           update: q <- q * (1/D), D = 1 + dt*g*nM^2*|u|/(h*cbrt(h)).
  *  R-cfl    dt = CFL * min over wet leaves (h >= tol_h) of
