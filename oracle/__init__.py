@@ -162,16 +162,6 @@ def zindex(n, code):
     return int(lib().orc_zindex(int(n), int(code)))
 
 
-def morton_map(n):
-    """Array m[j, i] = Morton code of cell (i, j) of a 2^n x 2^n level."""
-    s = 1 << n
-    out = np.empty((s, s), dtype=np.int64)
-    f = lib().orc_morton
-    for j in range(s):
-        for i in range(s):
-            out[j, i] = f(i, j)
-    return out
-
 
 def encode_parent(c):
     c = np.ascontiguousarray(c, dtype=np.float64)
@@ -283,8 +273,6 @@ class State:
     def next_dt(self):
         return float(lib().orc_next_dt(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy)))
 
-    def cfl_rmin(self):
-        return float(lib().orc_cfl_rmin(C.byref(self.cp), _d(self.h), _d(self.qx), _d(self.qy)))
 
     def step(self, dt=None, want=()):
         """One HWFV1 step of size dt (default: the current dt).  `want` may
