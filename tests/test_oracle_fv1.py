@@ -301,6 +301,29 @@ def test_dt_from_cfl_and_dry_default():
     assert st.dt == p["dt_max"]
 
 
+@pytest.mark.parametrize("dt_max", [1e-3, 2.5e-4])
+def test_wet_cfl_step_is_capped_at_dt_max(dt_max):
+    # R-cfl: a wet step is min(CFL * bound, dt_max).  The dam-break's CFL
+    # step at L=4 is 0.5 * (1/16) / sqrt(2 g) = 7.06e-3 s, above both caps,
+    # so the initial step and every step after it equal the cap exactly;
+    # the time then advances by the cap per step
+    p, f = synth.circular_dam_break(L=4)
+    cfl_dt = 0.5 * (1.0 / 16) / np.sqrt(2.0 * G)
+    assert cfl_dt > 5 * dt_max
+    p = dict(p, dt_max=dt_max)
+    st = oracle.State(p, f)
+    assert st.dt == dt_max
+    t = 0.0
+    for _ in range(3):
+        st.step()
+        t += dt_max
+        assert st.dt == dt_max
+        assert st.t == t
+    # above the CFL step the cap plays no part: the uncapped value returns
+    st2 = oracle.State(dict(p, dt_max=1.0), f)
+    assert st2.dt == pytest.approx(cfl_dt, rel=1e-15)
+
+
 def test_dry_bumpy_domain_stays_dry():
     # a dry coarse leaf hands its depth (0) down unchanged: no water appears
     # in the hollows of the bed

@@ -57,6 +57,7 @@ MUTANTS = [
     ("hydrograph_weight", "(p->inflow_Q[k + 1] - p->inflow_Q[k]) * w", "(p->inflow_Q[k + 1] - p->inflow_Q[k]) * (1.0 - w)"),
     ("cfl_celerity", "    double a = sqrt(p->g * h);\n", "    double a = sqrt(h);\n"),
     ("cfl_number", "double dt = p->cfl * r;", "double dt = r;"),
+    ("cfl_wet_cap", "return dt < p->dt_max ? dt : p->dt_max;", "return dt < INFINITY ? dt : p->dt_max;"),
     ("cfl_spacing", "double dx = ldexp(p->lx, -p->L), dy = ldexp(p->ly, -p->L);\n    double rh",
      "double dx = ldexp(p->lx, -p->L + 1), dy = ldexp(p->ly, -p->L + 1);\n    double rh"),
     ("decode_hands_down_depth", "int restore = n < L && hl >= p->tol_h;", "int restore = 0;"),
