@@ -358,9 +358,15 @@ void hwfv1_batch_destroy(hwfv1_batch* b);
  *   num_leaves  device output, one uint32: the number of leaves (may exceed
  *               cap, so the caller can tell the list was cut)
  *   stream      cudaStream_t the three kernels run on (asynchronous)
- * No call allocates memory.  The first call on each device looks up the
- * scratch array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the scratch, so calls
+ * No call allocates memory.  Outside a stream capture every call looks up
+ * the scratch array's device address in the current context
+ * (cudaGetSymbolAddress, a host-side query that allocates nothing), so a
+ * context that was reset or replaced between calls gets the right address;
+ * while `stream` is capturing, the address of the last uncaptured call on
+ * that device is used, so make the first call on each device before any
+ * stream capture.  If an error from an earlier, unrelated call is pending
+ * (cudaPeekAtLastError), the call launches nothing, leaves that error
+ * pending and returns HWFV1_ERR_CUDA.  All calls share the scratch, so calls
  * that overlap on the GPU (different streams or devices' contexts running
  * concurrently on one device) race; serialise them.  Every scratch word a
  * call reads is written by that call first, so no clearing is needed

@@ -9,10 +9,34 @@ y[o, i, j] = b[o] + sum_{c, di, dj} w[o, c, di+1, dj+1] * x[c, i+di, j+dj]),
 ReLU after the first two, softmax cross-entropy on the last (one class per
 pixel), averaged over the pixels.  Arrays are channel-first per image:
 x[batch, channel, row, col].
+
+BF16 operands: the network's stated precision is BF16 weights and
+activations with higher-precision accumulation.  `forward` and `backward`
+take an optional rounding `rnd` (`bf16` below) applied to every operand of
+a convolution that the network holds in BF16: the two hidden activations in
+the forward pass, the loss gradient and the two masked hidden gradients in
+the backward pass (the weights and the input are already BF16 values when
+they are given).  Every other operation stays in float64.  Without `rnd`
+the network is evaluated in plain float64.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+def bf16(a):
+    """Round to bfloat16 (1 sign, 8 exponent, 7 stored significand bits), as
+    a float32 value is converted: to float32 first (nearest, ties to even),
+    then the low 16 bits of the float32 pattern dropped with round to
+    nearest, ties to even (finite inputs in float32's normal or subnormal
+    range).  Returned as float64."""
+    f = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    keep = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return keep.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _exact(a):
+    return a
 
 
 def conv3x3(x, w, b):
@@ -44,13 +68,14 @@ def conv3x3_backward(x, w, dy):
     return dxp[:, :, 1:H + 1, 1:W + 1], dw, db
 
 
-def forward(params, x):
-    """Returns (logits, cache)."""
+def forward(params, x, rnd=None):
+    """Returns (logits, cache); `rnd` rounds the hidden activations."""
+    rnd = rnd or _exact
     w1, b1, w2, b2, w3, b3 = params
     z1 = conv3x3(x, w1, b1)
-    a1 = np.maximum(z1, 0.0)
+    a1 = rnd(np.maximum(z1, 0.0))
     z2 = conv3x3(a1, w2, b2)
-    a2 = np.maximum(z2, 0.0)
+    a2 = rnd(np.maximum(z2, 0.0))
     z3 = conv3x3(a2, w3, b3)
     return z3, (x, z1, a1, z2, a2)
 
@@ -69,14 +94,16 @@ def loss_and_dlogits(logits, labels):
     return loss, (p - onehot) / npix
 
 
-def backward(params, cache, dlogits):
-    """Gradients (dw1, db1, dw2, db2, dw3, db3) of the loss."""
+def backward(params, cache, dlogits, rnd=None):
+    """Gradients (dw1, db1, dw2, db2, dw3, db3) of the loss; `rnd` rounds
+    the loss gradient and the masked hidden gradients."""
+    rnd = rnd or _exact
     w1, b1, w2, b2, w3, b3 = params
     x, z1, a1, z2, a2 = cache
-    da2, dw3, db3 = conv3x3_backward(a2, w3, dlogits)
-    dz2 = da2 * (z2 > 0)
+    da2, dw3, db3 = conv3x3_backward(a2, w3, rnd(dlogits))
+    dz2 = rnd(da2 * (z2 > 0))
     da1, dw2, db2 = conv3x3_backward(a1, w2, dz2)
-    dz1 = da1 * (z1 > 0)
+    dz1 = rnd(da1 * (z1 > 0))
     _, dw1, db1 = conv3x3_backward(x, w1, dz1)
     return dw1, db1, dw2, db2, dw3, db3
 

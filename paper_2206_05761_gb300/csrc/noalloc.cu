@@ -26,9 +26,11 @@ constexpr uint32_t kMaxTiles = 1u << (2 * (kNoAllocMaxL - kNoAllocKt));   // 163
 // Scratch shared by every call on a device: counts at [0, kMaxTiles),
 // offsets at [kMaxTiles, 2*kMaxTiles).  Host code must not pass this name
 // to a kernel: on the host it is only a stand-in for the symbol, so its
-// device address is looked up once per device below.
+// device address is looked up (below) and passed instead.
 static __device__ __align__(256) uint32_t g_scratch[2 * kMaxTiles];
 
+// Last address looked up per device, used only while the caller's stream
+// is capturing a graph (a symbol lookup is not made during a capture).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t* g_scratch_ptr[kMaxDevices] = {};
@@ -70,19 +72,27 @@ __global__ void __launch_bounds__(256) k_write_noalloc(const uint32_t* __restric
     }
 }
 
-// Device address of g_scratch on the current device, looked up on the first
-// call for that device.
-cudaError_t scratch_on_current_device(uint32_t** out) {
+// Device address of g_scratch in the current context.  Outside a stream
+// capture it is looked up on every call (a host-side query that allocates
+// nothing), so a context that was reset or replaced since the last call is
+// never handed a stale address.  During a capture the last address looked
+// up on this device is used; a capture needs one earlier uncaptured call.
+cudaError_t scratch_address(cudaStream_t st, uint32_t** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+    } else if (!g_scratch_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -96,16 +106,21 @@ extern "C" hwfv1_status hwfv1_traverse_noalloc(const uint32_t* sig_bits, int32_t
     using namespace hwfv1;
     if (!sig_bits || !leaves || !num_leaves || cap < 0) return HWFV1_ERR_INVALID_SPEC;
     if (L < 1 || L > kNoAllocMaxL) return HWFV1_ERR_INVALID_SPEC;   // scratch holds L <= 12
-    uint32_t* scratch = nullptr;
-    if (scratch_on_current_device(&scratch) != cudaSuccess) return HWFV1_ERR_CUDA;
+    // an error left pending by an earlier, unrelated call stays pending for
+    // its owner: this call launches nothing and reports HWFV1_ERR_CUDA
+    if (cudaPeekAtLastError() != cudaSuccess) return HWFV1_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t* scratch = nullptr;
+    if (scratch_address(st, &scratch) != cudaSuccess) return HWFV1_ERR_CUDA;
     const int kt = L < kNoAllocKt ? L : kNoAllocKt;
     const uint32_t ntiles = 1u << (2 * (L - kt));
     uint32_t* counts = scratch;
     uint32_t* offs = scratch + kMaxTiles;
     // every count and offset the call reads is written by the call itself
     k_trav_count_walk<<<ntiles, 256, 0, st>>>(sig_bits, counts, L, kt, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return HWFV1_ERR_CUDA;
     k_scan_noalloc<<<1, 1024, 0, st>>>(counts, offs, ntiles, num_leaves);
+    if (cudaGetLastError() != cudaSuccess) return HWFV1_ERR_CUDA;
     k_write_noalloc<<<ntiles, 256, 0, st>>>(sig_bits, offs, leaves, (uint64_t)cap, L, kt);
     return cudaGetLastError() == cudaSuccess ? HWFV1_OK : HWFV1_ERR_CUDA;
 }

@@ -114,20 +114,25 @@ CNN_MUTANTS = [
     ("convolution_not_correlation", 'y += np.einsum("oc,bchw->bohw", w[:, :, di, dj], patch)',
      'y += np.einsum("oc,bchw->bohw", w[:, :, 2 - di, 2 - dj], patch)'),
     ("no_bias", "y = np.zeros((B, w.shape[0], H, W)) + b[None, :, None, None]", "y = np.zeros((B, w.shape[0], H, W))"),
-    ("no_first_relu", "a1 = np.maximum(z1, 0.0)", "a1 = z1"),
-    ("no_second_relu", "a2 = np.maximum(z2, 0.0)", "a2 = z2"),
+    ("no_first_relu", "a1 = rnd(np.maximum(z1, 0.0))", "a1 = rnd(z1)"),
+    ("no_second_relu", "a2 = rnd(np.maximum(z2, 0.0))", "a2 = rnd(z2)"),
     ("softmax_over_all", "p = e / e.sum(axis=1, keepdims=True)", "p = e / e.sum()"),
     ("loss_per_image", "loss = -np.sum(onehot * np.log(p)) / npix", "loss = -np.sum(onehot * np.log(p)) / B"),
     ("dlogits_sign", "return loss, (p - onehot) / npix", "return loss, (onehot - p) / npix"),
     ("dlogits_per_image", "return loss, (p - onehot) / npix", "return loss, (p - onehot) / B"),
-    ("no_second_relu_mask", "dz2 = da2 * (z2 > 0)", "dz2 = da2"),
-    ("no_first_relu_mask", "dz1 = da1 * (z1 > 0)", "dz1 = da1"),
+    ("no_second_relu_mask", "dz2 = rnd(da2 * (z2 > 0))", "dz2 = rnd(da2)"),
+    ("no_first_relu_mask", "dz1 = rnd(da1 * (z1 > 0))", "dz1 = rnd(da1)"),
     ("weight_gradient_transposed", "            patch = xp[:, :, di:di + H, dj:dj + W]\n            dw[",
      "            patch = xp[:, :, dj:dj + H, di:di + W]\n            dw["),
     ("input_gradient_flipped", 'dxp[:, :, di:di + H, dj:dj + W] += np.einsum("oc,bohw->bchw", w[:, :, di, dj], dy)',
      'dxp[:, :, di:di + H, dj:dj + W] += np.einsum("oc,bohw->bchw", w[:, :, 2 - di, 2 - dj], dy)'),
     ("bias_gradient_scale", "db = dy.sum(axis=(0, 2, 3))", "db = dy.sum(axis=(0, 2, 3)) * 0.5"),
     ("layer_input_before_relu", "da1, dw2, db2 = conv3x3_backward(a1, w2, dz2)", "da1, dw2, db2 = conv3x3_backward(z1, w2, dz2)"),
+    ("bf16_no_tie_to_even", "keep = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000", "keep = (f + 0x8000) & 0xFFFF0000"),
+    ("bf16_truncates", "keep = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000", "keep = f & 0xFFFF0000"),
+    ("bf16_hidden_gradient_not_rounded", "dz1 = rnd(da1 * (z1 > 0))", "dz1 = da1 * (z1 > 0)"),
+    ("bf16_loss_gradient_not_rounded", "conv3x3_backward(a2, w3, rnd(dlogits))", "conv3x3_backward(a2, w3, dlogits)"),
+    ("bf16_activation_not_rounded", "a2 = rnd(np.maximum(z2, 0.0))", "a2 = np.maximum(z2, 0.0)"),
 ]
 
 
