@@ -5,14 +5,18 @@ over a 10 km square, seeded 1/f^2 DEM with a carved channel, triangular
 inflow hydrograph peaking at 500 m^3/s, Manning n = 0.03, eps = 1e-3,
 float64 unless --precision 32).  A step is one pass of the whole hot path:
 encode + flag + regularise + traverse/compact + FV1 update + decode-back +
-time advance.  The state (about 1 GB) is larger than L2, so no flush is
-needed between steps.
+time advance.  The timed window starts from a generator-built state at the
+hydrograph peak (t = 1800 s, the channel running at its normal depth, the
+rest of the domain dry), the same state for both arms; the state (about
+1 GB) is larger than L2, so no flush is needed between steps.
 
 Prints one JSON line: steps/s of the timed window (value), the same through
 the C ABI with host buffers (e2e), the roofline of the wet-leaf update, the
-oracle's rate (cpu_baseline), clocks, and the side measurements (float32,
-uniform FV1, the conservative variant, the MRA at full size, the batched
-ensemble, the learned look-ahead, the pseudo-2D dam-break).
+oracle's rate on one core and on all cores (cpu_baseline), clocks, and the
+side measurements (float32 with its error against the float64 oracle,
+uniform FV1, the conservative variant, the MRA at full size, the whole
+simulated hour from the dry start, the small and mid-size dam-breaks, the
+batched ensemble, the learned subtree skip, the pseudo-2D dam-break).
 """
 from __future__ import annotations
 
@@ -44,9 +48,6 @@ def parse():
     a.add_argument("--t-spin", type=float, default=1800.0,
                    help="simulated seconds run before the timed window (the hydrograph peak)")
     a.add_argument("--t-full", type=float, default=3600.0, help="end of the whole-run measurement")
-    a.add_argument("--fill", type=float, default=0.0,
-                   help="start with the channel this deep (m, 1 m^2/s eastward) instead of dry; "
-                        "a wet-channel case for profiling with --t-spin 0")
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--no-ensemble", action="store_true")
     a.add_argument("--no-learned", action="store_true")
@@ -56,6 +57,10 @@ def parse():
                    help="time the window with HWFV1_FULL_SWEEP (every tile encoded, updated and "
                         "decoded): the MRA kernels at full size, for an ncu launch list")
     a.add_argument("--no-mra", action="store_true")
+    a.add_argument("--no-spinup", action="store_true",
+                   help="skip the whole-hour run from the dry start and its t_spin window")
+    a.add_argument("--no-configs", action="store_true",
+                   help="skip the circular L=6 and bumpy L=10 dam-break measurements")
     a.add_argument("--only", choices=["ensemble", "learned"],
                    help="run only this side measurement, print its result, and bracket its timed "
                         "region (the batched advance; the learned run predicting every step) "
@@ -63,21 +68,38 @@ def parse():
     return a.parse_args()
 
 
-def workload(L, fill=0.0):
+def workload(L):
+    """The terrain flood from its dry start at t = 0."""
     import synth
-    return synth.terrain_flood(L=L, fill=fill, fill_q=1.0 if fill > 0 else 0.0)
+    return synth.terrain_flood(L=L)
+
+
+# The timed window's start state (synth.terrain_flood_peak): the hydrograph
+# peak (500 m^3/s through the 60 m channel, 8.33 m^2/s) with the channel
+# running at the Manning normal depth for that discharge on the 0.1 % tilt,
+# q = h^(5/3) S^(1/2) / n: h = (8.33 * 0.03 / 0.001^0.5)^(3/5) = 3.45 m; the
+# rest of the domain dry.
+WINDOW_T = 1800.0
+WINDOW_FILL_M = 3.45
+WINDOW_FILL_Q = 8.33
+
+
+def window_state(L):
+    """(problem, fields, t) of the timed window; built by the seeded
+    generator, so both arms and the parity tests start from the same state."""
+    import synth
+    return synth.terrain_flood_peak(L=L, depth=WINDOW_FILL_M, q=WINDOW_FILL_Q)
 
 
 def config_dict(args, extra=None):
     d = {"workload": "terrain_flood", "L": args.L, "finest_cells": 1 << (2 * args.L),
          "domain_m": 10000.0, "eps": 1e-3, "manning_n": 0.03, "inflow_peak_m3s": 500.0,
          "precision": args.precision, "simulated_s": 3600.0,
-         "window": "K steps from the state at t=%.0f s (hydrograph peak), reached from the dry "
-                   "start at t=0 by the GPU path" % args.t_spin,
+         "window": "K steps from the generator-built state at t=%.0f s (hydrograph peak): channel "
+                   "at its normal depth %.2f m with %.2f m^2/s downstream, the rest dry"
+                   % (WINDOW_T, WINDOW_FILL_M, WINDOW_FILL_Q),
          "l2_policy": "state (>1 GB) larger than L2; no flush",
          "parallelism": "replicas" if args.gpus > 1 else "single"}
-    if args.fill > 0:
-        d["fill_m"] = args.fill
     if args.full_sweep:
         d["full_sweep"] = True
     if extra:
@@ -102,7 +124,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -156,8 +178,8 @@ FV1_WET_FLOP_PER_LEAF = 294
 # 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the wet-leaf update (k_fv1_faces + k_fv1_update) of one
-# step in the timed window: mean over the launches of the ncu capture
-# summarised in profiles/terrain_flood_L12_f64_launches.md, valid while
+# step in the timed window: mean over the launches of the window's ncu
+# launch list (the committed summary under profiles/), valid while
 # kernels.cuh has this SHA-256.
 FV1_WET_TRAFFIC = {"kernels_sha256": "ce2a3fd4fd7da561af9087d25c298342f2768235a8dda54771d7ef489200726c",
                    "bytes_per_launch": 2889235 + 9541593}
@@ -203,15 +225,16 @@ def advance_to(sim, t_end, chunk=2000):
 
 
 def spin_up(args, stream):
-    """The workload from t = 0: the state at t_spin (host float64 arrays,
-    time, dt) and, run on to t_full, the whole-run statistics."""
+    """The workload from its dry start at t = 0 on the GPU path: the whole
+    simulated hour (device time, steps, leaves) and the steps/s of a K-step
+    window from the state the run reaches at t_spin."""
     import torch
     from paper_2206_05761_gb300.sim import Simulation
-    p, f = workload(args.L, args.fill)
+    p, f = workload(args.L)
     sim = Simulation(p, f, args.precision, stream=stream)
     sim.counters()                               # captures the step graph
-    out = {}
     halves = []
+    window = None
     for t_end in (args.t_spin, args.t_full):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0 = sim.counters()
@@ -221,18 +244,23 @@ def spin_up(args, stream):
         stream.synchronize()
         c1 = sim.counters()
         halves.append((e0.elapsed_time(e1), [x1 - x0 for x0, x1 in zip(c0, c1)]))
-        if not out:
+        if window is None:
             t, dt, n = sim.time()
-            out = {"fields": sim.fields(), "t": t, "dt": dt, "steps": n, "z": f["z"]}
+            window = {"t": t, "dt": dt, "steps_to_reach": n, "fields": sim.fields(), "z": f["z"]}
+    sim.close()
     ms = sum(h[0] for h in halves)
     tot = [sum(h[1][i] for h in halves) for i in range(4)]
-    out["full_run"] = {
+    full = {
         "t_end_s": args.t_full, "steps": tot[0], "device_s": ms / 1e3,
         "steps_per_s": tot[0] / max(ms / 1e3, 1e-9), "mean_leaves": tot[1] / max(tot[0], 1),
         "active_fraction": tot[2] / max(tot[1], 1), "wet_fraction": tot[3] / max(tot[1], 1),
-        "note": "t = 0 to t_end_s in one run, host reads the time every <= 2000 steps"}
-    sim.close()
-    return p, out
+        "note": "dry start at t = 0 to t_end_s in one run, host reads the time every <= 2000 steps"}
+    # the same K-step window from the state this run reached at t_spin
+    st = {"z": window["z"], **window["fields"]}
+    w = time_precision(args, args.precision, p, st, window["t"], window["dt"], args.steps)
+    w.update(t_start_s=window["t"], steps_to_reach=window["steps_to_reach"],
+             note="K steps from the state the GPU run reached at t=%.0f s from the dry start" % args.t_spin)
+    return full, w
 
 
 def run_ours(args, rank, world):
@@ -243,21 +271,23 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
     stream = torch.cuda.Stream()
     dev = torch.device("cuda")
-    p, snap = spin_up(args, stream)
+    p, f, t_s = window_state(args.L)
     if args.full_sweep:
         p = dict(p, full_sweep=True)
     N = 1 << (2 * args.L)
-    t_s, dt_s = snap["t"], snap["dt"]
-    state = {"z": snap["z"], **snap["fields"]}
-
-    # ---- end-to-end through the C ABI with host buffers: the state at t_spin
-    # from pinned host memory -> init -> K steps -> fields back to the host
+    state = {k: f[k] for k in ("z", "h", "qx", "qy")}
+    spec = H.make_problem(p, args.precision)
     host = {k: torch.from_numpy(np.ascontiguousarray(state[k]).reshape(-1)).pin_memory()
             for k in ("z", "h", "qx", "qy")}
     outs = {k: torch.empty(N, dtype=torch.float64).pin_memory() for k in ("h", "qx", "qy")}
     dbufs = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("z", "h", "qx", "qy")}
-    spec = H.make_problem(p, args.precision)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()                       # covers the e2e trials, the warm-up and the timed window
+
+    # ---- end-to-end through the C ABI with host buffers: the window's state
+    # from pinned host memory -> init -> K steps -> fields back to the host
     e2e_trials = []
+    dt_s = None
     for _ in range(3):                      # three whole trials; the median is reported
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -265,6 +295,8 @@ def run_ours(args, rank, world):
             for k in dbufs:
                 dbufs[k].copy_(host[k], non_blocking=True)
         hd = H.hwfv1_init(spec, dbufs["z"], dbufs["h"], dbufs["qx"], dbufs["qy"], stream)
+        if dt_s is None:
+            dt_s = H.hwfv1_get_time(hd)[1]   # the initial step (one host read, first trial only)
         H.hwfv1_set_time(hd, t_s, dt_s)
         H.hwfv1_advance(hd, float("inf"), args.steps)
         H.hwfv1_get_fields(hd, dbufs["h"], dbufs["qx"], dbufs["qy"])
@@ -299,14 +331,11 @@ def run_ours(args, rank, world):
         w0 = H.hwfv1_get_counters(hd)[3]
         upd.append(H.hwfv1_profile_update(hd, 20))
         wet.append(H.hwfv1_get_counters(hd)[3] - w0)
-    Ms = [H.hwfv1_get_stats(hd)[0]]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     c0 = H.hwfv1_get_counters(hd)          # also captures the step graph (untimed)
     torch.cuda.synchronize()
-    clk = ClockSampler(torch.cuda.current_device())
-    clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # profiler range = the timed region (for ncu --profile-from-start off)
     torch.cuda.profiler.start()
@@ -318,15 +347,18 @@ def run_ours(args, rank, world):
     torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     clocks = clk.stop()
+    clocks["window"] = "sampled every 20 ms from the first e2e trial to the end of the timed steps"
     ms = e0.elapsed_time(e1)
     t_now, dt_now, nsteps = H.hwfv1_get_time(hd)
     c1 = H.hwfv1_get_counters(hd)
     H.hwfv1_destroy(hd)
     ph = {k: statistics.median(v) for k, v in kern.items()}
-    return dict(ms=ms, e2e_s=t_e2e, e2e_trials=e2e_trials, kernels_ms=ph, update_ms=statistics.median(upd), wet_per_step=statistics.median(wet), M_mean=float(sum(Ms) / len(Ms)), t=t_now, dt=dt_now,
-                t_start=t_s, dt_start=dt_s, spin_steps=snap["steps"], full_run=snap["full_run"], snapshot=state,
+    return dict(ms=ms, e2e_s=t_e2e, e2e_trials=e2e_trials, kernels_ms=ph, update_ms=statistics.median(upd),
+                wet_per_step=statistics.median(wet), t=t_now, dt=dt_now,
+                t_start=t_s, dt_start=dt_s, snapshot=state,
                 problem=p, clocks=clocks, N=N, timed_steps=c1[0] - c0[0], timed_leaf_updates=c1[1] - c0[1],
-                timed_active_updates=c1[2] - c0[2], timed_wet_updates=c1[3] - c0[3], kernels_per_step=c1[4])
+                timed_active_updates=c1[2] - c0[2], timed_wet_updates=c1[3] - c0[3], kernels_per_step=c1[4],
+                stream=stream)
 
 
 def run_ensemble(args, steps=50):
@@ -639,10 +671,23 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def _oracle_replica(L, steps):
+    """One oracle process of the all-cores baseline: the window's state, then
+    `steps` oracle steps; returns the seconds they took."""
+    import oracle
+    p, f, t_s = window_state(L)
+    st = oracle.State(p, f, t=t_s)
+    t0 = time.perf_counter()
+    st.run(max_steps=steps)
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(args, p, state, t_s, dt_s, min_steps, min_seconds=12.0, max_steps=30):
-    """The oracle from the window's start state: steps one at a time until
-    at least min_steps steps and min_seconds of CPU work (at most
-    max_steps)."""
+    """The oracle (single-threaded C) from the window's start state: on one
+    core, stepping until at least min_steps steps and min_seconds of CPU work
+    (at most max_steps); then on every host core at once, one independent
+    replica per core (each one oracle step), for the box's aggregate rate."""
+    import multiprocessing as mp
     import oracle
     st = oracle.State(p, state, t=t_s, dt=dt_s)
     n = 0
@@ -652,9 +697,98 @@ def cpu_baseline(args, p, state, t_s, dt_s, min_steps, min_seconds=12.0, max_ste
         st.run(max_steps=1)
         n += 1
         el = time.perf_counter() - t0
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d oracle steps of the same L=%d workload from the same t=%.0f s state "
-                      "(single-threaded C, %.1f s)" % (n, args.L, t_s, el)}
+    ncpu = os.cpu_count() or 1
+    out = {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cores": ncpu,
+           "sample": "%d oracle steps of the same L=%d window from the same t=%.0f s state "
+                     "(single-threaded C, %.1f s)" % (n, args.L, t_s, el)}
+    try:
+        ctx = mp.get_context("spawn")
+        t1 = time.perf_counter()
+        with ctx.Pool(ncpu) as pool:
+            per = pool.starmap(_oracle_replica, [(args.L, 1)] * ncpu)
+        wall = time.perf_counter() - t1
+        slowest = max(per)
+        out["all_cores"] = {"value": ncpu / slowest, "unit": UNIT, "cores": ncpu,
+                            "sample": "%d independent oracle replicas, one per core, one step each from "
+                                      "the window's state; rate = replicas / slowest replica's step "
+                                      "time (%.1f s; %.1f s wall with set-up)" % (ncpu, slowest, wall)}
+    except Exception as e:  # pragma: no cover - reported, not hidden
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
+
+
+def fp32_error(args, p, state, t_s, dt_s, steps=3):
+    """Float32 path against the float64 oracle on the window: both advance
+    `steps` steps from the window's state (each with its own time step); per
+    field the L-inf and mean absolute (L1 per cell) differences, relative
+    L-inf, and the leaf-set difference of the last step.  The float64 GPU
+    path is compared the same way, for scale."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2206_05761_gb300.sim import Simulation
+    ref = oracle.State(p, state, t=t_s, dt=dt_s)
+    for _ in range(steps - 1):
+        ref.step()
+    last = ref.step(want=("leaves",))
+    exp_leaves = set(last["leaves"].tolist())
+    out = {"steps": steps, "oracle": "float64 C oracle from the same state",
+           "workload": "terrain flood window at t=%.0f s, L=%d" % (t_s, args.L)}
+    stream = torch.cuda.Stream()
+    for prec in (32, 64):
+        sim = Simulation(p, state, prec, stream=stream)
+        sim.set_time(t_s, dt_s)
+        sim.advance(max_steps=steps)
+        stream.synchronize()
+        g = sim.fields()
+        got = set(sim.leaves().tolist())
+        sim.close()
+        fields = {}
+        for k in ("h", "qx", "qy"):
+            o = getattr(ref, k)
+            d = np.abs(g[k].astype(np.float64) - o)
+            fields[k] = {"linf": float(d.max()), "l1_mean": float(d.mean()),
+                         "linf_rel": float(d.max() / max(np.abs(o).max(), 1e-300))}
+        out["f32" if prec == 32 else "f64"] = {"fields": fields, "leaves_oracle": len(exp_leaves),
+                                               "leaves_gpu": len(got), "leaf_set_mismatch": len(exp_leaves ^ got)}
+    return out
+
+
+def run_small_configs(args):
+    """Steps/s and leaf-updates/s of the two smaller dam-breaks, float64 on
+    the GPU: the circular dam-break at L=6 (100 steps) and the bumpy
+    dam-break at L=10 to t = 2 s at eps 1e-3 and 1e-4."""
+    import torch
+    import synth
+    from paper_2206_05761_gb300.sim import Simulation
+    stream = torch.cuda.Stream()
+
+    def timed(p, f, t_end, max_steps):
+        sim = Simulation(p, f, args.precision, stream=stream)
+        sim.counters()                        # captures the step graphs (untimed)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if t_end == float("inf"):
+            sim.advance(max_steps=max_steps)
+        else:
+            advance_to(sim, t_end)            # chunks sized from dt, no idle steps past t_end
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        n, lu, _, _, _ = sim.counters()
+        t = sim.time()[0]
+        sim.close()
+        return {"steps": n, "sim_time_s": t, "ms": ms, "steps_per_s": n / (ms / 1e3),
+                "leaf_updates_per_s": lu / (ms / 1e3), "mean_leaves": lu / max(n, 1)}
+
+    out = {"circular_L6": dict(timed(*synth.circular_dam_break(L=6, eps=1e-3), float("inf"), 100),
+                               workload="circular dam-break, L=6, eps=1e-3, 100 steps from the start")}
+    for eps in (1e-3, 1e-4):
+        p, f = synth.bumpy_dam_break(L=10, eps=eps)
+        out["bumpy_L10_eps%g" % eps] = dict(timed(p, f, 2.0, None),
+                                            workload="bumpy dam-break, L=10, eps=%g, t = 0 to 2 s" % eps)
+    return out
 
 
 def main():
@@ -664,43 +798,29 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # the oracle (single-threaded C) on the same window: the state at
-        # t_spin comes from the GPU path (untimed; the oracle would need many
-        # hours to get there); a step takes seconds at L = 12, so the timed
-        # sample is bounded to ~2 minutes
+        # the oracle (single-threaded C, on the host) on the same window: the
+        # generator-built state at the hydrograph peak, W warm-up steps, then
+        # K timed steps (a step takes seconds at L = 12, so K is bounded to
+        # about two minutes of steps); no GPU and no library of the CUDA path
         import oracle
-        p, f = workload(args.L, args.fill)
-        t_s = 0.0
-        try:
-            import torch
-            if torch.cuda.is_available():
-                p, snap = spin_up(args, torch.cuda.Stream())
-                f = {"z": snap["z"], **snap["fields"]}
-                t_s = snap["t"]
-                st = oracle.State(p, f, t=t_s, dt=snap["dt"])
-            else:
-                st = oracle.State(p, f)
-        except Exception:
-            st = oracle.State(p, f)
+        p, f, t_s = window_state(args.L)
+        st = oracle.State(p, f, t=t_s)
         t0 = time.perf_counter()
-        st.run(max_steps=1)                      # one warm-up step
-        per = time.perf_counter() - t0
+        st.run(max_steps=max(args.warmup, 1))
+        per = (time.perf_counter() - t0) / max(args.warmup, 1)
         k = max(1, min(args.steps, int(120.0 / max(per, 1e-3))))
         t1 = time.perf_counter()
         st.run(max_steps=k)
         el = time.perf_counter() - t1
         v = k / el
-        sample = ("%d oracle steps of the L=%d workload from the t=%.0f s state after 1 warm-up "
-                  "step (single-threaded C, %.1f s)" % (k, args.L, t_s, el))
-        cfg = config_dict(args)
-        if t_s == 0.0:
-            cfg["window"] = "K steps from the dry start at t=0 (no GPU here to reach the t=%.0f s state)" % args.t_spin
+        sample = ("%d oracle steps of the L=%d window from the t=%.0f s state after %d warm-up "
+                  "steps (single-threaded C, %.1f s)" % (k, args.L, t_s, max(args.warmup, 1), el))
         out = {"impl": "reference", "metric": metric(args.L), "value": v, "unit": UNIT, "n_gpus": 0,
-               "steps": k, "warmup": 1, "ms_per_step": 1e3 * el / k,
+               "steps": k, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * el / k,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": cfg,
+               "data": "synthetic", "config": config_dict(args),
                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample},
+                                "host_cores": os.cpu_count() or 1, "sample": sample},
                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
         return
@@ -742,12 +862,18 @@ def main():
                         "to the host; median of 3 trials" % (r["t_start"], args.steps),
                 "trials_steps_per_s": [args.steps / t for t in r["e2e_trials"]]},
         "gpu_launches": r["kernels_per_step"] * r["timed_steps"],
-        "clocks": r["clocks"], "sim_time_s": [r["t_start"], r["t"]], "spinup_steps": r["spin_steps"],
-        "full_run": r["full_run"],
+        "clocks": r["clocks"], "sim_time_s": [r["t_start"], r["t"]],
     }
+    if world == 1 and not args.no_spinup:
+        out["full_run"], out["spinup_window"] = spin_up(args, r["stream"])
     if world == 1:
         out["other_precision"] = time_precision(args, 32 if args.precision == 64 else 64, r["problem"],
                                                 r["snapshot"], r["t_start"], r["dt_start"], args.steps)
+        if args.precision == 64 and not args.no_cpu_baseline:
+            out["other_precision"]["error_vs_f64_oracle"] = fp32_error(
+                args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"])
+    if world == 1 and not args.no_configs:
+        out["configs"] = run_small_configs(args)
     if world == 1:
         u = time_uniform(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"], args.steps)
         u["hwfv1_speedup"] = value / u["value"]

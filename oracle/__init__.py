@@ -103,6 +103,11 @@ def lib():
             L.orc_fv1_step.restype = C.c_int
             L.orc_fv1_step.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, C.c_double,
                                        C.c_double]
+            L.orc_skip_step.restype = C.c_int
+            L.orc_skip_step.argtypes = [C.POINTER(Problem), C.POINTER(_dp), _u8p, _u8p, _dp, C.c_double,
+                                        C.c_double, C.POINTER(StepOut)]
+            L.orc_skip_prolong_all.restype = C.c_int
+            L.orc_skip_prolong_all.argtypes = [C.POINTER(Problem), C.POINTER(_dp), _u8p, _dp]
             L.orc_run.restype = C.c_int
             L.orc_run.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double,
                                   C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -335,3 +340,121 @@ class State:
         self.steps += steps.value
         self.leaf_updates += lu.value
         return steps.value
+
+
+class SkipState:
+    """State of the learned subtree skip (reading R-skip in the C source):
+    full hierarchies of h, qx, qy with each level-(L-4) subtree's state at
+    its storage level m (row-major [j, i] over level L-4), the bed, time and
+    next dt.  `skip_step(levels)` takes the predicted level of every subtree
+    (an integer array [j, i] over level L-4, values in [L-4, L]);
+    `plain_step()` is the exact audit step; `fields()` the finest fields."""
+
+    def __init__(self, p, fields, t=0.0, dt=None):
+        self.p = p
+        self.cp = make_problem(p)
+        L = p["L"]
+        self.L, self.Ls = L, L - 4
+        H = level_start(L + 1)
+        self.hier = np.zeros((3, H))
+        for q, k in enumerate(("h", "qx", "qy")):
+            self.hier[q, level_start(L):] = np.asarray(fields[k], dtype=np.float64).reshape(-1)
+        self.z = np.ascontiguousarray(fields["z"], dtype=np.float64).reshape(-1).copy()
+        self.m = np.full(1 << (2 * self.Ls), L, dtype=np.uint8)
+        self.t = float(t)
+        fin = self.hier[:, level_start(L):]
+        self.dt = (float(lib().orc_next_dt(C.byref(self.cp), _d(np.ascontiguousarray(fin[0])),
+                                           _d(np.ascontiguousarray(fin[1])), _d(np.ascontiguousarray(fin[2]))))
+                   if dt is None else float(dt))
+        self.steps = 0
+        self.leaf_updates = 0
+
+    def _rows(self, hier=None):
+        h = self.hier if hier is None else hier
+        return (_dp * 3)(*[h[q].ctypes.data_as(_dp) for q in range(3)])
+
+    def _out(self, want, res):
+        L = self.L
+        P, N = level_start(L), 1 << (2 * L)
+        o = StepOut()
+        if "T" in want:
+            res["T"] = np.zeros(max(P, 1), np.uint8)
+            o.T = res["T"].ctypes.data_as(_u8p)
+        if "S" in want:
+            res["S"] = np.zeros(max(P, 1), np.uint8)
+            o.S = res["S"].ctypes.data_as(_u8p)
+        res["leaves"] = np.zeros(N, np.uint32)
+        o.leaves = res["leaves"].ctypes.data_as(C.POINTER(C.c_uint32))
+        o.leaves_cap = N
+        return o
+
+    def _finish(self, o, res, dt):
+        P = level_start(self.L)
+        for k in ("T", "S"):
+            if k in res:
+                res[k] = res[k][:P]
+        res["leaves"] = res["leaves"][: o.num_leaves]
+        res["num_leaves"] = int(o.num_leaves)
+        self.t += dt
+        self.dt = o.dt_next
+        self.steps += 1
+        self.leaf_updates += o.num_leaves
+        return res
+
+    def skip_step(self, levels, dt=None, want=()):
+        levels = np.ascontiguousarray(levels, dtype=np.uint8).reshape(-1)
+        assert levels.size == self.m.size
+        dt = self.dt if dt is None else float(dt)
+        res = {}
+        o = self._out(want, res)
+        rc = lib().orc_skip_step(C.byref(self.cp), self._rows(), self.m.ctypes.data_as(_u8p),
+                                 levels.ctypes.data_as(_u8p), _d(self.z), self.t, dt, C.byref(o))
+        if rc:
+            raise RuntimeError("oracle skip step failed (%d)" % rc)
+        return self._finish(o, res, dt)
+
+    def to_finest(self):
+        """Bring every subtree to level L in place (before a plain step)."""
+        rc = lib().orc_skip_prolong_all(C.byref(self.cp), self._rows(), self.m.ctypes.data_as(_u8p), _d(self.z))
+        if rc:
+            raise RuntimeError("oracle prolongation failed (%d)" % rc)
+
+    def plain_step(self, dt=None, want=()):
+        self.to_finest()
+        L = self.L
+        dt = self.dt if dt is None else float(dt)
+        res = {}
+        o = self._out(want, res)
+        fin = [np.ascontiguousarray(self.hier[q, level_start(L):]) for q in range(3)]
+        rc = lib().orc_hwfv1_step(C.byref(self.cp), _d(fin[0]), _d(fin[1]), _d(fin[2]), _d(self.z),
+                                  self.t, dt, C.byref(o))
+        if rc:
+            raise RuntimeError("oracle step failed (%d)" % rc)
+        for q in range(3):
+            self.hier[q, level_start(L):] = fin[q]
+        return self._finish(o, res, dt)
+
+    def fields(self):
+        """Finest h, qx, qy ([j, i]) of the state, formed on a copy."""
+        L = self.L
+        hier = self.hier.copy()
+        m = self.m.copy()
+        rc = lib().orc_skip_prolong_all(C.byref(self.cp), self._rows(hier), m.ctypes.data_as(_u8p), _d(self.z))
+        if rc:
+            raise RuntimeError("oracle prolongation failed (%d)" % rc)
+        n = 1 << L
+        return {k: hier[q, level_start(L):].reshape(n, n).copy() for q, k in enumerate(("h", "qx", "qy"))}
+
+    def stored(self):
+        """The stored state: per subtree its level and its level-m cells
+        (a list of (level, h, qx, qy) blocks, row-major over level L-4)."""
+        out = []
+        Ls = self.Ls
+        for sj in range(1 << Ls):
+            for si in range(1 << Ls):
+                ms = int(self.m[sj * (1 << Ls) + si])
+                w = 1 << (ms - Ls)
+                lv = [self.hier[q, level_start(ms): level_start(ms) + (1 << (2 * ms))].reshape(1 << ms, 1 << ms)
+                      [sj * w:(sj + 1) * w, si * w:(si + 1) * w] for q in range(3)]
+                out.append((ms, *lv))
+        return out

@@ -85,6 +85,10 @@
  *           (mass is conserved up to rounding), and a still free surface
  *           stays still.  Needs R2 (a significant cell then has only
  *           significant ancestors).
+ *  R-skip   (the learned subtree skip, a layer the project adds; the paper
+ *           has no learned part) each level-(L-4) subtree is encoded,
+ *           flagged and stored only down to a given predicted level; the
+ *           steps are stated with orc_skip_step below.
  */
 #include <math.h>
 #include <stdint.h>
@@ -257,25 +261,30 @@ double orc_smax(int L, const double* fine) {
     return m;
 }
 
-/* Threshold flags.  `det4[q]` are the details of quantity q (layout of
- * orc_encode), q = h, qx, qy, z; `smax4[q]` their s_max.  A parent is
- * significant when, for any q, max(|da|,|db|,|dg|) >= 2^(n-L)*eps*s_max,q. */
+/* Threshold test of the parent at hierarchy index p: significant when, for
+ * any q, max(|da|,|db|,|dg|) >= thr * s_max,q with thr = 2^(n-L) eps.
+ * `det4[q]` are the details of quantity q (layout of orc_encode), q = h,
+ * qx, qy, z; `smax4[q]` their s_max. */
+static int parent_significant(const double* const* det4, int64_t p, double thr, const double* smax4) {
+    int sig = 0;
+    for (int q = 0; q < 4; ++q) {
+        const double* d = det4[q] + 3 * p;
+        double dnorm = maxd(maxd(absd(d[0]), absd(d[1])), absd(d[2]));
+        if (dnorm >= thr * smax4[q]) sig = 1;
+    }
+    return sig;
+}
+
+/* Threshold flags of every parent (levels 0..L-1). */
 void orc_threshold_flags(int L, double eps, const double* const* det4, const double* smax4,
                          uint8_t* T) {
     for (int n = 0; n < L; ++n) {
         double thr = ldexp(eps, n - L);
-        for (int64_t j = 0; j < side(n); ++j) {
+        for (int64_t j = 0; j < side(n); ++j)
             for (int64_t i = 0; i < side(n); ++i) {
                 int64_t p = level_start(n) + rm(n, i, j);
-                int sig = 0;
-                for (int q = 0; q < 4; ++q) {
-                    const double* d = det4[q] + 3 * p;
-                    double dnorm = maxd(maxd(absd(d[0]), absd(d[1])), absd(d[2]));
-                    if (dnorm >= thr * smax4[q]) sig = 1;
-                }
-                T[p] = (uint8_t)sig;
+                T[p] = (uint8_t)parent_significant(det4, p, thr, smax4);
             }
-        }
     }
 }
 
@@ -840,5 +849,231 @@ int orc_run(const orc_problem* p, double* h, double* qx, double* qy, const doubl
         }
         *steps += 1;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned subtree skip: the project's learned layer on Algorithm 3         */
+/* (reading R-skip; the paper has no learned part).                         */
+/*                                                                          */
+/* The subtrees are the cells of level Ls = L - 4 (16 x 16 finest cells     */
+/* each).  Subtree s keeps its state at a storage level m_s, Ls <= m_s <= L: */
+/* the values of its level-m_s cells (m_s = L at the start and after every  */
+/* plain step).  A skip step is given a level p_s in [Ls, L] per subtree    */
+/* (the prediction of the deepest level the subtree needs) and              */
+/*  1. takes P_s = max(p_s, p of the subtrees sharing an edge with s): the  */
+/*     level s is kept down to, so that a leaf of a neighbouring subtree    */
+/*     (no finer than its own p) finds its same-level neighbour cells in s; */
+/*  2. takes s_max,q = max(1, max |value|) over the stored state (the       */
+/*     level-m_s cells of every subtree) as it is when the step starts;     */
+/*  3. when P_s > m_s, forms the level-P_s cells of s from its level-m_s    */
+/*     cells as the decode-back forms the cells under a leaf (R-decode,     */
+/*     with the level-m_s cell as the leaf and z^(P_s) below it);           */
+/*  4. encodes s from level E_s = max(m_s, P_s) up to level Ls (Eq. 3), and */
+/*     the levels Ls-1 .. 0 from level Ls;                                  */
+/*  5. flags a parent (n, c) as the plain step does (q over h, qx, qy, z)   */
+/*     when n < Ls, and when n >= Ls only if n < p_s: the subtree's details */
+/*     at levels >= p_s are neither used nor tested;                        */
+/*  6. regularises (R1, R2) and then clears every cell of a level n >= Ls   */
+/*     with n >= p_s, so the leaves of s are no finer than p_s;             */
+/*  7. finds the leaves (Algorithm 2) and updates them from their           */
+/*     same-level neighbours (Sec. 2.1.3) as the plain step does, with the  */
+/*     finest spacing in the CFL bound (R-cfl);                             */
+/*  8. stores s at level P_s: every level-P_s cell takes its covering       */
+/*     leaf's new value, with the R-decode free surface against z^(P_s)     */
+/*     when the leaf is coarser than P_s; then m_s = P_s.                   */
+/* A plain step (the exact audit) first forms level L of every subtree as   */
+/* in 3, then runs orc_hwfv1_step on the finest grid.                       */
+/* State layout: h, qx, qy each a full hierarchy (levels 0..L, level n at   */
+/* level_start(n), row-major); m and p row-major over level Ls.             */
+/* ------------------------------------------------------------------------ */
+
+/* Level-P cells of subtree (si, sj) from its level-m cells, m < P (step 3). */
+static void skip_prolong(const orc_problem* p, double* const* hier3, const double* zh, int Ls,
+                         int64_t si, int64_t sj, int m, int P) {
+    int64_t w = side(P - Ls);                   /* level-P cells per subtree side */
+    for (int64_t jj = sj * w; jj < (sj + 1) * w; ++jj)
+        for (int64_t ii = si * w; ii < (si + 1) * w; ++ii) {
+            int64_t ai = ii >> (P - m), aj = jj >> (P - m);
+            int64_t ka = level_start(m) + rm(m, ai, aj), kc = level_start(P) + rm(P, ii, jj);
+            double hl = hier3[0][ka];
+            double hf = hl;
+            if (hl >= p->tol_h) {
+                double eta = hl + zh[ka];
+                double d = eta - zh[kc];
+                hf = d > 0.0 ? d : 0.0;
+            }
+            hier3[0][kc] = hf;
+            hier3[1][kc] = hier3[1][ka];
+            hier3[2][kc] = hier3[2][ka];
+        }
+}
+
+/* Every subtree stored above level L is brought to level L (step 3 with
+ * P = L), for the plain step and for reading the finest fields. */
+int orc_skip_prolong_all(const orc_problem* p, double* const* hier3, uint8_t* m, const double* z) {
+    int L = p->L, Ls = L - 4;
+    if (Ls < 0) return 2;
+    double* zh = (double*)malloc(sizeof(double) * (size_t)level_start(L + 1));
+    if (!zh) return 1;
+    orc_encode(L, z, zh, NULL);
+    for (int64_t sj = 0; sj < side(Ls); ++sj)
+        for (int64_t si = 0; si < side(Ls); ++si) {
+            uint8_t* ms = &m[rm(Ls, si, sj)];
+            if (*ms < L) skip_prolong(p, hier3, zh, Ls, si, sj, *ms, L);
+            *ms = (uint8_t)L;
+        }
+    free(zh);
+    return 0;
+}
+
+/* Subtree (row-major index at level Ls) of the cell (n, i, j), n >= Ls. */
+static int64_t subtree_of(int Ls, int n, int64_t i, int64_t j) {
+    return rm(Ls, i >> (n - Ls), j >> (n - Ls));
+}
+
+/* One skip step of size dt at time t (steps 1-8 above).  `pred` holds p_s.
+ * Returns 0 on success, 2 for an unsupported problem (L < 4, R-match, or
+ * the regularisation not fully on), 3 for a level outside [Ls, L]. */
+int orc_skip_step(const orc_problem* p, double* const* hier3, uint8_t* m, const uint8_t* pred,
+                  const double* z, double t, double dt, orc_step_out* o) {
+    int L = p->L, Ls = L - 4;
+    if (Ls < 0 || p->flux_match || !p->reg_predict || !p->reg_close) return 2;
+    int64_t ns = side(Ls), NSUB = ns * ns, P_ = level_start(L), H = level_start(L + 1);
+    for (int64_t k = 0; k < NSUB; ++k)
+        if (pred[k] < Ls || pred[k] > L || m[k] < Ls || m[k] > L) return 3;
+    /* 1. storage level of each subtree */
+    uint8_t* P = (uint8_t*)malloc((size_t)NSUB);
+    for (int64_t sj = 0; sj < ns; ++sj)
+        for (int64_t si = 0; si < ns; ++si) {
+            int v = pred[rm(Ls, si, sj)];
+            if (si > 0 && pred[rm(Ls, si - 1, sj)] > v) v = pred[rm(Ls, si - 1, sj)];
+            if (si < ns - 1 && pred[rm(Ls, si + 1, sj)] > v) v = pred[rm(Ls, si + 1, sj)];
+            if (sj > 0 && pred[rm(Ls, si, sj - 1)] > v) v = pred[rm(Ls, si, sj - 1)];
+            if (sj < ns - 1 && pred[rm(Ls, si, sj + 1)] > v) v = pred[rm(Ls, si, sj + 1)];
+            P[rm(Ls, si, sj)] = (uint8_t)v;
+        }
+    /* 2. s_max over the stored state */
+    double smax[4] = {1.0, 1.0, 1.0, orc_smax(L, z)};
+    for (int64_t sj = 0; sj < ns; ++sj)
+        for (int64_t si = 0; si < ns; ++si) {
+            int ms = m[rm(Ls, si, sj)];
+            int64_t w = side(ms - Ls);
+            for (int64_t jj = sj * w; jj < (sj + 1) * w; ++jj)
+                for (int64_t ii = si * w; ii < (si + 1) * w; ++ii)
+                    for (int q = 0; q < 3; ++q)
+                        smax[q] = maxd(smax[q], absd(hier3[q][level_start(ms) + rm(ms, ii, jj)]));
+        }
+    /* the bed: every level and detail (static) */
+    double* zh = (double*)malloc(sizeof(double) * (size_t)H);
+    double* zdet = (double*)malloc(sizeof(double) * (size_t)(3 * (P_ > 0 ? P_ : 1)));
+    orc_encode(L, z, zh, zdet);
+    /* 3. prolongation where P_s > m_s; E_s = max(m_s, P_s) */
+    uint8_t* E = (uint8_t*)malloc((size_t)NSUB);
+    for (int64_t sj = 0; sj < ns; ++sj)
+        for (int64_t si = 0; si < ns; ++si) {
+            int64_t s = rm(Ls, si, sj);
+            if (P[s] > m[s]) skip_prolong(p, hier3, zh, Ls, si, sj, m[s], P[s]);
+            E[s] = P[s] > m[s] ? P[s] : m[s];
+        }
+    /* 4. encode: inside each subtree from level E_s, then above Ls */
+    double* det[3];
+    for (int q = 0; q < 3; ++q) det[q] = (double*)calloc((size_t)(3 * (P_ > 0 ? P_ : 1)), sizeof(double));
+    for (int n = L - 1; n >= 0; --n)
+        for (int64_t j = 0; j < side(n); ++j)
+            for (int64_t i = 0; i < side(n); ++i) {
+                if (n >= Ls && n >= E[subtree_of(Ls, n, i, j)]) continue;  /* level n+1 not formed */
+                for (int q = 0; q < 3; ++q) {
+                    const double* kid = hier3[q] + level_start(n + 1);
+                    double c[4] = {kid[rm(n + 1, 2 * i, 2 * j)], kid[rm(n + 1, 2 * i + 1, 2 * j)],
+                                   kid[rm(n + 1, 2 * i, 2 * j + 1)], kid[rm(n + 1, 2 * i + 1, 2 * j + 1)]};
+                    double out[4];
+                    orc_encode_parent(c, out);
+                    int64_t k = level_start(n) + rm(n, i, j);
+                    hier3[q][k] = out[0];
+                    det[q][3 * k] = out[1];
+                    det[q][3 * k + 1] = out[2];
+                    det[q][3 * k + 2] = out[3];
+                }
+            }
+    /* 5. threshold flags of the parents allowed to refine */
+    uint8_t* T = (uint8_t*)calloc((size_t)(P_ > 0 ? P_ : 1), 1);
+    uint8_t* S = (uint8_t*)calloc((size_t)(P_ > 0 ? P_ : 1), 1);
+    const double* det4[4] = {det[0], det[1], det[2], zdet};
+    for (int n = 0; n < L; ++n) {
+        double thr = ldexp(p->eps, n - L);
+        for (int64_t j = 0; j < side(n); ++j)
+            for (int64_t i = 0; i < side(n); ++i) {
+                if (n >= Ls && n >= pred[subtree_of(Ls, n, i, j)]) continue;
+                int64_t k = level_start(n) + rm(n, i, j);
+                T[k] = (uint8_t)parent_significant(det4, k, thr, smax);
+            }
+    }
+    /* 6. regularisation, then no leaf of s finer than p_s */
+    orc_regularise(L, 1, 1, T, S);
+    for (int n = Ls; n < L; ++n)
+        for (int64_t j = 0; j < side(n); ++j)
+            for (int64_t i = 0; i < side(n); ++i)
+                if (n >= pred[subtree_of(Ls, n, i, j)]) S[level_start(n) + rm(n, i, j)] = 0;
+    /* 7. leaves and their update */
+    int64_t M = orc_leaves_dft(L, S, NULL, 0);
+    uint32_t* leaves = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(M > 0 ? M : 1));
+    orc_leaves_dft(L, S, leaves, M);
+    double* newU = (double*)malloc(sizeof(double) * (size_t)(3 * (M > 0 ? M : 1)));
+    const double* hier4[4] = {hier3[0], hier3[1], hier3[2], zh};
+    for (int64_t k = 0; k < M; ++k) {
+        int n = (int)(leaves[k] >> 28);
+        uint32_t i, j;
+        orc_demorton(leaves[k] & 0x0FFFFFFFu, &i, &j);
+        leaf_update(p, hier4, S, n, i, j, t, dt, newU + 3 * k);
+    }
+    double rmin = INFINITY;
+    for (int64_t k = 0; k < M; ++k) {
+        double rr = cfl_bound(p, newU[3 * k], newU[3 * k + 1], newU[3 * k + 2]);
+        if (rr < rmin) rmin = rr;
+    }
+    /* 8. store each subtree at level P_s: the leaves' new values at their
+     * own cells first (a map from cell to value), then every level-P_s
+     * cell from its covering leaf */
+    double* nv[3];
+    for (int q = 0; q < 3; ++q) nv[q] = (double*)malloc(sizeof(double) * (size_t)H);
+    for (int64_t k = 0; k < M; ++k) {
+        int n = (int)(leaves[k] >> 28);
+        uint32_t i, j;
+        orc_demorton(leaves[k] & 0x0FFFFFFFu, &i, &j);
+        for (int q = 0; q < 3; ++q) nv[q][level_start(n) + rm(n, i, j)] = newU[3 * k + q];
+    }
+    for (int64_t sj = 0; sj < ns; ++sj)
+        for (int64_t si = 0; si < ns; ++si) {
+            int Ps = P[rm(Ls, si, sj)];
+            int64_t w = side(Ps - Ls);
+            for (int64_t jj = sj * w; jj < (sj + 1) * w; ++jj)
+                for (int64_t ii = si * w; ii < (si + 1) * w; ++ii) {
+                    int n = 0;                  /* the covering leaf (Algorithm 5's walk) */
+                    while (n < Ps && S[level_start(n) + rm(n, ii >> (Ps - n), jj >> (Ps - n))]) n++;
+                    int64_t kl = level_start(n) + rm(n, ii >> (Ps - n), jj >> (Ps - n));
+                    int64_t kc = level_start(Ps) + rm(Ps, ii, jj);
+                    double hl = nv[0][kl];
+                    double hf = hl;
+                    if (n < Ps && hl >= p->tol_h) {
+                        double eta = hl + zh[kl];
+                        double d = eta - zh[kc];
+                        hf = d > 0.0 ? d : 0.0;
+                    }
+                    hier3[0][kc] = hf;
+                    hier3[1][kc] = nv[1][kl];
+                    hier3[2][kc] = nv[2][kl];
+                }
+        }
+    for (int64_t s = 0; s < NSUB; ++s) m[s] = P[s];
+    if (o) {
+        if (o->T) memcpy(o->T, T, (size_t)P_);
+        if (o->S) memcpy(o->S, S, (size_t)P_);
+        if (o->leaves) memcpy(o->leaves, leaves, sizeof(uint32_t) * (size_t)(M < o->leaves_cap ? M : o->leaves_cap));
+        o->num_leaves = M;
+        o->dt_next = dt_from_rmin(p, rmin);
+    }
+    for (int q = 0; q < 3; ++q) { free(det[q]); free(nv[q]); }
+    free(P); free(E); free(zh); free(zdet); free(T); free(S); free(leaves); free(newU);
     return 0;
 }

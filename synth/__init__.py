@@ -12,7 +12,9 @@ Workloads (the paper's test cases, Sec. 3, replaced by seeded stand-ins):
 * ``bumpy_dam_break`` -- a dam-break over seeded Gaussian humps with wet/dry
   fronts, standing in for the hump tests of Sec. 3.1.
 * ``terrain_flood`` -- a seeded 1/f^2 spectral DEM with a carved channel and
-  an inflow hydrograph, standing in for the DEM-based tests of Sec. 3.3.
+  an inflow hydrograph, standing in for the DEM-based tests of Sec. 3.3;
+  ``terrain_flood_peak`` is its state at the hydrograph peak with the channel
+  running full.
 * ``ensemble`` -- many independent bumpy dam-breaks of mixed depth L.
 * small fixtures for the pins: lake at rest, a wet mound in a closed basin,
   pseudo-2D dam-break (Sec. 3.2),
@@ -181,6 +183,15 @@ def terrain_flood(L=12, eps=1e-3, seed=3, side_m=10_000.0, relief=50.0, width=60
                        qy=np.zeros_like(h), z=np.ascontiguousarray(z))
     eta = np.full_like(z, -1e9)          # dry start
     return p, _fields(p, eta, z)
+
+
+def terrain_flood_peak(L=12, eps=1e-3, depth=3.45, q=8.33):
+    """The terrain flood at its hydrograph peak, t = 1800 s: the channel runs
+    `depth` metres deep (3.45 m is the Manning normal depth of the peak's
+    500 m^3/s through the 60 m channel on the 0.1 % tilt) with `q` m^2/s
+    towards +x, the rest of the domain dry.  Returns (problem, fields, t)."""
+    p, f = terrain_flood(L=L, eps=eps, fill=depth, fill_q=q)
+    return p, f, 1800.0
 
 
 def ensemble(count=64, seed=4, levels=(7, 8, 9, 10), eps=1e-3):

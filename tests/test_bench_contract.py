@@ -14,8 +14,12 @@ KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "
 
 
 def test_reference_arm_prints_one_contract_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--L", "5", "--steps", "2",
-                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    # run in a process that afterwards checks it never loaded the CUDA path
+    code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--L', '5', '--steps', '2', "
+            "'--warmup', '3']; runpy.run_path('bench.py', run_name='__main__'); "
+            "maps = open('/proc/self/maps').read(); "
+            "assert 'libhwfv1' not in maps and 'paper_2206_05761_gb300' not in sys.modules, 'CUDA path loaded'")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -23,8 +27,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and KEYS <= set(d)
     assert d["value"] > 0 and d["unit"] == "steps/s" and d["higher_is_better"] is True
     assert d["config"]["workload"] == "terrain_flood" and d["config"]["L"] == 5
+    assert d["warmup"] == 3 and d["steps"] == 2
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host_cores"] == os.cpu_count()
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 

@@ -44,6 +44,22 @@ def test_batch_matches_oracle_per_member():
     ens.close()
 
 
+def test_batch_members_at_the_benched_depths():
+    # the benched ensemble's deeper members (L = 9 and 10: 256 and 1024
+    # tiles, other tile paths than the small members) next to a small one,
+    # with the autotuner's choice, against the oracle
+    from paper_2206_05761_gb300.sim import Ensemble
+    cases = [synth.bumpy_dam_break(L=10, eps=1e-3, seed=4, eta_up=1.7),
+             synth.bumpy_dam_break(L=9, eps=1e-3, seed=5, eta_up=0.8),
+             synth.bumpy_dam_break(L=7, eps=1e-3, seed=6, eta_up=1.2)]
+    ens = Ensemble(cases)
+    ens.advance(max_steps=4)
+    _check_members(ens, cases, 4)
+    ens.autotune(trial_steps=1)               # 12 candidates x 2 steps
+    _check_members(ens, cases, 28)
+    ens.close()
+
+
 def test_autotune_keeps_results_bit_identical():
     from paper_2206_05761_gb300.sim import Ensemble
     cases = _cases()

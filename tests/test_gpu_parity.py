@@ -424,28 +424,32 @@ def test_float32_path_errors_stated():
     sim.close()
 
 
-def test_full_size_terrain_flood_L12_bench_launch_path():
-    # the bench workload at full size (4096 x 4096, 10 km, eps 1e-3, Manning
-    # 0.03, inflow) with its channel flowing, advanced three steps through
-    # the same graph-replay path bench.py times (dry tiles skipped from the
-    # second step on), against three oracle steps
-    p, f = synth.terrain_flood(L=12, fill=2.0, fill_q=1.0)
+@pytest.mark.parametrize("steps", [3, 5])
+def test_full_size_terrain_flood_L12_bench_window(steps):
+    # the bench's timed window at full size (4096 x 4096, 10 km, eps 1e-3,
+    # Manning 0.03): its generator-built start state at the hydrograph peak
+    # (t = 1800 s, inflow at 500 m^3/s, the channel running full, the rest
+    # dry), advanced through the same graph-replay path bench.py times (dry
+    # tiles skipped from the second step on), against the oracle's steps;
+    # leaves exactly, fields within 1e-12 (friction)
+    p, f, t0 = synth.terrain_flood_peak(L=12)
     sim = _sim(p, f)
-    ref = oracle.State(p, f)
+    ref = oracle.State(p, f, t=t0)
     t, dt, _ = sim.time()
     assert dt == ref.dt
-    sim.advance(max_steps=3)
-    ref.step()
-    ref.step()
+    sim.set_time(t0, dt)
+    sim.advance(max_steps=steps)
+    for _ in range(steps - 1):
+        ref.step()
     res = ref.step(want=("leaves",))
     lv = sim.leaves()
     assert len(lv) == res["num_leaves"] and np.array_equal(lv, res["leaves"])
     _compare_fields(sim, ref, exact=False)
-    t, dt, steps = sim.time()
-    assert steps == 3 and abs(t - ref.t) <= RTOL_FRICTION * ref.t
+    t, dt, n = sim.time()
+    assert n == steps and abs(t - ref.t) <= RTOL_FRICTION * ref.t
     assert abs(dt - ref.dt) <= RTOL_FRICTION * ref.dt
     n, lu, au, wu, kps = sim.counters()
-    assert lu == ref.leaf_updates and au < lu
+    assert lu == ref.leaf_updates and au < lu and wu > 0
     sim.close()
 
 

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "hwfv1_oracle.c")
 WORK = os.path.join(ROOT, "oracle", "_build", "mutants")
 PINS = ["tests/test_oracle_mra.py", "tests/test_oracle_tree.py", "tests/test_oracle_fv1.py",
-        "tests/test_oracle_match.py"]
+        "tests/test_oracle_match.py", "tests/test_oracle_skip.py"]
 
 # (name, text in the oracle, the same text with the mistake)
 MUTANTS = [
@@ -30,8 +30,8 @@ MUTANTS = [
     ("threshold_level_power", "double thr = ldexp(eps, n - L);", "double thr = ldexp(eps, L - n);"),
     ("threshold_strict", "if (dnorm >= thr * smax4[q]) sig = 1;", "if (dnorm > thr * smax4[q]) sig = 1;"),
     ("smax_floor", "    double m = 1.0;\n", "    double m = 0.0;\n"),
-    ("threshold_without_bed", "for (int q = 0; q < 4; ++q) {\n                    const double* d",
-     "for (int q = 0; q < 3; ++q) {\n                    const double* d"),
+    ("threshold_without_bed", "for (int q = 0; q < 4; ++q) {\n        const double* d",
+     "for (int q = 0; q < 3; ++q) {\n        const double* d"),
     ("detail_without_abs", "maxd(maxd(absd(d[0]), absd(d[1])), absd(d[2]))", "maxd(maxd(d[0], d[1]), d[2])"),
     ("predict_last_level", "for (int n = 0; n + 1 <= L - 1; ++n)", "for (int n = 0; n + 1 <= L - 2; ++n)"),
     ("predict_child_index", "2 * i + (k & 1), 2 * j + (k >> 1)", "2 * i + (k >> 1), 2 * j + (k >> 1)"),
@@ -68,6 +68,20 @@ MUTANTS = [
     ("matched_depth_half", "*own2 = 0.5 * (oa + ob);", "*own2 = oa;"),
     ("matched_child", "cni = 2 * ni + (s == ORC_E ? 0 : 1);", "cni = 2 * ni + (s == ORC_E ? 1 : 0);"),
     ("uniform_neighbour", "orc_cell E = i < last ? CELL(i + 1, j)", "orc_cell E = i < last ? CELL(i, j + 1)"),
+    # the learned subtree skip (R-skip)
+    ("skip_storage_ignores_neighbours", "if (si > 0 && pred[rm(Ls, si - 1, sj)] > v) v = pred[rm(Ls, si - 1, sj)];",
+     "if (0) v = pred[rm(Ls, si - 1, sj)];"),
+    ("skip_encode_from_storage_level_only", "E[s] = P[s] > m[s] ? P[s] : m[s];", "E[s] = P[s];"),
+    ("skip_leaf_clamp_off_by_one", "if (n >= pred[subtree_of(Ls, n, i, j)]) S[level_start(n) + rm(n, i, j)] = 0;",
+     "if (n > pred[subtree_of(Ls, n, i, j)]) S[level_start(n) + rm(n, i, j)] = 0;"),
+    ("skip_flags_below_prediction", "if (n >= Ls && n >= pred[subtree_of(Ls, n, i, j)]) continue;",
+     "if (n >= Ls && n > pred[subtree_of(Ls, n, i, j)]) continue;"),
+    ("skip_prolong_hands_down_depth", "            if (hl >= p->tol_h) {\n                double eta = hl + zh[ka];",
+     "            if (0) {\n                double eta = hl + zh[ka];"),
+    ("skip_store_bed_of_leaf_level", "                        double d = eta - zh[kc];\n                        hf = d > 0.0 ? d : 0.0;\n                    }\n                    hier3[0][kc] = hf;\n                    hier3[1][kc] = nv[1][kl];",
+     "                        double d = eta - zh[kl];\n                        hf = d > 0.0 ? d : 0.0;\n                    }\n                    hier3[0][kc] = hf;\n                    hier3[1][kc] = nv[1][kl];"),
+    ("skip_smax_without_floor", "double smax[4] = {1.0, 1.0, 1.0, orc_smax(L, z)};", "double smax[4] = {0.0, 0.0, 0.0, orc_smax(L, z)};"),
+    ("skip_storage_level_not_updated", "for (int64_t s = 0; s < NSUB; ++s) m[s] = P[s];", "for (int64_t s = 0; s < NSUB; ++s) m[s] = m[s];"),
 ]
 
 
