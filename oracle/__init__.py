@@ -106,6 +106,9 @@ def lib():
             L.orc_skip_step.restype = C.c_int
             L.orc_skip_step.argtypes = [C.POINTER(Problem), C.POINTER(_dp), _u8p, _u8p, _dp, C.c_double,
                                         C.c_double, C.POINTER(StepOut)]
+            L.orc_skip_audit_step.restype = C.c_int
+            L.orc_skip_audit_step.argtypes = [C.POINTER(Problem), C.POINTER(_dp), _u8p, _dp, C.c_double,
+                                              C.c_double, C.POINTER(StepOut)]
             L.orc_skip_prolong_all.restype = C.c_int
             L.orc_skip_prolong_all.argtypes = [C.POINTER(Problem), C.POINTER(_dp), _u8p, _dp]
             L.orc_run.restype = C.c_int
@@ -420,18 +423,15 @@ class SkipState:
             raise RuntimeError("oracle prolongation failed (%d)" % rc)
 
     def plain_step(self, dt=None, want=()):
-        self.to_finest()
-        L = self.L
+        """The exact audit step: s_max over the stored state, every subtree
+        brought to level L, then the plain step."""
         dt = self.dt if dt is None else float(dt)
         res = {}
         o = self._out(want, res)
-        fin = [np.ascontiguousarray(self.hier[q, level_start(L):]) for q in range(3)]
-        rc = lib().orc_hwfv1_step(C.byref(self.cp), _d(fin[0]), _d(fin[1]), _d(fin[2]), _d(self.z),
-                                  self.t, dt, C.byref(o))
+        rc = lib().orc_skip_audit_step(C.byref(self.cp), self._rows(), self.m.ctypes.data_as(_u8p),
+                                       _d(self.z), self.t, dt, C.byref(o))
         if rc:
-            raise RuntimeError("oracle step failed (%d)" % rc)
-        for q in range(3):
-            self.hier[q, level_start(L):] = fin[q]
+            raise RuntimeError("oracle audit step failed (%d)" % rc)
         return self._finish(o, res, dt)
 
     def fields(self):

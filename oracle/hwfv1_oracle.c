@@ -719,8 +719,18 @@ typedef struct {
  * find the leaves by DFT (Algorithm 2); FV1-update every leaf from its
  * same-level neighbours (Sec. 2.1.3); put the new leaf values on the finest
  * grid (R-decode); compute the next dt (R-cfl). */
+static int hwfv1_step_smax(const orc_problem* p, double* h, double* qx, double* qy, const double* z,
+                           double t, double dt, const double* smax_in, orc_step_out* o);
+
 int orc_hwfv1_step(const orc_problem* p, double* h, double* qx, double* qy, const double* z,
                    double t, double dt, orc_step_out* o) {
+    return hwfv1_step_smax(p, h, qx, qy, z, t, dt, NULL, o);
+}
+
+/* The step with the s_max of h, qx, qy given (smax_in, 3 values) instead of
+ * taken over the finest fields; NULL takes them over the finest fields. */
+static int hwfv1_step_smax(const orc_problem* p, double* h, double* qx, double* qy, const double* z,
+                           double t, double dt, const double* smax_in, orc_step_out* o) {
     int L = p->L;
     if (p->flux_match && !p->reg_close) return 2;     /* R-match needs R2 */
     int64_t N = side(L) * side(L), P = level_start(L), H = N + P;
@@ -733,7 +743,7 @@ int orc_hwfv1_step(const orc_problem* p, double* h, double* qx, double* qy, cons
         det[q] = (double*)malloc(sizeof(double) * (size_t)(3 * (P > 0 ? P : 1)));
         if (!hier[q] || !det[q]) return 1;
         orc_encode(L, fine[q], hier[q], det[q]);
-        smax[q] = orc_smax(L, fine[q]);
+        smax[q] = (smax_in && q < 3) ? smax_in[q] : orc_smax(L, fine[q]);
     }
     uint8_t* T = (uint8_t*)malloc((size_t)(P > 0 ? P : 1));
     uint8_t* S = (uint8_t*)malloc((size_t)(P > 0 ? P : 1));
@@ -882,8 +892,8 @@ int orc_run(const orc_problem* p, double* h, double* qx, double* qy, const doubl
 /*  8. stores s at level P_s: every level-P_s cell takes its covering       */
 /*     leaf's new value, with the R-decode free surface against z^(P_s)     */
 /*     when the leaf is coarser than P_s; then m_s = P_s.                   */
-/* A plain step (the exact audit) first forms level L of every subtree as   */
-/* in 3, then runs orc_hwfv1_step on the finest grid.                       */
+/* A plain step (the exact audit) takes s_max as in 2, forms level L of     */
+/* every subtree as in 3, then runs the plain step on the finest grid.      */
 /* State layout: h, qx, qy each a full hierarchy (levels 0..L, level n at   */
 /* level_start(n), row-major); m and p row-major over level Ls.             */
 /* ------------------------------------------------------------------------ */
@@ -927,6 +937,36 @@ int orc_skip_prolong_all(const orc_problem* p, double* const* hier3, uint8_t* m,
     return 0;
 }
 
+/* s_max of h, qx, qy over the stored state (the level-m_s cells of every
+ * subtree), floored at 1 (R-norm). */
+static void skip_smax(const double* const* hier3, const uint8_t* m, int Ls, double smax3[3]) {
+    smax3[0] = smax3[1] = smax3[2] = 1.0;
+    for (int64_t sj = 0; sj < side(Ls); ++sj)
+        for (int64_t si = 0; si < side(Ls); ++si) {
+            int ms = m[rm(Ls, si, sj)];
+            int64_t w = side(ms - Ls);
+            for (int64_t jj = sj * w; jj < (sj + 1) * w; ++jj)
+                for (int64_t ii = si * w; ii < (si + 1) * w; ++ii)
+                    for (int q = 0; q < 3; ++q)
+                        smax3[q] = maxd(smax3[q], absd(hier3[q][level_start(ms) + rm(ms, ii, jj)]));
+        }
+}
+
+/* The plain step (the exact audit) from a skip state: s_max over the stored
+ * state as the step starts, every subtree brought to level L, then the
+ * plain step on the finest grid (level L of the hierarchies, in place). */
+int orc_skip_audit_step(const orc_problem* p, double* const* hier3, uint8_t* m, const double* z,
+                        double t, double dt, orc_step_out* o) {
+    int L = p->L, Ls = L - 4;
+    if (Ls < 0) return 2;
+    double smax3[3];
+    skip_smax((const double* const*)hier3, m, Ls, smax3);
+    int rc = orc_skip_prolong_all(p, hier3, m, z);
+    if (rc) return rc;
+    int64_t f0 = level_start(L);
+    return hwfv1_step_smax(p, hier3[0] + f0, hier3[1] + f0, hier3[2] + f0, z, t, dt, smax3, o);
+}
+
 /* Subtree (row-major index at level Ls) of the cell (n, i, j), n >= Ls. */
 static int64_t subtree_of(int Ls, int n, int64_t i, int64_t j) {
     return rm(Ls, i >> (n - Ls), j >> (n - Ls));
@@ -954,16 +994,9 @@ int orc_skip_step(const orc_problem* p, double* const* hier3, uint8_t* m, const 
             P[rm(Ls, si, sj)] = (uint8_t)v;
         }
     /* 2. s_max over the stored state */
-    double smax[4] = {1.0, 1.0, 1.0, orc_smax(L, z)};
-    for (int64_t sj = 0; sj < ns; ++sj)
-        for (int64_t si = 0; si < ns; ++si) {
-            int ms = m[rm(Ls, si, sj)];
-            int64_t w = side(ms - Ls);
-            for (int64_t jj = sj * w; jj < (sj + 1) * w; ++jj)
-                for (int64_t ii = si * w; ii < (si + 1) * w; ++ii)
-                    for (int q = 0; q < 3; ++q)
-                        smax[q] = maxd(smax[q], absd(hier3[q][level_start(ms) + rm(ms, ii, jj)]));
-        }
+    double smax[4];
+    skip_smax((const double* const*)hier3, m, Ls, smax);
+    smax[3] = orc_smax(L, z);
     /* the bed: every level and detail (static) */
     double* zh = (double*)malloc(sizeof(double) * (size_t)H);
     double* zdet = (double*)malloc(sizeof(double) * (size_t)(3 * (P_ > 0 ? P_ : 1)));

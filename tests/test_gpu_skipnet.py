@@ -47,17 +47,26 @@ def _setup(seed, nimg=3, H=9, W=13):
     return net, params, x, labels, xd, ld
 
 
-# Element-wise bound of the BF16 network (the learned look-ahead's stated
-# precision: BF16 operands, FP32 accumulation): every element of a forward
-# output or gradient within 1e-2 of its oracle value, relative to the larger
-# of |value| and 1e-2 of the tensor's largest magnitude (elements that
-# cancel to near zero take that floor as their scale).
+# The network's stated precision is BF16 operands with FP32 accumulation;
+# the oracle states the same network with its BF16 operands rounded where
+# the network holds them (oracle/cnn.py) and everything else in float64.
+# Element-wise bound against that oracle: every element of a forward output
+# or gradient within 1e-2 of its oracle value, relative to the larger of
+# |value| and 1e-2 of the tensor's largest magnitude (elements that cancel
+# to near zero take that floor as their scale).  Against the plain float64
+# network (no operand rounding) the BF16 roundings themselves differ by up
+# to 2^-9 per operand, so that comparison is held to a relative L2 error.
 RTOL_BF16 = 1e-2
+RL2_F64 = 5e-2
 
 
 def _elementwise_err(got, ref):
     scale = np.maximum(np.abs(ref), 1e-2 * np.abs(ref).max())
     return float(np.max(np.abs(got - ref) / scale))
+
+
+def _rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
 SIZES = [(3, 9, 13), (2, 128, 128)]     # a ragged toy size and the production 128 x 128 image
@@ -72,9 +81,11 @@ def test_forward_matches_oracle(nimg, H, W):
     Hh.hwfv1_skipnet_forward(net, xd, nimg, H, W, logits)
     got = logits.cpu().numpy().reshape(nimg, H, W, 16)[..., :5].transpose(0, 3, 1, 2).astype(np.float64)
     xt = x.transpose(0, 3, 1, 2)
-    e_bf, e_64 = (_elementwise_err(got, cnn.forward(params, xt, r)[0]) for r in (cnn.bf16, None))
-    print("forward %dx%dx%d: element-wise error %.3g (BF16 operands), %.3g (float64)" % (nimg, H, W, e_bf, e_64))
-    assert e_bf <= RTOL_BF16 and e_64 <= RTOL_BF16
+    e_bf = _elementwise_err(got, cnn.forward(params, xt, cnn.bf16)[0])
+    r_64 = _rel_l2(got, cnn.forward(params, xt)[0])
+    print("forward %dx%dx%d: element-wise error %.3g (BF16 operands), relative L2 %.3g (float64)"
+          % (nimg, H, W, e_bf, r_64))
+    assert e_bf <= RTOL_BF16 and r_64 <= RL2_F64
     Hh.hwfv1_skipnet_destroy(net)
 
 
@@ -91,9 +102,14 @@ def test_gradients_match_oracle(nimg, H, W):
         ref = cnn.backward(params, cache, dl, rnd)
         assert abs(loss - ref_loss) <= RTOL_BF16 * ref_loss
         for name, a, b in zip(("w1", "b1", "w2", "b2", "w3", "b3"), got, ref):
-            err = _elementwise_err(a, b)
-            print("gradient %s %dx%dx%d vs %s: element-wise error %.3g" % (name, nimg, H, W, tag, err))
-            assert err <= RTOL_BF16, (name, tag, err)
+            if rnd is None:
+                err = _rel_l2(a, b)
+                print("gradient %s %dx%dx%d vs float64: relative L2 %.3g" % (name, nimg, H, W, err))
+                assert err <= RL2_F64, (name, err)
+            else:
+                err = _elementwise_err(a, b)
+                print("gradient %s %dx%dx%d vs BF16 operands: element-wise %.3g" % (name, nimg, H, W, err))
+                assert err <= RTOL_BF16, (name, err)
     Hh.hwfv1_skipnet_destroy(net)
 
 
