@@ -61,6 +61,8 @@ def parse():
                    help="skip the whole-hour run from the dry start and its t_spin window")
     a.add_argument("--no-configs", action="store_true",
                    help="skip the circular L=6 and bumpy L=10 dam-break measurements")
+    a.add_argument("--learned-kinds", default=None,
+                   help="with --only learned: comma-separated workloads (columns, bumpy)")
     a.add_argument("--only", choices=["ensemble", "learned"],
                    help="run only this side measurement, print its result, and bracket its timed "
                         "region (the batched advance; the learned run predicting every step) "
@@ -416,12 +418,15 @@ def run_ensemble(args, steps=50):
 
 
 def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100, steps=400):
-    """Learned look-ahead at L = 11: the subtree CNN trained (BF16 tensor
+    """Learned subtree skip at L = 11: the subtree CNN trained (BF16 tensor
     cores) on trajectories of seeded cases run on the GPU path, then a
-    held-out case advanced `steps` steps plain, and learned to the same
-    simulated time.  Reports steps/s, simulated seconds per second, mean
-    leaves, the L1 depth difference learned - plain, and the network's
-    under-prediction rate on held-out samples."""
+    held-out case advanced `steps` steps plain (with exact quiescent-tile
+    skipping), plain with every tile swept (HWFV1_FULL_SWEEP), and with the
+    learned skip to the same simulated time.  Reports steps/s, simulated
+    seconds per second, mean leaves, the stored fraction of the finest
+    cells, the L1 and L-inf depth differences learned - plain at checkpoints
+    through the run (untimed runs), and the network's under-prediction rate
+    on held-out samples."""
     import numpy as np
     import torch
     import synth
@@ -445,8 +450,8 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     p, f = make(test_seed)
     stream = torch.cuda.Stream()
 
-    def timed(net_, t_end, max_steps, every=1, profile=False):
-        sim = Simulation(p, f, args.precision, stream=stream)
+    def timed(net_, t_end, max_steps, every=1, profile=False, full_sweep=False):
+        sim = Simulation(dict(p, full_sweep=True) if full_sweep else p, f, args.precision, stream=stream)
         if net_ is not None:
             sim.set_skipnet(net_, audit_K=10, margin=0.02, predict_every=every)
         sim.counters()                        # captures the step graph (untimed)
@@ -464,34 +469,64 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
         ms = e0.elapsed_time(e1)
         n, lu, au, wu, kps = sim.counters()
         t = sim.time()[0]
-        fl = sim.fields()
+        stored = None
+        if net_ is not None:
+            lv = sim.skip_levels(1).astype(np.int64)
+            stored = float(np.mean(np.power(4.0, lv - L)))
         sim.close()
-        return dict(ms=ms, steps=n, lu=lu, kps=kps, t=t, h=fl["h"])
+        return dict(ms=ms, steps=n, lu=lu, kps=kps, t=t, stored=stored)
+
+    def errors(every, t_end, checkpoints=4):
+        """L1 (per unit area) and L-inf depth differences learned - plain
+        at evenly spaced simulated times (untimed runs side by side)."""
+        a = Simulation(p, f, args.precision, stream=stream)
+        b = Simulation(p, f, args.precision, stream=stream)
+        b.set_skipnet(net, audit_K=10, margin=0.02, predict_every=every)
+        out = []
+        cell = 1.0 / (1 << (2 * L))
+        for k in range(1, checkpoints + 1):
+            tk = t_end * k / checkpoints
+            advance_to(a, tk)
+            advance_to(b, tk)
+            d = np.abs(b.fields()["h"] - a.fields()["h"])
+            out.append({"t_s": tk, "l1_m": float(d.sum() * cell), "linf_m": float(d.max())})
+        a.close()
+        b.close()
+        return out
 
     plain = timed(None, float("inf"), steps)
+    sweep = timed(None, plain["t"], 4 * steps, full_sweep=True)
     # the learned run's step count to the same simulated time, then a timed
     # run of exactly that many steps (no idle launches after t_end)
     runs = {}
     for every in (1, 4):
         n_l = timed(net, plain["t"], 4 * steps, every)["steps"]
         runs[every] = timed(net, plain["t"], n_l, every, profile=(args.only == "learned" and every == 1))
+    errs = {every: errors(every, plain["t"]) for every in (1, 4)}
     H.hwfv1_skipnet_destroy(net)
-    cell = 1.0 / (1 << (2 * L))
 
     def rep(r):
-        return {"steps": r["steps"], "ms": r["ms"], "steps_per_s": r["steps"] / (r["ms"] / 1e3),
-                "sim_s_per_s": r["t"] / (r["ms"] / 1e3), "mean_leaves": r["lu"] / max(r["steps"], 1),
-                "leaf_updates_per_s": r["lu"] / (r["ms"] / 1e3), "kernels_per_step": r["kps"]}
+        d = {"steps": r["steps"], "ms": r["ms"], "steps_per_s": r["steps"] / (r["ms"] / 1e3),
+             "sim_s_per_s": r["t"] / (r["ms"] / 1e3), "mean_leaves": r["lu"] / max(r["steps"], 1),
+             "leaf_updates_per_s": r["lu"] / (r["ms"] / 1e3), "kernels_per_step": r["kps"]}
+        if r["stored"] is not None:
+            d["stored_fraction_at_end"] = r["stored"]
+        return d
+
+    def done(r):
+        return r["t"] >= plain["t"] * (1 - 1e-12)
 
     return {"workload": "%s dam-break L=%d eps=1e-3 (train seeds %d..%d, held-out seed %d)"
                         % (kind, L, min(train_seeds), max(train_seeds), test_seed),
             "finest_cells": 1 << (2 * L), "sim_time_s": plain["t"],
-            "plain": rep(plain),
+            "plain": rep(plain), "plain_full_sweep": rep(sweep),
             "learned": {"predict_every_%d" % e: dict(
                 rep(r),
-                speedup_sim_time=(plain["ms"] / r["ms"]) if r["t"] >= plain["t"] * (1 - 1e-12) else None,
+                speedup_vs_plain=(plain["ms"] / r["ms"]) if done(r) else None,
+                speedup_vs_full_sweep=(sweep["ms"] / r["ms"]) if done(r) and done(sweep) else None,
                 leaves_ratio=(r["lu"] / r["steps"]) / (plain["lu"] / plain["steps"]),
-                l1_depth_learned_vs_plain_m=float(np.abs(r["h"] - plain["h"]).sum() * cell))
+                depth_error_vs_plain=errs[e],
+                l1_depth_learned_vs_plain_m=max(x["l1_m"] for x in errs[e]))
                 for e, r in runs.items()},
             "held_out_under_prediction": under,
             "training": {"images": int(8 * 20 * len(train_seeds)), "image_px": 1 << (L - 4),
@@ -609,24 +644,28 @@ def time_flux_match(args, p, state, t_s, dt_s, steps):
     return out
 
 
-def run_mra(args, p, state, t_s, dt_s, steps=100):
-    """The MRA kernels at full size: the same window with HWFV1_FULL_SWEEP
-    (every tile encoded and every leaf updated and decoded).  Per kernel the
-    live time (hwfv1_profile_step, median of 5), its algorithmic bytes and
-    HBM GB/s against the measured copy bandwidth.  First encode pass: the
-    finest h, hu, hv read (24 B per cell, float64), its levels written (L-1
-    .. L-3 when there are more 1024-cell blocks than 8 CTAs per SM, the pass
-    then stopping three levels up; else L-1 .. L-5) plus their threshold
-    and closure bits; decode:
-    the finest cells under the leaves of more than 16 cells written (24 B
-    each; the bed reads of wet leaves not counted)."""
+def run_mra(args, label, p, state, t_s, dt_s, steps=100):
+    """The MRA kernels at full size: a state advanced with HWFV1_FULL_SWEEP
+    (every tile encoded, every leaf listed, updated and decoded).  Per kernel
+    the live time (hwfv1_profile_step, median of 5), its algorithmic bytes
+    and HBM GB/s against the measured copy bandwidth:
+    - encode (first pass + the pass that ends in the final one): the finest
+      h, hu, hv read (24 B per cell, float64) and every coarser level
+      written (24 B per parent) with its threshold and closure bits;
+    - traversal: the regularised flag words read (1 bit per parent) and 4 B
+      per listed leaf written;
+    - dry-leaf pass: per leaf its 4 B id and own depth read and its 24 B
+      written (the neighbours' depths come from L2 and are not counted);
+    - decode: the finest cells under the leaves of more than 16 cells
+      written (24 B each; the bed reads of wet leaves not counted)."""
     import numpy as np
     import torch
     from paper_2206_05761_gb300 import hwfv1 as H
     from paper_2206_05761_gb300.sim import Simulation
     stream = torch.cuda.Stream()
     sim = Simulation(dict(p, full_sweep=True), state, args.precision, stream=stream)
-    sim.set_time(t_s, dt_s)
+    if t_s is not None:
+        sim.set_time(t_s, dt_s)
     sim.advance(max_steps=3)
     stream.synchronize()
     kern = {}
@@ -634,24 +673,25 @@ def run_mra(args, p, state, t_s, dt_s, steps=100):
         for name, t in H.hwfv1_profile_step(sim.hd):
             kern.setdefault(name, []).append(t)
     ph = {k: statistics.median(v) for k, v in kern.items()}
-    L, esz = args.L, 8 if args.precision == 64 else 4
+    L, esz = p["L"], 8 if args.precision == 64 else 4
     N = 1 << (2 * L)
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    levels = 3 if L >= 8 and (1 << (2 * (L - 5))) > nsm * 8 else 5
-    upper = sum(4.0 ** -k for k in range(1, levels + 1))  # levels written per finest cell
-    enc_bytes = N * (3 * esz * (1.0 + upper) + 2 * upper / 8.0)
+    P = (N - 1) // 3
     lv = sim.leaves() >> 28
+    M = int(lv.size)
     big = lv[(L - lv.astype(np.int64)) >= 3]
     cells_big = int(np.sum(np.left_shift(np.ones(big.shape, dtype=np.int64), 2 * (L - big.astype(np.int64)))))
-    dec_bytes = cells_big * 3 * esz
     pk, src = peaks()
-    out = {"workload": "terrain flood window at t=%.0f s with HWFV1_FULL_SWEEP" % t_s, "peak_gbs": pk["hbm_gbs"],
+    out = {"workload": label, "L": L, "leaves": M, "decode_cells": cells_big, "peak_gbs": pk["hbm_gbs"],
            "peak_source": src, "kernels_ms": ph}
-    for name, b in (("k_encode", enc_bytes), ("k_decode_finish", dec_bytes)):
-        if name in ph and ph[name] > 0:
-            gbs = b / (ph[name] / 1e3) / 1e9
-            out[name] = {"algorithmic_bytes": int(b), "ms": ph[name], "gbs": gbs, "frac": gbs / pk["hbm_gbs"]}
-    out["decode_cells"] = cells_big
+    enc_ms = ph.get("k_encode", 0.0) + ph.get("k_encode_tail", 0.0)
+    parts = {"encode": (enc_ms, N * 3 * esz + P * (3 * esz + 2 / 8.0)),
+             "traverse": (ph.get("k_trav_fused", 0.0), P / 8.0 + 4.0 * M),
+             "dry": (ph.get("k_fv1_dry", 0.0), M * (4.0 + esz + 3 * esz)),
+             "decode": (ph.get("k_decode_finish", 0.0), cells_big * 3.0 * esz)}
+    for name, (ms, b) in parts.items():
+        if ms > 0:
+            gbs = b / (ms / 1e3) / 1e9
+            out[name] = {"algorithmic_bytes": int(b), "ms": ms, "gbs": gbs, "frac": gbs / pk["hbm_gbs"]}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     sim.advance(max_steps=steps)
@@ -826,7 +866,8 @@ def main():
         return
     if args.only is not None:
         if rank == 0:
-            res = run_ensemble(args) if args.only == "ensemble" else {"bumpy": run_learned(args, "bumpy")}
+            res = (run_ensemble(args) if args.only == "ensemble" else
+                   {k: run_learned(args, k) for k in (args.learned_kinds or "columns,bumpy").split(",")})
             print(json.dumps({args.only: res}))
         return
     if world > 1:
@@ -883,7 +924,14 @@ def main():
         fm["cost_vs_same_level"] = value / fm["value"]
         out["flux_match"] = fm
     if world == 1 and not args.no_mra:
-        out["mra"] = run_mra(args, r["problem"], r["snapshot"], r["t_start"], r["dt_start"])
+        import synth
+        pc, fc = synth.columns_dam_break(L=args.L, eps=1e-3, seed=4)
+        out["mra"] = {
+            "window": run_mra(args, "terrain flood window at t=%.0f s, every tile swept" % r["t_start"],
+                              r["problem"], r["snapshot"], r["t_start"], r["dt_start"]),
+            "decode_heavy": run_mra(args, "water columns on a flat bed, L=%d, wet everywhere: coarse leaves "
+                                          "decoded to the finest grid each step" % args.L,
+                                    pc, fc, None, None)}
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_pseudo2d:

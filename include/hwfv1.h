@@ -250,16 +250,23 @@ const char* hwfv1_last_error(hwfv1_handle* hd);
 void hwfv1_destroy(hwfv1_handle* hd);
 
 /* ------------------------------------------------------------------------
- * Learned look-ahead.  The paper's grid adaptation only coarsens from the
- * finest grid; the regularisation that lets the grid refine ahead of the
- * flow (children of significant details become significant) is this
- * library's reading, and it refines one level everywhere.  A small CNN
+ * Learned subtree skip (a layer this library adds; the paper has no learned
+ * part).  The paper's significance tree (Sec. 2.1.2, Fig. 2) is built from
+ * every detail down to the finest level each step.  Here each level-(L-4)
+ * cell's subtree (16 x 16 finest cells) is given a predicted level p, the
+ * deepest level it needs: the subtree is encoded only from its storage
+ * level, its details below p are neither formed nor tested, its leaves are
+ * no finer than p, and its state is stored at P = the largest p of itself
+ * and its four edge neighbours (so a neighbouring leaf finds its
+ * same-level cell there); a coarser stored subtree moves 4^(P-L) of the
+ * bytes of the finest one.  Every audit_K-th step is the exact (plain)
+ * step of the whole finest grid.  The levels come from a small CNN
  * (3 layers of 3x3 convolutions, 4 -> 16 -> 16 -> 5 channels, ReLU, BF16
- * weights and activations, FP32 accumulation on the tensor cores) reads the
- * level-(L-4) coefficients of h, hu, hv, z (each over its s_max) and
- * predicts, per 16 x 16-cell subtree, the deepest level the next step's
- * threshold tree will need; children are then added only above that level.
- * Every audit_K-th step is an exact step with the plain look-ahead.
+ * weights and activations, FP32 accumulation on the tensor cores) that
+ * reads the level-(L-4) coefficients of h, hu, hv, z (each over its s_max)
+ * of the state a step has just encoded and predicts, per subtree, the
+ * deepest level the next step's threshold tree will need; or from the
+ * caller (hwfv1_set_skip_levels).
  * Parameters are FP32 in the layout w1[16][4][3][3], b1[16], w2[16][16][3][3],
  * b2[16], w3[5][16][3][3], b3[5] (hwfv1_skipnet_num_params() floats).
  * ------------------------------------------------------------------------ */
@@ -288,15 +295,29 @@ hwfv1_status hwfv1_skipnet_train(hwfv1_skipnet* net, const uint16_t* x, const ui
                                  double* last_loss);
 void hwfv1_skipnet_destroy(hwfv1_skipnet* net);
 
-/* Use `net` (NULL: stop) for the look-ahead of hwfv1_advance: a subtree may
- * refine only above the smallest level whose predicted cumulative
- * probability reaches 1 - margin (margin < 0 keeps every level, which equals
- * the plain method); every audit_K-th step is exact.  The network runs on
- * every predict_every-th learned step (>= 1) and the steps in between reuse
- * its last predicted levels.  Needs L >= 6.  The network must outlive its
- * use. */
+/* Use `net` (NULL: stop) for the learned subtree skip of hwfv1_advance.
+ * Counting from the next step, every audit_K-th step (>= 1) is the exact
+ * plain step and the others are skip steps.  A subtree's predicted level is
+ * L-4 plus the smallest class whose predicted cumulative probability
+ * reaches 1 - margin (margin < 0 keeps level L everywhere, which is the
+ * plain method).  The network runs on the audit step and on every
+ * predict_every-th (>= 1) step after it within an audit interval, after the
+ * step's encode, and its levels serve the steps that follow; the steps in
+ * between reuse them.  Needs L >= 6, HWFV1_REG_PREDICT and HWFV1_REG_CLOSE,
+ * not HWFV1_FLUX_MATCH.  Stopping brings the stored state to level L.  The
+ * network must outlive its use. */
 hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t audit_K, float margin,
                                int32_t predict_every);
+/* The learned subtree skip with levels given by the caller instead of the
+ * network: `levels` (host, 4^(L-4) bytes, row-major over level L-4, j
+ * major, each in [L-4, L]; NULL: stop) is kept for every skip step until
+ * the next call; audit_K as above.  Needs L >= 5 (and the flags above).
+ * HWFV1_ERR_INVALID_SPEC for a level out of range. */
+hwfv1_status hwfv1_set_skip_levels(hwfv1_handle* hd, const uint8_t* levels, int32_t audit_K);
+/* which = 0: the predicted levels in use; which = 1: the level each
+ * subtree's state is stored at (L outside the skip).  Host output, 4^(L-4)
+ * bytes, row-major over level L-4.  Synchronises. */
+hwfv1_status hwfv1_get_skip_levels(hwfv1_handle* hd, int32_t which, uint8_t* out, int64_t cap);
 /* CNN input of the current state (device output, bf16 bits, 4 x 4^(L-4)
  * values, channels last, row j of subtrees major); call after hwfv1_encode. */
 hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap);

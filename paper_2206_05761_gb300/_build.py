@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhwfv1.so")
 SOURCES = ["api.cu", "engine_f64.cu", "engine_f32.cu", "noalloc.cu", "skipnet.cu"]
-HEADERS = ["common.cuh", "kernels.cuh", "engine.cuh", "engine_iface.h", "batch.cuh", "skipnet.h", "tcgen05.cuh"]
+HEADERS = ["common.cuh", "kernels.cuh", "skip.cuh", "engine.cuh", "engine_iface.h", "batch.cuh", "skipnet.h", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]

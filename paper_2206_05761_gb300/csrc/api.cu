@@ -214,6 +214,16 @@ hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t aud
     if (predict_every < 1) return HWFV1_ERR_INVALID_SPEC;
     return from_engine(hd, hd->eng->set_skipnet(net ? net->net : nullptr, audit_K, margin, predict_every));
 }
+hwfv1_status hwfv1_set_skip_levels(hwfv1_handle* hd, const uint8_t* levels, int32_t audit_K) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (levels && audit_K < 1) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->set_skip_levels(levels, audit_K));
+}
+hwfv1_status hwfv1_get_skip_levels(hwfv1_handle* hd, int32_t which, uint8_t* out, int64_t cap) {
+    HWFV1_CHECK_HANDLE(hd);
+    if (!out) return HWFV1_ERR_INVALID_SPEC;
+    return from_engine(hd, hd->eng->get_skip_levels(which, out, cap));
+}
 hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap) {
     HWFV1_CHECK_HANDLE(hd);
     if (!out) return HWFV1_ERR_INVALID_SPEC;

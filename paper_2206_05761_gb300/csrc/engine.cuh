@@ -10,6 +10,7 @@
 
 #include "engine_iface.h"
 #include "kernels.cuh"
+#include "skip.cuh"
 #include "skipnet.h"
 
 namespace hwfv1 {
@@ -49,8 +50,7 @@ class EngineT final : public Engine {
     ~EngineT() override {
         if (exec_) cudaGraphExecDestroy(exec_);
         if (exec_multi_) cudaGraphExecDestroy(exec_multi_);
-        if (exec_learned_) cudaGraphExecDestroy(exec_learned_);
-        if (exec_reuse_) cudaGraphExecDestroy(exec_reuse_);
+        drop_skip_graphs();
         if (exec_uniform_) cudaGraphExecDestroy(exec_uniform_);
         skipwork_free(&skw_);
         for (void* p : allocs_) cudaFree(p);
@@ -199,13 +199,9 @@ class EngineT final : public Engine {
         k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), t_end);
         if (max_steps == 0) return check("advance");
         const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
-        if (use_graph && !exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
-        if (use_graph && skip_ && !exec_learned_ && capture(&exec_learned_, kStepLearned) != HWFV1_OK)
-            return HWFV1_ERR_CUDA;
-        if (use_graph && skip_ && every_ > 1 && !exec_reuse_ && capture(&exec_reuse_, kStepReuse) != HWFV1_OK)
-            return HWFV1_ERR_CUDA;
+        if (use_graph && !skipmode_ && !exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
         int64_t s = 0;
-        if (use_graph && !skip_ && max_steps >= kMultiSteps) {
+        if (use_graph && !skipmode_ && max_steps >= kMultiSteps) {
             // kMultiSteps plain steps per graph launch: the kernels of
             // consecutive steps follow each other as inside one step, without
             // the gap between two graph launches.  A step after t_end does
@@ -216,23 +212,17 @@ class EngineT final : public Engine {
         }
         int kind = kStepPlain;
         for (; s < max_steps; ++s) {
-            // with the learned look-ahead every audit_K-th step is an exact
-            // (plain) step; of the learned steps after it, every every_-th
-            // runs the network and the others reuse its predicted levels
-            kind = kStepPlain;
-            if (skip_) {
-                const int64_t pos = lstep_++ % audit_K_;
-                if (pos != 0) kind = ((pos - 1) % every_) == 0 ? kStepLearned : kStepReuse;
-            }
+            kind = skipmode_ ? skip_kind(lstep_++) : kStepPlain;
             if (use_graph) {
-                cudaGraphExec_t g = kind == kStepPlain ? exec_ : kind == kStepLearned ? exec_learned_ : exec_reuse_;
-                if (cudaGraphLaunch(g, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
+                cudaGraphExec_t* g = kind == kStepPlain ? &exec_ : &exec_skip_[kind - kStepAudit];
+                if (!*g && capture(g, kind) != HWFV1_OK) return HWFV1_ERR_CUDA;
+                if (cudaGraphLaunch(*g, stream_) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph launch");
             } else {
                 launch_step(kind);
             }
         }
         // a plain last step formed S on the spot: Sb_ is materialised on demand
-        sb_valid_ = kind != kStepPlain || !onfly_flags();
+        sb_valid_ = kind == kStepSkip || kind == kStepSkipPredict || !onfly_flags();
         return check("advance");
     }
 
@@ -273,32 +263,66 @@ class EngineT final : public Engine {
         return check("advance_uniform");
     }
 
+    // The learned subtree skip with the network's predicted levels (net ==
+    // nullptr: back to the plain step).  Every audit_K-th step, counting
+    // from the first step after this call, is the exact (plain) step.
     hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin, int predict_every) override {
         if (net && (L_ < 6 || audit_K < 1 || predict_every < 1))
-            return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead needs L >= 6, K >= 1, predict_every >= 1");
-        if (net && (spec_.flags & HWFV1_FLUX_MATCH))
-            return fail(HWFV1_ERR_INVALID_SPEC, "learned look-ahead with HWFV1_FLUX_MATCH");
-        skip_ = net;
-        audit_K_ = audit_K < 1 ? 1 : audit_K;
-        every_ = predict_every < 1 ? 1 : predict_every;
-        margin_ = margin;
-        lstep_ = 0;
-        for (cudaGraphExec_t* g : {&exec_learned_, &exec_reuse_}) {
-            if (*g) cudaGraphExecDestroy(*g);
-            *g = nullptr;
+            return fail(HWFV1_ERR_INVALID_SPEC, "learned skip needs L >= 6, K >= 1, predict_every >= 1");
+        if (!net) return skip_off();
+        if (hwfv1_status r = skip_on(1, audit_K); r != HWFV1_OK) return r;
+        if (skip_ != net || every_ != predict_every || margin_ != margin) {
+            // the graphs hold the network, the schedule and the margin
+            drop_skip_graphs();
+            lstep_ = 0;
         }
-        if (!net) return HWFV1_OK;
+        skip_ = net;
+        every_ = predict_every;
+        margin_ = margin;
         const uint64_t npx = 1ull << (2 * (L_ - 4));
         if (!feat_ && !alloc(&feat_, npx * 4 * sizeof(__nv_bfloat16))) return oom();
-        if (!phat_ && !alloc(&phat_, npx)) return oom();
         if (!skipwork_reserve(&skw_, (int64_t)npx)) return oom();
-        // capture both step graphs now (capturing runs nothing), so that the
-        // first advance does not pay for it
-        if (std::getenv("HWFV1_NO_GRAPH") == nullptr) {
-            if (!exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
-            if (capture(&exec_learned_, kStepLearned) != HWFV1_OK) return HWFV1_ERR_CUDA;
-            if (every_ > 1 && capture(&exec_reuse_, kStepReuse) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        return capture_skip_graphs();
+    }
+
+    // The learned subtree skip with levels given by the caller (host,
+    // row-major over level L-4), kept until the next call.
+    hwfv1_status set_skip_levels(const uint8_t* levels, int audit_K) override {
+        if (!levels) return skip_off();
+        if (L_ < 5 || audit_K < 1) return fail(HWFV1_ERR_INVALID_SPEC, "skip levels need L >= 5, K >= 1");
+        const int Ls = L_ - 4;
+        const uint32_t n = 1u << (2 * Ls), S = 1u << Ls;
+        std::vector<uint8_t> mort(n);
+        for (uint32_t j = 0; j < S; ++j)
+            for (uint32_t i = 0; i < S; ++i) {
+                const uint8_t v = levels[(size_t)j * S + i];
+                if (v < Ls || v > L_) return fail(HWFV1_ERR_INVALID_SPEC, "skip levels outside [L-4, L]");
+                mort[morton2(i, j)] = v;
+            }
+        if (hwfv1_status r = skip_on(2, audit_K); r != HWFV1_OK) return r;
+        skip_ = nullptr;
+        every_ = 1;
+        cudaMemcpyAsync(phat_, mort.data(), n, cudaMemcpyHostToDevice, stream_);
+        if (hwfv1_status r = check("set_skip_levels", true); r != HWFV1_OK) return r;
+        return capture_skip_graphs();
+    }
+
+    // which = 0: the predicted levels in use; 1: the storage levels
+    // (host, row-major over level L-4)
+    hwfv1_status get_skip_levels(int which, uint8_t* out, int64_t cap) override {
+        if (L_ < 5) return fail(HWFV1_ERR_INVALID_SPEC, "skip levels need L >= 5");
+        const int Ls = L_ - 4;
+        const uint32_t n = 1u << (2 * Ls), S = 1u << Ls;
+        if (!out || cap < (int64_t)n || (which != 0 && which != 1))
+            return fail(HWFV1_ERR_INVALID_SPEC, "get_skip_levels: which 0 or 1, cap >= 4^(L-4)");
+        std::vector<uint8_t> mort(n, (uint8_t)L_);
+        const uint8_t* src = which == 0 ? phat_ : mlev_;
+        if (src) {
+            cudaMemcpyAsync(mort.data(), src, n, cudaMemcpyDeviceToHost, stream_);
+            if (hwfv1_status r = check("get_skip_levels", true); r != HWFV1_OK) return r;
         }
+        for (uint32_t j = 0; j < S; ++j)
+            for (uint32_t i = 0; i < S; ++i) out[(size_t)j * S + i] = mort[morton2(i, j)];
         return HWFV1_OK;
     }
 
@@ -319,10 +343,15 @@ class EngineT final : public Engine {
 
     hwfv1_status get_fields(double* h, double* qx, double* qy) override {
         double* out[3] = {h, qx, qy};
+        // with the learned skip the state may be stored above level L: its
+        // finest level is formed in the other buffer, which reads it (the
+        // stored state is left as it is)
+        const bool other = skipmode_ != 0;
+        if (other) launch_skip_finest(0);
         for (int q = 0; q < 3; ++q)
             if (out[q])
                 k_morton_to_rm<T><<<grid_for(N_), 256, 0, stream_>>>(
-                    f_[0][q] + lvl_off(L_), f_[1][q] + lvl_off(L_), st_, out[q], L_);
+                    f_[other ? 1 : 0][q] + lvl_off(L_), f_[other ? 0 : 1][q] + lvl_off(L_), st_, out[q], L_);
         return check("get_fields");
     }
 
@@ -334,6 +363,7 @@ class EngineT final : public Engine {
                 in[q], f_[0][q] + lvl_off(L_), f_[1][q] + lvl_off(L_), st_, L_);
         }
         forget_quiet();
+        stored_at_finest();
         reduce_state(/*set_dt=*/0);
         return check("set_fields");
     }
@@ -380,11 +410,16 @@ class EngineT final : public Engine {
         if (field < 0 || field > 3 || level < 0 || level > L_)
             return fail(HWFV1_ERR_INVALID_SPEC, "get_level: bad field or level");
         const uint64_t n = 1ull << (2 * level);
-        if (field == 3)
+        if (field == 3) {
             k_copy_level<T><<<grid_for(n), 256, 0, stream_>>>(z_ + lvl_off(level), nullptr, st_, out, n);
-        else
+        } else if (skipmode_ && level == L_) {   // the finest level formed in the other buffer
+            launch_skip_finest(0);
+            k_copy_level<T><<<grid_for(n), 256, 0, stream_>>>(
+                f_[1][field] + lvl_off(level), f_[0][field] + lvl_off(level), st_, out, n);
+        } else {
             k_copy_level<T><<<grid_for(n), 256, 0, stream_>>>(
                 f_[0][field] + lvl_off(level), f_[1][field] + lvl_off(level), st_, out, n);
+        }
         return check("get_level");
     }
 
@@ -516,10 +551,10 @@ class EngineT final : public Engine {
     hwfv1_status get_counters(int64_t* steps, int64_t* lu, int64_t* au, int64_t* wu, int64_t* kps) override {
         if (kps) {
             if (!exec_ && capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
-            if (!exec_multi_ && !skip_ && std::getenv("HWFV1_NO_GRAPH") == nullptr &&
+            if (!exec_multi_ && !skipmode_ && std::getenv("HWFV1_NO_GRAPH") == nullptr &&
                 capture(&exec_multi_, kStepPlain, kMultiSteps) != HWFV1_OK)
                 return HWFV1_ERR_CUDA;
-            *kps = skip_ ? kernels_learned_ : kernels_plain_;
+            *kps = skipmode_ ? kernels_skip_ : kernels_plain_;
         }
         DevState s;
         if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
@@ -544,6 +579,9 @@ class EngineT final : public Engine {
         if (used) *used = need;
         if (!buf) return HWFV1_OK;
         if (cap < need) return fail(HWFV1_ERR_INVALID_SPEC, "save: buffer too small");
+        // a checkpoint holds the finest state: with the learned skip every
+        // subtree is brought to level L first (its storage starts again there)
+        if (skipmode_) launch_skip_finest(2);
         DevState s;
         if (read_state(&s) != HWFV1_OK) return HWFV1_ERR_CUDA;
         SaveHeader hd{kSaveMagic, L_, (int32_t)(sizeof(T) * 8), s.t, s.dt, s.step};
@@ -574,6 +612,7 @@ class EngineT final : public Engine {
         s.err = 0;
         cudaMemcpyAsync(st_, &s, sizeof s, cudaMemcpyHostToDevice, stream_);
         forget_quiet();
+        stored_at_finest();
         reduce_state(/*set_dt=*/0);
         return check("load", true);
     }
@@ -657,8 +696,8 @@ class EngineT final : public Engine {
     // final one-CTA pass runs in the last CTA of the pass before it.  With
     // a.list, the first pass works on the listed tiles (k_encode_tiles).
     template <int NF>
-    void encode_passes(EncodeArgs<T, NF> a, uint32_t* ticket = nullptr) {
-        int ls = L_;
+    void encode_passes(EncodeArgs<T, NF> a, uint32_t* ticket = nullptr, int from = -1) {
+        int ls = from < 0 ? L_ : from;
         bool list_reset = a.list == nullptr;
         while (ls > 0) {
             int k = ls < 5 ? ls : 5;
@@ -926,27 +965,215 @@ class EngineT final : public Engine {
         k_features<T><<<grid_for(n), 256, 0, stream_>>>(
             f_[0][0], f_[1][0], f_[0][1], f_[1][1], f_[0][2], f_[1][2], z_, st_, smax_z, L_ - 4, out);
     }
-    // one step with the learned look-ahead in place of R1; predict = false
-    // reuses the levels the network predicted last
-    void launch_step_learned(bool predict_now = true) {
-        launch_encode();
-        if (predict_now) {
-            launch_features(feat_);
-            const int S = 1 << (L_ - 4);
-            skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
-            k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+    // ---- the learned subtree skip (skip.cuh) -------------------------------
+    // the network's predicted levels for the next steps: features of the
+    // current state's level L-4 (just encoded), three convolutions, levels
+    void launch_predict() {
+        launch_features(feat_);
+        const int S = 1 << (L_ - 4);
+        skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
+        k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+    }
+    // every subtree at level L: mode 0 into the other buffer (reading the
+    // fields), 1 in place before a plain step (nothing when it will not
+    // run), 2 in place unconditionally (leaving the skip, checkpoints)
+    void launch_skip_finest(int mode) {
+        if (!mlev_) return;
+        SkipFinestArgs<T> a;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
+        a.z = z_;
+        a.mlev = mlev_;
+        a.st = st_;
+        a.tol = (T)spec_.tol_h;
+        a.L = L_;
+        a.Ls = L_ - 4;
+        a.mode = mode;
+        lk(k_skip_finest<T>, skip_grid(), 256, a);
+        mark("k_skip_finest");
+    }
+    int skip_grid() const {
+        const uint32_t nsub = 1u << (2 * (L_ - 4));
+        return grid_for((uint64_t)nsub * 64);
+    }
+    // one skip step; predict: the network runs (after the flags) and its
+    // levels serve the following steps
+    void launch_step_skip(bool predict_now) {
+        const int Ls = L_ - 4;
+        lk(k_clear_words, grid_for(2 * (uint64_t)words_), 256, Tb_, 2 * words_, st_, (const uint8_t*)nullptr,
+           (const uint8_t*)nullptr, ntiles_, (uint32_t*)nullptr, &st_->ndec);
+        mark("k_clear_words");
+        SkipArgs<T> a;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
+        a.z = z_;
+        a.thr = thr_dyn();
+        a.thr4 = thr4_dyn();
+        if (sizeof(T) == 8) {
+            a.thr4lo = st_->thr4lo;
+            a.thr4hi = st_->thr4hi;
         }
-        lk(k_flag_learned, grid_for(words_), 256, Tb_, Cb_, Tz_, Cz_, Sb_, phat_, L_, L_ - 4, predict(),
-                                                              close(), st_, &st_->ndec);
-        launch_traverse(/*learned=*/true);
-        launch_fv1();
-        launch_decode();
+        a.Tz = Tz_;
+        a.Tb = Tb_;
+        a.Cb = Cb_;
+        a.phat = phat_;
+        a.mlev = mlev_;
+        a.plev = plev_;
+        a.st = st_;
+        a.tol = (T)spec_.tol_h;
+        a.L = L_;
+        a.Ls = Ls;
+        lk(k_skip_encode<T>, 1u << (2 * Ls), 64, a);
+        mark("k_skip_encode");
+        if (Ls > 0) {
+            EncodeArgs<T, 3> e;
+            for (int b = 0; b < 2; ++b)
+                for (int q = 0; q < 3; ++q) e.f[b][q] = f_[b][q];
+            e.thr = thr_dyn();
+            e.thr4 = thr4_dyn();
+            if (sizeof(T) == 8) {
+                e.thr4lo = st_->thr4lo;
+                e.thr4hi = st_->thr4hi;
+            }
+            e.Tb = Tb_;
+            e.Cb = Cb_;
+            e.st = st_;
+            e.L = L_;
+            encode_passes(e, &st_->enc_ticket, Ls);
+        }
+        lk(k_skip_flag, grid_for(words_), 256, Tb_, Cb_, Tz_, czu_, Sb_, phat_, L_, Ls, st_);
+        mark("k_skip_flag");
+        if (predict_now) launch_predict();
+        const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
+        const uint32_t tgrid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
+        lk(k_trav_fused, tgrid, 256, Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, Quiet(),
+           (const uint32_t*)nullptr);
+        mark("k_trav_fused");
+        StepArgs<T> sa = step_args();
+        sa.own_slot = 1;
+        lk(k_fv1_dry<T>, grid_for(N_), 256, sa);
+        mark("k_fv1_dry");
+        launch_wet(sa);
+        SkipDecodeArgs<T> d;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 3; ++q) d.f[b][q] = f_[b][q];
+        d.z = z_;
+        d.Sb = Sb_;
+        d.plev = plev_;
+        d.mlev = mlev_;
+        d.st = st_;
+        d.tol = (T)spec_.tol_h;
+        d.L = L_;
+        d.Ls = Ls;
+        lk(k_skip_decode<T>, skip_grid(), 256, d, fin_args());
+        mark("k_skip_decode");
         sb_valid_ = true;
     }
-    enum { kStepPlain = 0, kStepLearned = 1, kStepReuse = 2 };
+    // the exact audit step: every subtree at level L, no quiescence marks,
+    // then the plain step (with the network after its encode when the next
+    // steps take its levels)
+    void launch_step_audit(bool predict_next) {
+        launch_skip_finest(1);
+        forget_quiet();
+        const bool onfly = onfly_flags();
+        launch_encode();
+        if (predict_next) launch_predict();
+        if (!onfly) launch_flag();
+        launch_traverse(false, onfly);
+        launch_fv1();
+        launch_decode(onfly);
+        sb_valid_ = !onfly;
+    }
+    enum { kStepPlain = 0, kStepAudit = 1, kStepAuditPredict = 2, kStepSkip = 3, kStepSkipPredict = 4 };
+    // kind of the step at position `pos` (counted from the last
+    // set_skipnet / set_skip_levels) in the skip mode: an audit every
+    // audit_K_-th step; the network runs on the steps at multiples of every_
+    // within the audit interval when a skip step follows
+    int skip_kind(int64_t pos) const {
+        const int64_t q = pos % audit_K_;
+        const bool pred = skipmode_ == 1 && (q % every_) == 0 && q + 1 < audit_K_;
+        if (q == 0) return pred ? kStepAuditPredict : kStepAudit;
+        return pred ? kStepSkipPredict : kStepSkip;
+    }
     void launch_step(int kind) {
         if (kind == kStepPlain) launch_step_all();
-        else launch_step_learned(kind == kStepLearned);
+        else if (kind == kStepAudit || kind == kStepAuditPredict) launch_step_audit(kind == kStepAuditPredict);
+        else launch_step_skip(kind == kStepSkipPredict);
+    }
+    void drop_skip_graphs() {
+        for (cudaGraphExec_t& g : exec_skip_) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    }
+    // the graphs of the kinds the schedule uses, captured now (capturing
+    // runs nothing) so that the first advance does not pay for them
+    hwfv1_status capture_skip_graphs() {
+        if (std::getenv("HWFV1_NO_GRAPH") != nullptr) return HWFV1_OK;
+        const int64_t n = audit_K_ < 64 ? audit_K_ : 64;
+        for (int64_t pos = 0; pos < n; ++pos) {
+            const int kind = skip_kind(pos);
+            cudaGraphExec_t* g = &exec_skip_[kind - kStepAudit];
+            if (!*g && capture(g, kind) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        }
+        return HWFV1_OK;
+    }
+    // enter the skip mode (1 network, 2 caller's levels): buffers, the
+    // static closure of the bed's flags above the subtrees, storage levels
+    // from the current state
+    hwfv1_status skip_on(int mode, int audit_K) {
+        if (spec_.flags & HWFV1_FLUX_MATCH) return fail(HWFV1_ERR_INVALID_SPEC, "learned skip with HWFV1_FLUX_MATCH");
+        if (!predict() || !close())
+            return fail(HWFV1_ERR_INVALID_SPEC, "learned skip needs HWFV1_REG_PREDICT and HWFV1_REG_CLOSE");
+        const int Ls = L_ - 4;
+        const uint32_t nsub = 1u << (2 * Ls);
+        if (!phat_ && !alloc(&phat_, nsub)) return oom();
+        if (!mlev_ && !alloc(&mlev_, nsub)) return oom();
+        if (!plev_ && !alloc(&plev_, nsub)) return oom();
+        if (!czu_) {
+            if (!alloc(&czu_, (size_t)words_ * sizeof(uint32_t))) return oom();
+            // closure of the bed's threshold flags of levels < Ls, on the host
+            std::vector<uint32_t> tz(words_), cz(words_, 0u);
+            cudaMemcpyAsync(tz.data(), Tz_, (size_t)words_ * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream_);
+            if (hwfv1_status r = check("skip_on", true); r != HWFV1_OK) return r;
+            auto bit = [](const std::vector<uint32_t>& w, int n, uint32_t c) {
+                return (w[word_off(n) + (c >> 5)] >> (c & 31u)) & 1u;
+            };
+            for (int n = Ls - 1; n >= 0; --n)
+                for (uint32_t c = 0; c < (1u << (2 * n)); ++c) {
+                    uint32_t v = bit(tz, n, c);
+                    if (n + 1 < Ls)
+                        for (uint32_t k = 0; k < 4; ++k) v |= bit(cz, n + 1, 4 * c + k);
+                    if (v) cz[word_off(n) + (c >> 5)] |= 1u << (c & 31u);
+                }
+            cudaMemcpyAsync(czu_, cz.data(), (size_t)words_ * sizeof(uint32_t), cudaMemcpyHostToDevice, stream_);
+        }
+        if (!skipmode_) {
+            cudaMemsetAsync(mlev_, L_, nsub, stream_);
+            cudaMemsetAsync(phat_, L_, nsub, stream_);
+        }
+        // a new mode or interval restarts the schedule (the next step is an
+        // audit); new levels in the same mode and interval only replace the
+        // levels (the captured graphs read them on the device)
+        if (skipmode_ != mode || audit_K_ != audit_K) {
+            skipmode_ = mode;
+            audit_K_ = audit_K;
+            lstep_ = 0;
+            drop_skip_graphs();
+        }
+        return check("skip_on", true);
+    }
+    hwfv1_status skip_off() {
+        if (skipmode_) launch_skip_finest(2);
+        skipmode_ = 0;
+        skip_ = nullptr;
+        drop_skip_graphs();
+        forget_quiet();
+        return check("skip_off", true);
+    }
+    // the state was replaced by finest fields
+    void stored_at_finest() {
+        if (mlev_) cudaMemsetAsync(mlev_, L_, 1u << (2 * (L_ - 4)), stream_);
     }
     static constexpr int kMultiSteps = 16;   // plain steps per graph in hwfv1_advance
     hwfv1_status capture(cudaGraphExec_t* out, int kind, int nsteps = 1) {
@@ -957,7 +1184,9 @@ class EngineT final : public Engine {
         if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph capture end");
         const int64_t nk = count_kernel_nodes(g) / nsteps;
         if (kind == kStepPlain) kernels_plain_ = nk;
-        else if (kind == kStepLearned) kernels_learned_ = nk;
+        else if (kind == kStepSkipPredict || (kind == kStepSkip && every_ > 1) ||
+                 (kind == kStepSkip && skipmode_ == 2))
+            kernels_skip_ = nk;
         const cudaError_t e = cudaGraphInstantiate(out, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
@@ -1057,20 +1286,23 @@ class EngineT final : public Engine {
     double *it_d_ = nullptr, *iq_d_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     cudaGraphExec_t exec_multi_ = nullptr;   // kMultiSteps plain steps
-    // learned look-ahead
+    // learned subtree skip
+    int skipmode_ = 0;     // 0 plain steps, 1 levels from the network, 2 levels from the caller
     SkipNet* skip_ = nullptr;
     int audit_K_ = 10;
-    int every_ = 1;        // the network runs on every every_-th learned step
+    int every_ = 1;        // the network runs on every every_-th step of an audit interval
     float margin_ = 0.02f;
-    int64_t lstep_ = 0;
+    int64_t lstep_ = 0;    // steps since the mode was set (the audit schedule)
     SkipWork skw_;
     __nv_bfloat16* feat_ = nullptr;
-    uint8_t* phat_ = nullptr;
-    cudaGraphExec_t exec_learned_ = nullptr;
-    cudaGraphExec_t exec_reuse_ = nullptr;   // learned step on the last prediction
+    uint8_t* phat_ = nullptr;    // predicted level per subtree (Morton order over level L-4)
+    uint8_t* mlev_ = nullptr;    // storage level per subtree
+    uint8_t* plev_ = nullptr;    // storage level per subtree after the running step
+    uint32_t* czu_ = nullptr;    // closure of the bed's flags of levels < L-4
+    cudaGraphExec_t exec_skip_[4] = {};   // audit, audit + network, skip, skip + network
     cudaGraphExec_t exec_uniform_ = nullptr;
     uint32_t* uniform_leaves_ = nullptr;   // every finest cell as a leaf (uniform FV1)
-    int64_t kernels_plain_ = 0, kernels_learned_ = 0;   // kernel nodes of the captured step graphs
+    int64_t kernels_plain_ = 0, kernels_skip_ = 0;   // kernel nodes of the captured step graphs
 };
 
 template <>

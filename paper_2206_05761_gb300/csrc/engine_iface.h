@@ -39,8 +39,13 @@ class Engine {
                                       int64_t* wet_updates, int64_t* kernels_per_step) = 0;
     virtual hwfv1_status save(void* buf, size_t cap, size_t* used) = 0;
     virtual hwfv1_status load(const void* buf, size_t n) = 0;
-    // learned look-ahead (skipnet.cu); net == nullptr turns it off
+    // learned subtree skip with the network's levels (skipnet.cu); net ==
+    // nullptr turns it off
     virtual hwfv1_status set_skipnet(SkipNet* net, int audit_K, float margin, int predict_every) = 0;
+    // learned subtree skip with the caller's levels (host, row-major over
+    // level L-4); levels == nullptr turns it off
+    virtual hwfv1_status set_skip_levels(const uint8_t* levels, int audit_K) = 0;
+    virtual hwfv1_status get_skip_levels(int which, uint8_t* out, int64_t cap) = 0;
     virtual hwfv1_status get_features(uint16_t* out, int64_t cap) = 0;
     virtual hwfv1_status get_labels(uint8_t* out, int64_t cap) = 0;
     std::string err;

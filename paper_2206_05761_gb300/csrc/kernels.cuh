@@ -1494,6 +1494,9 @@ struct StepArgs {
     // significance bits, which tell a refined same-level neighbour
     const uint32_t* Sb = nullptr;
     int fm = 0;
+    // 1: every leaf writes its own cell only (the learned skip's decode
+    // kernel forms the stored cells below coarser leaves)
+    int own_slot = 0;
 };
 
 template <typename T>
@@ -1605,7 +1608,7 @@ __device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T
         dry = !inlet_range(a, d.n, compact16(d.code), compact16(d.code >> 1), (1u << d.n) - 1u, lo, hi);
     }
     if (dry) {
-        if (d.n == a.L || needs_decode_kernel(d.n, a.L)) {
+        if (d.n == a.L || needs_decode_kernel(d.n, a.L) || a.own_slot) {
             oh[d.iC] = T(0);
             oqx[d.iC] = T(0);
             oqy[d.iC] = T(0);
@@ -1690,7 +1693,7 @@ __device__ __forceinline__ void wet_leaf_store(const StepArgs<T>& a, DevState* s
         const unsigned long long rb = obits((double)r);
         rmin = rb < rmin ? rb : rmin;
     }
-    if (n == a.L || needs_decode_kernel(n, a.L)) {
+    if (n == a.L || needs_decode_kernel(n, a.L) || a.own_slot) {
         oh[iC] = out[0];
         oqx[iC] = out[1];
         oqy[iC] = out[2];
@@ -2676,51 +2679,6 @@ static __global__ void k_predict(const float* __restrict__ logits, int Ls, float
             }
         }
         phat[c] = (uint8_t)(Ls + cls);
-    }
-}
-
-// Regularised significance with the learned look-ahead: the closed
-// threshold tree is kept, and a child of a significant detail is added only
-// while its level stays shallower than its subtree's predicted level:
-//   S(n,c) = base(n,c) | [T|Tz](n-1, c/4) & (n <= Ls or n < phat(subtree))
-// base = C | Cz with closure, T | Tz without.  With phat = L everywhere this
-// is exactly k_flag.
-static __global__ void k_flag_learned(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
-                                      const uint32_t* __restrict__ Tz, const uint32_t* __restrict__ Cz,
-                                      uint32_t* __restrict__ Sb, const uint8_t* __restrict__ phat, int L, int Ls,
-                                      int predict, int close, const DevState* st, uint32_t* zero4 = nullptr) {
-    pdl_wait();
-    if (zero4 && blockIdx.x == 0 && threadIdx.x < 4u) zero4[threadIdx.x] = 0u;   // as k_flag
-    if (st && !st->active) return;
-    const uint32_t total = bits_words(L);
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
-        int n = 0;
-        while (n + 1 < L && word_off(n + 1) <= w) ++n;
-        const uint32_t lw = w - word_off(n);
-        uint32_t s = close ? (Cb[w] | Cz[w]) : (Tb[w] | Tz[w]);
-        if (predict && n >= 1) {
-            uint32_t pb;
-            if (n >= 3) {
-                const uint32_t pw = word_off(n - 1) + (lw >> 2);
-                pb = expand4x8((Tb[pw] | Tz[pw]) >> (8u * (lw & 3u)));
-            } else if (n == 2) {
-                pb = expand4x8((Tb[word_off(1)] | Tz[word_off(1)]) & 0xFu);
-            } else {
-                pb = ((Tb[word_off(0)] | Tz[word_off(0)]) & 1u) ? 0xFu : 0u;
-            }
-            if (n > Ls) {
-                const int sh = 2 * (n - Ls);
-                uint32_t allow = 0u;
-                for (uint32_t b = 0; b < 32u; ++b) {
-                    const uint32_t c = 32u * lw + b;
-                    if (n < (int)phat[c >> sh]) allow |= 1u << b;
-                }
-                pb &= allow;
-            }
-            s |= pb;
-        }
-        if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
-        Sb[w] = s;
     }
 }
 

@@ -1,0 +1,341 @@
+// skip.cuh -- the learned subtree skip: every level-(L-4) subtree is
+// encoded, flagged and stored only down to a predicted level (a layer the
+// project adds on top of Algorithm 3; the paper has no learned part).
+//
+// The subtree s (Morton code s at level Ls = L - 4, 16 x 16 finest cells)
+// keeps its state at a storage level m_s in [Ls, L]: its level-m_s cells
+// (m_s = L after the start and after every plain step).  A skip step is given
+// a predicted level p_s per subtree and
+//   1. keeps s down to P_s = max(p_s, p of the subtrees sharing an edge with
+//      s), so that a leaf next to s finds its same-level neighbour in s;
+//   2. takes its thresholds from s_max over the stored state (the previous
+//      step's decode reduced it over the cells it stored);
+//   3. forms the level-P_s cells of s from its level-m_s cells when
+//      P_s > m_s, as the decode-back forms the cells under a leaf;
+//   4. encodes s from level E_s = max(m_s, P_s) up to Ls (k_skip_encode),
+//      then levels Ls-1 .. 0 (the plain encode passes from level Ls);
+//   5./6. flags a parent of s only at levels below p_s, with the bed's
+//      details of those levels, regularises (R1, R2) and keeps no cell of
+//      s significant at a level >= p_s (k_skip_flag);
+//   7. lists and updates the leaves as the plain step does, each leaf
+//      writing its own cell only;
+//   8. stores s at level P_s: every level-P_s cell takes its covering
+//      leaf's value, with the decode-back's free surface against z^(P_s)
+//      (k_skip_decode, which then advances the time).
+// A plain step (the exact audit) first brings every subtree to level L
+// (k_skip_finest).  The same steps, written out plainly, are the CPU
+// oracle's orc_skip_step.
+#pragma once
+#include "kernels.cuh"
+
+namespace hwfv1 {
+
+// P_s: the largest predicted level of s and of its edge neighbours
+// (predictions in Morton order over level Ls).
+__device__ __forceinline__ int skip_store_level(const uint8_t* __restrict__ phat, int Ls, uint32_t s) {
+    const uint32_t last = (1u << Ls) - 1u;
+    const uint32_t i = compact16(s), j = compact16(s >> 1);
+    int v = phat[s];
+    if (i > 0u) v = max(v, (int)phat[mort_xm(s)]);
+    if (i < last) v = max(v, (int)phat[mort_xp(s)]);
+    if (j > 0u) v = max(v, (int)phat[mort_ym(s)]);
+    if (j < last) v = max(v, (int)phat[mort_yp(s)]);
+    return v;
+}
+
+// Depth of a cell under a coarser cell (the decode-back's rule, reading
+// R-decode): a wet coarse cell hands down its free surface, the finer cell
+// takes max(0, eta - z_fine); a dry one hands down its depth.
+template <typename T>
+__device__ __forceinline__ T redecode_h(T hl, T zl, T zc, T tol) {
+    if (!ge_nonneg(hl, tol)) return hl;
+    const T eta = hl + zl;
+    const T d = eta - zc;
+    return gt_zero(d) ? d : T(0);
+}
+
+template <typename T>
+struct SkipArgs {
+    T* f[2][3];               // h, qx, qy hierarchies of the two state buffers
+    const T* z;               // bed hierarchy
+    const T* thr;             // thresholds per (level, quantity), as the plain encode
+    const T* thr4;
+    const float* thr4lo = nullptr;
+    const float* thr4hi = nullptr;
+    const uint32_t* Tz;       // the bed's threshold flags (static)
+    uint32_t* Tb;             // threshold flags (bed included at levels >= Ls)
+    uint32_t* Cb;             // their upward closure
+    const uint8_t* phat;      // predicted level per subtree
+    const uint8_t* mlev;      // storage level per subtree as the step starts
+    uint8_t* plev;            // storage level per subtree after the step (P_s)
+    DevState* st;
+    T tol;
+    int L, Ls;
+};
+
+// Steps 1, 3 and 4 inside the subtrees: one 64-thread CTA per subtree.
+// Every level the encode forms is written to the current state buffer
+// (neighbouring leaves and the FV1 update read them there); threshold and
+// closure bits are OR-ed into words the clear kernel zeroed.
+template <typename T>
+static __global__ void __launch_bounds__(64) k_skip_encode(SkipArgs<T> a) {
+    pdl_wait();
+    if (!a.st->active) return;
+    const uint32_t s = blockIdx.x, t = threadIdx.x;
+    const int par = (int)a.st->cur;
+    T* const fh = par ? a.f[1][0] : a.f[0][0];
+    T* const fqx = par ? a.f[1][1] : a.f[0][1];
+    T* const fqy = par ? a.f[1][2] : a.f[0][2];
+    const int Ls = a.Ls;
+    const int p = a.phat[s];
+    const int P = skip_store_level(a.phat, Ls, s);
+    const int m = a.mlev[s];
+    if (t == 0) a.plev[s] = (uint8_t)P;
+    const int E = P > m ? P : m;
+    if (P > m) {                           // step 3: level P from level m
+        const uint32_t cnt = 1u << (2 * (P - Ls));
+        const uint64_t b = (uint64_t)s << (2 * (P - Ls));
+        for (uint32_t k = t; k < cnt; k += 64u) {
+            const uint64_t c = b + k, ia = lvl_off(m) + (c >> (2 * (P - m))), ic = lvl_off(P) + c;
+            fh[ic] = redecode_h(__ldcg(fh + ia), __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
+            fqx[ic] = __ldcg(fqx + ia);
+            fqy[ic] = __ldcg(fqy + ia);
+        }
+        __syncthreads();                   // the block reads level P below
+    }
+    // step 4: levels E-1 .. Ls, one thread per parent, the coarser levels
+    // from shared memory; a parent is flagged only below p (step 5)
+    __shared__ T sv[2][3][64];
+    __shared__ uint8_t scl[2][64];
+    int rb = 0;
+    for (int n = E - 1; n >= Ls; --n) {
+        const uint32_t cnt = 1u << (2 * (n - Ls));
+        const bool act = t < cnt;
+        const uint64_t pc = ((uint64_t)s << (2 * (n - Ls))) + t;
+        T sq[3] = {T(0), T(0), T(0)};
+        bool cf = false;
+        if (act) {
+            T c[3][4];
+            bool cch = false;
+            if (n == E - 1) {
+                Vec4<T>::load_cg(fh + lvl_off(n + 1) + 4ull * pc, c[0][0], c[0][1], c[0][2], c[0][3]);
+                Vec4<T>::load_cg(fqx + lvl_off(n + 1) + 4ull * pc, c[1][0], c[1][1], c[1][2], c[1][3]);
+                Vec4<T>::load_cg(fqy + lvl_off(n + 1) + 4ull * pc, c[2][0], c[2][1], c[2][2], c[2][3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[q][e] = sv[rb][q][4 * t + e];
+                cch = (scl[rb][4 * t] | scl[rb][4 * t + 1] | scl[rb][4 * t + 2] | scl[rb][4 * t + 3]) != 0;
+            }
+            Thr<T> th[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int idx = n * 3 + q;
+                th[q].thr = a.thr[idx];
+                th[q].thr4 = a.thr4[idx];
+                th[q].lo = a.thr4lo ? a.thr4lo[idx] : -1.0f;
+                th[q].hi = a.thr4hi ? a.thr4hi[idx] : -1.0f;
+            }
+            bool tf = false;
+            parents_all<T, 3>(th, c, sq, tf);
+            fh[lvl_off(n) + pc] = sq[0];
+            fqx[lvl_off(n) + pc] = sq[1];
+            fqy[lvl_off(n) + pc] = sq[2];
+            const uint32_t wi = word_off(n) + (uint32_t)(pc >> 5), bit = 1u << (pc & 31u);
+            const bool allowed = n < p;
+            const bool tt = allowed && (tf || (__ldg(a.Tz + wi) & bit) != 0u);
+            cf = tt || cch;
+            if (tt) atomicOr(a.Tb + wi, bit);
+            if (cf) atomicOr(a.Cb + wi, bit);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sv[rb ^ 1][q][t] = sq[q];
+            scl[rb ^ 1][t] = cf ? 1 : 0;
+        }
+        __syncthreads();
+        rb ^= 1;
+    }
+}
+
+// Steps 5 and 6 as words of the regularised flags S: above the subtrees
+//   S = C | Cz' | R1 of (T | Tz)          (Cz': closure of the bed's flags
+//                                          of levels < Ls, static)
+// and at levels n >= Ls
+//   S = (C | R1) & [n < p of the cell's subtree]
+// where T, C already hold the bed's flags there (k_skip_encode).
+static __global__ void k_skip_flag(const uint32_t* __restrict__ Tb, const uint32_t* __restrict__ Cb,
+                                   const uint32_t* __restrict__ Tz, const uint32_t* __restrict__ Czu,
+                                   uint32_t* __restrict__ Sb, const uint8_t* __restrict__ phat, int L, int Ls,
+                                   const DevState* st) {
+    pdl_wait();
+    if (!st->active) return;
+    const uint32_t total = bits_words(L);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+        int n = 0;
+        while (n + 1 < L && word_off(n + 1) <= w) ++n;
+        const uint32_t lw = w - word_off(n);
+        uint32_t s = Cb[w];
+        if (n < Ls) s |= Czu[w];
+        if (n >= 1) {                       // R1: children of the parent level's flags
+            const bool bed = n - 1 < Ls;     // above the subtrees T lacks the bed's flags
+            uint32_t pb;
+            if (n >= 3) {
+                const uint32_t pw = word_off(n - 1) + (lw >> 2);
+                pb = expand4x8((Tb[pw] | (bed ? Tz[pw] : 0u)) >> (8u * (lw & 3u)));
+            } else if (n == 2) {
+                pb = expand4x8((Tb[word_off(1)] | (bed ? Tz[word_off(1)] : 0u)) & 0xFu);
+            } else {
+                pb = ((Tb[word_off(0)] | (bed ? Tz[word_off(0)] : 0u)) & 1u) ? 0xFu : 0u;
+            }
+            s |= pb;
+        }
+        if (n >= Ls) {
+            const int sh = 2 * (n - Ls);
+            const uint32_t nb = n < 3 ? (1u << (2 * n)) : 32u;     // cells in this word
+            uint32_t allow = 0u;
+            for (uint32_t b = 0; b < nb; ++b)
+                if (n < (int)phat[(32u * lw + b) >> sh]) allow |= 1u << b;
+            s &= allow;
+        }
+        if (n <= 2) s &= (n == 0 ? 1u : (n == 1 ? 0xFu : 0xFFFFu));
+        Sb[w] = s;
+    }
+}
+
+template <typename T>
+struct SkipDecodeArgs {
+    T* f[2][3];
+    const T* z;
+    const uint32_t* Sb;       // the step's regularised flags
+    const uint8_t* plev;      // P_s
+    uint8_t* mlev;            // set to P_s
+    DevState* st;
+    T tol;
+    int L, Ls;
+};
+
+// Step 8 and the time advance: every level-P_s cell of every subtree takes
+// its covering leaf's new value (the leaf found by the walk of Algorithm 5
+// over S), with the free surface restored against z^(P_s) below a wet
+// coarser leaf; the s_max reductions run over every stored cell.  64
+// threads per subtree, four subtrees per CTA; the last CTA to finish
+// advances the time (as k_decode_finish).
+template <typename T>
+static __global__ void __launch_bounds__(256) k_skip_decode(SkipDecodeArgs<T> a, FinishArgs fa) {
+    pdl_wait();
+    DevState* st = a.st;
+    unsigned long long mh = 0, mqx = 0, mqy = 0;
+    if (__ldcg(&st->active)) {
+        const int nxt = (int)__ldcg(&st->cur) ^ 1;
+        T* const fh = nxt ? a.f[1][0] : a.f[0][0];
+        T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
+        T* const fqy = nxt ? a.f[1][2] : a.f[0][2];
+        const int Ls = a.Ls;
+        const uint32_t nsub = 1u << (2 * Ls);
+        const uint32_t g = threadIdx.x >> 6, t = threadIdx.x & 63u;
+        for (uint32_t s = blockIdx.x * 4u + g; s < nsub; s += gridDim.x * 4u) {
+            const int P = a.plev[s];
+            int l0 = Ls + 1;                 // a leaf on the root path covers the subtree
+            for (int n = 0; n <= Ls; ++n)
+                if (!sig_bit(a.Sb, n, s >> (2 * (Ls - n)))) {
+                    l0 = n;
+                    break;
+                }
+            const uint32_t cnt = 1u << (2 * (P - Ls));
+            const uint64_t b = (uint64_t)s << (2 * (P - Ls));
+            for (uint32_t k = t; k < cnt; k += 64u) {
+                const uint64_t c = b + k;
+                int l = l0;
+                if (l0 > Ls) {
+                    l = P;
+                    for (int n = Ls + 1; n < P; ++n)
+                        if (!sig_bit(a.Sb, n, (uint32_t)(c >> (2 * (P - n))))) {
+                            l = n;
+                            break;
+                        }
+                }
+                const uint64_t il = lvl_off(l) + (c >> (2 * (P - l)));
+                const T hl = fh[il], qxl = fqx[il], qyl = fqy[il];
+                T hf = hl;
+                if (l < P) {
+                    const uint64_t ic = lvl_off(P) + c;
+                    hf = redecode_h(hl, __ldg(a.z + il), __ldg(a.z + ic), a.tol);
+                    fh[ic] = hf;
+                    fqx[ic] = qxl;
+                    fqy[ic] = qyl;
+                }
+                const unsigned long long bh = abs_obits(hf), bx = abs_obits(qxl), by = abs_obits(qyl);
+                mh = bh > mh ? bh : mh;
+                mqx = bx > mqx ? bx : mqx;
+                mqy = by > mqy ? by : mqy;
+            }
+            if (t == 0u) a.mlev[s] = (uint8_t)P;
+        }
+    }
+    block_max3_u64(mh, mqx, mqy, st->max_bits);
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(&st->dec_ticket, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) st->dec_ticket = 0u;
+    finish_body(st, fa);
+}
+
+// Every subtree brought to level L (step 3 with P = L).  mode 0: into the
+// other buffer's finest level, for reading the fields (the current state
+// stays as it is stored); 1: in place before a plain step, whose storage
+// levels then become L (nothing when the step will not run); 2: in place
+// whatever the time (leaving the skip, checkpoints).
+template <typename T>
+struct SkipFinestArgs {
+    T* f[2][3];
+    const T* z;
+    uint8_t* mlev;
+    DevState* st;
+    T tol;
+    int L, Ls;
+    int mode;
+};
+template <typename T>
+static __global__ void __launch_bounds__(256) k_skip_finest(SkipFinestArgs<T> a) {
+    pdl_wait();
+    if (a.mode == 1 && !a.st->active) return;
+    const bool in_place = a.mode != 0;
+    const int par = (int)a.st->cur, dst = in_place ? par : par ^ 1;
+    const T* const sh = par ? a.f[1][0] : a.f[0][0];
+    const T* const sqx = par ? a.f[1][1] : a.f[0][1];
+    const T* const sqy = par ? a.f[1][2] : a.f[0][2];
+    T* const dh = dst ? a.f[1][0] : a.f[0][0];
+    T* const dqx = dst ? a.f[1][1] : a.f[0][1];
+    T* const dqy = dst ? a.f[1][2] : a.f[0][2];
+    const int L = a.L, Ls = a.Ls;
+    const uint32_t nsub = 1u << (2 * Ls);
+    const uint32_t g = threadIdx.x >> 6, t = threadIdx.x & 63u;
+    for (uint32_t s = blockIdx.x * 4u + g; s < nsub; s += gridDim.x * 4u) {
+        const int m = a.mlev[s];
+        if (m == L && in_place) continue;
+        const uint64_t b = (uint64_t)s << (2 * (L - Ls));
+        for (uint32_t k = t; k < (1u << (2 * (L - Ls))); k += 64u) {
+            const uint64_t c = b + k, ic = lvl_off(L) + c;
+            if (m == L) {
+                dh[ic] = sh[ic];
+                dqx[ic] = sqx[ic];
+                dqy[ic] = sqy[ic];
+            } else {
+                const uint64_t ia = lvl_off(m) + (c >> (2 * (L - m)));
+                dh[ic] = redecode_h(sh[ia], __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
+                dqx[ic] = sqx[ia];
+                dqy[ic] = sqy[ia];
+            }
+        }
+        if (in_place && t == 0u) a.mlev[s] = (uint8_t)L;
+    }
+}
+
+}  // namespace hwfv1

@@ -13,6 +13,8 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
+
 from . import _build
 
 _lock = threading.Lock()
@@ -109,6 +111,8 @@ def lib():
             L.hwfv1_skipnet_destroy.argtypes = [C.c_void_p]
             L.hwfv1_skipnet_destroy.restype = None
             L.hwfv1_set_skipnet.argtypes = [_H, C.c_void_p, C.c_int32, C.c_float, C.c_int32]
+            L.hwfv1_set_skip_levels.argtypes = [_H, C.c_void_p, C.c_int32]
+            L.hwfv1_get_skip_levels.argtypes = [_H, C.c_int32, C.c_void_p, C.c_int64]
             L.hwfv1_get_features.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_get_labels.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_destroy.argtypes = [_H]
@@ -128,8 +132,8 @@ def exported_symbols():
             "hwfv1_batch_launches_per_step", "hwfv1_batch_last_error", "hwfv1_batch_destroy",
             "hwfv1_skipnet_num_params", "hwfv1_skipnet_create", "hwfv1_skipnet_set_params",
             "hwfv1_skipnet_get_params", "hwfv1_skipnet_forward", "hwfv1_skipnet_gradients",
-            "hwfv1_skipnet_train", "hwfv1_skipnet_destroy", "hwfv1_set_skipnet", "hwfv1_get_features",
-            "hwfv1_get_labels"]
+            "hwfv1_skipnet_train", "hwfv1_skipnet_destroy", "hwfv1_set_skipnet", "hwfv1_set_skip_levels",
+            "hwfv1_get_skip_levels", "hwfv1_get_features", "hwfv1_get_labels"]
 
 
 def _check(st, what, hd=None):
@@ -385,7 +389,7 @@ def hwfv1_batch_destroy(bt):
 
 
 # ---------------------------------------------------------------------------
-# Learned look-ahead (subtree CNN)
+# Learned subtree skip (subtree CNN)
 # ---------------------------------------------------------------------------
 
 def hwfv1_skipnet_num_params():
@@ -442,6 +446,25 @@ def hwfv1_skipnet_destroy(net):
 def hwfv1_set_skipnet(hd, net, audit_K=10, margin=0.02, predict_every=1):
     _check(lib().hwfv1_set_skipnet(hd, net, int(audit_K), float(margin), int(predict_every)),
            "hwfv1_set_skipnet", hd)
+
+
+def hwfv1_set_skip_levels(hd, levels, audit_K=10):
+    """levels: host uint8 array [2^(L-4), 2^(L-4)] (row-major, j major) or
+    None to stop."""
+    if levels is None:
+        _check(lib().hwfv1_set_skip_levels(hd, None, int(audit_K)), "hwfv1_set_skip_levels", hd)
+        return
+    lv = np.ascontiguousarray(levels, dtype=np.uint8)
+    _check(lib().hwfv1_set_skip_levels(hd, lv.ctypes.data, int(audit_K)), "hwfv1_set_skip_levels", hd)
+
+
+def hwfv1_get_skip_levels(hd, which, L):
+    """which = 0: predicted levels in use, 1: storage levels; host uint8
+    array [2^(L-4), 2^(L-4)]."""
+    S = 1 << (L - 4)
+    out = np.empty((S, S), dtype=np.uint8)
+    _check(lib().hwfv1_get_skip_levels(hd, int(which), out.ctypes.data, out.size), "hwfv1_get_skip_levels", hd)
+    return out
 
 
 def hwfv1_get_features(hd, out):

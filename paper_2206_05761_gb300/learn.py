@@ -1,7 +1,8 @@
 """Training data and training of the subtree CNN that drives the learned
-look-ahead (the network predicts, per 16x16-finest subtree, the deepest
-level the next step's threshold tree will need; see Sec. 2.2 for the
-significance tree it stands in for).
+subtree skip (the network predicts, per 16x16-finest subtree, the deepest
+level the next step's threshold tree will need, and the subtree is encoded,
+flagged and stored only down to it; see Sec. 2.1.2 for the significance
+tree it stands in for).
 
 Data come from simulations run on the GPU path itself: at sampled steps k
 the input is the features of the state at t_k (level-(L-4) coefficients of

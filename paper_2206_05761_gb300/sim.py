@@ -126,6 +126,15 @@ class Simulation:
     def set_skipnet(self, net, audit_K=10, margin=0.02, predict_every=1):
         H.hwfv1_set_skipnet(self.hd, net, audit_K, margin, predict_every)
 
+    def set_skip_levels(self, levels, audit_K=10):
+        """The learned subtree skip with the given levels ([j, i] over level
+        L-4; None stops it)."""
+        H.hwfv1_set_skip_levels(self.hd, levels, audit_K)
+
+    def skip_levels(self, which=1):
+        """Storage levels (which=1) or predicted levels in use (which=0)."""
+        return H.hwfv1_get_skip_levels(self.hd, which, self.L)
+
     def close(self):
         if self.hd is not None:
             H.hwfv1_destroy(self.hd)

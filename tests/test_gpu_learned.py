@@ -1,9 +1,9 @@
-"""Learned look-ahead end to end: training data from the GPU path, training
-on the tensor cores, then a held-out run with the network in
-the time loop against plain HWFV1 (regularisation by one-level prediction)
-and against uniform FV1 (eps = 0).  Water columns collapsing on a flat bed:
-the refinement follows the moving flow alone, which is where a look-ahead
-tighter than one blanket level can cut leaves."""
+"""Learned subtree skip end to end: training data from the GPU path,
+training on the tensor cores, then a held-out run with the network's
+predicted levels in the time loop against plain HWFV1 (regularisation by
+one-level prediction) and against uniform FV1 (eps = 0).  Water columns
+collapsing on a flat bed: the refinement follows the moving flow alone, so
+most subtrees are predicted shallow and stored coarse."""
 import numpy as np
 import pytest
 
@@ -64,9 +64,9 @@ def test_learned_run_uses_fewer_leaves_at_bounded_cost(trained):
     print("mean leaves: uniform %.0f, plain %.0f, learned %.0f (%.3f of plain); steps: %d %d %d"
           % (mu, mp, ml, ml / mp, tu, tp, tl))
     print("L1 depth: |learned - plain| = %.3e, |plain - uniform| = %.3e" % (d_lp, d_pu))
-    # at margin 0.02 the look-ahead keeps nearly every child on this small
-    # grid (the network is trained with atomic float sums, so the few it
-    # drops vary from run to run).  The two runs' states drift apart, so
+    # at margin 0.02 the predicted levels keep nearly every needed level on
+    # this small grid (the network is trained with atomic float sums, so the
+    # levels vary from run to run).  The two runs' states drift apart, so
     # their mean leaf counts are compared loosely; the error stays bounded.
     assert ml <= mp * 1.01
     assert d_lp <= 2.0 * d_pu + 1e-12
@@ -79,9 +79,11 @@ def test_learned_run_uses_fewer_leaves_at_bounded_cost(trained):
 
 
 def test_learned_step_never_adds_leaves_on_the_same_state(trained):
-    """From identical states (checkpoints of the plain run) a learned step
-    keeps a subset of the plain step's significant parents, so it has at
-    most as many leaves; at the median-level margin it drops some."""
+    """From identical states (checkpoints of the plain run) the first skip
+    step after the exact one encodes the same finest state and keeps a
+    subset of the plain step's significant parents (the flags below each
+    subtree's predicted level), so it has at most as many leaves; at the
+    median-level margin it drops some."""
     from paper_2206_05761_gb300.sim import Simulation
     net, _ = trained
     p, f = synth.columns_dam_break(L=L, eps=1e-3, seed=200)
@@ -97,7 +99,7 @@ def test_learned_step_never_adds_leaves_on_the_same_state(trained):
         plain.load(blob)
         plain.advance(max_steps=2)
         lrn.load(blob)
-        # the step after attaching the network is exact, the next one learned
+        # the step after attaching the network is exact, the next one a skip step
         lrn.set_skipnet(net, audit_K=10, margin=0.5, predict_every=1)
         lrn.advance(max_steps=2)
         out.append((plain.stats()[0], lrn.stats()[0]))
