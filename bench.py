@@ -417,7 +417,8 @@ def run_ensemble(args, steps=50):
             "launches_per_step": lps}
 
 
-def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100, steps=400):
+def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100, steps=400, margin=0.005,
+                audit_K=10, epochs=20, sample_every=10, everys=(1, 4)):
     """Learned subtree skip at L = 11: the subtree CNN trained (BF16 tensor
     cores) on trajectories of seeded cases run on the GPU path, then a
     held-out case advanced `steps` steps plain (with exact quiescent-tile
@@ -437,15 +438,16 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     make = {"bumpy": lambda s: synth.bumpy_dam_break(L=L, eps=1e-3, seed=s),
             "columns": lambda s: synth.columns_dam_break(L=L, eps=1e-3, seed=s)}[kind]
     t0 = time.perf_counter()
-    x, y = learn.collect([make(s) for s in train_seeds], steps=400, every=20)
+    x, y = learn.collect([make(s) for s in train_seeds], steps=400, every=sample_every)
     x, y = learn.augment(x, y)
+    nimg = int(x.shape[0])
     t_collect = time.perf_counter() - t0
     t0 = time.perf_counter()
-    net, loss = learn.train(x, y, epochs=6, batch=8, lr=3e-3, seed=1)
+    net, loss = learn.train(x, y, epochs=epochs, batch=8, lr=3e-3, seed=1)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     xh, yh = learn.collect([make(test_seed)], steps=steps, every=40)
-    under = learn.under_prediction_rate(net, xh, yh, 0.02)
+    under = learn.under_prediction_rate(net, xh, yh, margin)
     del x, y, xh, yh
     p, f = make(test_seed)
     stream = torch.cuda.Stream()
@@ -453,7 +455,7 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     def timed(net_, t_end, max_steps, every=1, profile=False, full_sweep=False):
         sim = Simulation(dict(p, full_sweep=True) if full_sweep else p, f, args.precision, stream=stream)
         if net_ is not None:
-            sim.set_skipnet(net_, audit_K=10, margin=0.02, predict_every=every)
+            sim.set_skipnet(net_, audit_K=audit_K, margin=margin, predict_every=every)
         sim.counters()                        # captures the step graph (untimed)
         sim.advance(max_steps=0)
         stream.synchronize()
@@ -481,7 +483,7 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
         at evenly spaced simulated times (untimed runs side by side)."""
         a = Simulation(p, f, args.precision, stream=stream)
         b = Simulation(p, f, args.precision, stream=stream)
-        b.set_skipnet(net, audit_K=10, margin=0.02, predict_every=every)
+        b.set_skipnet(net, audit_K=audit_K, margin=margin, predict_every=every)
         out = []
         cell = 1.0 / (1 << (2 * L))
         for k in range(1, checkpoints + 1):
@@ -499,10 +501,10 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     # the learned run's step count to the same simulated time, then a timed
     # run of exactly that many steps (no idle launches after t_end)
     runs = {}
-    for every in (1, 4):
+    for every in everys:
         n_l = timed(net, plain["t"], 4 * steps, every)["steps"]
         runs[every] = timed(net, plain["t"], n_l, every, profile=(args.only == "learned" and every == 1))
-    errs = {every: errors(every, plain["t"]) for every in (1, 4)}
+    errs = {every: errors(every, plain["t"]) for every in everys}
     H.hwfv1_skipnet_destroy(net)
 
     def rep(r):
@@ -529,10 +531,11 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
                 l1_depth_learned_vs_plain_m=max(x["l1_m"] for x in errs[e]))
                 for e, r in runs.items()},
             "held_out_under_prediction": under,
-            "training": {"images": int(8 * 20 * len(train_seeds)), "image_px": 1 << (L - 4),
+            "training": {"images": nimg, "image_px": 1 << (L - 4),
                          "last_batch_loss": loss, "collect_s": t_collect, "train_s": t_train,
-                         "epochs": 6, "batch": 8, "augment": "8 symmetries of the square"},
-            "audit_K": 10, "margin": 0.02}
+                         "epochs": epochs, "batch": 8, "augment": "8 symmetries of the square",
+                         "samples_every_steps": sample_every},
+            "audit_K": audit_K, "margin": margin}
 
 
 def run_pseudo2d(args):
