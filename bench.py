@@ -183,8 +183,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
 # step in the timed window: mean over the launches of the window's ncu
 # launch list (the committed summary under profiles/), valid while
 # kernels.cuh has this SHA-256.
-FV1_WET_TRAFFIC = {"kernels_sha256": "ce2a3fd4fd7da561af9087d25c298342f2768235a8dda54771d7ef489200726c",
-                   "bytes_per_launch": 2889235 + 9541593}
+FV1_WET_TRAFFIC = {"kernels_sha256": "6580c42f39fb7d346da8232828c5bbc28fdde4a8ac207b77e2978d6647a5f6d8",
+                   "bytes_per_launch": 5898880 + 17915392}
 
 
 def kernels_sha256():

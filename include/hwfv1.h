@@ -122,7 +122,11 @@ hwfv1_status hwfv1_init(const hwfv1_problem* spec, const double* z, const double
                         const double* qx, const double* qy, void* stream,
                         hwfv1_handle** out);
 
-/* Encoding (Eq. 3a-3d, Algorithm 1): scaling coefficients of h, hu, hv for
+/* The phases of one plain step, one call each (encode, flag, traverse,
+ * step, decode); hwfv1_advance runs them in one graph.  While the learned
+ * subtree skip is on they return HWFV1_ERR_STATE (the stored state may be
+ * above level L there).
+ * Encoding (Eq. 3a-3d, Algorithm 1): scaling coefficients of h, hu, hv for
  * every level below L from the finest grid, threshold flags of every
  * parent against the normalised threshold 2^(n-L)*eps*s_max (Sec. 2.1.2),
  * and the upward closure of those flags. */
@@ -204,8 +208,9 @@ hwfv1_status hwfv1_set_time(hwfv1_handle* hd, double t, double dt);
  * number of leaves and the maxima of |h|, |hu|, |hv| used for s_max. */
 hwfv1_status hwfv1_get_stats(hwfv1_handle* hd, int64_t* num_leaves, double* smax3);
 
-/* One step (encode .. time advance, the plain step of hwfv1_advance) with
- * a CUDA event recorded after every kernel: the step is captured as a graph
+/* One step (encode .. time advance: the step hwfv1_advance takes next, the
+ * plain step outside the learned skip) with a CUDA event recorded after
+ * every kernel: the step is captured as a graph
  * whose kernels are separated by event-record nodes (HWFV1_NO_GRAPH set:
  * ordinary launches on the handle's stream).  Writes the duration in ms of
  * each kernel (from the previous event) to ms[0..cap) and its name (static
@@ -216,7 +221,8 @@ hwfv1_status hwfv1_profile_step(hwfv1_handle* hd, float* ms, const char** names,
 
 /* One plain step whose full update of the queued (wet) leaves, Eq. 2 on the
  * leaf grid, is captured on its own and replayed `reps` (>= 1) times between
- * two CUDA events on the handle's stream before the step goes on.  Every
+ * two CUDA events on the handle's stream before the step goes on
+ * (HWFV1_ERR_STATE while the learned skip is on).  Every
  * replay reads the same state and queue and writes the same values (leaf
  * values of the next state, min/max reductions), so the simulation still
  * advances by exactly one step.  *ms (host) = the mean time of one update,

@@ -166,16 +166,25 @@ class EngineT final : public Engine {
         return check("init", true);
     }
 
+    // The phases one by one are those of the plain step: with the learned
+    // skip on, the stored state may be above level L, so they are refused.
+    hwfv1_status phase_guard(const char* what) {
+        if (skipmode_) return fail(HWFV1_ERR_STATE, std::string(what) + ": the learned skip is on (use hwfv1_advance)");
+        return HWFV1_OK;
+    }
     hwfv1_status encode() override {
+        if (hwfv1_status r = phase_guard("encode"); r != HWFV1_OK) return r;
         launch_encode();
         return check("encode");
     }
     hwfv1_status flag() override {
+        if (hwfv1_status r = phase_guard("flag"); r != HWFV1_OK) return r;
         launch_flag();
         sb_valid_ = true;
         return check("flag");
     }
     hwfv1_status traverse(int64_t* num_leaves) override {
+        if (hwfv1_status r = phase_guard("traverse"); r != HWFV1_OK) return r;
         cudaMemsetAsync(&st_->ndec, 0, 4 * sizeof(uint32_t), stream_);     // ndec, Mall, M, nact
         launch_traverse();
         if (num_leaves) {
@@ -186,10 +195,12 @@ class EngineT final : public Engine {
         return check("traverse");
     }
     hwfv1_status step() override {
+        if (hwfv1_status r = phase_guard("step"); r != HWFV1_OK) return r;
         launch_fv1();
         return check("step");
     }
     hwfv1_status decode() override {
+        if (hwfv1_status r = phase_guard("decode"); r != HWFV1_OK) return r;
         launch_decode();
         return check("decode");
     }
@@ -235,7 +246,9 @@ class EngineT final : public Engine {
             k_fill_finest_leaves<<<grid_for(N_), 256, 0, stream_>>>(uniform_leaves_, L_, N_);
         }
         // uniform steps keep no quiescence marks: forget them for later
-        // adaptive steps
+        // adaptive steps; with the learned skip on, the state is brought to
+        // level L first
+        if (skipmode_) launch_skip_finest(2);
         forget_quiet();
         k_set_tend<<<1, 64, 0, stream_>>>(st_, fin_args(), t_end);
         if (max_steps == 0) return check("advance_uniform");
@@ -456,6 +469,8 @@ class EngineT final : public Engine {
         cudaEvent_t e0;
         if (cudaEventCreate(&e0) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "event");
         const bool use_graph = std::getenv("HWFV1_NO_GRAPH") == nullptr;
+        // the step the schedule takes next (the plain step outside the skip)
+        const int pkind = skipmode_ ? skip_kind(lstep_++) : kStepPlain;
         hwfv1_status r = HWFV1_OK;
         if (use_graph) {
             cudaGraph_t g = nullptr;
@@ -467,7 +482,7 @@ class EngineT final : public Engine {
             cudaEventRecordWithFlags(e0, stream_, cudaEventRecordExternal);
             prof_ = &ev;
             prof_external_ = true;
-            launch_step_all();
+            launch_step(pkind);
             prof_ = nullptr;
             prof_external_ = false;
             if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) r = fail(HWFV1_ERR_CUDA, "graph capture end");
@@ -480,7 +495,7 @@ class EngineT final : public Engine {
         } else {
             cudaEventRecord(e0, stream_);
             prof_ = &ev;
-            launch_step_all();
+            launch_step(pkind);
             prof_ = nullptr;
             r = check("profile_step", true);
         }
@@ -510,6 +525,7 @@ class EngineT final : public Engine {
     // same values.  *ms = the mean time of one update.
     hwfv1_status profile_update(int32_t reps, float* ms) override {
         if (reps < 1 || !ms) return fail(HWFV1_ERR_INVALID_SPEC, "profile_update: reps >= 1 and ms");
+        if (hwfv1_status r = phase_guard("profile_update"); r != HWFV1_OK) return r;
         const bool onfly = onfly_flags();
         launch_encode();
         if (!onfly) launch_flag();

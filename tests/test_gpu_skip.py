@@ -129,3 +129,48 @@ def test_rejects_levels_out_of_range_and_unsupported_problems():
     with pytest.raises(H.Hwfv1Error):
         sim.set_skip_levels(np.full((4, 4), 6), audit_K=3)
     sim.close()
+
+
+def test_reading_the_fields_leaves_the_run_unchanged():
+    # the finest fields of a state stored above level L are formed in the
+    # other buffer: reading them after every step changes nothing
+    from paper_2206_05761_gb300.sim import Simulation
+    rng = np.random.default_rng(12)
+    L = 7
+    p, f = synth.bumpy_dam_break(L=L, eps=1e-3, seed=13, eta_up=1.3)
+    seq = [_levels(rng, L) for _ in range(9)]
+    a, b = Simulation(p, f), Simulation(p, f)
+    for lev in seq:
+        for s in (a, b):
+            s.set_skip_levels(lev, audit_K=4)
+            s.advance(max_steps=1)
+        b.fields()
+    ga, gb = a.fields(), b.fields()
+    for q in ga:
+        assert np.array_equal(ga[q], gb[q])
+    assert np.array_equal(a.skip_levels(1), b.skip_levels(1))
+    a.close()
+    b.close()
+
+
+def test_phases_refused_and_profiled_skip_step():
+    from paper_2206_05761_gb300 import hwfv1 as H
+    from paper_2206_05761_gb300.sim import Simulation
+    L = 7
+    p, f = synth.bumpy_dam_break(L=L, eps=1e-3, seed=3)
+    sim = Simulation(p, f)
+    sim.set_skip_levels(np.full((8, 8), L - 2), audit_K=3)
+    with pytest.raises(H.Hwfv1Error) as e:
+        sim.encode()
+    assert e.value.status == 7                       # HWFV1_ERR_STATE
+    names = [n for n, _ in H.hwfv1_profile_step(sim.hd)]     # the audit step
+    assert names[0] == "k_skip_finest" and names[1] == "k_clear_words" and names[-1] == "k_decode_finish"
+    names = [n for n, _ in H.hwfv1_profile_step(sim.hd)]     # a skip step
+    assert names[:2] == ["k_clear_words", "k_skip_encode"] and names[-1] == "k_skip_decode"
+    ref = oracle.SkipState(p, f)
+    ref.plain_step()
+    ref.skip_step(np.full((8, 8), L - 2))
+    g, o = sim.fields(), ref.fields()
+    for q in g:
+        assert np.array_equal(g[q], o[q])
+    sim.close()
