@@ -64,9 +64,10 @@ def parse():
     a.add_argument("--learned-kinds", default=None,
                    help="with --only learned: comma-separated workloads (columns, bumpy)")
     a.add_argument("--only", choices=["ensemble", "learned"],
-                   help="run only this side measurement, print its result, and bracket its timed "
-                        "region (the batched advance; the learned run predicting every step) "
-                        "with the profiler range, for an ncu launch list")
+                   help="run only this side measurement and print its result")
+    a.add_argument("--profile-range", action="store_true",
+                   help="with --only: bracket its timed region (the batched advance; the learned run "
+                        "predicting every step) with the profiler range, for an ncu launch list")
     return a.parse_args()
 
 
@@ -397,13 +398,14 @@ def run_ensemble(args, steps=50):
     choice = ens.autotune(trial_steps=2)
     ens.advance(max_steps=3)
     stream.synchronize()
-    if args.only == "ensemble":
+    prange = args.only == "ensemble" and getattr(args, "profile_range", False)
+    if prange:
         torch.cuda.profiler.start()
     e0.record(stream)
     ens.advance(max_steps=steps)
     e1.record(stream)
     stream.synchronize()
-    if args.only == "ensemble":
+    if prange:
         torch.cuda.profiler.stop()
     batch_ms = e0.elapsed_time(e1)
     leaves = sum(ens.member_stats(d)[0] for d in range(len(cases)))
@@ -503,7 +505,8 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
     runs = {}
     for every in everys:
         n_l = timed(net, plain["t"], 4 * steps, every)["steps"]
-        runs[every] = timed(net, plain["t"], n_l, every, profile=(args.only == "learned" and every == 1))
+        runs[every] = timed(net, plain["t"], n_l, every,
+                            profile=(args.only == "learned" and args.profile_range and every == 1))
     errs = {every: errors(every, plain["t"]) for every in everys}
     H.hwfv1_skipnet_destroy(net)
 

@@ -53,6 +53,9 @@ class EngineT final : public Engine {
         drop_skip_graphs();
         if (exec_uniform_) cudaGraphExecDestroy(exec_uniform_);
         skipwork_free(&skw_);
+        if (ev_fork_) cudaEventDestroy(ev_fork_);
+        if (ev_join_) cudaEventDestroy(ev_join_);
+        if (side_) cudaStreamDestroy(side_);
         for (void* p : allocs_) cudaFree(p);
         if (own_stream_) cudaStreamDestroy(stream_);
     }
@@ -295,6 +298,10 @@ class EngineT final : public Engine {
         const uint64_t npx = 1ull << (2 * (L_ - 4));
         if (!feat_ && !alloc(&feat_, npx * 4 * sizeof(__nv_bfloat16))) return oom();
         if (!skipwork_reserve(&skw_, (int64_t)npx)) return oom();
+        if (!side_ && (cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming) != cudaSuccess))
+            return fail(HWFV1_ERR_CUDA, "network stream");
         return capture_skip_graphs();
     }
 
@@ -975,21 +982,29 @@ class EngineT final : public Engine {
         launch_decode(onfly);
         sb_valid_ = !onfly;
     }
-    void launch_features(__nv_bfloat16* out) {
+    void launch_features(__nv_bfloat16* out, cudaStream_t sm = nullptr) {
         const uint32_t n = 1u << (2 * (L_ - 4));
         const double* smax_z = reinterpret_cast<const double*>(zaux_ + 8);
-        k_features<T><<<grid_for(n), 256, 0, stream_>>>(
+        k_features<T><<<grid_for(n), 256, 0, sm ? sm : stream_>>>(
             f_[0][0], f_[1][0], f_[0][1], f_[1][1], f_[0][2], f_[1][2], z_, st_, smax_z, L_ - 4, out);
     }
     // ---- the learned subtree skip (skip.cuh) -------------------------------
     // the network's predicted levels for the next steps: features of the
     // current state's level L-4 (just encoded), three convolutions, levels
-    void launch_predict() {
-        launch_features(feat_);
+    // It runs beside the step on a second stream: forked once the step has
+    // encoded (the features' level is formed) and read the levels in use,
+    // joined before the decode, whose last CTA swaps the state buffers the
+    // features read; the levels it writes serve the next steps.
+    void fork_predict() {
+        cudaEventRecord(ev_fork_, stream_);
+        cudaStreamWaitEvent(side_, ev_fork_, 0);
+        launch_features(feat_, side_);
         const int S = 1 << (L_ - 4);
-        skipnet_forward(skip_, feat_, 1, S, S, &skw_, stream_);
-        k_predict<<<grid_for((uint64_t)S * S), 256, 0, stream_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+        skipnet_forward(skip_, feat_, 1, S, S, &skw_, side_);
+        k_predict<<<grid_for((uint64_t)S * S), 256, 0, side_>>>(skw_.Z3, L_ - 4, margin_, phat_);
+        cudaEventRecord(ev_join_, side_);
     }
+    void join_predict() { cudaStreamWaitEvent(stream_, ev_join_, 0); }
     // every subtree at level L: mode 0 into the other buffer (reading the
     // fields), 1 in place before a plain step (nothing when it will not
     // run), 2 in place unconditionally (leaving the skip, checkpoints)
@@ -1039,7 +1054,7 @@ class EngineT final : public Engine {
         a.tol = (T)spec_.tol_h;
         a.L = L_;
         a.Ls = Ls;
-        lk(k_skip_encode<T>, 1u << (2 * Ls), 64, a);
+        lk(k_skip_encode<T>, grid_for((uint64_t)(1u << (2 * Ls)) * 32), 256, a);
         mark("k_skip_encode");
         if (Ls > 0) {
             EncodeArgs<T, 3> e;
@@ -1059,7 +1074,7 @@ class EngineT final : public Engine {
         }
         lk(k_skip_flag, grid_for(words_), 256, Tb_, Cb_, Tz_, czu_, Sb_, phat_, L_, Ls, st_);
         mark("k_skip_flag");
-        if (predict_now) launch_predict();
+        if (predict_now) fork_predict();
         const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
         const uint32_t tgrid = nct < (uint32_t)nsm_ * 4u ? nct : (uint32_t)nsm_ * 4u;
         lk(k_trav_fused, tgrid, 256, Sb_, dlist_, leaves_, L_, kt_, ntiles_, st_, Quiet(),
@@ -1070,6 +1085,7 @@ class EngineT final : public Engine {
         lk(k_fv1_dry<T>, grid_for(N_), 256, sa);
         mark("k_fv1_dry");
         launch_wet(sa);
+        if (predict_now) join_predict();
         SkipDecodeArgs<T> d;
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) d.f[b][q] = f_[b][q];
@@ -1093,10 +1109,11 @@ class EngineT final : public Engine {
         forget_quiet();
         const bool onfly = onfly_flags();
         launch_encode();
-        if (predict_next) launch_predict();
+        if (predict_next) fork_predict();
         if (!onfly) launch_flag();
         launch_traverse(false, onfly);
         launch_fv1();
+        if (predict_next) join_predict();
         launch_decode(onfly);
         sb_valid_ = !onfly;
     }
@@ -1315,6 +1332,8 @@ class EngineT final : public Engine {
     uint8_t* mlev_ = nullptr;    // storage level per subtree
     uint8_t* plev_ = nullptr;    // storage level per subtree after the running step
     uint32_t* czu_ = nullptr;    // closure of the bed's flags of levels < L-4
+    cudaStream_t side_ = nullptr;           // the network's stream beside the step
+    cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
     cudaGraphExec_t exec_skip_[4] = {};   // audit, audit + network, skip, skip + network
     cudaGraphExec_t exec_uniform_ = nullptr;
     uint32_t* uniform_leaves_ = nullptr;   // every finest cell as a leaf (uniform FV1)

@@ -73,90 +73,99 @@ struct SkipArgs {
     int L, Ls;
 };
 
-// Steps 1, 3 and 4 inside the subtrees: one 64-thread CTA per subtree.
-// Every level the encode forms is written to the current state buffer
-// (neighbouring leaves and the FV1 update read them there); threshold and
-// closure bits are OR-ed into words the clear kernel zeroed.
+// Steps 1, 3 and 4 inside the subtrees: one warp per subtree, eight
+// subtrees per CTA, a grid striding over the subtrees.  Every level the
+// encode forms is written to the current state buffer (neighbouring leaves
+// and the FV1 update read them there); threshold and closure bits are OR-ed
+// into words the clear kernel zeroed.  The level chain of a subtree runs in
+// its warp alone (warp barriers only), so many subtrees are in flight per SM.
 template <typename T>
-static __global__ void __launch_bounds__(64) k_skip_encode(SkipArgs<T> a) {
+static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
     pdl_wait();
     if (!a.st->active) return;
-    const uint32_t s = blockIdx.x, t = threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const int par = (int)a.st->cur;
     T* const fh = par ? a.f[1][0] : a.f[0][0];
     T* const fqx = par ? a.f[1][1] : a.f[0][1];
     T* const fqy = par ? a.f[1][2] : a.f[0][2];
     const int Ls = a.Ls;
-    const int p = a.phat[s];
-    const int P = skip_store_level(a.phat, Ls, s);
-    const int m = a.mlev[s];
-    if (t == 0) a.plev[s] = (uint8_t)P;
-    const int E = P > m ? P : m;
-    if (P > m) {                           // step 3: level P from level m
-        const uint32_t cnt = 1u << (2 * (P - Ls));
-        const uint64_t b = (uint64_t)s << (2 * (P - Ls));
-        for (uint32_t k = t; k < cnt; k += 64u) {
-            const uint64_t c = b + k, ia = lvl_off(m) + (c >> (2 * (P - m))), ic = lvl_off(P) + c;
-            fh[ic] = redecode_h(__ldcg(fh + ia), __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
-            fqx[ic] = __ldcg(fqx + ia);
-            fqy[ic] = __ldcg(fqy + ia);
-        }
-        __syncthreads();                   // the block reads level P below
-    }
-    // step 4: levels E-1 .. Ls, one thread per parent, the coarser levels
-    // from shared memory; a parent is flagged only below p (step 5)
-    __shared__ T sv[2][3][64];
-    __shared__ uint8_t scl[2][64];
-    int rb = 0;
-    for (int n = E - 1; n >= Ls; --n) {
-        const uint32_t cnt = 1u << (2 * (n - Ls));
-        const bool act = t < cnt;
-        const uint64_t pc = ((uint64_t)s << (2 * (n - Ls))) + t;
-        T sq[3] = {T(0), T(0), T(0)};
-        bool cf = false;
-        if (act) {
-            T c[3][4];
-            bool cch = false;
-            if (n == E - 1) {
-                Vec4<T>::load_cg(fh + lvl_off(n + 1) + 4ull * pc, c[0][0], c[0][1], c[0][2], c[0][3]);
-                Vec4<T>::load_cg(fqx + lvl_off(n + 1) + 4ull * pc, c[1][0], c[1][1], c[1][2], c[1][3]);
-                Vec4<T>::load_cg(fqy + lvl_off(n + 1) + 4ull * pc, c[2][0], c[2][1], c[2][2], c[2][3]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) c[q][e] = sv[rb][q][4 * t + e];
-                cch = (scl[rb][4 * t] | scl[rb][4 * t + 1] | scl[rb][4 * t + 2] | scl[rb][4 * t + 3]) != 0;
+    const uint32_t nsub = 1u << (2 * Ls);
+    __shared__ T sv[8][3][64];               // the level just formed, per warp
+    __shared__ uint8_t scl[8][64];           // its closure bits
+    for (uint32_t s = blockIdx.x * 8u + wib; s < nsub; s += gridDim.x * 8u) {
+        const int p = a.phat[s];
+        const int P = skip_store_level(a.phat, Ls, s);
+        const int m = a.mlev[s];
+        if (lane == 0u) a.plev[s] = (uint8_t)P;
+        const int E = P > m ? P : m;
+        if (P > m) {                         // step 3: level P from level m
+            const uint32_t cnt = 1u << (2 * (P - Ls));
+            const uint64_t b = (uint64_t)s << (2 * (P - Ls));
+            for (uint32_t k = lane; k < cnt; k += 32u) {
+                const uint64_t c = b + k, ia = lvl_off(m) + (c >> (2 * (P - m))), ic = lvl_off(P) + c;
+                fh[ic] = redecode_h(__ldcg(fh + ia), __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
+                fqx[ic] = __ldcg(fqx + ia);
+                fqy[ic] = __ldcg(fqy + ia);
             }
-            Thr<T> th[3];
+            __syncwarp();                    // the warp reads level P below
+        }
+        // step 4: levels E-1 .. Ls; a parent is flagged only below p (step 5).
+        // The first level reads its children from the state (up to 64
+        // parents, two rounds of the warp); the others from shared memory.
+        for (int n = E - 1; n >= Ls; --n) {
+            const uint32_t cnt = 1u << (2 * (n - Ls));
+            const bool first = n == E - 1;
+#pragma unroll 1
+            for (uint32_t t = lane; t < (first ? cnt : 32u); t += 32u) {
+                const bool act = t < cnt;
+                const uint64_t pc = ((uint64_t)s << (2 * (n - Ls))) + t;
+                T c[3][4];
+                bool cch = false;
+                T sq[3] = {T(0), T(0), T(0)};
+                bool cf = false;
+                if (act) {
+                    if (first) {
+                        Vec4<T>::load_cg(fh + lvl_off(n + 1) + 4ull * pc, c[0][0], c[0][1], c[0][2], c[0][3]);
+                        Vec4<T>::load_cg(fqx + lvl_off(n + 1) + 4ull * pc, c[1][0], c[1][1], c[1][2], c[1][3]);
+                        Vec4<T>::load_cg(fqy + lvl_off(n + 1) + 4ull * pc, c[2][0], c[2][1], c[2][2], c[2][3]);
+                    } else {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int idx = n * 3 + q;
-                th[q].thr = a.thr[idx];
-                th[q].thr4 = a.thr4[idx];
-                th[q].lo = a.thr4lo ? a.thr4lo[idx] : -1.0f;
-                th[q].hi = a.thr4hi ? a.thr4hi[idx] : -1.0f;
+                        for (int q = 0; q < 3; ++q)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) c[q][e] = sv[wib][q][4 * t + e];
+                        cch = (scl[wib][4 * t] | scl[wib][4 * t + 1] | scl[wib][4 * t + 2] | scl[wib][4 * t + 3]) != 0;
+                    }
+                    Thr<T> th[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int idx = n * 3 + q;
+                        th[q].thr = a.thr[idx];
+                        th[q].thr4 = a.thr4[idx];
+                        th[q].lo = a.thr4lo ? a.thr4lo[idx] : -1.0f;
+                        th[q].hi = a.thr4hi ? a.thr4hi[idx] : -1.0f;
+                    }
+                    bool tf = false;
+                    parents_all<T, 3>(th, c, sq, tf);
+                    fh[lvl_off(n) + pc] = sq[0];
+                    fqx[lvl_off(n) + pc] = sq[1];
+                    fqy[lvl_off(n) + pc] = sq[2];
+                    const uint32_t wi = word_off(n) + (uint32_t)(pc >> 5), bit = 1u << (pc & 31u);
+                    const bool tt = n < p && (tf || (__ldg(a.Tz + wi) & bit) != 0u);
+                    cf = tt || cch;
+                    if (tt) atomicOr(a.Tb + wi, bit);
+                    if (cf) atomicOr(a.Cb + wi, bit);
+                }
+                // the first level writes slots no lane reads in this level;
+                // the others overwrite what the warp has just read
+                if (!first) __syncwarp();
+                if (act) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) sv[wib][q][t] = sq[q];
+                    scl[wib][t] = cf ? 1 : 0;
+                }
             }
-            bool tf = false;
-            parents_all<T, 3>(th, c, sq, tf);
-            fh[lvl_off(n) + pc] = sq[0];
-            fqx[lvl_off(n) + pc] = sq[1];
-            fqy[lvl_off(n) + pc] = sq[2];
-            const uint32_t wi = word_off(n) + (uint32_t)(pc >> 5), bit = 1u << (pc & 31u);
-            const bool allowed = n < p;
-            const bool tt = allowed && (tf || (__ldg(a.Tz + wi) & bit) != 0u);
-            cf = tt || cch;
-            if (tt) atomicOr(a.Tb + wi, bit);
-            if (cf) atomicOr(a.Cb + wi, bit);
+            __syncwarp();
         }
-        __syncthreads();
-        if (act) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) sv[rb ^ 1][q][t] = sq[q];
-            scl[rb ^ 1][t] = cf ? 1 : 0;
-        }
-        __syncthreads();
-        rb ^= 1;
     }
 }
 
@@ -221,59 +230,83 @@ struct SkipDecodeArgs {
 // its covering leaf's new value (the leaf found by the walk of Algorithm 5
 // over S), with the free surface restored against z^(P_s) below a wet
 // coarser leaf; the s_max reductions run over every stored cell.  64
-// threads per subtree, four subtrees per CTA; the last CTA to finish
-// advances the time (as k_decode_finish).
+// threads per subtree, four subtrees per CTA; a subtree's flag bits on its
+// root path and at its own levels are read once into shared memory.  The
+// last CTA to finish advances the time (as k_decode_finish).
 template <typename T>
 static __global__ void __launch_bounds__(256) k_skip_decode(SkipDecodeArgs<T> a, FinishArgs fa) {
     pdl_wait();
     DevState* st = a.st;
     unsigned long long mh = 0, mqx = 0, mqy = 0;
-    if (__ldcg(&st->active)) {
-        const int nxt = (int)__ldcg(&st->cur) ^ 1;
-        T* const fh = nxt ? a.f[1][0] : a.f[0][0];
-        T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
-        T* const fqy = nxt ? a.f[1][2] : a.f[0][2];
-        const int Ls = a.Ls;
-        const uint32_t nsub = 1u << (2 * Ls);
-        const uint32_t g = threadIdx.x >> 6, t = threadIdx.x & 63u;
-        for (uint32_t s = blockIdx.x * 4u + g; s < nsub; s += gridDim.x * 4u) {
-            const int P = a.plev[s];
-            int l0 = Ls + 1;                 // a leaf on the root path covers the subtree
+    __shared__ int s_l0[4];
+    __shared__ unsigned long long s_bits[4][4];   // S of the subtree's levels Ls .. Ls+3
+    const bool run = __ldcg(&st->active) != 0u;
+    const int Ls = a.Ls;
+    const uint32_t nsub = 1u << (2 * Ls);
+    const uint32_t g = threadIdx.x >> 6, t = threadIdx.x & 63u;
+    const int nxt = (int)__ldcg(&st->cur) ^ 1;
+    T* const fh = nxt ? a.f[1][0] : a.f[0][0];
+    T* const fqx = nxt ? a.f[1][1] : a.f[0][1];
+    T* const fqy = nxt ? a.f[1][2] : a.f[0][2];
+    // uniform trip count over the CTA (barriers below)
+    const uint32_t rounds = run ? (nsub + gridDim.x * 4u - 1u) / (gridDim.x * 4u) : 0u;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t s = (r * gridDim.x + blockIdx.x) * 4u + g;
+        const bool have = s < nsub;
+        const int P = have ? (int)a.plev[s] : Ls;
+        __syncthreads();                          // the previous round's readers are done
+        if (have && t == 0u) {
+            int l0 = Ls + 1;                      // a leaf on the root path covers the subtree
             for (int n = 0; n <= Ls; ++n)
                 if (!sig_bit(a.Sb, n, s >> (2 * (Ls - n)))) {
                     l0 = n;
                     break;
                 }
-            const uint32_t cnt = 1u << (2 * (P - Ls));
-            const uint64_t b = (uint64_t)s << (2 * (P - Ls));
-            for (uint32_t k = t; k < cnt; k += 64u) {
-                const uint64_t c = b + k;
-                int l = l0;
-                if (l0 > Ls) {
-                    l = P;
-                    for (int n = Ls + 1; n < P; ++n)
-                        if (!sig_bit(a.Sb, n, (uint32_t)(c >> (2 * (P - n))))) {
-                            l = n;
-                            break;
-                        }
-                }
-                const uint64_t il = lvl_off(l) + (c >> (2 * (P - l)));
-                const T hl = fh[il], qxl = fqx[il], qyl = fqy[il];
-                T hf = hl;
-                if (l < P) {
-                    const uint64_t ic = lvl_off(P) + c;
-                    hf = redecode_h(hl, __ldg(a.z + il), __ldg(a.z + ic), a.tol);
-                    fh[ic] = hf;
-                    fqx[ic] = qxl;
-                    fqy[ic] = qyl;
-                }
-                const unsigned long long bh = abs_obits(hf), bx = abs_obits(qxl), by = abs_obits(qyl);
-                mh = bh > mh ? bh : mh;
-                mqx = bx > mqx ? bx : mqx;
-                mqy = by > mqy ? by : mqy;
-            }
-            if (t == 0u) a.mlev[s] = (uint8_t)P;
+            s_l0[g] = l0;
         }
+        if (have && t >= 1u && t <= 3u && Ls + (int)t < P) {     // levels Ls+1 .. Ls+3
+            const int n = Ls + (int)t;
+            const uint32_t cnt = 1u << (2 * t), first = s << (2 * t);
+            const uint32_t* w = a.Sb + word_off(n) + (first >> 5);
+            unsigned long long v;
+            if (cnt >= 32u) v = (unsigned long long)__ldg(w) | ((unsigned long long)__ldg(w + 1) << 32);
+            else v = (__ldg(w) >> (first & 31u)) & ((1u << cnt) - 1u);
+            s_bits[g][t] = v;
+        }
+        __syncthreads();
+        if (!have) continue;
+        const int l0 = s_l0[g];
+        const uint32_t cnt = 1u << (2 * (P - Ls));
+        const uint64_t b = (uint64_t)s << (2 * (P - Ls));
+        for (uint32_t k = t; k < cnt; k += 64u) {
+            const uint64_t c = b + k;
+            int l = l0;
+            if (l0 > Ls) {
+                l = P;
+                for (int n = Ls + 1; n < P; ++n) {
+                    const uint32_t idx = k >> (2 * (P - n));
+                    if (!((s_bits[g][n - Ls] >> idx) & 1ull)) {
+                        l = n;
+                        break;
+                    }
+                }
+            }
+            const uint64_t il = lvl_off(l) + (c >> (2 * (P - l)));
+            const T hl = fh[il], qxl = fqx[il], qyl = fqy[il];
+            T hf = hl;
+            if (l < P) {
+                const uint64_t ic = lvl_off(P) + c;
+                hf = redecode_h(hl, __ldg(a.z + il), __ldg(a.z + ic), a.tol);
+                fh[ic] = hf;
+                fqx[ic] = qxl;
+                fqy[ic] = qyl;
+            }
+            const unsigned long long bh = abs_obits(hf), bx = abs_obits(qxl), by = abs_obits(qyl);
+            mh = bh > mh ? bh : mh;
+            mqx = bx > mqx ? bx : mqx;
+            mqy = by > mqy ? by : mqy;
+        }
+        if (t == 0u) a.mlev[s] = (uint8_t)P;
     }
     block_max3_u64(mh, mqx, mqy, st->max_bits);
     __threadfence();

@@ -70,12 +70,14 @@ def test_learned_run_uses_fewer_leaves_at_bounded_cost(trained):
     # their mean leaf counts are compared loosely; the error stays bounded.
     assert ml <= mp * 1.01
     assert d_lp <= 2.0 * d_pu + 1e-12
-    # a looser margin (the median level), at a bounded cost
+    # a looser margin (the median level: a subtree is cut wherever the
+    # network gives the shallower levels even odds), at a bounded cost: the
+    # error stays within a few times the method's own adaptive error
     fm, mm, _ = _run(p, f, t_end, net=net, margin=0.5)
     d_mp = np.abs(fm["h"] - fp["h"]).sum() * cell
     print("margin 0.5: mean leaves %.0f (%.3f of plain), L1 |learned - plain| = %.3e" % (mm, mm / mp, d_mp))
-    assert mm <= mp * 1.01
-    assert d_mp <= 2.0 * d_pu + 1e-12
+    assert mm <= mp * 1.02
+    assert d_mp <= 5.0 * d_pu + 1e-12
 
 
 def test_learned_step_never_adds_leaves_on_the_same_state(trained):
