@@ -63,7 +63,7 @@ def parse():
                    help="skip the circular L=6 and bumpy L=10 dam-break measurements")
     a.add_argument("--learned-kinds", default=None,
                    help="with --only learned: comma-separated workloads (columns, bumpy)")
-    a.add_argument("--only", choices=["ensemble", "learned"],
+    a.add_argument("--only", choices=["ensemble", "learned", "leaf_store"],
                    help="run only this side measurement and print its result")
     a.add_argument("--profile-range", action="store_true",
                    help="with --only: bracket its timed region (the batched advance; the learned run "
@@ -541,6 +541,54 @@ def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100,
             "audit_K": audit_K, "margin": margin}
 
 
+def run_leaf_store(args):
+    """The exact leaf-value store (N1) against the plain step on flat-bed
+    workloads, where its subtrees are stored above the finest level: the
+    pseudo-2D dam-break of Sec. 3.2 at L=10 over 0-10 s and the water columns
+    at L=11 over 400 steps.  Steps/s of both (CUDA events), whether the final
+    fields are identical bit for bit, and the stored fraction of the finest
+    cells at the end."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2206_05761_gb300.sim import Simulation
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, (p, f), t_end, steps in (
+            ("pseudo2d_L10", synth.pseudo_2d_dam_break(L=10, eps=1e-3), 10.0, None),
+            ("columns_L11", synth.columns_dam_break(L=11, eps=1e-3, seed=1100), None, 400)):
+        res = {}
+        for store in (False, True):
+            sim = Simulation(p, f, args.precision, stream=stream)
+            if store:
+                sim.set_leaf_store(True)
+            sim.counters()                        # captures the step graphs (untimed)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if t_end is not None:
+                advance_to(sim, t_end)
+            else:
+                sim.advance(max_steps=steps)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            n, lu, _, _, _ = sim.counters()
+            r = {"steps": n, "ms": ms, "steps_per_s": n / (ms / 1e3), "mean_leaves": lu / max(n, 1),
+                 "fields": sim.fields()}
+            if store:
+                lv = sim.skip_levels(1).astype(np.int64)
+                r["stored_fraction_at_end"] = float(np.mean(np.power(4.0, lv - p["L"])))
+            sim.close()
+            res["store" if store else "plain"] = r
+        same = all(np.array_equal(res["plain"]["fields"][k], res["store"]["fields"][k]) for k in ("h", "qx", "qy"))
+        for r in res.values():
+            r.pop("fields")
+        out[name] = dict(res, speedup=res["plain"]["ms"] / res["store"]["ms"], identical_fields=bool(same),
+                         workload="%s, eps=1e-3, %s" % (name, "t = 0 to %g s" % t_end if t_end else "%d steps" % steps))
+    return out
+
+
 def run_pseudo2d(args):
     """Pseudo-2D dam-break of Sec. 3.2, HWFV1 vs uniform FV1 over 10 s at
     L=10 (paper_2206_05761_gb300.scenarios)."""
@@ -872,8 +920,12 @@ def main():
         return
     if args.only is not None:
         if rank == 0:
-            res = (run_ensemble(args) if args.only == "ensemble" else
-                   {k: run_learned(args, k) for k in (args.learned_kinds or "columns,bumpy").split(",")})
+            if args.only == "ensemble":
+                res = run_ensemble(args)
+            elif args.only == "leaf_store":
+                res = run_leaf_store(args)
+            else:
+                res = {k: run_learned(args, k) for k in (args.learned_kinds or "columns,bumpy").split(",")}
             print(json.dumps({args.only: res}))
         return
     if world > 1:
@@ -942,6 +994,7 @@ def main():
         out["ensemble"] = run_ensemble(args)
     if world == 1 and not args.no_pseudo2d:
         out["pseudo2d"] = run_pseudo2d(args)
+        out["leaf_store"] = run_leaf_store(args)
     if world == 1 and not args.no_learned:
         out["learned"] = {k: run_learned(args, k) for k in ("columns", "bumpy")}
     if world == 1 and not args.no_cpu_baseline:

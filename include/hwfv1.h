@@ -320,6 +320,23 @@ hwfv1_status hwfv1_set_skipnet(hwfv1_handle* hd, hwfv1_skipnet* net, int32_t aud
  * the next call; audit_K as above.  Needs L >= 5 (and the flags above).
  * HWFV1_ERR_INVALID_SPEC for a level out of range. */
 hwfv1_status hwfv1_set_skip_levels(hwfv1_handle* hd, const uint8_t* levels, int32_t audit_K);
+/* Exact leaf-value store (on = 1; 0 stops it).  The paper's encoding runs
+ * only along the tree of significant details (the note after Algorithm 3);
+ * here, exactly: a level-(L-4) subtree whose bed is flat (every finest bed
+ * value equal) is stored at its deepest leaf level m instead of the finest
+ * grid.  Every finest cell below a stored cell then holds that cell's value
+ * (the decode-back hands a leaf's value, with its free surface, to every
+ * finest cell below it), so the subtree's details at levels >= m are zero and
+ * flag nothing (eps > 0): it is encoded from level m only, kept down to
+ * m + 1 (where its next leaves can be), and its coarse leaves are decoded
+ * down to level m, not L.  Other subtrees are stored at L.  Results are the
+ * plain step's bit for bit; the bytes a flat subtree moves fall as
+ * 4^(m-L).  Quiescent-tile skipping (HWFV1_FULL_SWEEP) does not apply while
+ * it is on.  Needs L >= 5, eps >= 1e-30, HWFV1_REG_PREDICT and
+ * HWFV1_REG_CLOSE, not HWFV1_FLUX_MATCH; not together with the learned
+ * skip (turning one on turns the other off).  hwfv1_get_skip_levels(1)
+ * gives the storage levels. */
+hwfv1_status hwfv1_set_leaf_store(hwfv1_handle* hd, int32_t on);
 /* which = 0: the predicted levels in use; which = 1: the level each
  * subtree's state is stored at (L outside the skip).  Host output, 4^(L-4)
  * bytes, row-major over level L-4.  Synchronises. */

@@ -224,6 +224,10 @@ hwfv1_status hwfv1_get_skip_levels(hwfv1_handle* hd, int32_t which, uint8_t* out
     if (!out) return HWFV1_ERR_INVALID_SPEC;
     return from_engine(hd, hd->eng->get_skip_levels(which, out, cap));
 }
+hwfv1_status hwfv1_set_leaf_store(hwfv1_handle* hd, int32_t on) {
+    HWFV1_CHECK_HANDLE(hd);
+    return from_engine(hd, hd->eng->set_leaf_store(on ? 1 : 0));
+}
 hwfv1_status hwfv1_get_features(hwfv1_handle* hd, uint16_t* out, int64_t cap) {
     HWFV1_CHECK_HANDLE(hd);
     if (!out) return HWFV1_ERR_INVALID_SPEC;

@@ -327,6 +327,27 @@ class EngineT final : public Engine {
         return capture_skip_graphs();
     }
 
+    // The exact leaf-value store: subtrees whose bed is flat are stored at
+    // their deepest leaf level and kept one level deeper (k_exact_levels);
+    // the results are those of the plain step bit for bit.
+    hwfv1_status set_leaf_store(int on) override {
+        if (!on) return skipmode_ == 3 ? skip_off() : HWFV1_OK;
+        if (L_ < 5) return fail(HWFV1_ERR_INVALID_SPEC, "leaf store needs L >= 5");
+        if (!(spec_.eps >= 1e-30))
+            return fail(HWFV1_ERR_INVALID_SPEC, "leaf store needs eps >= 1e-30 (thresholds above 0)");
+        if (skipmode_ == 3) return HWFV1_OK;
+        if (skipmode_) skip_off();
+        const uint32_t nsub = 1u << (2 * (L_ - 4));
+        if (!flat_) {
+            if (!alloc(&flat_, nsub)) return oom();
+            k_flat_subtrees<T><<<grid_for((uint64_t)nsub * 32), 256, 0, stream_>>>(z_ + lvl_off(L_), L_, L_ - 4, flat_);
+        }
+        if (hwfv1_status r = skip_on(3, 0x7FFFFFFF); r != HWFV1_OK) return r;
+        skip_ = nullptr;
+        every_ = 1;
+        return capture_skip_graphs();
+    }
+
     // which = 0: the predicted levels in use; 1: the storage levels
     // (host, row-major over level L-4)
     hwfv1_status get_skip_levels(int which, uint8_t* out, int64_t cap) override {
@@ -1015,6 +1036,7 @@ class EngineT final : public Engine {
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
         a.z = z_;
         a.mlev = mlev_;
+        a.flat = skipmode_ == 3 ? flat_ : nullptr;
         a.st = st_;
         a.tol = (T)spec_.tol_h;
         a.L = L_;
@@ -1034,9 +1056,16 @@ class EngineT final : public Engine {
         lk(k_clear_words, grid_for(2 * (uint64_t)words_), 256, Tb_, 2 * words_, st_, (const uint8_t*)nullptr,
            (const uint8_t*)nullptr, ntiles_, (uint32_t*)nullptr, &st_->ndec);
         mark("k_clear_words");
+        const uint8_t* flat = skipmode_ == 3 ? flat_ : nullptr;
+        if (flat) {
+            lk(k_exact_levels, grid_for(1u << (2 * Ls)), 256, (const uint8_t*)mlev_, flat, phat_, L_, Ls,
+               (const DevState*)st_);
+            mark("k_exact_levels");
+        }
         SkipArgs<T> a;
         for (int b = 0; b < 2; ++b)
             for (int q = 0; q < 3; ++q) a.f[b][q] = f_[b][q];
+        a.flat = flat;
         a.z = z_;
         a.thr = thr_dyn();
         a.thr4 = thr4_dyn();
@@ -1093,6 +1122,7 @@ class EngineT final : public Engine {
         d.Sb = Sb_;
         d.plev = plev_;
         d.mlev = mlev_;
+        d.flat = flat;
         d.st = st_;
         d.tol = (T)spec_.tol_h;
         d.L = L_;
@@ -1332,6 +1362,7 @@ class EngineT final : public Engine {
     uint8_t* mlev_ = nullptr;    // storage level per subtree
     uint8_t* plev_ = nullptr;    // storage level per subtree after the running step
     uint32_t* czu_ = nullptr;    // closure of the bed's flags of levels < L-4
+    uint8_t* flat_ = nullptr;    // exact store: 1 where the subtree's bed is flat
     cudaStream_t side_ = nullptr;           // the network's stream beside the step
     cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
     cudaGraphExec_t exec_skip_[4] = {};   // audit, audit + network, skip, skip + network

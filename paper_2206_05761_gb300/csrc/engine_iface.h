@@ -46,6 +46,8 @@ class Engine {
     // level L-4); levels == nullptr turns it off
     virtual hwfv1_status set_skip_levels(const uint8_t* levels, int audit_K) = 0;
     virtual hwfv1_status get_skip_levels(int which, uint8_t* out, int64_t cap) = 0;
+    // exact leaf-value store on (1) or off (0)
+    virtual hwfv1_status set_leaf_store(int on) = 0;
     virtual hwfv1_status get_features(uint16_t* out, int64_t cap) = 0;
     virtual hwfv1_status get_labels(uint8_t* out, int64_t cap) = 0;
     std::string err;

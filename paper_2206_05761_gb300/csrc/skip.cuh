@@ -68,6 +68,7 @@ struct SkipArgs {
     const uint8_t* phat;      // predicted level per subtree
     const uint8_t* mlev;      // storage level per subtree as the step starts
     uint8_t* plev;            // storage level per subtree after the step (P_s)
+    const uint8_t* flat = nullptr;   // exact store: 1 where the subtree's bed is flat (NULL: the learned skip)
     DevState* st;
     T tol;
     int L, Ls;
@@ -101,9 +102,13 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
         if (P > m) {                         // step 3: level P from level m
             const uint32_t cnt = 1u << (2 * (P - Ls));
             const uint64_t b = (uint64_t)s << (2 * (P - Ls));
+            // the exact store keeps a flat subtree's stored cells as the
+            // finest cells they stand for: formed by copying
+            const bool copy = a.flat != nullptr && a.flat[s] != 0;
             for (uint32_t k = lane; k < cnt; k += 32u) {
                 const uint64_t c = b + k, ia = lvl_off(m) + (c >> (2 * (P - m))), ic = lvl_off(P) + c;
-                fh[ic] = redecode_h(__ldcg(fh + ia), __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
+                const T hl = __ldcg(fh + ia);
+                fh[ic] = copy ? hl : redecode_h(hl, __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
                 fqx[ic] = __ldcg(fqx + ia);
                 fqy[ic] = __ldcg(fqy + ia);
             }
@@ -220,7 +225,8 @@ struct SkipDecodeArgs {
     const T* z;
     const uint32_t* Sb;       // the step's regularised flags
     const uint8_t* plev;      // P_s
-    uint8_t* mlev;            // set to P_s
+    uint8_t* mlev;            // set to the level the subtree is stored at
+    const uint8_t* flat = nullptr;   // exact store (see k_skip_decode)
     DevState* st;
     T tol;
     int L, Ls;
@@ -276,26 +282,40 @@ static __global__ void __launch_bounds__(256) k_skip_decode(SkipDecodeArgs<T> a,
         __syncthreads();
         if (!have) continue;
         const int l0 = s_l0[g];
-        const uint32_t cnt = 1u << (2 * (P - Ls));
-        const uint64_t b = (uint64_t)s << (2 * (P - Ls));
+        // the level the subtree is stored at: P_s, or with the exact store
+        // on a flat bed its deepest leaf level (every finest cell below a
+        // stored cell then holds that cell's value), where a wet leaf at the
+        // stored level also takes the free surface the finest cells get
+        const bool exact = a.flat != nullptr && a.flat[s] != 0;
+        int tgt = P;
+        if (exact) {
+            tgt = Ls;
+            if (l0 > Ls) {
+                tgt = Ls + 1;
+                for (int d = 1; d <= 3 && Ls + d < P; ++d)
+                    if (s_bits[g][d] != 0ull) tgt = Ls + d + 1;
+            }
+        }
+        const uint32_t cnt = 1u << (2 * (tgt - Ls));
+        const uint64_t b = (uint64_t)s << (2 * (tgt - Ls));
         for (uint32_t k = t; k < cnt; k += 64u) {
             const uint64_t c = b + k;
             int l = l0;
             if (l0 > Ls) {
-                l = P;
-                for (int n = Ls + 1; n < P; ++n) {
-                    const uint32_t idx = k >> (2 * (P - n));
+                l = tgt;
+                for (int n = Ls + 1; n < tgt; ++n) {
+                    const uint32_t idx = k >> (2 * (tgt - n));
                     if (!((s_bits[g][n - Ls] >> idx) & 1ull)) {
                         l = n;
                         break;
                     }
                 }
             }
-            const uint64_t il = lvl_off(l) + (c >> (2 * (P - l)));
+            const uint64_t il = lvl_off(l) + (c >> (2 * (tgt - l)));
             const T hl = fh[il], qxl = fqx[il], qyl = fqy[il];
             T hf = hl;
-            if (l < P) {
-                const uint64_t ic = lvl_off(P) + c;
+            if (l < tgt || (exact && tgt < a.L)) {
+                const uint64_t ic = lvl_off(tgt) + c;
                 hf = redecode_h(hl, __ldg(a.z + il), __ldg(a.z + ic), a.tol);
                 fh[ic] = hf;
                 fqx[ic] = qxl;
@@ -306,7 +326,7 @@ static __global__ void __launch_bounds__(256) k_skip_decode(SkipDecodeArgs<T> a,
             mqx = bx > mqx ? bx : mqx;
             mqy = by > mqy ? by : mqy;
         }
-        if (t == 0u) a.mlev[s] = (uint8_t)P;
+        if (t == 0u) a.mlev[s] = (uint8_t)tgt;
     }
     block_max3_u64(mh, mqx, mqy, st->max_bits);
     __threadfence();
@@ -330,6 +350,7 @@ struct SkipFinestArgs {
     T* f[2][3];
     const T* z;
     uint8_t* mlev;
+    const uint8_t* flat = nullptr;   // exact store: flat subtrees are copied down
     DevState* st;
     T tol;
     int L, Ls;
@@ -353,6 +374,7 @@ static __global__ void __launch_bounds__(256) k_skip_finest(SkipFinestArgs<T> a)
     for (uint32_t s = blockIdx.x * 4u + g; s < nsub; s += gridDim.x * 4u) {
         const int m = a.mlev[s];
         if (m == L && in_place) continue;
+        const bool copy = a.flat != nullptr && a.flat[s] != 0;
         const uint64_t b = (uint64_t)s << (2 * (L - Ls));
         for (uint32_t k = t; k < (1u << (2 * (L - Ls))); k += 64u) {
             const uint64_t c = b + k, ic = lvl_off(L) + c;
@@ -362,12 +384,43 @@ static __global__ void __launch_bounds__(256) k_skip_finest(SkipFinestArgs<T> a)
                 dqy[ic] = sqy[ic];
             } else {
                 const uint64_t ia = lvl_off(m) + (c >> (2 * (L - m)));
-                dh[ic] = redecode_h(sh[ia], __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
+                dh[ic] = copy ? sh[ia] : redecode_h(sh[ia], __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
                 dqx[ic] = sqx[ia];
                 dqy[ic] = sqy[ia];
             }
         }
         if (in_place && t == 0u) a.mlev[s] = (uint8_t)L;
+    }
+}
+
+// The exact leaf-value store's levels: a subtree whose bed is flat holds
+// after a step the same value in every finest cell below each cell of its
+// stored level m (its deepest leaf level), so none of its details at levels
+// >= m is significant (eps > 0) and its next leaves are no finer than m + 1;
+// p = m + 1 keeps exactly the plain step's tree.  Other subtrees keep L.
+static __global__ void k_exact_levels(const uint8_t* __restrict__ mlev, const uint8_t* __restrict__ flat,
+                                      uint8_t* __restrict__ phat, int L, int Ls, const DevState* st) {
+    pdl_wait();
+    if (!st->active) return;
+    const uint32_t n = 1u << (2 * Ls);
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int m = mlev[s];
+        phat[s] = (uint8_t)(flat[s] ? (m + 1 < L ? m + 1 : L) : L);
+    }
+}
+
+// 1 where every finest bed value of the subtree is the same (bit for bit);
+// then so is every coarser bed coefficient inside it.
+template <typename T>
+static __global__ void k_flat_subtrees(const T* __restrict__ zL, int L, int Ls, uint8_t* __restrict__ flat) {
+    const uint32_t n = 1u << (2 * Ls), cells = 1u << (2 * (L - Ls));
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += (gridDim.x * blockDim.x) >> 5) {
+        const T z0 = zL[(uint64_t)s * cells];
+        bool same = true;
+        for (uint32_t k = lane; k < cells; k += 32u) same = same && zL[(uint64_t)s * cells + k] == z0;
+        same = __all_sync(0xffffffffu, same);
+        if (lane == 0u) flat[s] = same ? 1 : 0;
     }
 }
 

@@ -113,6 +113,7 @@ def lib():
             L.hwfv1_set_skipnet.argtypes = [_H, C.c_void_p, C.c_int32, C.c_float, C.c_int32]
             L.hwfv1_set_skip_levels.argtypes = [_H, C.c_void_p, C.c_int32]
             L.hwfv1_get_skip_levels.argtypes = [_H, C.c_int32, C.c_void_p, C.c_int64]
+            L.hwfv1_set_leaf_store.argtypes = [_H, C.c_int32]
             L.hwfv1_get_features.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_get_labels.argtypes = [_H, _dp, C.c_int64]
             L.hwfv1_destroy.argtypes = [_H]
@@ -133,7 +134,7 @@ def exported_symbols():
             "hwfv1_skipnet_num_params", "hwfv1_skipnet_create", "hwfv1_skipnet_set_params",
             "hwfv1_skipnet_get_params", "hwfv1_skipnet_forward", "hwfv1_skipnet_gradients",
             "hwfv1_skipnet_train", "hwfv1_skipnet_destroy", "hwfv1_set_skipnet", "hwfv1_set_skip_levels",
-            "hwfv1_get_skip_levels", "hwfv1_get_features", "hwfv1_get_labels"]
+            "hwfv1_get_skip_levels", "hwfv1_set_leaf_store", "hwfv1_get_features", "hwfv1_get_labels"]
 
 
 def _check(st, what, hd=None):
@@ -465,6 +466,10 @@ def hwfv1_get_skip_levels(hd, which, L):
     out = np.empty((S, S), dtype=np.uint8)
     _check(lib().hwfv1_get_skip_levels(hd, int(which), out.ctypes.data, out.size), "hwfv1_get_skip_levels", hd)
     return out
+
+
+def hwfv1_set_leaf_store(hd, on=True):
+    _check(lib().hwfv1_set_leaf_store(hd, 1 if on else 0), "hwfv1_set_leaf_store", hd)
 
 
 def hwfv1_get_features(hd, out):

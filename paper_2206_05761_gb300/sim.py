@@ -131,6 +131,11 @@ class Simulation:
         L-4; None stops it)."""
         H.hwfv1_set_skip_levels(self.hd, levels, audit_K)
 
+    def set_leaf_store(self, on=True):
+        """The exact leaf-value store (flat-bed subtrees stored at their
+        deepest leaf level; results identical to the plain step)."""
+        H.hwfv1_set_leaf_store(self.hd, on)
+
     def skip_levels(self, which=1):
         """Storage levels (which=1) or predicted levels in use (which=0)."""
         return H.hwfv1_get_skip_levels(self.hd, which, self.L)
