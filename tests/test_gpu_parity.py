@@ -572,3 +572,43 @@ def test_uniform_and_adaptive_steps_mix():
     _compare_fields(sim, ref)
     assert sim.time()[:2] == (ref.t, ref.dt)
     sim.close()
+
+
+def test_top_of_range_L13_one_step_matches_oracle():
+    # 8192 x 8192 (67 M finest cells), the circular dam-break: one step of
+    # the graph-replay path against one oracle step, leaves and fields bit
+    # for bit (the level offsets, 28-bit Morton codes and tile counts of the
+    # top of the accepted range, L <= 14, in use)
+    p, f = synth.circular_dam_break(L=13, eps=1e-3)
+    sim = _sim(p, f)
+    ref = oracle.State(p, f)
+    assert sim.time()[1] == ref.dt
+    sim.advance(max_steps=1)
+    res = ref.step(want=("leaves",))
+    lv = sim.leaves()
+    assert len(lv) == res["num_leaves"] and np.array_equal(lv, res["leaves"])
+    _compare_fields(sim, ref)
+    sim.close()
+
+
+def test_top_of_range_L14_keeps_the_symmetries():
+    # 16384 x 16384 (268 M finest cells): too large for the oracle in a
+    # test, so the properties the oracle pins for this case hold instead --
+    # the circular dam-break stays symmetric under the transpose (hu and hv
+    # swap) and under both mirrors (the normal discharge flips) up to the
+    # rounding of the x- and y-sums' different order (1e-12, as the oracle's
+    # pin), and the leaves tile the domain
+    p, f = synth.circular_dam_break(L=14, eps=1e-3)
+    sim = _sim(p, f)
+    del f
+    sim.advance(max_steps=3)
+    g = sim.fields()
+    h, qx, qy = g["h"], g["qx"], g["qy"]
+    assert np.isfinite(h).all() and h.max() > 1.0 and np.abs(qx).max() > 0.0
+    tol = 1e-12
+    assert np.abs(h - h.T).max() <= tol and np.abs(qx - qy.T).max() <= tol
+    assert np.abs(h - h[::-1, :]).max() <= tol and np.abs(qy + qy[::-1, :]).max() <= tol
+    assert np.abs(h - h[:, ::-1]).max() <= tol and np.abs(qx + qx[:, ::-1]).max() <= tol
+    lv = (sim.leaves() >> 28).astype(np.int64)
+    assert np.sum(np.ldexp(1.0, -2 * lv)) == 1.0
+    sim.close()
