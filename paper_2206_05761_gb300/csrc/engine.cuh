@@ -1185,6 +1185,7 @@ class EngineT final : public Engine {
     // static closure of the bed's flags above the subtrees, storage levels
     // from the current state
     hwfv1_status skip_on(int mode, int audit_K) {
+        if (batched_) return fail(HWFV1_ERR_STATE, "a batch member is stepped by its batch (plain steps only)");
         if (spec_.flags & HWFV1_FLUX_MATCH) return fail(HWFV1_ERR_INVALID_SPEC, "learned skip with HWFV1_FLUX_MATCH");
         if (!predict() || !close())
             return fail(HWFV1_ERR_INVALID_SPEC, "learned skip needs HWFV1_REG_PREDICT and HWFV1_REG_CLOSE");

@@ -106,3 +106,21 @@ def test_batch_float32_matches_single_domain_path():
         assert tuple(ens.member_time(d)) == tuple(sim.time())
         sim.close()
     ens.close()
+
+
+def test_batch_member_refuses_the_skip_modes():
+    # the batched kernels read a member's finest leaves; a member stored
+    # above level L (learned skip, exact leaf-value store) would break them
+    import paper_2206_05761_gb300.hwfv1 as H
+    from paper_2206_05761_gb300.sim import Ensemble
+    ens = Ensemble([synth.bumpy_dam_break(L=7, eps=1e-3, seed=3)])
+    hd = H.hwfv1_batch_member(ens.bt, 0)
+    with pytest.raises(H.Hwfv1Error):
+        H.hwfv1_set_leaf_store(hd, 1)
+    with pytest.raises(H.Hwfv1Error):
+        H.hwfv1_set_skip_levels(hd, np.full((8, 8), 7, np.uint8), 10)
+    ens.advance(t_end=0.002, max_steps=100)
+    ref = oracle.State(*synth.bumpy_dam_break(L=7, eps=1e-3, seed=3))
+    ref.run(t_end=0.002)
+    assert np.array_equal(ens.member_fields(0)["h"], ref.h)
+    ens.close()

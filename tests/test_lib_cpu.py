@@ -62,6 +62,12 @@ def test_bad_inflow_rejected():
 def test_null_handle_is_state_error():
     assert H.lib().hwfv1_encode(None) == 7
     assert H.lib().hwfv1_last_error(None) == b"NULL handle"
+    # the learned skip and the exact leaf-value store check the handle first
+    levels = (C.c_uint8 * 16)()
+    assert H.lib().hwfv1_set_skip_levels(None, C.cast(levels, C.c_void_p), 10) == 7
+    assert H.lib().hwfv1_get_skip_levels(None, 1, C.cast(levels, C.c_void_p), 16) == 7
+    assert H.lib().hwfv1_set_leaf_store(None, 1) == 7
+    assert H.lib().hwfv1_set_skipnet(None, None, 10, 0.0, 1) == 7
 
 
 def _batch_init(specs, n, ptrs):
