@@ -419,7 +419,7 @@ def run_ensemble(args, steps=50):
             "launches_per_step": lps}
 
 
-def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100, steps=400, margin=0.005,
+def run_learned(args, kind, L=11, train_seeds=range(1000, 1008), test_seed=1100, steps=400, margin=0.002,
                 audit_K=10, epochs=20, sample_every=10, everys=(1, 4)):
     """Learned subtree skip at L = 11: the subtree CNN trained (BF16 tensor
     cores) on trajectories of seeded cases run on the GPU path, then a
