@@ -249,9 +249,14 @@ struct DevState {
 
 enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };
 
-// a double that is +0 or -0 (integer test, no FP64 instruction)
+// a double that is +0 or -0, tested on its two 32-bit halves.  The halves
+// are taken by a register move the compiler cannot see through: the same
+// test on the 64-bit pattern is recognised as a comparison with 0.0 and
+// issued as a floating-point compare on the FP64 pipe.
 __device__ __forceinline__ bool is_zero(double x) {
-    return (__double_as_longlong(x) << 1) == 0;
+    uint32_t lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+    return ((hi << 1) | lo) == 0u;
 }
 __device__ __forceinline__ bool is_zero(float x) { return (__float_as_int(x) << 1) == 0; }
 
