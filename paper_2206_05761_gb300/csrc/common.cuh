@@ -17,6 +17,22 @@
 
 namespace hwfv1 {
 
+// The bit pattern of a double and back, by register moves the compiler
+// cannot see through.  Integer tests written on __double_as_longlong are
+// recognised as floating-point operations (x == 0, |x|, x < y) and issued
+// on the FP64 pipe, the bottleneck of this GPU; on these patterns they stay
+// integer instructions.
+__device__ __forceinline__ long long dbits(double x) {
+    long long b;
+    asm("mov.b64 %0, %1;" : "=l"(b) : "d"(x));
+    return b;
+}
+__device__ __forceinline__ double dval(long long b) {
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(b));
+    return x;
+}
+
 constexpr int kMaxL = 14;
 constexpr int kLeafShift = 28;              // packed leaf: level << 28 | code
 constexpr uint32_t kCodeMask = (1u << kLeafShift) - 1u;
@@ -93,19 +109,19 @@ __host__ __device__ inline uint32_t expand4x8(uint32_t x) {
 
 // ordered bits of |x| (sign cleared with an integer op)
 __device__ __forceinline__ unsigned long long abs_obits(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    return (unsigned long long)dbits(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 __device__ __forceinline__ unsigned long long abs_obits(float x) {
     // |x| widened to double is exact; its bits order like the value
-    return (unsigned long long)__double_as_longlong((double)__int_as_float(__float_as_int(x) & 0x7FFFFFFF));
+    return (unsigned long long)dbits((double)__int_as_float(__float_as_int(x) & 0x7FFFFFFF));
 }
 
 // ordered bits of a non-negative double (min/max by integer atomics)
 __device__ __forceinline__ unsigned long long obits(double x) {
-    return (unsigned long long)__double_as_longlong(x);
+    return (unsigned long long)dbits(x);
 }
 __device__ __forceinline__ double from_obits(unsigned long long b) {
-    return __longlong_as_double((long long)b);
+    return dval((long long)b);
 }
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
@@ -249,23 +265,16 @@ struct DevState {
 
 enum : uint32_t { kErrNonFinite = 1u, kErrTimeout = 2u };
 
-// a double that is +0 or -0, tested on its two 32-bit halves.  The halves
-// are taken by a register move the compiler cannot see through: the same
-// test on the 64-bit pattern is recognised as a comparison with 0.0 and
-// issued as a floating-point compare on the FP64 pipe.
-__device__ __forceinline__ bool is_zero(double x) {
-    uint32_t lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
-    return ((hi << 1) | lo) == 0u;
-}
+// a double that is +0 or -0 (integer test, no FP64 instruction)
+__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
 __device__ __forceinline__ bool is_zero(float x) { return (__float_as_int(x) << 1) == 0; }
 
 // x >= y decided on the bit patterns.  Equal to the IEEE comparison for
 // every x (negative, NaN and inf included) when y > 0, and when y == +0 for
 // every x except -0 (callers use it with y > 0, or with x never -0).
 __device__ __forceinline__ bool ge_nonneg(double x, double y) {
-    const long long bx = __double_as_longlong(x);
-    return bx >= __double_as_longlong(y) && bx <= 0x7FF0000000000000ll;
+    const long long bx = dbits(x);
+    return bx >= dbits(y) && bx <= 0x7FF0000000000000ll;
 }
 __device__ __forceinline__ bool ge_nonneg(float x, float y) {
     const int bx = __float_as_int(x);

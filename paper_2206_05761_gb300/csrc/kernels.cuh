@@ -72,10 +72,10 @@ template <> struct Vec4<uint32_t> {
 
 template <typename T> __device__ __forceinline__ bool same4(T a, T b, T c, T d);
 template <> __device__ __forceinline__ bool same4<double>(double a, double b, double c, double d) {
-    const long long x = __double_as_longlong(a);
+    const long long x = dbits(a);
     // equal bit patterns and |a| < 2^1022 (so 4a does not overflow)
-    return x == __double_as_longlong(b) && x == __double_as_longlong(c) &&
-           x == __double_as_longlong(d) && ((x >> 52) & 0x7FF) < 0x7FD;
+    return x == dbits(b) && x == dbits(c) &&
+           x == dbits(d) && ((x >> 52) & 0x7FF) < 0x7FD;
 }
 template <> __device__ __forceinline__ bool same4<float>(float a, float b, float c, float d) {
     const int x = __float_as_int(a);
@@ -85,7 +85,7 @@ template <> __device__ __forceinline__ bool same4<float>(float a, float b, float
 
 // |x| by clearing the sign bit (no FP64 instruction)
 __device__ __forceinline__ double absval(double x) {
-    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+    return dval(dbits(x) & 0x7FFFFFFFFFFFFFFFll);
 }
 __device__ __forceinline__ float absval(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
 
@@ -99,9 +99,9 @@ __device__ __forceinline__ float absval(float x) { return __int_as_float(__float
 // executed when the integer path applies).
 template <int K>
 __device__ __forceinline__ double pow2_scale(double x) {
-    const long long b = __double_as_longlong(x);
+    const long long b = dbits(x);
     const int e = (int)((b >> 52) & 0x7FF);
-    if (e + K >= 1 && e + K <= 0x7FE && e >= 1 && e <= 0x7FE) return __longlong_as_double(b + ((long long)K << 52));
+    if (e + K >= 1 && e + K <= 0x7FE && e >= 1 && e <= 0x7FE) return dval(b + ((long long)K << 52));
     double r;
     if (K == -2) asm volatile("mul.rn.f64 %0, %1, 0d3FD0000000000000;" : "=d"(r) : "d"(x));
     else if (K == -1) asm volatile("mul.rn.f64 %0, %1, 0d3FE0000000000000;" : "=d"(r) : "d"(x));
@@ -122,9 +122,9 @@ __device__ __forceinline__ float pow2_scale(float x) {
 // x * 2^n for 0 <= n <= 30: an exponent step when x and the result are
 // normal numbers, otherwise the IEEE product (the same bits either way).
 __device__ __forceinline__ double mul_pow2(double x, int n) {
-    const long long b = __double_as_longlong(x);
+    const long long b = dbits(x);
     const int e = (int)((b >> 52) & 0x7FF);
-    if (e >= 1 && e + n <= 0x7FE) return __longlong_as_double(b + ((long long)n << 52));
+    if (e >= 1 && e + n <= 0x7FE) return dval(b + ((long long)n << 52));
     return x * (double)(1u << n);
 }
 __device__ __forceinline__ float mul_pow2(float x, int n) {
@@ -139,7 +139,7 @@ template <typename T> __device__ __forceinline__ T twice(T x) { return pow2_scal
 
 // Integer key with the order of the IEEE comparison (+0 and -0 equal).
 __device__ __forceinline__ long long ord_key(double x) {
-    const long long b = __double_as_longlong(x);
+    const long long b = dbits(x);
     return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFll);
 }
 __device__ __forceinline__ int ord_key(float x) {
@@ -154,12 +154,12 @@ template <typename T> __device__ __forceinline__ bool ge_zero(T x) { return ord_
 template <typename T> __device__ __forceinline__ bool le_zero(T x) { return ord_key(x) <= 0; }
 // x is finite (not inf or NaN)
 __device__ __forceinline__ bool finite_bits(double x) {
-    return (__double_as_longlong(x) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
+    return (dbits(x) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
 }
 __device__ __forceinline__ bool finite_bits(float x) { return (__float_as_int(x) & 0x7F800000) != 0x7F800000; }
 // x > 0, false for NaN as in IEEE
 __device__ __forceinline__ bool gt_zero(double x) {
-    const long long b = __double_as_longlong(x);
+    const long long b = dbits(x);
     return b > 0 && b <= 0x7FF0000000000000ll;
 }
 __device__ __forceinline__ bool gt_zero(float x) {
@@ -210,7 +210,7 @@ __device__ __forceinline__ bool passes_thr(T m4, T thr, T thr4) {
 // bits, so |f - x| <= 2^-23 |x| and |f| <= |x| in the normal float range;
 // +-0 when |x| < 2^-126; an infinity when |x| >= 2^128, or x is not finite.
 __device__ __forceinline__ float trunc_float(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long b = (unsigned long long)dbits(x);
     const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
     const uint32_t sign = hi & 0x80000000u;
     const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
@@ -398,7 +398,7 @@ __device__ __forceinline__ T* quantity_ptr(const EncodeArgs<T, NF>& a, int par, 
 }
 
 // the value is +0 (all bits clear)
-__device__ __forceinline__ bool pos_zero(double x) { return __double_as_longlong(x) == 0ll; }
+__device__ __forceinline__ bool pos_zero(double x) { return dbits(x) == 0ll; }
 __device__ __forceinline__ bool pos_zero(float x) { return __float_as_int(x) == 0; }
 
 // One CTA encodes one tile: the 4^k cells of level ls under one level-(ls-k)
