@@ -80,7 +80,7 @@ MUTANTS = [
      "            if (0) {\n                double eta = hl + zh[ka];"),
     ("skip_store_bed_of_leaf_level", "                        double d = eta - zh[kc];\n                        hf = d > 0.0 ? d : 0.0;\n                    }\n                    hier3[0][kc] = hf;\n                    hier3[1][kc] = nv[1][kl];",
      "                        double d = eta - zh[kl];\n                        hf = d > 0.0 ? d : 0.0;\n                    }\n                    hier3[0][kc] = hf;\n                    hier3[1][kc] = nv[1][kl];"),
-    ("skip_smax_without_floor", "double smax[4] = {1.0, 1.0, 1.0, orc_smax(L, z)};", "double smax[4] = {0.0, 0.0, 0.0, orc_smax(L, z)};"),
+    ("skip_smax_without_floor", "smax3[0] = smax3[1] = smax3[2] = 1.0;", "smax3[0] = smax3[1] = smax3[2] = 0.0;"),
     ("skip_storage_level_not_updated", "for (int64_t s = 0; s < NSUB; ++s) m[s] = P[s];", "for (int64_t s = 0; s < NSUB; ++s) m[s] = m[s];"),
 ]
 
