@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "engine_iface.h"
@@ -559,7 +560,7 @@ class EngineT final : public Engine {
         if (!onfly) launch_flag();
         launch_traverse(false, onfly);
         StepArgs<T> a = step_args();
-        lk(k_fv1_dry<T>, grid_for(N_), 256, a);
+        lk(k_fv1_dry<T>, grid_res(k_fv1_dry<T>, grid_for(N_), 256), 256, a);
         cudaGraph_t g = nullptr;
         cudaGraphExec_t x = nullptr;
         hwfv1_status r = HWFV1_OK;
@@ -719,6 +720,29 @@ class EngineT final : public Engine {
     int wet_grid() const {
         const uint64_t g = (N_ + 63) / 64, cap = (uint64_t)nsm_ * 16;
         return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+    }
+    // Blocks of `threads` that one launch of kern keeps resident on the GPU.
+    // A grid-stride loop over more blocks than that runs its last ones as a
+    // second wave after the first, each with its full share of the work:
+    // such grids are capped here.
+    template <typename K>
+    int resident(K kern, int threads) {
+        const void* key = reinterpret_cast<const void*>(kern);
+        auto it = occ_.find(key);
+        if (it != occ_.end()) return it->second;
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            per = 0;
+        }
+        const int r = nsm_ * (per < 1 ? 1 : per);
+        occ_[key] = r;
+        return r;
+    }
+    template <typename K>
+    int grid_res(K kern, int g, int threads) {
+        const int r = resident(kern, threads);
+        return g < r ? g : r;
     }
     int grid_for(uint64_t n) const {
         uint64_t g = (n + 255) / 256;
@@ -939,7 +963,7 @@ class EngineT final : public Engine {
             a.leaves = leaves;
             a.fm = 0;            // every leaf on the finest level: nothing to match
         }
-        lk(k_fv1_dry<T>, grid_for(N_), 256, a);
+        lk(k_fv1_dry<T>, grid_res(k_fv1_dry<T>, grid_for(N_), 256), 256, a);
         mark("k_fv1_dry");
         launch_wet(a);
     }
@@ -948,23 +972,23 @@ class EngineT final : public Engine {
         if (a.fm && face_) {
             // matched fluxes with shared faces: a face toward a refined
             // neighbour takes the walk over its halves in either phase
-            lk(k_fv1_faces<T, true>, wet_grid(), 64, a);
+            lk(k_fv1_faces<T, true>, grid_res(k_fv1_faces<T, true>, wet_grid(), 64), 64, a);
             mark("k_fv1_faces");
-            lk(k_fv1_update<T, true>, wet_grid(), 64, a);
+            lk(k_fv1_update<T, true>, grid_res(k_fv1_update<T, true>, wet_grid(), 64), 64, a);
             mark("k_fv1_update");
         } else if (a.fm) {
-            lk(k_fv1_match<T>, wet_grid(), 64, a);
+            lk(k_fv1_match<T>, grid_res(k_fv1_match<T>, wet_grid(), 64), 64, a);
             mark("k_fv1_match");
         } else if (face_) {
             // 64-thread blocks: a short queue spreads over every SM's FP64 units
             // (one warp-wide FP64 instruction holds a sub-partition's unit for
             // tens of cycles, so few warps per unit means a shorter chain)
-            lk(k_fv1_faces<T>, wet_grid(), 64, a);
+            lk(k_fv1_faces<T>, grid_res(k_fv1_faces<T>, wet_grid(), 64), 64, a);
             mark("k_fv1_faces");
-            lk(k_fv1_update<T>, wet_grid(), 64, a);
+            lk(k_fv1_update<T>, grid_res(k_fv1_update<T>, wet_grid(), 64), 64, a);
             mark("k_fv1_update");
         } else {
-            lk(k_fv1_wet<T>, wet_grid(), 64, a);
+            lk(k_fv1_wet<T>, grid_res(k_fv1_wet<T>, wet_grid(), 64), 64, a);
             mark("k_fv1_wet");
         }
     }
@@ -986,7 +1010,7 @@ class EngineT final : public Engine {
         // the decode list is short once quiescent tiles are skipped: 2 CTAs per SM
         const int gd = quiet_on_ ? std::min(grid_for((uint64_t)ntiles_ * 256), nsm_ * 4)
                                  : grid_for((uint64_t)ntiles_ * 256);
-        lk(k_decode_finish<T>, gd, 256, decode_args(onfly), fin_args());
+        lk(k_decode_finish<T>, grid_res(k_decode_finish<T>, gd, 256), 256, decode_args(onfly), fin_args());
         mark("k_decode_finish");
     }
     void launch_step_uniform() {
@@ -1042,7 +1066,7 @@ class EngineT final : public Engine {
         a.L = L_;
         a.Ls = L_ - 4;
         a.mode = mode;
-        lk(k_skip_finest<T>, skip_grid(), 256, a);
+        lk(k_skip_finest<T>, grid_res(k_skip_finest<T>, skip_grid(), 256), 256, a);
         mark("k_skip_finest");
     }
     int skip_grid() const {
@@ -1083,7 +1107,7 @@ class EngineT final : public Engine {
         a.tol = (T)spec_.tol_h;
         a.L = L_;
         a.Ls = Ls;
-        lk(k_skip_encode<T>, grid_for((uint64_t)(1u << (2 * Ls)) * 32), 256, a);
+        lk(k_skip_encode<T>, grid_res(k_skip_encode<T>, grid_for((uint64_t)(1u << (2 * Ls)) * 32), 256), 256, a);
         mark("k_skip_encode");
         if (Ls > 0) {
             EncodeArgs<T, 3> e;
@@ -1111,7 +1135,7 @@ class EngineT final : public Engine {
         mark("k_trav_fused");
         StepArgs<T> sa = step_args();
         sa.own_slot = 1;
-        lk(k_fv1_dry<T>, grid_for(N_), 256, sa);
+        lk(k_fv1_dry<T>, grid_res(k_fv1_dry<T>, grid_for(N_), 256), 256, sa);
         mark("k_fv1_dry");
         launch_wet(sa);
         if (predict_now) join_predict();
@@ -1127,7 +1151,7 @@ class EngineT final : public Engine {
         d.tol = (T)spec_.tol_h;
         d.L = L_;
         d.Ls = Ls;
-        lk(k_skip_decode<T>, skip_grid(), 256, d, fin_args());
+        lk(k_skip_decode<T>, grid_res(k_skip_decode<T>, skip_grid(), 256), 256, d, fin_args());
         mark("k_skip_decode");
         sb_valid_ = true;
     }
@@ -1336,6 +1360,7 @@ class EngineT final : public Engine {
     uint8_t* tilebytes_ = nullptr;      // per tile: zf of buffer 0, zf of buffer 1, inlet, act
     bool batched_ = false;
     T* face_ = nullptr;                 // shared faces (10 x fcap_)
+    std::unordered_map<const void*, int> occ_;   // resident blocks per kernel
     uint32_t fcap_ = 0;
     unsigned long long* mark_ = nullptr;   // per hierarchy cell: (epoch + 1) << 32 | queue slot
     uint32_t* scount_ = nullptr;        // per tile: leaves when it holds the bed's flags alone

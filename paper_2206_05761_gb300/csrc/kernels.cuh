@@ -401,6 +401,35 @@ __device__ __forceinline__ T* quantity_ptr(const EncodeArgs<T, NF>& a, int par, 
 __device__ __forceinline__ bool pos_zero(double x) { return dbits(x) == 0ll; }
 __device__ __forceinline__ bool pos_zero(float x) { return __float_as_int(x) == 0; }
 
+// R-decode's free surface and finest depths with the FP64 work a flat bed
+// does not need: x + (+0) = x for x != -0 and x - (+0) = x for every x are
+// exact, and four beds of one bit pattern give four equal differences.
+// eta_of: hl + zl for a wet leaf (hl >= tol > 0).
+template <typename T>
+__device__ __forceinline__ T eta_of(T hl, T zl) { return pos_zero(zl) ? hl : hl + zl; }
+__device__ __forceinline__ bool bits_eq4(double a, double b, double c, double d) {
+    const long long x = dbits(a);
+    return x == dbits(b) && x == dbits(c) && x == dbits(d);
+}
+__device__ __forceinline__ bool bits_eq4(float a, float b, float c, float d) {
+    const int x = __float_as_int(a);
+    return x == __float_as_int(b) && x == __float_as_int(c) && x == __float_as_int(d);
+}
+// hf[k] = max(0, eta - z_k) as (eta - z_k > 0 ? eta - z_k : 0)
+template <typename T>
+__device__ __forceinline__ void restore4(T eta, T z0, T z1, T z2, T z3, T (&hf)[4]) {
+    if (bits_eq4(z0, z1, z2, z3)) {
+        const T d = pos_zero(z0) ? eta : eta - z0;
+        hf[0] = hf[1] = hf[2] = hf[3] = gt_zero(d) ? d : T(0);
+        return;
+    }
+    const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
+    hf[0] = gt_zero(d0) ? d0 : T(0);
+    hf[1] = gt_zero(d1) ? d1 : T(0);
+    hf[2] = gt_zero(d2) ? d2 : T(0);
+    hf[3] = gt_zero(d3) ? d3 : T(0);
+}
+
 // One CTA encodes one tile: the 4^k cells of level ls under one level-(ls-k)
 // cell, k <= 5 levels in one pass.  The first level reads four children
 // per thread with 128-bit loads; the next levels work from shared memory.
@@ -1335,8 +1364,11 @@ template <typename T>
 __device__ __forceinline__ void hll_face(T g, T hg, T tol, T hL, T zL, T unL, T utL, T hR, T zR, T unR,
                                          T utR, T F[3], T& hLs_o, T& hRs_o) {
     const T zf = sel_max(zR, zL);                       // zL > zR ? zL : zR
-    const T dL = (hL + zL) - zf;
-    const T dR = (hR + zR) - zf;
+    // on a +0 bed both sides are exact: (h + 0) - 0 = h for h != -0, and a
+    // -0 depth gives +0 where the shortcut gives -0, both below tol
+    const bool bed0 = pos_zero(zL) && pos_zero(zR);
+    const T dL = bed0 ? hL : (hL + zL) - zf;
+    const T dR = bed0 ? hR : (hR + zR) - zf;
     const T hLs = ge_nonneg(dL, tol) ? dL : T(0);        // tol > 0
     const T hRs = ge_nonneg(dR, tol) ? dR : T(0);
     hLs_o = hLs;
@@ -1711,17 +1743,13 @@ __device__ __forceinline__ void wet_leaf_store(const StepArgs<T>& a, DevState* s
         const uint32_t cnt = 1u << (2 * (a.L - n));
         const T hl = out[0];
         const bool restore = ge_nonneg(hl, a.P.tol);
-        const T eta = restore ? hl + C.z : T(0);
+        const T eta = restore ? eta_of(hl, C.z) : T(0);
         for (uint32_t e = 0; e < cnt; e += 4) {
             T hf[4];
             if (restore) {
                 T z0, z1, z2, z3;
                 Vec4<T>::load(z + fo + e, z0, z1, z2, z3);
-                const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
-                hf[0] = gt_zero(d0) ? d0 : T(0);
-                hf[1] = gt_zero(d1) ? d1 : T(0);
-                hf[2] = gt_zero(d2) ? d2 : T(0);
-                hf[3] = gt_zero(d3) ? d3 : T(0);
+                restore4(eta, z0, z1, z2, z3, hf);
             } else {
                 hf[0] = hf[1] = hf[2] = hf[3] = hl;
             }
@@ -2246,14 +2274,10 @@ __device__ __forceinline__ void decode_body(const DecodeArgs<T>& a, Blk B) {
         const uint64_t fo = lvl_off(a.L) + m0;
         T hf[4];
         if (restore) {
-            const T eta = hl + __ldg(a.z + slot);
+            const T eta = eta_of(hl, __ldg(a.z + slot));
             T z0, z1, z2, z3;
             Vec4<T>::load(a.z + fo, z0, z1, z2, z3);
-            const T d0 = eta - z0, d1 = eta - z1, d2 = eta - z2, d3 = eta - z3;
-            hf[0] = gt_zero(d0) ? d0 : T(0);
-            hf[1] = gt_zero(d1) ? d1 : T(0);
-            hf[2] = gt_zero(d2) ? d2 : T(0);
-            hf[3] = gt_zero(d3) ? d3 : T(0);
+            restore4(eta, z0, z1, z2, z3, hf);
         } else {
             hf[0] = hf[1] = hf[2] = hf[3] = hl;
         }

@@ -49,8 +49,8 @@ __device__ __forceinline__ int skip_store_level(const uint8_t* __restrict__ phat
 template <typename T>
 __device__ __forceinline__ T redecode_h(T hl, T zl, T zc, T tol) {
     if (!ge_nonneg(hl, tol)) return hl;
-    const T eta = hl + zl;
-    const T d = eta - zc;
+    const T eta = eta_of(hl, zl);                    // hl + zl (exact shortcuts on a +0 bed)
+    const T d = pos_zero(zc) ? eta : eta - zc;
     return gt_zero(d) ? d : T(0);
 }
 
