@@ -370,7 +370,9 @@ hwfv1_status hwfv1_batch_advance(hwfv1_batch* b, double t_end, int64_t max_steps
 
 /* Time trial_steps ensemble steps under each candidate launch configuration
  * (encode levels per pass in {5,4,3}, finest cells per FV1 thread in
- * {8,32,128,512}) and keep the fastest; choice (host, 2 int32, may be NULL)
+ * {8,32,128,512}; with 5, the first pass of a member of L >= 8 covers
+ * 1024-cell blocks but stops three levels up) and keep the fastest; choice
+ * (host, 2 int32, may be NULL)
  * receives it.  All candidates give bit-identical results; the trials
  * advance the ensemble by 12 x (trial_steps + 1) steps.  Synchronises. */
 hwfv1_status hwfv1_batch_autotune(hwfv1_batch* b, int64_t trial_steps, int32_t* choice);

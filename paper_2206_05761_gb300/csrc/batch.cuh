@@ -284,7 +284,8 @@ class BatchT final : public Batch {
             auto set = [&](int kind, uint32_t n) { nb[(size_t)kind * D + d] = n; };
             set(BK_CLEAR, std::min<uint32_t>(64u, (p.clear_n + 255u) / 256u));
             for (int q = 0; q < kMaxPasses; ++q)
-                set(BK_ENC0 + q, q < p.npass ? (1u << (2 * (p.ls[q] - p.kk[q]))) : 0u);
+                set(BK_ENC0 + q, q < p.npass ? (1u << (2 * (p.ls[q] - ((q == 0 && p.enc.span) ? p.enc.span
+                                                                                          : p.kk[q])))) : 0u);
             set(BK_FLAG, std::min<uint32_t>(64u, (bits_words(p.L) + 255u) / 256u));
             set(BK_TCOUNT, p.nct);
             set(BK_TSCAN, 1u);

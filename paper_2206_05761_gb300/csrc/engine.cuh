@@ -682,8 +682,16 @@ class EngineT final : public Engine {
         p.enc.ls = L_;
         p.enc.k = enc_k;
         p.npass = 0;
+        p.enc.span = 0;
         for (int ls = L_; ls > 0 && p.npass < (int)(sizeof(p.ls) / sizeof(p.ls[0]));) {
-            const int k = ls < enc_k ? ls : enc_k;
+            int k = ls < enc_k ? ls : enc_k;
+            // with 5 levels per pass, the first pass of a domain of L >= 8
+            // stops after three levels of each 1024-cell block, as the
+            // single-domain full sweep does (a shorter chain per CTA)
+            if (ls == L_ && enc_k == 5 && ls >= 8) {
+                k = 3;
+                p.enc.span = 5;
+            }
             p.ls[p.npass] = ls;
             p.kk[p.npass] = k;
             p.npass++;
