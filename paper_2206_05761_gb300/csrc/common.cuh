@@ -38,9 +38,11 @@ constexpr int kLeafShift = 28;              // packed leaf: level << 28 | code
 constexpr uint32_t kCodeMask = (1u << kLeafShift) - 1u;
 
 // element offset of level n in a hierarchy array
+// (32-bit arithmetic: 4^n < 2^32 for n <= 15 = kMaxL + 1, and a 32-bit
+// division by a constant is two instructions where the 64-bit one is a chain)
 __host__ __device__ inline uint64_t lvl_off(int n) {
     if (n <= 3) return 64ull * (uint64_t)n;
-    return 192ull + (((1ull << (2 * n)) - 64ull) / 3ull);
+    return (uint64_t)(192u + (((1u << (2 * n)) - 64u) / 3u));
 }
 // element count of a hierarchy with levels 0..L
 __host__ __device__ inline uint64_t hier_size(int L) { return lvl_off(L + 1); }
@@ -48,7 +50,7 @@ __host__ __device__ inline uint64_t hier_size(int L) { return lvl_off(L + 1); }
 // word offset of level n in a significance bit array
 __host__ __device__ inline uint32_t word_off(int n) {
     if (n <= 3) return (uint32_t)n;
-    return 3u + (uint32_t)(((1ull << (2 * n)) - 64ull) / 96ull);
+    return 3u + (((1u << (2 * n)) - 64u) / 96u);
 }
 __host__ __device__ inline uint32_t bits_words(int L) { return word_off(L); }
 
