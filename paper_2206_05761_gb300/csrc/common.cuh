@@ -231,6 +231,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
 struct DevState {
     double t, dt, dt_use, t_end;
     double Qdt;                       // Q(t) * dt_use of the current step
+    double fric_k;                    // ((dt_use * g) * n) * n: the friction term's step factor
+    float fric_kf;                    // the same in float arithmetic (float32 path)
     double smax[4];                   // s_max of h, qx, qy, z
     unsigned long long rmin_bits;     // min CFL bound over updated leaves
     unsigned long long speed_bits[3]; // max |u|+sqrt(gh), |v|+sqrt(gh) over updated wet leaves

@@ -1302,6 +1302,8 @@ class EngineT final : public Engine {
         a.dt_max = spec_.dt_max;
         a.lx = spec_.lx;
         a.ly = spec_.ly;
+        a.g = spec_.g;
+        a.manning_n = spec_.manning_n;
         return a;
     }
     // s_max (and dt when set_dt) from the finest fields of the current buffer

@@ -1410,14 +1410,14 @@ __device__ __forceinline__ void hll_face(T g, T hg, T tol, T hL, T zL, T unL, T 
 }
 
 template <typename T>
-__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T fk, const Cell<T>& C,
                                                   const T FW[3], const T FE[3], const T GS[3], const T GN[3],
                                                   T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3],
                                                   T* rh_out = nullptr);
 
 // New (h, qx, qy) of a cell of size dx x dy: rx = dt/dx, ry = dt/dy.
 template <typename T>
-__device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+__device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T fk, const Cell<T>& C,
                                             const Cell<T>& W, const Cell<T>& E, const Cell<T>& S,
                                             const Cell<T>& N, bool inlet, T dh, T out[3]) {
     const T g = P.g, hg = P.hg, tol = P.tol;
@@ -1441,20 +1441,56 @@ __device__ __forceinline__ void cell_update(const Phys<T>& P, T rx, T ry, T dt, 
         hll_face(g, hg, tol, S.h, S.z, vS, uS, C.h, C.z, vC, uC, GS, dummy, hS_R);
         hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hN_L, dummy);
     }
-    cell_update_faces(P, rx, ry, dt, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out);
+    cell_update_faces(P, rx, ry, fk, C, FW, FE, GS, GN, hW_R, hE_L, hS_R, hN_L, inlet, dh, out);
 }
+
+// The friction term's per-step factor ((dt * g) * n) * n (formed once per
+// step by the finish, in the arithmetic of T).
+template <typename T> __device__ __forceinline__ T fric_k_of(const DevState* st);
+template <> __device__ __forceinline__ double fric_k_of<double>(const DevState* st) { return st->fric_k; }
+template <> __device__ __forceinline__ float fric_k_of<float>(const DevState* st) { return st->fric_kf; }
+
+// h^(-1/3) of a double h whose float truncation is a normal number: the
+// float inverse cube root as the seed, then one Newton step for
+// f(r) = r^-3 - h, r <- r + r (1 - h r^3) / 3, which squares the seed's
+// relative error (below 2^-21) up to a factor 2: about 2^-41 in all, where
+// the double cube root and a division cost some 20 FP64 additions' worth of
+// the FP64 pipe.  Not correctly rounded; the friction term is the one use.
+__device__ __forceinline__ double rcbrt_newton(float hf, double h) {
+    const float rf = rcbrtf(hf);
+    // the float widened to a double by integer operations (exact)
+    const uint32_t b = (uint32_t)__float_as_int(rf);
+    const long long e = (long long)((b >> 23) & 0xFFu) - 127 + 1023;
+    const double r = dval((e << 52) | ((long long)(b & 0x7FFFFFu) << 29));
+    const double r3 = (r * r) * r;
+    const double d = __fma_rn(-h, r3, 1.0);
+    return __fma_rn(r * d, 1.0 / 3.0, r);
+}
+
+// x / (h cbrt(h)) = x h^(-4/3) of Manning's friction term for a wet cell
+// (h >= tol > 0, rh = 1/h).  float64: x (1/h) h^(-1/3) with the Newton
+// inverse cube root, within some 2^-40 relative of the quotient as written
+// (the friction factor 1 + this term then within 2^-40 (D - 1)/D); outside
+// the float range the quotient as written.  float32: the quotient as written.
+__device__ __forceinline__ double friction_term(double x, double h, double rh) {
+    const float hf = trunc_float(h);
+    const uint32_t eb = ((uint32_t)__float_as_int(hf) >> 23) & 0xFFu;
+    if (eb != 0u && eb != 0xFFu) return (x * rh) * rcbrt_newton(hf, h);
+    return x / (h * cbrt(h));
+}
+__device__ __forceinline__ float friction_term(float x, float h, float /*rh*/) { return x / (h * cbrtf(h)); }
 
 // The update from the four face fluxes and the squares of the cell's own
 // reconstructed depths at them (hW2, hE2, hS2, hN2: the bed source term's
 // face values).  rh_out (if given) receives 1/h of the new depth when the
 // friction step formed it, else 0.
 template <typename T>
-__device__ __forceinline__ void cell_update_faces_sq(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+__device__ __forceinline__ void cell_update_faces_sq(const Phys<T>& P, T rx, T ry, T fk, const Cell<T>& C,
                                                      const T FW[3], const T FE[3], const T GS[3], const T GN[3],
                                                      T hW2, T hE2, T hS2, T hN2, bool inlet, T dh, T out[3],
                                                      T* rh_out = nullptr) {
     if (rh_out) *rh_out = T(0);
-    const T g = P.g, hg = P.hg, tol = P.tol;
+    const T hg = P.hg, tol = P.tol;
     const T bx = hg * (hW2 - hE2);
     const T by = hg * (hS2 - hN2);
     T h = C.h - rx * (FE[0] - FW[0]) - ry * (GN[0] - GS[0]);
@@ -1470,8 +1506,7 @@ __device__ __forceinline__ void cell_update_faces_sq(const Phys<T>& P, T rx, T r
         if (rh_out) *rh_out = rh;
         const T u = qx * rh, v = qy * rh;
         const T speed = sqrt(u * u + v * v);
-        const T nM = P.nM;
-        const T D = T(1) + dt * g * nM * nM * speed / (h * cbrt(h));
+        const T D = T(1) + friction_term(fk * speed, h, rh);
         const T rD = T(1) / D;
         qx = qx * rD;
         qy = qy * rD;
@@ -1484,11 +1519,11 @@ __device__ __forceinline__ void cell_update_faces_sq(const Phys<T>& P, T rx, T r
 // The update of cell_update from its four face fluxes and its own
 // reconstructed depths at them (hW_R, hE_L, hS_R, hN_L).
 template <typename T>
-__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T dt, const Cell<T>& C,
+__device__ __forceinline__ void cell_update_faces(const Phys<T>& P, T rx, T ry, T fk, const Cell<T>& C,
                                                   const T FW[3], const T FE[3], const T GS[3], const T GN[3],
                                                   T hW_R, T hE_L, T hS_R, T hN_L, bool inlet, T dh, T out[3],
                                                   T* rh_out) {
-    cell_update_faces_sq(P, rx, ry, dt, C, FW, FE, GS, GN, hW_R * hW_R, hE_L * hE_L, hS_R * hS_R, hN_L * hN_L,
+    cell_update_faces_sq(P, rx, ry, fk, C, FW, FE, GS, GN, hW_R * hW_R, hE_L * hE_L, hS_R * hS_R, hN_L * hN_L,
                          inlet, dh, out, rh_out);
 }
 
@@ -1780,7 +1815,7 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
     const uint32_t nq = st->nwet;
     if (B.id * blockDim.x >= nq) return;          // whole block idle
     const int par = (int)st->cur, nxt = par ^ 1;
-    const T dt = (T)st->dt_use;
+    const T fk = fric_k_of<T>(st);
     const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
     const T Qdt = (T)st->Qdt;
     CellSrc<T> src;
@@ -1817,7 +1852,7 @@ __device__ __forceinline__ void fv1_wet_body(const StepArgs<T>& a, Blk B) {
             dh = (Qdt * frac) / (dxn * dyn);
         }
         T out[3];
-        cell_update(a.P, rx, ry, dt, C, W, E, S, N, inlet, dh, out);
+        cell_update(a.P, rx, ry, fk, C, W, E, S, N, inlet, dh, out);
         wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
@@ -1949,7 +1984,7 @@ __device__ __forceinline__ void fv1_match_body(const StepArgs<T>& a, Blk B) {
     const uint32_t nq = st->nwet;
     if (B.id * blockDim.x >= nq) return;          // whole block idle
     const int par = (int)st->cur, nxt = par ^ 1;
-    const T dt = (T)st->dt_use;
+    const T fk = fric_k_of<T>(st);
     const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
     const T Qdt = (T)st->Qdt;
     CellSrc<T> src;
@@ -1986,7 +2021,7 @@ __device__ __forceinline__ void fv1_match_body(const StepArgs<T>& a, Blk B) {
             dh = (Qdt * frac) / (dxn * dyn);
         }
         T out[3], rh;
-        cell_update_faces_sq(a.P, rx, ry, dt, C, FW, FE, GS, GN, w2, e2, s2, n2, inlet, dh, out, &rh);
+        cell_update_faces_sq(a.P, rx, ry, fk, C, FW, FE, GS, GN, w2, e2, s2, n2, inlet, dh, out, &rh);
         wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd, rh);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
@@ -2092,7 +2127,7 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
     }
     if (B.id * blockDim.x >= nq) return;          // whole block idle
     const int par = (int)st->cur, nxt = par ^ 1;
-    const T dt = (T)st->dt_use;
+    const T fk = fric_k_of<T>(st);
     const T rx0 = rx0_of<T>(st), ry0 = ry0_of<T>(st);
     const T Qdt = (T)st->Qdt;
     CellSrc<T> src;
@@ -2188,7 +2223,7 @@ __device__ __forceinline__ void fv1_update_body(const StepArgs<T>& a, Blk B) {
             dh = (Qdt * frac) / (dxn * dyn);
         }
         T out[3], rh;
-        cell_update_faces_sq(a.P, rx, ry, dt, C, FW, FE, GS, GN, hW2, hE2, hS2, hN2, inlet, dh, out, &rh);
+        cell_update_faces_sq(a.P, rx, ry, fk, C, FW, FE, GS, GN, hW2, hE2, hS2, hN2, inlet, dh, out, &rh);
         wet_leaf_store(a, st, src.z, oh, oqx, oqy, n, code, iC, C, out, rmin, mh, mqx, mqy, spd, rh);
     }
     block_atomic_u64<false>(rmin, &st->rmin_bits);
@@ -2309,6 +2344,7 @@ struct FinishArgs {
     int inflow_n;
     int L;
     double eps, cfl, dt_max, lx, ly;
+    double g, manning_n;
 };
 
 __device__ inline double inflow_Q(const FinishArgs& a, double t) {
@@ -2362,6 +2398,10 @@ __device__ inline void prepare_vals(DevState* st, const FinishArgs& a, double t,
             st->rmin_bits = kInfBits;
             st->max_bits[0] = st->max_bits[1] = st->max_bits[2] = 0ull;
             st->speed_bits[0] = st->speed_bits[1] = st->speed_bits[2] = 0ull;
+            // the friction term's product with dt, in the operation order of
+            // dt * g * n * n * |u| (the leaf's part follows in the update)
+            st->fric_k = ((dt_use * a.g) * a.manning_n) * a.manning_n;
+            st->fric_kf = (((float)dt_use * (float)a.g) * (float)a.manning_n) * (float)a.manning_n;
         } else if (task == 1) {
             st->rx0 = dt_use / a.lx;            // dt/dx_n = (dt/lx) * 2^n exactly
         } else if (task == 2) {
