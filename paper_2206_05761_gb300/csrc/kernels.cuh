@@ -2491,14 +2491,22 @@ __device__ __forceinline__ void finish_body(DevState* st, const FinishArgs& a) {
 // Decode-back followed, in its last CTA to finish, by the time advance (one
 // launch instead of two).  decode_body reads the state through L2 only, so
 // the last CTA sees every other CTA's reductions after the fence.
+//
+// Only the first min(ndec, grid) CTAs (at least one) take part: the others
+// have no tile to decode (decode_body strides over the list by the grid)
+// and leave at once, so a short decode list costs few fences and ticket
+// atomics.  ndec is fixed from the traversal to the next step's clear.
 template <typename T>
 static __global__ void __launch_bounds__(256) k_decode_finish(DecodeArgs<T> a, FinishArgs fa) {
     pdl_wait();
+    const uint32_t nd = __ldcg(&a.st->ndec);
+    const uint32_t parts = nd < gridDim.x ? (nd > 0u ? nd : 1u) : gridDim.x;
+    if (blockIdx.x >= parts) return;
     decode_body<T>(a, this_blk());
     __threadfence();
     __syncthreads();
     __shared__ bool last;
-    if (threadIdx.x == 0) last = atomicAdd(&a.st->dec_ticket, 1u) == gridDim.x - 1u;
+    if (threadIdx.x == 0) last = atomicAdd(&a.st->dec_ticket, 1u) == parts - 1u;
     __syncthreads();
     if (!last) return;
     __threadfence();
