@@ -86,12 +86,13 @@ class EngineT final : public Engine {
         if (!alloc(&counts_, (size_t)ntiles_ * 3 * sizeof(uint32_t))) return oom();
         offs_ = counts_ + ntiles_;
         dlist_ = counts_ + 2 * ntiles_;
-        // shared faces of the wet-leaf update: 10 values per queued leaf, a
-        // stamp per hierarchy cell.  Float64 only: in float32 the arithmetic
-        // saved costs less than the extra launch and face traffic.
+        // shared faces of the wet-leaf update: 10 values per queued leaf and
+        // its two velocities, a stamp per hierarchy cell.  Float64 only: in
+        // float32 the arithmetic saved costs less than the extra launch and
+        // face traffic.
         if (sizeof(T) == 8) {
             fcap_ = (uint32_t)std::min<uint64_t>(N_, 1ull << 22);
-            if (!alloc(&face_, (size_t)fcap_ * 10 * sizeof(T))) return oom();
+            if (!alloc(&face_, (size_t)fcap_ * 12 * sizeof(T))) return oom();
             if (!alloc(&mark_, H_ * sizeof(unsigned long long))) return oom();
             cudaMemsetAsync(mark_, 0, H_ * sizeof(unsigned long long), stream_);
         }
@@ -1369,7 +1370,7 @@ class EngineT final : public Engine {
     uint32_t *counts_ = nullptr, *offs_ = nullptr, *dlist_ = nullptr;
     uint8_t* tilebytes_ = nullptr;      // per tile: zf of buffer 0, zf of buffer 1, inlet, act
     bool batched_ = false;
-    T* face_ = nullptr;                 // shared faces (10 x fcap_)
+    T* face_ = nullptr;                 // shared faces and velocities (12 x fcap_)
     std::unordered_map<const void*, int> occ_;   // resident blocks per kernel
     uint32_t fcap_ = 0;
     unsigned long long* mark_ = nullptr;   // per hierarchy cell: (epoch + 1) << 32 | queue slot

@@ -1551,8 +1551,9 @@ struct StepArgs {
     int bc_ref[4];           // 1: the side reflects (closed or inflow)
     int inflow_side;         // -1: none
     int a0, a1;
-    // shared faces (k_fv1_faces / k_fv1_update): 10 arrays of fcap values
-    // (east face F0..F2, h*_L, h*_R, then the north face's), and a stamp per
+    // shared faces (k_fv1_faces / k_fv1_update): 12 arrays of fcap values
+    // (east face F0..F2, h*_L, h*_R, then the north face's, then the
+    // leaf's velocities u, v, written by k_fv1_dry), and a stamp per
     // hierarchy cell ((epoch + 1) << 32 | queue slot)
     T* face = nullptr;
     uint32_t fcap = 0;
@@ -1669,7 +1670,8 @@ __device__ __forceinline__ bool dry5(const T* __restrict__ h, const DryProbe& d)
 // iteration, so many independent loads are in flight.
 template <typename T>
 __device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T* oh, T* oqx, T* oqy,
-                                           const DryProbe& d, bool dry, uint32_t pk) {
+                                           const DryProbe& d, bool dry, uint32_t pk, const CellSrc<T>& src,
+                                           unsigned long long stamp) {
     if (dry && a.inflow_side >= 0) {
         int64_t lo, hi;
         dry = !inlet_range(a, d.n, compact16(d.code), compact16(d.code >> 1), (1u << d.n) - 1u, lo, hi);
@@ -1696,7 +1698,23 @@ __device__ __forceinline__ void dry_finish(const StepArgs<T>& a, DevState* st, T
         uint32_t base_pos = 0;
         if (lane == leader) base_pos = atomicAdd(&st->nwet, (uint32_t)__popc(m));
         base_pos = __shfl_sync(m, base_pos, leader);
-        a.wet[base_pos + __popc(m & ((1u << lane) - 1u))] = pk;   // the packed leaf
+        const uint32_t w = base_pos + __popc(m & ((1u << lane) - 1u));
+        a.wet[w] = pk;                                            // the packed leaf
+        // float64 with shared faces: the leaf's velocities (the operations
+        // of velocity() in k_fv1_faces, which reads them here instead of
+        // forming them for the leaf and for the two neighbours whose west
+        // and south faces it is) and its stamp, once per queued leaf
+        if (sizeof(T) == 8 && a.face != nullptr && !a.fm && w < a.fcap) {
+            Cell<T> C;
+            C.h = __ldg(src.h + d.iC);
+            C.qx = __ldg(src.qx + d.iC);
+            C.qy = __ldg(src.qy + d.iC);
+            T u, v;
+            velocity(C, a.P.tol, u, v);
+            a.face[10 * (size_t)a.fcap + w] = u;
+            a.face[11 * (size_t)a.fcap + w] = v;
+            a.mark[d.iC] = stamp | w;
+        }
     }
 }
 
@@ -1707,6 +1725,12 @@ __device__ __forceinline__ void fv1_dry_body(const StepArgs<T>& a, Blk B) {
     const int par = (int)st->cur, nxt = par ^ 1;
     const uint32_t M = st->M;
     const T* __restrict__ hsrc = par ? a.f[1][0] : a.f[0][0];
+    CellSrc<T> src;
+    src.h = hsrc;
+    src.qx = par ? a.f[1][1] : a.f[0][1];
+    src.qy = par ? a.f[1][2] : a.f[0][2];
+    src.z = a.z;
+    const unsigned long long stamp = (unsigned long long)(st->epoch + 1u) << 32;
     T* const oh = nxt ? a.f[1][0] : a.f[0][0];
     T* const oqx = nxt ? a.f[1][1] : a.f[0][1];
     T* const oqy = nxt ? a.f[1][2] : a.f[0][2];
@@ -1725,8 +1749,8 @@ __device__ __forceinline__ void fv1_dry_body(const StepArgs<T>& a, Blk B) {
             y1 = y1 && !refined_nbr(a.Sb, d1, a.L);
             y2 = y2 && !refined_nbr(a.Sb, d2, a.L);
         }
-        dry_finish(a, st, oh, oqx, oqy, d1, y1, p1);
-        if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, p2);
+        dry_finish(a, st, oh, oqx, oqy, d1, y1, p1, src, stamp);
+        if (two) dry_finish(a, st, oh, oqx, oqy, d2, y2, p2, src, stamp);
     }
 }
 template <typename T>
@@ -2040,6 +2064,19 @@ static __global__ void __launch_bounds__(256) k_fv1_match(StepArgs<T> a) {
 // queued leaf whose west (south) same-level neighbour carries this step's
 // stamp takes that neighbour's east (north) face -- the same call with the
 // same operands, so the same bits -- and computes only its other faces.
+// The velocities k_fv1_dry formed for the queued leaf at hierarchy index
+// idx, if that cell holds one this step (its stamp is this step's).
+template <typename T>
+__device__ __forceinline__ bool queued_velocity(const StepArgs<T>& a, unsigned long long stamp, uint64_t idx,
+                                                T& u, T& v) {
+    const unsigned long long m = __ldg(a.mark + idx);
+    if ((m >> 32) != (stamp >> 32)) return false;
+    const uint32_t wn = (uint32_t)m;
+    u = a.face[10 * (size_t)a.fcap + wn];
+    v = a.face[11 * (size_t)a.fcap + wn];
+    return true;
+}
+
 template <typename T, bool FM = false>
 __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
     DevState* st = a.st;
@@ -2077,16 +2114,26 @@ __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
             const Cell<T> E = i < last ? fetch(src, base + morton2(i + 1, j)) : ghost(C, a.bc_ref[1], true);
             const Cell<T> N = j < last ? fetch(src, base + morton2(i, j + 1)) : ghost(C, a.bc_ref[3], false);
             T uC, vC, uE, vE, uN, vN;
-            velocity(C, tol, uC, vC);
+            // velocities formed by k_fv1_dry for every queued leaf (the
+            // leaf's own, and a same-level neighbour's when it is queued:
+            // its stamp is this step's), else formed here
+            if (!FM) {
+                uC = a.face[10 * (size_t)cap + w];
+                vC = a.face[11 * (size_t)cap + w];
+            } else {
+                velocity(C, tol, uC, vC);
+            }
             if (!mE) {
-                velocity(E, tol, uE, vE);
+                if (!(!FM && i < last && queued_velocity(a, stamp, base + morton2(i + 1, j), uE, vE)))
+                    velocity(E, tol, uE, vE);
                 T hEL, hER;
                 hll_face(g, hg, tol, C.h, C.z, uC, vC, E.h, E.z, uE, vE, FE, hEL, hER);
                 hEL2 = hEL * hEL;
                 hER2 = hER * hER;
             }
             if (!mN) {
-                velocity(N, tol, uN, vN);
+                if (!(!FM && j < last && queued_velocity(a, stamp, base + morton2(i, j + 1), uN, vN)))
+                    velocity(N, tol, uN, vN);
                 T hNL, hNR;
                 hll_face(g, hg, tol, C.h, C.z, vC, uC, N.h, N.z, vN, uN, GN, hNL, hNR);
                 hNL2 = hNL * hNL;
@@ -2106,7 +2153,7 @@ __device__ __forceinline__ void fv1_faces_body(const StepArgs<T>& a, Blk B) {
         f[7 * (size_t)cap] = GN[2];
         f[8 * (size_t)cap] = hNL2;
         f[9 * (size_t)cap] = hNR2;
-        a.mark[iC] = stamp | w;
+        if (FM) a.mark[iC] = stamp | w;      // (k_fv1_dry stamped the leaf otherwise)
     }
 }
 template <typename T, bool FM = false>
