@@ -717,7 +717,8 @@ def run_mra(args, label, p, state, t_s, dt_s, steps=100):
     - dry-leaf pass: per leaf its 4 B id and own depth read and its 24 B
       written (the neighbours' depths come from L2 and are not counted);
     - decode: the finest cells under the leaves of more than 16 cells
-      written (24 B each; the bed reads of wet leaves not counted)."""
+      written (24 B each), and the bed of those under wet leaves read (8 B
+      each, R-decode's free surface)."""
     import numpy as np
     import torch
     from paper_2206_05761_gb300 import hwfv1 as H
@@ -736,18 +737,27 @@ def run_mra(args, label, p, state, t_s, dt_s, steps=100):
     L, esz = p["L"], 8 if args.precision == 64 else 4
     N = 1 << (2 * L)
     P = (N - 1) // 3
-    lv = sim.leaves() >> 28
+    packed = sim.leaves()
+    lv = packed >> 28
     M = int(lv.size)
     big = lv[(L - lv.astype(np.int64)) >= 3]
     cells_big = int(np.sum(np.left_shift(np.ones(big.shape, dtype=np.int64), 2 * (L - big.astype(np.int64)))))
+    # finest cells under wet leaves of more than 16 cells: R-decode reads
+    # their bed (8 B each) to restore the free surface
+    cells_wet = 0
+    for n in np.unique(big):
+        codes = (packed[lv == n] & 0x0FFFFFFF).astype(np.int64)
+        hl = sim.level(0, int(n))[codes]
+        cells_wet += int(np.count_nonzero(hl >= p.get("tol_h", 1e-3))) << (2 * (L - int(n)))
     pk, src = peaks()
-    out = {"workload": label, "L": L, "leaves": M, "decode_cells": cells_big, "peak_gbs": pk["hbm_gbs"],
+    out = {"workload": label, "L": L, "leaves": M, "decode_cells": cells_big, "decode_cells_wet": cells_wet,
+           "peak_gbs": pk["hbm_gbs"],
            "peak_source": src, "kernels_ms": ph}
     enc_ms = ph.get("k_encode", 0.0) + ph.get("k_encode_tail", 0.0)
     parts = {"encode": (enc_ms, N * 3 * esz + P * (3 * esz + 2 / 8.0)),
              "traverse": (ph.get("k_trav_fused", 0.0), P / 8.0 + 4.0 * M),
              "dry": (ph.get("k_fv1_dry", 0.0), M * (4.0 + esz + 3 * esz)),
-             "decode": (ph.get("k_decode_finish", 0.0), cells_big * 3.0 * esz)}
+             "decode": (ph.get("k_decode_finish", 0.0), cells_big * 3.0 * esz + cells_wet * esz)}
     for name, (ms, b) in parts.items():
         if ms > 0:
             gbs = b / (ms / 1e3) / 1e9
