@@ -30,8 +30,14 @@
  *    on the device (non-finite values) are latched and returned by the next
  *    call that synchronises (hwfv1_get_time, hwfv1_advance with
  *    synchronisation, hwfv1_save); hwfv1_last_error gives a message.
- *  - Nothing here allocates memory outside hwfv1_init, and no call falls
- *    back to a CPU computation.
+ *  - hwfv1_init allocates the handle's buffers; the step, its phases, the
+ *    getters, hwfv1_save and hwfv1_load allocate nothing.  A mode's first
+ *    use allocates the buffers it adds, once per handle: uniform FV1
+ *    (hwfv1_advance_uniform), the learned skip (hwfv1_set_skipnet,
+ *    hwfv1_set_skip_levels) and the exact leaf-value store
+ *    (hwfv1_set_leaf_store).  hwfv1_batch_init and
+ *    the network calls (hwfv1_skipnet_*) allocate their own.  No call
+ *    falls back to a CPU computation.
  */
 #ifndef HWFV1_H
 #define HWFV1_H

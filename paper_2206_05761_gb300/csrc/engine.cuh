@@ -57,7 +57,11 @@ class EngineT final : public Engine {
         if (ev_fork_) cudaEventDestroy(ev_fork_);
         if (ev_join_) cudaEventDestroy(ev_join_);
         if (side_) cudaStreamDestroy(side_);
-        for (void* p : allocs_) cudaFree(p);
+        for (void* p : allocs_)
+            if (cudaFreeAsync(p, stream_) != cudaSuccess) {     // (a stream the caller destroyed)
+                cudaGetLastError();
+                cudaFree(p);
+            }
         if (own_stream_) cudaStreamDestroy(stream_);
     }
 
@@ -83,9 +87,12 @@ class EngineT final : public Engine {
         Sb_ = bits_ + 5 * words_;
         if (!alloc(&leaves_, N_ * sizeof(uint32_t))) return oom();
         if (!alloc(&wet_, N_ * sizeof(uint32_t))) return oom();
-        if (!alloc(&counts_, (size_t)ntiles_ * 3 * sizeof(uint32_t))) return oom();
+        // tile counters: counts and offsets of the ordered traversal, the
+        // decode list after them (one spare word: get_leaves keeps its
+        // 2 nct + 1 words below the decode list for every tile count)
+        if (!alloc(&counts_, ((size_t)ntiles_ * 3 + 1) * sizeof(uint32_t))) return oom();
         offs_ = counts_ + ntiles_;
-        dlist_ = counts_ + 2 * ntiles_;
+        dlist_ = counts_ + 2 * ntiles_ + 1;
         // shared faces of the wet-leaf update: 10 values per queued leaf and
         // its two velocities, a stamp per hierarchy cell.  Float64 only: in
         // float32 the arithmetic saved costs less than the extra launch and
@@ -119,6 +126,7 @@ class EngineT final : public Engine {
         }
         if (!alloc(&st_, sizeof(DevState))) return oom();
         if (!alloc(&zaux_, kZauxBytes)) return oom();
+        cudaMemsetAsync(zaux_, 0, kZauxBytes, stream_);      // zmax is a max-reduction target
         if (!it_.empty()) {
             if (!alloc(&it_d_, it_.size() * sizeof(double))) return oom();
             if (!alloc(&iq_d_, iq_.size() * sizeof(double))) return oom();
@@ -421,19 +429,16 @@ class EngineT final : public Engine {
             // the step's list is in Z-order within tiles only and leaves out
             // skipped tiles: list every leaf of the current flags into `out`
             // in Z-order (no state changes)
+            // per-CTA counts, offsets and the total in the first 2 nct + 1
+            // words of the handle's tile counters, below the decode list (the
+            // step needs none of them across calls)
             const uint32_t nct = (ntiles_ + kTilesPerCta - 1) / kTilesPerCta;
-            uint32_t* cnt = nullptr;
-            if (cudaMalloc(&cnt, ((size_t)2 * nct + 1) * sizeof(uint32_t)) != cudaSuccess) {
-                cudaGetLastError();
-                return oom();
-            }
+            uint32_t* cnt = counts_;
             ensure_sig_words();
             k_trav_count<<<nct, 256, 0, stream_>>>(Sb_, cnt, nullptr, L_, kt_, ntiles_, st_, nullptr, Quiet());
             k_trav_scan<<<1, 1024, 0, stream_>>>(cnt, cnt + nct, nct, st_, cnt + 2 * nct);
             k_trav_write<<<nct, 256, 0, stream_>>>(Sb_, cnt + nct, out, L_, kt_, ntiles_, st_, nullptr);
-            const hwfv1_status r = check("get_leaves", true);
-            cudaFree(cnt);
-            return r;
+            return check("get_leaves", true);
         }
     }
 
@@ -1329,10 +1334,27 @@ class EngineT final : public Engine {
             return fail(HWFV1_ERR_CUDA, std::string("read_state: ") + cudaGetErrorString(cudaGetLastError()));
         return HWFV1_OK;
     }
+    // Stream-ordered allocations from the device's default pool, which keeps
+    // what handles free for the next ones (release threshold: everything),
+    // so that a handle created after another one (a new run of the same
+    // problem) does not map its memory again.
+    static void keep_pool_memory() {
+        static bool done[64] = {};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+        done[dev] = true;
+    }
     template <typename P>
     bool alloc(P** p, size_t bytes) {
         void* v = nullptr;
-        if (cudaMalloc(&v, bytes) != cudaSuccess) {
+        keep_pool_memory();
+        if (cudaMallocAsync(&v, bytes, stream_) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
