@@ -258,7 +258,11 @@ hwfv1_status hwfv1_load(hwfv1_handle* hd, const void* host_buf, size_t n);
 /* Message of the last error on this handle ("" if none). */
 const char* hwfv1_last_error(hwfv1_handle* hd);
 
-/* Free all device memory of the handle. */
+/* Free all device memory of the handle.  The handle's buffers come from
+ * the device's default stream-ordered memory pool (cudaMallocAsync on the
+ * handle's stream), whose release threshold the library sets to keep freed
+ * memory for the next handle; cudaMemPoolTrimTo on that pool returns it to
+ * the device. */
 void hwfv1_destroy(hwfv1_handle* hd);
 
 /* ------------------------------------------------------------------------
