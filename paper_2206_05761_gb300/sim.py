@@ -25,6 +25,14 @@ class Simulation:
         self.hd = H.hwfv1_init(self.spec, z, h, qx, qy, stream)
         self._bufs = [torch.empty(self.N, dtype=torch.float64, device=self.dev) for _ in range(3)]
 
+    def _wait(self):
+        """Wait for the library's stream before torch touches a tensor the
+        library wrote (torch copies on its own current stream)."""
+        if self.stream is not None:
+            self.stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+
     # -- the five phases of a step and the loop ---------------------------
     def encode(self):
         H.hwfv1_encode(self.hd)
@@ -59,6 +67,7 @@ class Simulation:
     def fields(self):
         h, qx, qy = self._bufs
         H.hwfv1_get_fields(self.hd, h, qx, qy)
+        self._wait()
         s = 1 << self.L
         return {k: v.cpu().numpy().reshape(s, s).copy() for k, v in zip(("h", "qx", "qy"), (h, qx, qy))}
 
@@ -66,22 +75,26 @@ class Simulation:
         t = [torch.as_tensor(np.ascontiguousarray(f[k], dtype=np.float64).reshape(-1), device=self.dev)
              for k in ("h", "qx", "qy")]
         H.hwfv1_set_fields(self.hd, *t)
+        self._wait()                      # before t is released
 
     def leaves(self):
         n = H.hwfv1_get_leaves(self.hd)
         out = torch.empty(max(n, 1), dtype=torch.int32, device=self.dev)
         H.hwfv1_get_leaves(self.hd, out)
+        self._wait()
         return out[:n].cpu().numpy().view(np.uint32).copy()
 
     def flags(self, which):
         w = H.bits_words(self.L)
         out = torch.zeros(max(w, 1), dtype=torch.int32, device=self.dev)
         H.hwfv1_get_flags(self.hd, which, out)
+        self._wait()
         return out[:w].cpu().numpy().view(np.uint32).copy()
 
     def level(self, field, n):
         out = torch.empty(1 << (2 * n), dtype=torch.float64, device=self.dev)
         H.hwfv1_get_level(self.hd, field, n, out)
+        self._wait()
         return out.cpu().numpy()
 
     def time(self):
@@ -109,6 +122,7 @@ class Simulation:
         S = 1 << (self.L - 4)
         out = torch.empty(S * S * 4, dtype=torch.bfloat16, device=self.dev)
         H.hwfv1_get_features(self.hd, out)
+        self._wait()
         return out.float().cpu().numpy().reshape(S, S, 4)
 
     def features_dev(self, out):
@@ -118,6 +132,7 @@ class Simulation:
         S = 1 << (self.L - 4)
         out = torch.empty(S * S, dtype=torch.uint8, device=self.dev)
         H.hwfv1_get_labels(self.hd, out)
+        self._wait()
         return out.cpu().numpy().reshape(S, S)
 
     def labels_dev(self, out):
@@ -176,9 +191,19 @@ class Ensemble:
         self.L = [p["L"] for p, _ in cases]
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device=self.dev)
         self._inputs = {k: [t(f[k]) for _, f in cases] for k in ("z", "h", "qx", "qy")}
+        self.stream = stream
         self.bt = H.hwfv1_batch_init(self.specs, self._inputs["z"], self._inputs["h"], self._inputs["qx"],
                                      self._inputs["qy"], stream)
+        self._wait()
         self._inputs = None
+
+    def _wait(self):
+        """Wait for the library's stream before torch touches a tensor the
+        library read or wrote."""
+        if self.stream is not None:
+            self.stream.synchronize()
+        else:
+            torch.cuda.synchronize()
 
     def advance(self, t_end=float("inf"), max_steps=1):
         H.hwfv1_batch_advance(self.bt, t_end, max_steps)
@@ -191,6 +216,7 @@ class Ensemble:
         n = 1 << (2 * self.L[d])
         bufs = [torch.empty(n, dtype=torch.float64, device=self.dev) for _ in range(3)]
         H.hwfv1_get_fields(hd, *bufs)
+        self._wait()
         s = 1 << self.L[d]
         return {k: v.cpu().numpy().reshape(s, s) for k, v in zip(("h", "qx", "qy"), bufs)}
 
@@ -199,6 +225,7 @@ class Ensemble:
         n = H.hwfv1_get_leaves(hd)
         out = torch.empty(max(n, 1), dtype=torch.int32, device=self.dev)
         H.hwfv1_get_leaves(hd, out)
+        self._wait()
         return out[:n].cpu().numpy().view(np.uint32).copy()
 
     def member_time(self, d):
