@@ -184,8 +184,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
 # step in the timed window: mean over the launches of the window's ncu
 # launch list (the committed summary under profiles/), valid while
 # kernels.cuh and common.cuh (in that order) have this SHA-256.
-FV1_WET_TRAFFIC = {"kernels_sha256": "cb2686e94f4e65198d46fbbba6d88f744ea7693c48ef07d3dc336a89395454e8",
-                   "bytes_per_launch": 5900288 + 17914112}
+FV1_WET_TRAFFIC = {"kernels_sha256": "07e065366723334f49a4e5a096e7828e2d2bf55f4dd03d48666eb155cfeefd32",
+                   "bytes_per_launch": 9344128 + 4864 + 17912704 + 1792}
 
 
 def kernels_sha256():
