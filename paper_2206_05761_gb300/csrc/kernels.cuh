@@ -513,39 +513,53 @@ __device__ __forceinline__ void encode_body(const EncodeArgs<T, NF>& a, int ls, 
             if (tid == 0) zfp[tile] = any ? 0 : 1;
         }
     }
-    // Levels of at most 64 parents: one thread per (quantity, parent), so
-    // that the quantities' FP64 work, which costs a full warp instruction
-    // however few lanes are active, runs in different warps side by side.
-    // The quantities' flags of a parent are the bytes of one word.
-    __shared__ uint32_t sflag[64];
+    // Levels of at most 64 parents: one warp per quantity, each through the
+    // levels on its own, with no block barrier between them.  A parent's
+    // threshold flag is the OR of its quantities' flags, and its upward
+    // closure the OR of per-quantity closures that start from the full
+    // closure of the pass's first level.  Every warp ORs its words into the
+    // flag words, which were cleared before the pass.
+    if (kk < 2) return;
+    __syncthreads();                 // the first level's values and closure words
+    if (warp >= (uint32_t)NF) return;
+    const uint32_t q = warp;
+    T* const fq = quantity_ptr(a, par, q);
+    uint32_t cprev0 = 0u, cprev1 = 0u;   // this warp's closure bits of the level below (<= 64)
     for (int j = 2; j <= kk; ++j) {
-        __syncthreads();
         n = ls - j;
         cnt >>= 2;
         const int rbuf = (j - 2) & 1, wbuf = (j - 1) & 1;   // level j-1 wrote buffer (j-2)&1
-        if (tid < NF * cnt) {
-            const uint32_t q = tid / cnt, pp = tid - q * cnt;
-            const T* r = rbuf ? sv1[q] : sv0[q];
-            const T c0 = r[4 * pp], c1 = r[4 * pp + 1], c2 = r[4 * pp + 2], c3 = r[4 * pp + 3];
-            T s = T(0);
+        const T* const r = rbuf ? sv1[q] : sv0[q];
+        T* const w = wbuf ? sv1[q] : sv0[q];
+        uint32_t cnow0 = 0u, cnow1 = 0u;
+        for (uint32_t k = 0u; k * 32u < cnt; ++k) {        // cnt <= 64: at most two rounds
+            const uint32_t pp = k * 32u + lane;
+            const bool act = pp < cnt;
             bool f = false;
-            parent_coef(sthr[j - 1][q], c0, c1, c2, c3, s, f);
-            quantity_ptr(a, par, q)[lvl_off(n) + tile * cnt + pp] = s;
-            (wbuf ? sv1[q] : sv0[q])[pp] = s;              // the level read next (other buffer)
-            reinterpret_cast<uint8_t*>(sflag)[4 * pp + q] = f ? 1 : 0;
+            uint32_t cchild = 0u;
+            if (act) {
+                const T c0 = r[4 * pp], c1 = r[4 * pp + 1], c2 = r[4 * pp + 2], c3 = r[4 * pp + 3];
+                T sp = T(0);
+                parent_coef(sthr[j - 1][q], c0, c1, c2, c3, sp, f);
+                fq[lvl_off(n) + tile * cnt + pp] = sp;
+                w[pp] = sp;
+                const uint32_t cb = 4u * pp;                  // the first child's bit
+                const uint32_t cw = j == 2 ? sc[0][cb >> 5] : ((cb >> 5) ? cprev1 : cprev0);
+                cchild = (cw >> (cb & 31u)) & 0xFu;
+            }
+            const uint32_t tb = __ballot_sync(0xffffffffu, act && f);
+            const uint32_t cbl = __ballot_sync(0xffffffffu, act && (f || cchild != 0u));
+            if (k == 0u) cnow0 = cbl;
+            else cnow1 = cbl;
+            if (lane == 0u) {
+                const uint32_t base = tile * cnt + k * 32u;
+                if (tb) atomicOr(a.Tb + word_off(n) + (base >> 5), tb << (base & 31u));
+                if (cbl) atomicOr(a.Cb + word_off(n) + (base >> 5), cbl << (base & 31u));
+            }
         }
-        __syncthreads();
-        const bool act = tid < cnt;
-        bool tf = false;
-        uint32_t cchild = 0;
-        if (act) {
-            tf = (sflag[tid] & (0xFFFFFFFFu >> (32 - 8 * NF))) != 0u;   // bytes 0 .. NF-1
-            cchild = (sc[rbuf][(4u * tid) >> 5] >> ((4u * tid) & 31u)) & 0xFu;
-        }
-        const bool cf = act && (tf || cchild);
-        put_bits(a.Tb, n, tile * cnt, cnt, act && tf);
-        const uint32_t cball = put_bits(a.Cb, n, tile * cnt, cnt, cf);
-        if (lane == 0) sc[wbuf][warp] = cball;
+        cprev0 = cnow0;
+        cprev1 = cnow1;
+        __syncwarp();                // this level's values before the next level reads them
     }
 }
 
