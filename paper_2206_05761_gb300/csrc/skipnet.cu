@@ -10,6 +10,7 @@
 // with zero padding over channels-last images.  Parameters are kept in FP32
 // (the CPU oracle's layout [cout][cin][3][3]) and packed to BF16 operand
 // tiles after every update.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -204,11 +205,13 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, Im
 }
 
 // ---------------------------------------------------------------------------
-// Input gradient: dXcol = dZ W (K = 16 output channels), scattered to dX.
+// Input gradient: dXcol = dZ W (K = 16 output channels) into dcol [pix][kpad];
+// k_col2im then sums each input cell's nine taps in a fixed order (no float
+// atomics: the same gradients on every run).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_conv_bwd_data(const bf16* __restrict__ dZ, Img g,
                                                        const bf16* __restrict__ wt, int kpad,
-                                                       float* __restrict__ dX, int* err) {
+                                                       float* __restrict__ dcol, int* err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcCta s;
     uint8_t* sA = smem;                        // 128 x 16
@@ -228,39 +231,44 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const bf16* __restrict__ 
         tc::mma_commit(&s.bar);
     }
     tc_wait(s, err);
-    int b = 0, y = 0, x = 0;
-    if (p < npix) {
-        b = p / (g.H * g.W);
-        const int rem = p % (g.H * g.W);
-        y = rem / g.W;
-        x = rem % g.W;
-    }
     for (int c0 = 0; c0 < kpad; c0 += 16) {
         float v[16];
         tc::tmem_ld16(s.tmem + ((uint32_t)(32 * (t >> 5)) << 16) + c0, v);
         if (p < npix) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int k = c0 + j;
-                if (k >= 9 * g.cin) continue;
-                const int tap = k / g.cin, c = k % g.cin;
-                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-                if (yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) continue;
-                atomicAdd(dX + ((size_t)(b * g.H + yy) * g.W + xx) * g.cin + c, v[j]);
-            }
+            for (int j = 0; j < 16; ++j) dcol[(size_t)p * kpad + c0 + j] = v[j];
         }
     }
     tc_end(s, ncols);
 }
 
+// dX[b][y][x][c] = sum over the taps (0..8, in order) of the column entry of
+// the output cell that the tap maps onto (b, y, x): the transpose of the
+// forward's im2col.
+__global__ void k_col2im(const float* __restrict__ dcol, Img g, int kpad, float* __restrict__ dX) {
+    const int64_t n = (int64_t)g.B * g.H * g.W * g.cin;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % g.cin);
+        const int64_t q = i / g.cin;
+        const int x = (int)(q % g.W), y = (int)((q / g.W) % g.H), b = (int)(q / ((int64_t)g.W * g.H));
+        float acc = 0.f;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ys = y - (tap / 3 - 1), xs = x - (tap % 3 - 1);     // the output cell of this tap
+            if (ys < 0 || ys >= g.H || xs < 0 || xs >= g.W) continue;
+            acc += dcol[((size_t)(b * g.H + ys) * g.W + xs) * kpad + tap * g.cin + c];
+        }
+        dX[i] = acc;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Weight gradient of 128 pixels: D[k][o] = sum_p Xcol[p][k] dZ[p][o], summed
-// into dW[o][k] (FP32 atomics); db[o] = sum_p dZ[p][o].
+// Weight gradient of 128 pixels: D[k][o] = sum_p Xcol[p][k] dZ[p][o] and
+// sum_p dZ[p][o], this block's part (part + blockIdx.x * (16 kpad + 16):
+// [o][k] then [o]); k_sum_parts adds the blocks' parts in block order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_conv_bwd_weight(const bf16* __restrict__ X, Img g,
                                                          const bf16* __restrict__ dZ, int kpad, int cout,
-                                                         float* __restrict__ dW, float* __restrict__ db,
-                                                         int* err) {
+                                                         float* __restrict__ part, int* err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcCta s;
     const int mt = (kpad + 127) / 128;         // 128-row tiles of k
@@ -287,24 +295,39 @@ __global__ void __launch_bounds__(128) k_conv_bwd_weight(const bf16* __restrict_
         tc::mma_commit(&s.bar);
     }
     tc_wait(s, err);
+    float* const pw = part + (size_t)blockIdx.x * (16 * kpad + 16);
     for (int m = 0; m < mt; ++m) {
         float v[16];
         tc::tmem_ld16(s.tmem + ((uint32_t)(32 * (t >> 5)) << 16) + 16 * m, v);
         const int k = m * 128 + t;
-        if (k < 9 * g.cin) {
+        if (k < kpad) {
 #pragma unroll
-            for (int o = 0; o < 16; ++o)
-                if (o < cout) atomicAdd(dW + (size_t)o * kpad + k, v[o]);
+            for (int o = 0; o < 16; ++o) pw[(size_t)o * kpad + k] = (o < cout && k < 9 * g.cin) ? v[o] : 0.f;
         }
     }
-    // bias gradient: warp sums, one atomic per warp and channel
+    // bias gradient: warp sums, then the four warps' sums in order
+    __shared__ float sdb[4][16];
 #pragma unroll
     for (int o = 0; o < 16; ++o) {
         float x = dzv[o];
         for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if ((t & 31) == 0 && o < cout) atomicAdd(db + o, x);
+        if ((t & 31) == 0) sdb[t >> 5][o] = x;
     }
+    __syncthreads();
+    if (t < 16) pw[16 * kpad + t] = t < cout ? ((sdb[0][t] + sdb[1][t]) + sdb[2][t]) + sdb[3][t] : 0.f;
     tc_end(s, 32);
+}
+
+// dW[o][k] and db[o]: the nb blocks' parts added in block order.
+__global__ void k_sum_parts(const float* __restrict__ part, int nb, int kpad, float* __restrict__ dW,
+                            float* __restrict__ db) {
+    const int per = 16 * kpad + 16;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int b = 0; b < nb; ++b) acc += part[(size_t)b * per + e];
+        if (e < 16 * kpad) dW[e] = acc;
+        else db[e - 16 * kpad] = acc;
+    }
 }
 
 // softmax cross-entropy over the 5 classes of every pixel
@@ -378,6 +401,10 @@ struct SkipNet {
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
     bf16 *wf = nullptr, *wt = nullptr;      // 3 layers x (16 x 144) and (144 x 16)
     float *dW = nullptr, *db = nullptr;     // per-layer weight/bias gradient scratch [16][144], [16]
+    // training scratch of the fixed-order reductions: the input gradient's
+    // columns [pix][144] and the weight gradient's per-block parts
+    float *dcol = nullptr, *part = nullptr;
+    int64_t dcol_cap = 0, part_cap = 0;
     int* err = nullptr;
     double* loss = nullptr;
     int64_t adam_t = 0;
@@ -431,7 +458,7 @@ SkipNet* skipnet_create(uint32_t seed) {
 void skipnet_destroy(SkipNet* n) {
     if (!n) return;
     for (void* p : {(void*)n->params, (void*)n->grads, (void*)n->m, (void*)n->v, (void*)n->wf, (void*)n->wt,
-                    (void*)n->dW, (void*)n->db, (void*)n->err, (void*)n->loss})
+                    (void*)n->dW, (void*)n->db, (void*)n->err, (void*)n->loss, (void*)n->dcol, (void*)n->part})
         if (p) cudaFree(p);
     skipwork_free(&n->work);
     delete n;
@@ -495,6 +522,21 @@ static cudaError_t skipnet_backprop(SkipNet* n, const bf16* x, const uint8_t* la
     SkipWork* w = &n->work;
     const int npix = nimg * H * W;
     if (!skipwork_reserve(w, npix)) return cudaErrorMemoryAllocation;
+    const int64_t nb_all = (npix + 127) / 128;
+    if (n->dcol_cap < npix) {
+        if (n->dcol) cudaFree(n->dcol);
+        n->dcol = nullptr;
+        n->dcol_cap = 0;
+        if (!dalloc(&n->dcol, sizeof(float) * 144 * (size_t)npix)) return cudaErrorMemoryAllocation;
+        n->dcol_cap = npix;
+    }
+    if (n->part_cap < nb_all) {
+        if (n->part) cudaFree(n->part);
+        n->part = nullptr;
+        n->part_cap = 0;
+        if (!dalloc(&n->part, sizeof(float) * (16 * 144 + 16) * (size_t)nb_all)) return cudaErrorMemoryAllocation;
+        n->part_cap = nb_all;
+    }
     cudaError_t e = skipnet_forward(n, x, nimg, H, W, w, st);
     if (e != cudaSuccess) return e;
     const int nb = (npix + 127) / 128;
@@ -507,16 +549,16 @@ static cudaError_t skipnet_backprop(SkipNet* n, const bf16* x, const uint8_t* la
     for (int l = 2; l >= 0; --l) {
         const Layer ly = kLayers[l];
         Img g{nimg, H, W, ly.cin};
-        cudaMemsetAsync(n->dW, 0, sizeof(float) * 16 * 144, st);
-        cudaMemsetAsync(n->db, 0, sizeof(float) * 16, st);
-        k_conv_bwd_weight<<<nb, 128, smem_bwd_weight(ly.kpad), st>>>(acts[l], g, dZ[l], ly.kpad, ly.cout, n->dW,
-                                                                     n->db, n->err);
+        k_conv_bwd_weight<<<nb, 128, smem_bwd_weight(ly.kpad), st>>>(acts[l], g, dZ[l], ly.kpad, ly.cout, n->part,
+                                                                     n->err);
+        k_sum_parts<<<(16 * ly.kpad + 16 + 127) / 128, 128, 0, st>>>(n->part, nb, ly.kpad, n->dW, n->db);
         k_unpack_grads<<<1, 256, 0, st>>>(n->dW, n->db, l, n->grads);
         if (l > 0) {
             // gradient w.r.t. this layer's input = the previous layer's activation
-            cudaMemsetAsync(dA[l], 0, sizeof(float) * 16 * (size_t)npix, st);
-            k_conv_bwd_data<<<nb, 128, smem_bwd_data(ly.kpad), st>>>(dZ[l], g, n->wt + l * 144 * 16, ly.kpad, dA[l],
-                                                                     n->err);
+            k_conv_bwd_data<<<nb, 128, smem_bwd_data(ly.kpad), st>>>(dZ[l], g, n->wt + l * 144 * 16, ly.kpad,
+                                                                     n->dcol, n->err);
+            k_col2im<<<(int)std::min<int64_t>(((int64_t)npix * g.cin + 255) / 256, 4096), 256, 0, st>>>(
+                n->dcol, g, ly.kpad, dA[l]);
             k_relu_bwd<<<(npix * 16 + 255) / 256, 256, 0, st>>>(dA[l], Zs[l - 1], (int64_t)npix * 16, dZ[l - 1]);
         }
     }

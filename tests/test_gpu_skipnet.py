@@ -139,6 +139,27 @@ def test_training_reduces_loss():
     Hh.hwfv1_skipnet_destroy(net)
 
 
+def test_training_is_deterministic():
+    # the backward pass sums in a fixed order (no float atomics): two networks
+    # from one seed, trained on the same samples, end with the same bits
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    rng = np.random.default_rng(5)
+    nimg, H, W = 16, 32, 32
+    x = torch.as_tensor(rng.standard_normal((nimg, H, W, 4)).astype(np.float32)).to(torch.bfloat16)
+    labels = torch.as_tensor(rng.integers(0, 5, (nimg, H, W)).astype(np.uint8))
+    xd, ld = x.reshape(-1).cuda(), labels.reshape(-1).cuda()
+    out = []
+    for _ in range(2):
+        net = Hh.hwfv1_skipnet_create(11)
+        Hh.hwfv1_skipnet_train(net, xd, ld, nimg, H, W, batch=4, epochs=3, lr=3e-3, seed=2)
+        _, g = Hh.hwfv1_skipnet_gradients(net, xd, ld, nimg, H, W)
+        out.append((Hh.hwfv1_skipnet_get_params(net), np.asarray(g)))
+        Hh.hwfv1_skipnet_destroy(net)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def _closure_labels(T, L):
     """Training labels from the oracle's threshold flags (row-major per level):
     close the flags upward and take, per level-(L-4) subtree, 1 + the deepest
