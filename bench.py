@@ -217,8 +217,10 @@ def roofline(kernel, ms, r, args, pk, src):
         traffic = (FV1_WET_TRAFFIC["bytes_per_launch"]
                    if FV1_WET_TRAFFIC["kernels_sha256"] == kernels_sha256() and kernel != "k_fv1_wet"
                    else None)
+        meas = r.get("fp64_measured_tflops")
         return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "measured_fp64_tflops": meas, "frac_of_measured_fp64": (ach / meas) if meas else None,
                 "units_per_launch": r["wet_per_step"], "flop_per_unit": FV1_WET_FLOP_PER_LEAF,
                 "peak_source": "derived: FP64 pipe, 2 instructions/clk/SM x 152 SMs x 2.07 GHz, "
                                "1 FLOP per instruction (no FMA)"}
@@ -369,8 +371,10 @@ def run_ours(args, rank, world):
     t_now, dt_now, nsteps = H.hwfv1_get_time(hd)
     c1 = H.hwfv1_get_counters(hd)
     H.hwfv1_destroy(hd)
+    fp64_meas = H.hwfv1_fp64_throughput()     # after the timed region
     ph = {k: statistics.median(v) for k, v in kern.items()}
     return dict(ms=ms, e2e_s=t_e2e, e2e_trials=e2e_trials, kernels_ms=ph, update_ms=statistics.median(upd),
+                fp64_measured_tflops=fp64_meas,
                 wet_per_step=statistics.median(wet), t=t_now, dt=dt_now,
                 t_start=t_s, dt_start=dt_s, snapshot=state,
                 problem=p, clocks=clocks, N=N, timed_steps=c1[0] - c0[0], timed_leaf_updates=c1[1] - c0[1],

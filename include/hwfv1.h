@@ -236,6 +236,14 @@ hwfv1_status hwfv1_profile_step(hwfv1_handle* hd, float* ms, const char** names,
  * counterpart in the paper: diagnostics. */
 hwfv1_status hwfv1_profile_update(hwfv1_handle* hd, int32_t reps, float* ms);
 
+/* Measured FP64 add throughput of the current device (host output, TFLOP/s
+ * at one FLOP per instruction): a grid of 8 CTAs of 256 threads per SM,
+ * each thread running eight independent chains of dependent double
+ * additions, timed with CUDA events, best of three after a warm-up.  The
+ * wet-leaf update is bound by this pipe.  No counterpart in the paper:
+ * diagnostics.  Synchronises; allocates and frees a small buffer. */
+hwfv1_status hwfv1_fp64_throughput(double* tflops);
+
 /* Running counters (host outputs, any may be NULL; synchronises): steps
  * taken; leaves updated summed over those steps (sum of M, the work of
  * Sec. 2.3's leaf loop); the part of them outside skipped quiescent tiles

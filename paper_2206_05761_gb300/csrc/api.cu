@@ -307,6 +307,63 @@ const char* hwfv1_batch_last_error(hwfv1_batch* bt) {
     return bt->msg.c_str();
 }
 
+}  // extern "C"
+
+namespace {
+// Eight independent chains of dependent double additions per thread: the
+// sub-partitions' FP64 units stay busy, nothing else is issued in between.
+__global__ void k_fp64_add_loop(double* out, int iters) {
+    const double c = 1.0000000001;
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __dadd_rn(x[k], c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = __dadd_rn(s, x[k]);
+    out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" {
+
+hwfv1_status hwfv1_fp64_throughput(double* tflops) {
+    if (!tflops) return HWFV1_ERR_INVALID_SPEC;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HWFV1_ERR_CUDA;
+    const int threads = 256, blocks = nsm * 8, iters = 2048;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * (size_t)threads * blocks) != cudaSuccess) {
+        cudaGetLastError();
+        return HWFV1_ERR_OOM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {            // the first launch warms up
+        cudaEventRecord(e0);
+        k_fp64_add_loop<<<blocks, threads>>>(out, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < best) best = ms;
+    }
+    const cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return HWFV1_ERR_CUDA;
+    *tflops = (double)blocks * threads * iters * 8.0 / (best * 1e-3) / 1e12;
+    return HWFV1_OK;
+}
+
 void hwfv1_batch_destroy(hwfv1_batch* bt) {
     if (!bt) return;
     for (hwfv1_handle* v : bt->views) delete v;

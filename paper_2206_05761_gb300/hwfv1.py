@@ -82,6 +82,7 @@ def lib():
             L.hwfv1_profile_step.argtypes = [_H, C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int32,
                                              C.POINTER(C.c_int32)]
             L.hwfv1_profile_update.argtypes = [_H, C.c_int32, C.POINTER(C.c_float)]
+            L.hwfv1_fp64_throughput.argtypes = [C.POINTER(C.c_double)]
             L.hwfv1_save.argtypes = [_H, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
             L.hwfv1_load.argtypes = [_H, C.c_void_p, C.c_size_t]
             L.hwfv1_last_error.argtypes = [_H]
@@ -127,7 +128,7 @@ def exported_symbols():
             "hwfv1_decode", "hwfv1_advance", "hwfv1_advance_uniform", "hwfv1_get_fields", "hwfv1_set_fields",
             "hwfv1_get_leaves", "hwfv1_get_flags", "hwfv1_get_level", "hwfv1_get_time",
             "hwfv1_set_time", "hwfv1_get_stats", "hwfv1_get_counters", "hwfv1_profile_step",
-            "hwfv1_profile_update", "hwfv1_save", "hwfv1_load",
+            "hwfv1_profile_update", "hwfv1_fp64_throughput", "hwfv1_save", "hwfv1_load",
             "hwfv1_last_error", "hwfv1_destroy", "hwfv1_version", "hwfv1_traverse_noalloc",
             "hwfv1_batch_init", "hwfv1_batch_advance", "hwfv1_batch_autotune", "hwfv1_batch_member",
             "hwfv1_batch_launches_per_step", "hwfv1_batch_last_error", "hwfv1_batch_destroy",
@@ -270,6 +271,13 @@ def hwfv1_profile_step(hd, cap=64):
     n = C.c_int32()
     _check(lib().hwfv1_profile_step(hd, ms, names, cap, C.byref(n)), "hwfv1_profile_step", hd)
     return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
+
+
+def hwfv1_fp64_throughput():
+    """Measured FP64 add throughput of the current device (TFLOP/s)."""
+    v = C.c_double()
+    _check(lib().hwfv1_fp64_throughput(C.byref(v)), "hwfv1_fp64_throughput")
+    return v.value
 
 
 def hwfv1_profile_update(hd, reps=20):

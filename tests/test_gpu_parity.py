@@ -612,3 +612,14 @@ def test_top_of_range_L14_keeps_the_symmetries():
     lv = (sim.leaves() >> 28).astype(np.int64)
     assert np.sum(np.ldexp(1.0, -2 * lv)) == 1.0
     sim.close()
+
+
+def test_fp64_throughput_probe():
+    # the measured DADD rate behind the roofline's context figure: positive
+    # and below the FP64 pipe's nominal rate (2 per cycle per SM)
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as Hh
+    v = Hh.hwfv1_fp64_throughput()
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 2 * 2.2e9 / 1e12
+    assert 0.0 < v <= nominal

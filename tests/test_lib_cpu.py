@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     txt = open(os.path.join(ROOT, "include", "hwfv1.h")).read()
-    return sorted(set(re.findall(r"\b(hwfv1_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(hwfv1_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_and_binding_agree():
