@@ -121,13 +121,14 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
             const uint32_t cnt = 1u << (2 * (n - Ls));
             const bool first = n == E - 1;
 #pragma unroll 1
-            for (uint32_t t = lane; t < (first ? cnt : 32u); t += 32u) {
+            for (uint32_t t0 = 0u; t0 < (first ? cnt : 32u); t0 += 32u) {   // warp-uniform rounds
+                const uint32_t t = t0 + lane;
                 const bool act = t < cnt;
                 const uint64_t pc = ((uint64_t)s << (2 * (n - Ls))) + t;
                 T c[3][4];
                 bool cch = false;
                 T sq[3] = {T(0), T(0), T(0)};
-                bool cf = false;
+                bool cf = false, tt = false;
                 if (act) {
                     if (first) {
                         Vec4<T>::load_cg(fh + lvl_off(n + 1) + 4ull * pc, c[0][0], c[0][1], c[0][2], c[0][3]);
@@ -155,10 +156,18 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
                     fqx[lvl_off(n) + pc] = sq[1];
                     fqy[lvl_off(n) + pc] = sq[2];
                     const uint32_t wi = word_off(n) + (uint32_t)(pc >> 5), bit = 1u << (pc & 31u);
-                    const bool tt = n < p && (tf || (__ldg(a.Tz + wi) & bit) != 0u);
+                    tt = n < p && (tf || (__ldg(a.Tz + wi) & bit) != 0u);
                     cf = tt || cch;
-                    if (tt) atomicOr(a.Tb + wi, bit);
-                    if (cf) atomicOr(a.Cb + wi, bit);
+                }
+                // one OR per word: a round's parents are consecutive codes
+                // within one word (aligned to their count, or to 32)
+                const uint32_t tb = __ballot_sync(0xffffffffu, act && tt);
+                const uint32_t cb = __ballot_sync(0xffffffffu, act && cf);
+                if (lane == 0u && (tb | cb)) {
+                    const uint64_t pc0 = ((uint64_t)s << (2 * (n - Ls))) + t0;
+                    const uint32_t w0 = word_off(n) + (uint32_t)(pc0 >> 5), sh = (uint32_t)(pc0 & 31u);
+                    if (tb) atomicOr(a.Tb + w0, tb << sh);
+                    if (cb) atomicOr(a.Cb + w0, cb << sh);
                 }
                 // the first level writes slots no lane reads in this level;
                 // the others overwrite what the warp has just read
