@@ -318,15 +318,22 @@ __global__ void __launch_bounds__(128) k_conv_bwd_weight(const bf16* __restrict_
     tc_end(s, 32);
 }
 
-// dW[o][k] and db[o]: the nb blocks' parts added in block order.
+// dW[o][k] and db[o]: the nb blocks' parts added in a fixed order, one warp
+// per entry (lane l adds blocks l, l + 32, ... in turn, then a fixed
+// shuffle tree adds the lanes' sums).
 __global__ void k_sum_parts(const float* __restrict__ part, int nb, int kpad, float* __restrict__ dW,
                             float* __restrict__ db) {
     const int per = 16 * kpad + 16;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < per; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < per; e += nw) {
         float acc = 0.f;
-        for (int b = 0; b < nb; ++b) acc += part[(size_t)b * per + e];
-        if (e < 16 * kpad) dW[e] = acc;
-        else db[e - 16 * kpad] = acc;
+        for (int b = lane; b < nb; b += 32) acc += part[(size_t)b * per + e];
+        for (int off = 16; off; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            if (e < 16 * kpad) dW[e] = acc;
+            else db[e - 16 * kpad] = acc;
+        }
     }
 }
 
@@ -551,7 +558,7 @@ static cudaError_t skipnet_backprop(SkipNet* n, const bf16* x, const uint8_t* la
         Img g{nimg, H, W, ly.cin};
         k_conv_bwd_weight<<<nb, 128, smem_bwd_weight(ly.kpad), st>>>(acts[l], g, dZ[l], ly.kpad, ly.cout, n->part,
                                                                      n->err);
-        k_sum_parts<<<(16 * ly.kpad + 16 + 127) / 128, 128, 0, st>>>(n->part, nb, ly.kpad, n->dW, n->db);
+        k_sum_parts<<<(16 * ly.kpad + 16 + 7) / 8, 256, 0, st>>>(n->part, nb, ly.kpad, n->dW, n->db);
         k_unpack_grads<<<1, 256, 0, st>>>(n->dW, n->db, l, n->grads);
         if (l > 0) {
             // gradient w.r.t. this layer's input = the previous layer's activation
