@@ -80,6 +80,10 @@ struct SkipArgs {
 // and the FV1 update read them there); threshold and closure bits are OR-ed
 // into words the clear kernel zeroed.  The level chain of a subtree runs in
 // its warp alone (warp barriers only), so many subtrees are in flight per SM.
+// The chain is bound by load latency, so the loads a level needs are issued
+// ahead of it: the thresholds of the subtree levels sit in shared memory,
+// the bed's flag words of a subtree are read with its levels, and the
+// level-P cells are formed four warp rounds at a time, loads first.
 template <typename T>
 static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
     pdl_wait();
@@ -93,7 +97,25 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
     const uint32_t nsub = 1u << (2 * Ls);
     __shared__ T sv[8][3][64];               // the level just formed, per warp
     __shared__ uint8_t scl[8][64];           // its closure bits
+    __shared__ Thr<T> sth[4][3];             // thresholds of levels Ls .. Ls+3
+    if (threadIdx.x < 12u) {
+        const int d = (int)threadIdx.x / 3, q = (int)threadIdx.x % 3, idx = (Ls + d) * 3 + q;
+        sth[d][q].thr = a.thr[idx];
+        sth[d][q].thr4 = a.thr4[idx];
+        sth[d][q].lo = a.thr4lo ? a.thr4lo[idx] : -1.0f;
+        sth[d][q].hi = a.thr4hi ? a.thr4hi[idx] : -1.0f;
+    }
+    __syncthreads();
     for (uint32_t s = blockIdx.x * 8u + wib; s < nsub; s += gridDim.x * 8u) {
+        // the bed's flag words of the parents of s: lane d < 3 holds level
+        // Ls+d's word (at most 16 parents, one word), lanes 3 and 4 the two
+        // words of level Ls+3's 64 parents
+        uint32_t tzw = 0u;
+        if (lane < 5u) {
+            const int d = lane < 3u ? (int)lane : 3;
+            const uint32_t pc = (s << (2 * d)) + (lane == 4u ? 32u : 0u);
+            tzw = __ldg(a.Tz + word_off(Ls + d) + (pc >> 5));
+        }
         const int p = a.phat[s];
         const int P = skip_store_level(a.phat, Ls, s);
         const int m = a.mlev[s];
@@ -105,12 +127,33 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
             // the exact store keeps a flat subtree's stored cells as the
             // finest cells they stand for: formed by copying
             const bool copy = a.flat != nullptr && a.flat[s] != 0;
-            for (uint32_t k = lane; k < cnt; k += 32u) {
-                const uint64_t c = b + k, ia = lvl_off(m) + (c >> (2 * (P - m))), ic = lvl_off(P) + c;
-                const T hl = __ldcg(fh + ia);
-                fh[ic] = copy ? hl : redecode_h(hl, __ldg(a.z + ia), __ldg(a.z + ic), a.tol);
-                fqx[ic] = __ldcg(fqx + ia);
-                fqy[ic] = __ldcg(fqy + ia);
+#pragma unroll 1
+            for (uint32_t k0 = 0u; k0 < cnt; k0 += 64u) {
+                T hl[2], zl[2], zc[2], ql[2], rl[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t k = k0 + 32u * j + lane;
+                    if (k < cnt) {
+                        const uint64_t c = b + k, ia = lvl_off(m) + (c >> (2 * (P - m))), ic = lvl_off(P) + c;
+                        hl[j] = __ldcg(fh + ia);
+                        ql[j] = __ldcg(fqx + ia);
+                        rl[j] = __ldcg(fqy + ia);
+                        if (!copy) {
+                            zl[j] = __ldg(a.z + ia);
+                            zc[j] = __ldg(a.z + ic);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t k = k0 + 32u * j + lane;
+                    if (k < cnt) {
+                        const uint64_t ic = lvl_off(P) + b + k;
+                        fh[ic] = copy ? hl[j] : redecode_h(hl[j], zl[j], zc[j], a.tol);
+                        fqx[ic] = ql[j];
+                        fqy[ic] = rl[j];
+                    }
+                }
             }
             __syncwarp();                    // the warp reads level P below
         }
@@ -125,6 +168,7 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
                 const uint32_t t = t0 + lane;
                 const bool act = t < cnt;
                 const uint64_t pc = ((uint64_t)s << (2 * (n - Ls))) + t;
+                const uint32_t tz = __shfl_sync(0xffffffffu, tzw, n - Ls < 3 ? (uint32_t)(n - Ls) : 3u + (t0 >> 5));
                 T c[3][4];
                 bool cch = false;
                 T sq[3] = {T(0), T(0), T(0)};
@@ -141,22 +185,12 @@ static __global__ void __launch_bounds__(256, 3) k_skip_encode(SkipArgs<T> a) {
                             for (int e = 0; e < 4; ++e) c[q][e] = sv[wib][q][4 * t + e];
                         cch = (scl[wib][4 * t] | scl[wib][4 * t + 1] | scl[wib][4 * t + 2] | scl[wib][4 * t + 3]) != 0;
                     }
-                    Thr<T> th[3];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const int idx = n * 3 + q;
-                        th[q].thr = a.thr[idx];
-                        th[q].thr4 = a.thr4[idx];
-                        th[q].lo = a.thr4lo ? a.thr4lo[idx] : -1.0f;
-                        th[q].hi = a.thr4hi ? a.thr4hi[idx] : -1.0f;
-                    }
                     bool tf = false;
-                    parents_all<T, 3>(th, c, sq, tf);
+                    parents_all<T, 3>(sth[n - Ls], c, sq, tf);
                     fh[lvl_off(n) + pc] = sq[0];
                     fqx[lvl_off(n) + pc] = sq[1];
                     fqy[lvl_off(n) + pc] = sq[2];
-                    const uint32_t wi = word_off(n) + (uint32_t)(pc >> 5), bit = 1u << (pc & 31u);
-                    tt = n < p && (tf || (__ldg(a.Tz + wi) & bit) != 0u);
+                    tt = n < p && (tf || (tz & (1u << (pc & 31u))) != 0u);
                     cf = tt || cch;
                 }
                 // one OR per word: a round's parents are consecutive codes
@@ -270,14 +304,13 @@ static __global__ void __launch_bounds__(256) k_skip_decode(SkipDecodeArgs<T> a,
         const bool have = s < nsub;
         const int P = have ? (int)a.plev[s] : Ls;
         __syncthreads();                          // the previous round's readers are done
-        if (have && t == 0u) {
-            int l0 = Ls + 1;                      // a leaf on the root path covers the subtree
-            for (int n = 0; n <= Ls; ++n)
-                if (!sig_bit(a.Sb, n, s >> (2 * (Ls - n)))) {
-                    l0 = n;
-                    break;
-                }
-            s_l0[g] = l0;
+        if (t < 32u) {                            // the group's first warp, warp-uniform
+            // the leaf on the root path that covers the subtree: the first
+            // level n <= Ls whose cell over s is not significant (Ls + 1:
+            // none), its bits loaded by lane n, all at once
+            const bool clear = have && (int)t <= Ls && !sig_bit(a.Sb, (int)t, s >> (2 * (Ls - (int)t)));
+            const uint32_t cb = __ballot_sync(0xffffffffu, clear);
+            if (have && t == 0u) s_l0[g] = cb ? __ffs((int)cb) - 1 : Ls + 1;
         }
         if (have && t >= 1u && t <= 3u && Ls + (int)t < P) {     // levels Ls+1 .. Ls+3
             const int n = Ls + (int)t;
