@@ -353,12 +353,18 @@ static __global__ void __launch_bounds__(256) k_skip_decode(SkipDecodeArgs<T> a,
                     }
                 }
             }
-            const uint64_t il = lvl_off(l) + (c >> (2 * (tgt - l)));
+            const uint64_t il = lvl_off(l) + (c >> (2 * (tgt - l))), ic = lvl_off(tgt) + c;
+            // the leaf's values and the two bed values in one round of loads
+            const bool fill = l < tgt || (exact && tgt < a.L);
             const T hl = fh[il], qxl = fqx[il], qyl = fqy[il];
+            T zl = T(0), zc = T(0);
+            if (fill) {
+                zl = __ldg(a.z + il);
+                zc = __ldg(a.z + ic);
+            }
             T hf = hl;
-            if (l < tgt || (exact && tgt < a.L)) {
-                const uint64_t ic = lvl_off(tgt) + c;
-                hf = redecode_h(hl, __ldg(a.z + il), __ldg(a.z + ic), a.tol);
+            if (fill) {
+                hf = redecode_h(hl, zl, zc, a.tol);
                 fh[ic] = hf;
                 fqx[ic] = qxl;
                 fqy[ic] = qyl;
