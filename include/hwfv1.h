@@ -31,7 +31,8 @@
  *    call that synchronises (hwfv1_get_time, hwfv1_advance with
  *    synchronisation, hwfv1_save); hwfv1_last_error gives a message.
  *  - hwfv1_init allocates the handle's buffers; the step, its phases, the
- *    getters, hwfv1_save and hwfv1_load allocate nothing.  A mode's first
+ *    getters (hwfv1_get_fields into host memory aside: a staging area,
+ *    returned before it ends), hwfv1_save and hwfv1_load allocate nothing.  A mode's first
  *    use allocates the buffers it adds, once per handle: uniform FV1
  *    (hwfv1_advance_uniform), the learned skip (hwfv1_set_skipnet,
  *    hwfv1_set_skip_levels) and the exact leaf-value store
@@ -118,11 +119,18 @@ typedef struct hwfv1_problem {
 
 typedef struct hwfv1_handle hwfv1_handle;
 
-/* Create a simulation from the initial finest fields (device, row-major,
- * float64, 4^L elements each; qx = hu, qy = hv) and bed z.  Copies them into
- * the handle's Morton-ordered hierarchy, encodes the static bed once, and
- * sets t = 0 and dt from the CFL condition on the initial state.  `stream`
- * is a cudaStream_t (NULL = legacy default stream).  Synchronises.
+/* Create a simulation from the initial finest fields (row-major, float64,
+ * 4^L elements each; qx = hu, qy = hv) and bed z.  Each of the four may be
+ * device memory or host memory (pinned or pageable): a host field is copied
+ * to the device on a stream of the handle's own, in the order z, h, qx, qy,
+ * through a staging area of 2 x 4^L doubles taken from the device pool and
+ * returned before the call ends, so that the bed is converted and encoded
+ * while the other fields are still being copied.  Copies the fields into
+ * the handle's Morton-ordered hierarchy, encodes the static bed once, sets
+ * t = 0 and dt from the CFL condition on the initial state, and captures
+ * the plain step's graphs (which hwfv1_advance launches).  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Synchronises: the caller's
+ * buffers are no longer read when it returns.
  * Initial discretisation: the first step of Algorithm 3. */
 hwfv1_status hwfv1_init(const hwfv1_problem* spec, const double* z, const double* h,
                         const double* qx, const double* qy, void* stream,
@@ -177,8 +185,13 @@ hwfv1_status hwfv1_advance(hwfv1_handle* hd, double t_end, int64_t max_steps);
  * use.  Does not synchronise. */
 hwfv1_status hwfv1_advance_uniform(hwfv1_handle* hd, double t_end, int64_t max_steps);
 
-/* Current finest fields h, hu, hv (device, row-major float64, 4^L each;
- * any pointer may be NULL). */
+/* Current finest fields h, hu, hv (row-major float64, 4^L each; any pointer
+ * may be NULL).  An output may be device or host memory (pinned or
+ * pageable).  Host outputs are formed in a staging area of 2 x 4^L doubles
+ * from the device pool (returned before the call ends) and copied out one
+ * field while the next is formed; the call then synchronises, and the host
+ * outputs are written when it returns.  With device outputs only it is
+ * asynchronous and allocates nothing. */
 hwfv1_status hwfv1_get_fields(hwfv1_handle* hd, double* h, double* qx, double* qy);
 
 /* Replace the finest h, hu, hv (device, row-major float64) keeping t and dt;

@@ -57,6 +57,9 @@ class EngineT final : public Engine {
         if (ev_fork_) cudaEventDestroy(ev_fork_);
         if (ev_join_) cudaEventDestroy(ev_join_);
         if (side_) cudaStreamDestroy(side_);
+        for (cudaEvent_t& e : hev_)
+            if (e) cudaEventDestroy(e);
+        if (cstream_) cudaStreamDestroy(cstream_);
         for (void* p : allocs_)
             if (cudaFreeAsync(p, stream_) != cudaSuccess) {     // (a stream the caller destroyed)
                 cudaGetLastError();
@@ -78,6 +81,36 @@ class EngineT final : public Engine {
             for (int q = 0; q < 3; ++q)
                 if (!alloc(&f_[b][q], H_ * sizeof(T))) return oom();
         if (!alloc(&z_, H_ * sizeof(T))) return oom();
+        // Fields in host memory (pinned or pageable) are copied in on the copy
+        // stream through two staging slots, in the order z, h, qx, qy: the
+        // bed is converted and encoded while h, qx and qy are on their way.
+        // Events 0-3: field k copied in; 4-7: field k converted (its slot free).
+        const double* src[4] = {z, h, qx, qy};
+        bool hostp[4];
+        bool any_host = false;
+        for (int k = 0; k < 4; ++k) any_host |= (hostp[k] = on_host(src[k]));
+        double* stage = nullptr;
+        if (any_host) {
+            if (hwfv1_status r = host_io_ready(); r != HWFV1_OK) return r;
+            if (hwfv1_status r = stage_alloc(&stage); r != HWFV1_OK) return r;
+        }
+        auto copy_in = [&](int k) -> bool {
+            if (!hostp[k]) return true;
+            if (k >= 2 && hostp[k - 2]) cudaStreamWaitEvent(cstream_, hev_[4 + k - 2], 0);
+            if (cudaMemcpyAsync(stage + (size_t)(k & 1) * N_, src[k], N_ * sizeof(double), cudaMemcpyHostToDevice,
+                                cstream_) != cudaSuccess)
+                return false;
+            return cudaEventRecord(hev_[k], cstream_) == cudaSuccess;
+        };
+        auto field = [&](int k) -> const double* {          // on stream_: field k on the device
+            if (!hostp[k]) return src[k];
+            cudaStreamWaitEvent(stream_, hev_[k], 0);
+            return stage + (size_t)(k & 1) * N_;
+        };
+        auto converted = [&](int k) {
+            if (hostp[k]) cudaEventRecord(hev_[4 + k], stream_);
+        };
+        if (!copy_in(0) || !copy_in(1)) return fail(HWFV1_ERR_CUDA, "init: copy of a host field");
         if (!alloc(&bits_, (size_t)words_ * 6 * sizeof(uint32_t))) return oom();
         Tb_ = bits_;
         Cb_ = bits_ + words_;
@@ -108,6 +141,16 @@ class EngineT final : public Engine {
         if (!alloc(&work_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
         cudaMemsetAsync(tilebytes_, 0, (size_t)ntiles_ * 4, stream_);
         quiet_on_ = !(spec_.flags & HWFV1_FULL_SWEEP) && spec_.eps >= 1e-30;
+        // With quiescent tiles on, the first step starts from marks as a
+        // later step does: both buffers are cleared (buffer 0 below its
+        // finest level, which the fields fill) and the tiles of +0 marked
+        // once the fields are in (k_quiet_tiles), so that the first encode,
+        // traversal and decode skip them as well.
+        if (quiet_on_)
+            for (int q = 0; q < 3; ++q) {
+                cudaMemsetAsync(f_[0][q], 0, lvl_off(L_) * sizeof(T), stream_);
+                cudaMemsetAsync(f_[1][q], 0, H_ * sizeof(T), stream_);
+            }
         pdl_ = std::getenv("HWFV1_NO_PDL") == nullptr;
         {
             std::vector<uint8_t> inl(ntiles_, 0);
@@ -142,12 +185,11 @@ class EngineT final : public Engine {
             cudaMemcpyAsync(st_, &s0, sizeof s0, cudaMemcpyHostToDevice, stream_);
             cudaStreamSynchronize(stream_);
         }
-        // finest fields into the Morton hierarchy
+        // finest fields into the Morton hierarchy, the bed's first
         const int g = grid_for(N_);
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(z, z_ + lvl_off(L_), L_);
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(h, f_[0][0] + lvl_off(L_), L_);
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(qx, f_[0][1] + lvl_off(L_), L_);
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(qy, f_[0][2] + lvl_off(L_), L_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(0), z_ + lvl_off(L_), L_);
+        converted(0);
+        if (!copy_in(2)) return fail(HWFV1_ERR_CUDA, "init: copy of a host field");
         // bed: s_max, thresholds, one-off encode and its static flags
         unsigned long long* zmax = reinterpret_cast<unsigned long long*>(zaux_);
         double* smax_z = reinterpret_cast<double*>(zaux_ + 8);
@@ -174,8 +216,27 @@ class EngineT final : public Engine {
         if (!alloc(&scount_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
         k_static_counts<<<(ntiles_ + kTilesPerCta - 1) / kTilesPerCta, 256, 0, stream_>>>(Sz_, L_, kt_, ntiles_,
                                                                                        scount_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(1), f_[0][0] + lvl_off(L_), L_);
+        converted(1);
+        if (!copy_in(3)) return fail(HWFV1_ERR_CUDA, "init: copy of a host field");
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(2), f_[0][1] + lvl_off(L_), L_);
+        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(3), f_[0][2] + lvl_off(L_), L_);
+        if (stage) cudaFreeAsync(stage, stream_);      // every copy is ordered before it on stream_
+        if (quiet_on_) {
+            k_quiet_tiles<T><<<grid_for((uint64_t)ntiles_ * 32), 256, 0, stream_>>>(
+                f_[0][0] + lvl_off(L_), f_[0][1] + lvl_off(L_), f_[0][2] + lvl_off(L_), tilebytes_, ntiles_, kt_);
+            cudaMemsetAsync(tilebytes_ + ntiles_, 1, ntiles_, stream_);     // buffer 1: all +0
+        }
         // initial state scalars
         reduce_state(/*set_dt=*/1);
+        // the plain step's graphs, captured while the device initialises
+        // (capturing runs nothing), so that the first hwfv1_advance does not
+        // pay for them; a batch member is stepped by its batch
+        if (!batched_ && std::getenv("HWFV1_NO_GRAPH") == nullptr) {
+            if (hwfv1_status r = check("init"); r != HWFV1_OK) return r;
+            if (capture(&exec_, kStepPlain) != HWFV1_OK) return HWFV1_ERR_CUDA;
+            if (capture(&exec_multi_, kStepPlain, kMultiSteps) != HWFV1_OK) return HWFV1_ERR_CUDA;
+        }
         return check("init", true);
     }
 
@@ -399,11 +460,40 @@ class EngineT final : public Engine {
         // stored state is left as it is)
         const bool other = skipmode_ != 0;
         if (other) launch_skip_finest(0);
-        for (int q = 0; q < 3; ++q)
-            if (out[q])
-                k_morton_to_rm<T><<<grid_for(N_), 256, 0, stream_>>>(
-                    f_[other ? 1 : 0][q] + lvl_off(L_), f_[other ? 0 : 1][q] + lvl_off(L_), st_, out[q], L_);
-        return check("get_fields");
+        // a host output is formed in a staging slot and copied out on the
+        // copy stream while the next field is formed (events 0-2: copy j
+        // done, its slot free; 4-6: field j formed)
+        bool hostp[3];
+        bool any_host = false;
+        for (int q = 0; q < 3; ++q) any_host |= (hostp[q] = out[q] != nullptr && on_host(out[q]));
+        double* stage = nullptr;
+        if (any_host) {
+            if (hwfv1_status r = host_io_ready(); r != HWFV1_OK) return r;
+            if (hwfv1_status r = stage_alloc(&stage); r != HWFV1_OK) return r;
+        }
+        int j = 0;
+        for (int q = 0; q < 3; ++q) {
+            if (!out[q]) continue;
+            double* dst = out[q];
+            if (hostp[q]) {
+                if (j >= 2) cudaStreamWaitEvent(stream_, hev_[j - 2], 0);
+                dst = stage + (size_t)(j & 1) * N_;
+            }
+            k_morton_to_rm<T><<<grid_for(N_), 256, 0, stream_>>>(
+                f_[other ? 1 : 0][q] + lvl_off(L_), f_[other ? 0 : 1][q] + lvl_off(L_), st_, dst, L_);
+            if (hostp[q]) {
+                cudaEventRecord(hev_[4 + j], stream_);
+                cudaStreamWaitEvent(cstream_, hev_[4 + j], 0);
+                if (cudaMemcpyAsync(out[q], dst, N_ * sizeof(double), cudaMemcpyDeviceToHost, cstream_) != cudaSuccess ||
+                    cudaEventRecord(hev_[j], cstream_) != cudaSuccess)
+                    return fail(HWFV1_ERR_CUDA, "get_fields: copy to a host field");
+                ++j;
+            }
+        }
+        if (!any_host) return check("get_fields");
+        for (int k = 0; k < j; ++k) cudaStreamWaitEvent(stream_, hev_[k], 0);
+        cudaFreeAsync(stage, stream_);
+        return check("get_fields", true);            // host outputs are written when the call returns
     }
 
     hwfv1_status set_fields(const double* h, const double* qx, const double* qy) override {
@@ -1282,7 +1372,10 @@ class EngineT final : public Engine {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(HWFV1_ERR_CUDA, "graph capture begin");
+        // capturing runs nothing: host state the launches update is kept
+        const bool sbv = sb_valid_;
         for (int k = 0; k < nsteps; ++k) launch_step(kind);
+        sb_valid_ = sbv;
         if (cudaStreamEndCapture(stream_, &g) != cudaSuccess) return fail(HWFV1_ERR_CUDA, "graph capture end");
         const int64_t nk = count_kernel_nodes(g) / nsteps;
         if (kind == kStepPlain) kernels_plain_ = nk;
@@ -1367,6 +1460,39 @@ class EngineT final : public Engine {
         err = m;
         return s;
     }
+    // a pointer the host reads or writes (pinned or pageable memory), as
+    // opposed to device or managed memory
+    static bool on_host(const void* p) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return true;                  // unknown to CUDA: ordinary host memory
+        }
+        return at.type == cudaMemoryTypeUnregistered || at.type == cudaMemoryTypeHost;
+    }
+    hwfv1_status host_io_ready() {
+        if (!cstream_ && cudaStreamCreateWithFlags(&cstream_, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(HWFV1_ERR_CUDA, "copy stream");
+        for (cudaEvent_t& e : hev_)
+            if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return fail(HWFV1_ERR_CUDA, "copy events");
+        return HWFV1_OK;
+    }
+    // staging for host transfers: two field slots, stream-ordered on stream_
+    // and handed to the copy stream (event 8), freed by the caller on stream_
+    hwfv1_status stage_alloc(double** p) {
+        void* v = nullptr;
+        keep_pool_memory();
+        if (cudaMallocAsync(&v, 2 * N_ * sizeof(double), stream_) != cudaSuccess) {
+            cudaGetLastError();
+            return oom();
+        }
+        *p = static_cast<double*>(v);
+        cudaEventRecord(hev_[8], stream_);
+        cudaStreamWaitEvent(cstream_, hev_[8], 0);
+        return HWFV1_OK;
+    }
+
     hwfv1_status check(const char* what, bool sync = false) {
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream_);
@@ -1408,6 +1534,10 @@ class EngineT final : public Engine {
     double *it_d_ = nullptr, *iq_d_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     cudaGraphExec_t exec_multi_ = nullptr;   // kMultiSteps plain steps
+    // host field transfers (hwfv1_init, hwfv1_get_fields with host buffers):
+    // the copy stream and its events, made on first use
+    cudaStream_t cstream_ = nullptr;
+    cudaEvent_t hev_[9] = {};
     // learned subtree skip
     int skipmode_ = 0;     // 0 plain steps, 1 levels from the network, 2 levels from the caller
     SkipNet* skip_ = nullptr;

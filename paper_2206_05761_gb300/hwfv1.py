@@ -156,6 +156,16 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _ptr_io(t):
+    """Pointer of a contiguous float64 tensor on the device or on the host
+    (pinned or not): hwfv1_init and hwfv1_get_fields take either."""
+    if t is None:
+        return None
+    if not t.is_contiguous() or not t.is_floating_point() or t.element_size() != 8:
+        raise ValueError("expected a contiguous float64 tensor")
+    return t.data_ptr()
+
+
 def make_problem(p, precision=64):
     """hwfv1_problem from a problem dict (see synth.problem); keeps the
     hydrograph arrays alive on the returned object."""
@@ -188,11 +198,12 @@ def make_problem(p, precision=64):
 # ---------------------------------------------------------------------------
 
 def hwfv1_init(spec, z, h, qx, qy, stream=None):
-    """spec: Problem; z, h, qx, qy: CUDA float64 tensors; stream: a
+    """spec: Problem; z, h, qx, qy: float64 tensors on the device or on the
+    host (a host field is copied in by the library); stream: a
     torch.cuda.Stream or None (the library's own stream).  Returns a handle."""
     hd = _H()
     sp = stream.cuda_stream if stream is not None else None
-    st = lib().hwfv1_init(C.byref(spec), _ptr(z), _ptr(h), _ptr(qx), _ptr(qy), sp, C.byref(hd))
+    st = lib().hwfv1_init(C.byref(spec), _ptr_io(z), _ptr_io(h), _ptr_io(qx), _ptr_io(qy), sp, C.byref(hd))
     _check(st, "hwfv1_init")
     return hd
 
@@ -224,7 +235,8 @@ def hwfv1_advance(hd, t_end, max_steps):
 
 
 def hwfv1_get_fields(hd, h=None, qx=None, qy=None):
-    _check(lib().hwfv1_get_fields(hd, _ptr(h), _ptr(qx), _ptr(qy)), "hwfv1_get_fields", hd)
+    """Outputs on the device or on the host (written when the call returns)."""
+    _check(lib().hwfv1_get_fields(hd, _ptr_io(h), _ptr_io(qx), _ptr_io(qy)), "hwfv1_get_fields", hd)
 
 
 def hwfv1_set_fields(hd, h, qx, qy):
