@@ -216,19 +216,26 @@ class EngineT final : public Engine {
         if (!alloc(&scount_, (size_t)ntiles_ * sizeof(uint32_t))) return oom();
         k_static_counts<<<(ntiles_ + kTilesPerCta - 1) / kTilesPerCta, 256, 0, stream_>>>(Sz_, L_, kt_, ntiles_,
                                                                                        scount_);
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(1), f_[0][0] + lvl_off(L_), L_);
-        converted(1);
-        if (!copy_in(3)) return fail(HWFV1_ERR_CUDA, "init: copy of a host field");
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(2), f_[0][1] + lvl_off(L_), L_);
-        k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(3), f_[0][2] + lvl_off(L_), L_);
-        if (stage) cudaFreeAsync(stage, stream_);      // every copy is ordered before it on stream_
-        if (quiet_on_) {
-            k_quiet_tiles<T><<<grid_for((uint64_t)ntiles_ * 32), 256, 0, stream_>>>(
-                f_[0][0] + lvl_off(L_), f_[0][1] + lvl_off(L_), f_[0][2] + lvl_off(L_), tilebytes_, ntiles_, kt_);
-            cudaMemsetAsync(tilebytes_ + ntiles_, 1, ntiles_, stream_);     // buffer 1: all +0
+        // h, qx, qy: each field's share of the initial scalars (its s_max)
+        // and of the quiescence marks is taken as soon as it is in, so that
+        // only the last field's and the CFL pass follow the last copy
+        if (quiet_on_) cudaMemsetAsync(tilebytes_, 1, (size_t)ntiles_ * 2, stream_);   // both buffers +0 so far
+        k_reset_red<<<1, 32, 0, stream_>>>(st_);
+        for (int q = 0; q < 3; ++q) {
+            T* const x = f_[0][q] + lvl_off(L_);
+            k_rm_to_morton<T><<<g, 256, 0, stream_>>>(field(1 + q), x, L_);
+            converted(1 + q);
+            if (q == 0 && !copy_in(3)) return fail(HWFV1_ERR_CUDA, "init: copy of a host field");
+            k_maxabs_cur<T><<<g, 256, 0, stream_>>>(x, f_[1][q] + lvl_off(L_), st_, N_, q);
+            if (quiet_on_)
+                k_quiet_tiles<T><<<grid_for((uint64_t)ntiles_ * 32), 256, 0, stream_>>>(x, tilebytes_, ntiles_, kt_);
         }
-        // initial state scalars
-        reduce_state(/*set_dt=*/1);
+        if (stage) cudaFreeAsync(stage, stream_);      // every copy is ordered before it on stream_
+        // initial state scalars: the CFL step over the three fields
+        k_cfl_cur<T><<<g, 256, 0, stream_>>>(f_[0][0] + lvl_off(L_), f_[1][0] + lvl_off(L_), f_[0][1] + lvl_off(L_),
+                                              f_[1][1] + lvl_off(L_), f_[0][2] + lvl_off(L_), f_[1][2] + lvl_off(L_),
+                                              st_, N_, phys());
+        k_init_state<<<1, 64, 0, stream_>>>(st_, fin_args(), 1);
         // the plain step's graphs, captured while the device initialises
         // (capturing runs nothing), so that the first hwfv1_advance does not
         // pay for them; a batch member is stepped by its batch
