@@ -1,5 +1,6 @@
 // engine.cuh -- host side of one HWFV1 simulation: device buffers, the
-// launch sequence of a timestep, CUDA-graph replay, checkpoints.
+// launch sequence of a timestep, CUDA-graph replay, checkpoints, host field
+// transfers (and k_quiet_tiles, a kernel only the initialisation launches).
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -15,6 +16,24 @@
 #include "skipnet.h"
 
 namespace hwfv1 {
+
+// Quiescence marks of an initial state, one field at a time: zf[t] (set to
+// 1 beforehand) is cleared where the finest values of field x in tile t
+// (4^kt consecutive Morton codes) are not all +0.  The tiles' coarser levels
+// were cleared beforehand, so a mark left at 1 holds for them too.  One warp
+// per tile.
+template <typename T>
+static __global__ void k_quiet_tiles(const T* __restrict__ x, uint8_t* __restrict__ zf, uint32_t ntiles, int kt) {
+    const uint32_t lane = threadIdx.x & 31u, cells = 1u << (2 * kt);
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nw) {   // warp-uniform
+        const uint64_t b = (uint64_t)t * cells;
+        bool nz = false;
+        for (uint32_t i = lane; i < cells; i += 32u) nz |= !pos_zero(x[b + i]);
+        nz = __any_sync(0xffffffffu, nz);
+        if (lane == 0u && nz) zf[t] = 0;
+    }
+}
 
 // Kernel nodes of a captured graph (memset and copy nodes are not counted).
 inline int64_t count_kernel_nodes(cudaGraph_t g) {
