@@ -87,6 +87,19 @@ class EngineT final : public Engine {
         if (own_stream_) cudaStreamDestroy(stream_);
     }
 
+    // The staging area of a host transfer.  Whatever way the call leaves,
+    // no copy of the caller's buffers is still in flight and the area goes
+    // back to the pool (ordered after every kernel that reads it).
+    struct Staging {
+        EngineT* e;
+        double* p = nullptr;
+        ~Staging() {
+            if (!p) return;
+            cudaStreamSynchronize(e->cstream_);
+            cudaFreeAsync(p, e->stream_);
+        }
+    };
+
     hwfv1_status init(const double* z, const double* h, const double* qx,
                       const double* qy) override {
         if (!stream_) {
@@ -108,11 +121,12 @@ class EngineT final : public Engine {
         bool hostp[4];
         bool any_host = false;
         for (int k = 0; k < 4; ++k) any_host |= (hostp[k] = on_host(src[k]));
-        double* stage = nullptr;
+        Staging stg{this};
         if (any_host) {
             if (hwfv1_status r = host_io_ready(); r != HWFV1_OK) return r;
-            if (hwfv1_status r = stage_alloc(&stage); r != HWFV1_OK) return r;
+            if (hwfv1_status r = stage_alloc(&stg.p); r != HWFV1_OK) return r;
         }
+        double* const stage = stg.p;
         auto copy_in = [&](int k) -> bool {
             if (!hostp[k]) return true;
             if (k >= 2 && hostp[k - 2]) cudaStreamWaitEvent(cstream_, hev_[4 + k - 2], 0);
@@ -249,7 +263,6 @@ class EngineT final : public Engine {
             if (quiet_on_)
                 k_quiet_tiles<T><<<grid_for((uint64_t)ntiles_ * 32), 256, 0, stream_>>>(x, tilebytes_, ntiles_, kt_);
         }
-        if (stage) cudaFreeAsync(stage, stream_);      // every copy is ordered before it on stream_
         // initial state scalars: the CFL step over the three fields
         k_cfl_cur<T><<<g, 256, 0, stream_>>>(f_[0][0] + lvl_off(L_), f_[1][0] + lvl_off(L_), f_[0][1] + lvl_off(L_),
                                               f_[1][1] + lvl_off(L_), f_[0][2] + lvl_off(L_), f_[1][2] + lvl_off(L_),
@@ -492,11 +505,12 @@ class EngineT final : public Engine {
         bool hostp[3];
         bool any_host = false;
         for (int q = 0; q < 3; ++q) any_host |= (hostp[q] = out[q] != nullptr && on_host(out[q]));
-        double* stage = nullptr;
+        Staging stg{this};
         if (any_host) {
             if (hwfv1_status r = host_io_ready(); r != HWFV1_OK) return r;
-            if (hwfv1_status r = stage_alloc(&stage); r != HWFV1_OK) return r;
+            if (hwfv1_status r = stage_alloc(&stg.p); r != HWFV1_OK) return r;
         }
+        double* const stage = stg.p;
         int j = 0;
         for (int q = 0; q < 3; ++q) {
             if (!out[q]) continue;
@@ -518,7 +532,6 @@ class EngineT final : public Engine {
         }
         if (!any_host) return check("get_fields");
         for (int k = 0; k < j; ++k) cudaStreamWaitEvent(stream_, hev_[k], 0);
-        cudaFreeAsync(stage, stream_);
         return check("get_fields", true);            // host outputs are written when the call returns
     }
 

@@ -139,12 +139,3 @@ def _run_store(p, f, store, steps):
         return {k: v.cpu().numpy() for k, v in out.items()}, None
     finally:
         H.hwfv1_destroy(hd)
-
-
-def test_binding_rejects_non_float64_or_strided():
-    import torch
-    from paper_2206_05761_gb300 import hwfv1 as H
-    with pytest.raises(ValueError):
-        H._ptr_io(torch.zeros(8, dtype=torch.float32))
-    with pytest.raises(ValueError):
-        H._ptr_io(torch.zeros(8, 2, dtype=torch.float64)[:, 0])

@@ -136,3 +136,17 @@ def test_null_network_arguments_are_rejected_without_gpu():
     assert L.hwfv1_skipnet_get_params(None, None, 0) == 1
     assert L.hwfv1_skipnet_forward(None, None, 1, 8, 8, None) == 1
     L.hwfv1_skipnet_destroy(None)              # a no-op
+
+
+def test_field_pointers_take_contiguous_float64_only():
+    """hwfv1_init and hwfv1_get_fields take device or host float64 buffers;
+    the binding refuses other dtypes and strided views before any call."""
+    import torch
+    from paper_2206_05761_gb300 import hwfv1 as H
+    assert H._ptr_io(None) is None
+    x = torch.zeros(8, dtype=torch.float64)
+    assert H._ptr_io(x) == x.data_ptr()
+    with pytest.raises(ValueError):
+        H._ptr_io(torch.zeros(8, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        H._ptr_io(torch.zeros(8, 2, dtype=torch.float64)[:, 0])
